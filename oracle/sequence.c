@@ -1,0 +1,73 @@
+/*
+ * sequence.c -- oracle time-step sequence with Algorithm 1 (TEST
+ * INFRASTRUCTURE; see oracle.h).
+ *
+ * Sec. 2: the systems A_i = A(t_i, x_{i-1}), b_i = b(t_i, x_{i-1}) arrive one
+ * at a time.  Algorithm 1: solve A_i x_i = b_i with a recycling scheme, store
+ * x_i in the window X of the m most recent solutions (the oldest column leaves
+ * when it is full), and every ell steps replace the recycle space by the s
+ * leading left singular vectors of X.
+ * Readings: the window holds exactly `window` solver outputs (u0 is not one);
+ * before it is full all c stored columns are used with k_eff = min(k, c);
+ * singular values below rel_drop * sigma_1 are dropped; step 1 runs plain;
+ * with a recycle space the solve starts from x_in = 0 (so the initial guess is
+ * the paper's x0 = U E^{-1} U^T b), without one from the previous solution.
+ */
+#include "oracle.h"
+#include <stdlib.h>
+#include <string.h>
+
+int orc_sequence(const orc_seq_cfg *cfg, const double *u0, double *x_all, double *x_final,
+                 int *iters, int *k_used, double *relres, int *status)
+{
+    if (!cfg || !u0 || cfg->steps < 1 || cfg->window < 1) return ORC_E_ARG;
+    const int p = cfg->p, N = cfg->N;
+    const int64_t n = orc_fe_ndofs(p, N);
+    const int64_t nnz = orc_fe_pattern(p, N, 1, NULL, NULL);
+    int64_t *rowptr = malloc(sizeof(int64_t) * (n + 1));
+    int32_t *col = malloc(sizeof(int32_t) * nnz);
+    double *val = malloc(sizeof(double) * nnz), *b = malloc(sizeof(double) * n);
+    double *u = malloc(sizeof(double) * n), *x = malloc(sizeof(double) * n);
+    double *X = malloc(sizeof(double) * n * cfg->window);
+    double *U = malloc(sizeof(double) * n * (cfg->k > 0 ? cfg->k : 1));
+    if (!rowptr || !col || !val || !b || !u || !x || !X || !U) {
+        free(rowptr); free(col); free(val); free(b); free(u); free(x); free(X); free(U);
+        return ORC_E_NOMEM;
+    }
+    orc_fe_pattern(p, N, 1, rowptr, col);
+    orc_csr A = {n, rowptr, col, val};
+    memcpy(u, u0, sizeof(double) * n);
+    int count = 0, k_eff = 0, rc = ORC_OK;
+    for (int i = 1; i <= cfg->steps; ++i) {
+        rc = orc_fe_step_system(p, N, cfg->eps, cfg->dt, cfg->bx, cfg->by, u, rowptr, col, val, b);
+        if (rc) break;
+        int use_u = (cfg->mode != ORC_PLAIN && k_eff > 0);
+        if (use_u) memset(x, 0, sizeof(double) * n);
+        else memcpy(x, u, sizeof(double) * n);
+        orc_opts o = {cfg->mode, cfg->m, cfg->rtol, cfg->maxit, 0};
+        orc_stats st;
+        int s = orc_gmres(&A, b, x, use_u ? U : NULL, use_u ? k_eff : 0, &o, &st, NULL, 0);
+        if (s < 0) { rc = s; break; }
+        if (iters) iters[i - 1] = st.iters;
+        if (k_used) k_used[i - 1] = st.k_used;
+        if (relres) relres[i - 1] = st.true_relres;
+        if (status) status[i - 1] = st.status;
+        if (x_all) memcpy(x_all + (int64_t)(i - 1) * n, x, sizeof(double) * n);
+        /* FIFO window, oldest column first */
+        if (count == cfg->window) {
+            memmove(X, X + n, sizeof(double) * n * (cfg->window - 1));
+            --count;
+        }
+        memcpy(X + (int64_t)count * n, x, sizeof(double) * n);
+        ++count;
+        if (cfg->mode != ORC_PLAIN && cfg->k > 0 && i % cfg->ell == 0) {
+            rc = orc_recycle_from_window(n, count, X, cfg->k, cfg->select_smallest,
+                                         cfg->rel_drop, U, &k_eff);
+            if (rc) break;
+        }
+        memcpy(u, x, sizeof(double) * n);
+    }
+    if (x_final && rc == ORC_OK) memcpy(x_final, u, sizeof(double) * n);
+    free(rowptr); free(col); free(val); free(b); free(u); free(x); free(X); free(U);
+    return rc;
+}
