@@ -260,9 +260,9 @@ static int core_solve(core_t *c, const double *b, double *x, int *iters_out, int
             g[0] = bs;
             for (int j = 0; j < m && iters < c->maxit; ++j) {
                 spmv_vals(c->A, c->val, V + (int64_t)j * n, w, c->f32);
+                double wn0 = nrm2(n, w);                /* ||A v_j||, breakdown reference */
                 if (c->mode == ORC_DEFLATED) project(c, w, cv);
                 ++iters;
-                double wn0 = nrm2(n, w);
                 cgs2(n, j + 1, V, w, h, h2, c->f32);
                 double hn = nrm2(n, w);
                 double *hc = H + (int64_t)j * nrow_max;
