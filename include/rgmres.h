@@ -1,0 +1,183 @@
+/*
+ * rgmres.h -- C ABI of librgmres: recycled GMRES(m) for sequences of linear
+ * systems on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Pitton & Heltai, "Accelerating the iterative solution of
+ * convection-diffusion problems using singular value decomposition"
+ * (arXiv 1807.09467).  A sequence A_i x_i = b_i arrives one system at a time
+ * (Sec. 2, the systems depend on the previous solution); each is solved by
+ * restarted GMRES (Sec. 3) accelerated by a recycle space U, the leading left
+ * singular vectors of a window of previous solutions (Sec. 5.2, Algorithm 1),
+ * used to deflate (Sec. 3.2) or to augment (Sec. 3.1) the Krylov space.
+ *
+ * Conventions for every entry point:
+ *  - Return value: RGM_OK (0), a positive warning (the call completed) or a
+ *    negative error (nothing was changed unless stated).  rgm_status_string
+ *    gives the text.
+ *  - Pointers are host pointers unless `flags` contains RGM_DEVICE_PTRS, in
+ *    which case they are device pointers of the current CUDA device, read or
+ *    written in order on the solver's stream.
+ *  - The caller owns every array it passes; the library copies what it keeps.
+ *    The solver handle owns all device state (operator, Krylov basis, recycle
+ *    space, snapshot window, scratch) and frees it in rgm_solver_destroy.
+ *  - Dense arrays are column-major with the stated leading dimension.  CSR
+ *    uses int64 row pointers and int32 column indices.
+ *  - Calls on one handle must not overlap; distinct handles are independent.
+ *  - Nothing falls back to the CPU: without a usable CUDA device every call
+ *    that needs one returns RGM_E_CUDA.
+ */
+#ifndef RGMRES_H
+#define RGMRES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define RGM_OK                  0
+#define RGM_W_NOT_CONVERGED     1   /* maxit reached; x holds the last iterate            */
+#define RGM_W_SINGULAR_COARSE   2   /* E = U^T A U singular: this solve ran plain GMRES
+                                       (the paper takes no measure, Sec. 5.2 end)          */
+#define RGM_E_ARG             (-1)  /* invalid argument                                    */
+#define RGM_E_OOM             (-2)  /* device allocation failed                            */
+#define RGM_E_CUDA            (-3)  /* CUDA runtime error (no device, launch failure, ...) */
+#define RGM_E_STATE           (-4)  /* call out of order (e.g. solve before an operator)   */
+#define RGM_E_TIMEOUT         (-5)  /* a bounded device wait gave up                       */
+
+#define RGM_DEVICE_PTRS         1   /* flag: pointers are device pointers                  */
+
+/* ---------------------------------------------------------------- config */
+typedef enum {
+    RGM_PLAIN = 0,       /* GMRES(m), Sec. 1 / Sec. 3                                       */
+    RGM_DEFLATED = 1,    /* Table 1 "deflated oblique": operator P A, start P r,
+                            P = I - A U E^{-1} U^T (Eq. left_deflation), plus the coarse
+                            correction x += U E^{-1} U^T (b - A x) after each cycle          */
+    RGM_AUGMENTED = 2    /* Sec. 3.1: search space K_j(A, r) + span U, constraint space A S  */
+} rgm_mode;
+
+typedef enum {
+    RGM_FP64 = 0,        /* every step in binary64                                          */
+    RGM_FP32_IR = 1      /* GMRES-IR: binary32 Arnoldi/SpMV/projections inside a binary64
+                            refinement loop (residual, Hessenberg, E and SVD stay binary64)  */
+} rgm_precision;
+
+typedef struct {
+    int64_t n;            /* system size (fixed for the handle's life)                      */
+    int m;                /* restart length, 1..64                                          */
+    int k;                /* recycle dimension s of Algorithm 1, 0..32                      */
+    int window;           /* snapshots kept (m of Algorithm 1), k..64                       */
+    int svd_interval;     /* ell of Algorithm 1 (>= 1)                                      */
+    int select_smallest;  /* 1: keep the trailing singular modes instead of the leading    */
+    int mode;             /* rgm_mode                                                       */
+    int precision;        /* rgm_precision                                                  */
+    int start_r;          /* deflated mode only: 1 = start vector r (Table 1 aug. oblique) */
+    int maxit;            /* cap on Arnoldi steps per solve                                 */
+    int inner_cycles;     /* FP32_IR: GMRES cycles per refinement                           */
+    int max_refinements;  /* FP32_IR: cap on refinement steps                               */
+    double rtol;          /* converged when ||b - A x||_2 <= rtol ||b||_2                   */
+    double inner_rtol;    /* FP32_IR: inner solve to inner_rtol * ||r||                     */
+    double rel_drop;      /* drop singular values below rel_drop * sigma_1                 */
+    void *cuda_stream;    /* cudaStream_t to run on; NULL = the legacy default stream      */
+} rgm_config;
+
+typedef struct {
+    int iters;            /* Arnoldi steps (operator applications to basis vectors)         */
+    int cycles;           /* GMRES cycles                                                   */
+    int refinements;      /* FP32_IR refinement steps                                       */
+    int k_used;           /* recycle columns used by this solve                             */
+    int status;           /* same code the call returned                                    */
+    double true_relres;   /* ||b - A x||_2 / ||b||_2 of the returned x, in binary64         */
+} rgm_stats;
+
+typedef struct rgm_solver_s *rgm_solver;
+
+/* Fill *cfg with defaults: m 30, k 8, window 16, ell 1, deflated, FP64,
+ * rtol 1e-10, maxit 20000, inner_rtol 1e-4, inner_cycles 2, rel_drop 1e-7. */
+int rgm_config_default(rgm_config *cfg);
+
+/* Create a solver for systems of size cfg->n on the current device.  Allocates
+ * the Krylov basis (n x (m+k+1)), the recycle space and the snapshot window.
+ * Errors: RGM_E_ARG (limits above), RGM_E_OOM, RGM_E_CUDA. */
+int rgm_solver_create(rgm_solver *out, const rgm_config *cfg);
+int rgm_solver_destroy(rgm_solver s);
+
+/* Operator A (n x n) in CSR (Sec. 2, Eq. algebra_pde).  Sets pattern and values;
+ * the pattern may change between calls.  Invalidates A U and E.  Column indices
+ * must lie in [0, n); rows need not be sorted.  Errors: RGM_E_ARG, RGM_E_OOM. */
+int rgm_set_operator_csr(rgm_solver s, int64_t n, int64_t nnz, const int64_t *rowptr,
+                         const int32_t *col, const double *val, int flags);
+/* New values on the pattern of the last rgm_set_operator_csr (nnz doubles, same
+ * order).  This is the per-time-step call of Sec. 2: A_i = A(t_i, x_{i-1}). */
+int rgm_set_operator_values(rgm_solver s, const double *val, int flags);
+
+/* Recycle space U (n x k, leading dimension ld >= n) set by the caller instead
+ * of by rgm_update_recycle_svd.  Columns should be linearly independent; the
+ * library uses them as given (no re-orthonormalisation).  k = 0 clears it. */
+int rgm_set_recycle_space(rgm_solver s, const double *U, int k, int64_t ld, int flags);
+/* Copy the current recycle space out (n x k_used, leading dimension ld); *k
+ * receives k_used.  U may be NULL to query *k only. */
+int rgm_get_recycle_space(rgm_solver s, double *U, int64_t ld, int *k, int flags);
+
+/* Solve A x = b.  x: in = x_in, out = solution.  With a recycle space the solve
+ * starts from x0 = x_in + U E^{-1} U^T (b - A x_in) (Sec. 4.2, Eq.
+ * projection_t_s; the paper's x0 = U E^{-1} U^T b is x_in = 0).  st may be NULL.
+ * Returns RGM_OK, RGM_W_NOT_CONVERGED or RGM_W_SINGULAR_COARSE (x valid in all
+ * three), or an error. */
+int rgm_solve(rgm_solver s, const double *b, double *x, int flags, rgm_stats *st);
+
+/* Algorithm 1 after a solve: append x (n doubles) to the snapshot window (the
+ * oldest column leaves when `window` are stored); if the number of calls so far
+ * is a multiple of svd_interval, replace U by the k leading (or trailing) left
+ * singular vectors of the window (Sec. 5.2), dropping singular values below
+ * rel_drop * sigma_1.  *k_used (may be NULL) receives the new dimension. */
+int rgm_update_recycle_svd(rgm_solver s, const double *x, int flags, int *k_used);
+/* Singular values of the last window SVD, descending (up to `window` values);
+ * *count receives how many are valid. */
+int rgm_get_singular_values(rgm_solver s, double *sigma, int *count);
+
+/* Clear the snapshot window and the recycle space. */
+int rgm_reset_recycling(rgm_solver s);
+
+/* y = A x with the solver's operator (the SpMV of every Arnoldi step). */
+int rgm_spmv(rgm_solver s, const double *x, double *y, int flags);
+
+const char *rgm_status_string(int code);
+
+/* ------------------------------------------------------------ FE workload
+ * The time-step systems of Sec. 6.1 built on the device: Q_p Lagrange elements
+ * (p = 1..4, Gauss-Lobatto nodes) on a uniform N x N grid of the unit square,
+ * (p+1)^2 Gauss points per cell, implicit Euler with the convection coefficient
+ * lagged one step,
+ *   A = M/dt + eps K + N(u_prev; beta),  b = M u_prev / dt + F(f = 1),
+ * N_ij = (u_prev beta . grad phi_j, phi_i), homogeneous Dirichlet rows
+ * (identity, b_i = 0), boundary columns dropped from interior rows.
+ * Dofs are numbered lexicographically (x fastest) on the (pN+1)^2 lattice.
+ * This is the workload the solver is measured on, not part of the method.  */
+typedef struct rgm_fe_s *rgm_fe;
+
+int rgm_fe_create(rgm_fe *out, int p, int N, double eps, double dt, double beta_x,
+                  double beta_y, void *cuda_stream);
+int rgm_fe_destroy(rgm_fe fe);
+/* Sizes of the Dirichlet pattern. */
+int rgm_fe_sizes(rgm_fe fe, int64_t *n, int64_t *nnz);
+/* Copy the Dirichlet CSR pattern out (rowptr n+1, col nnz). */
+int rgm_fe_pattern(rgm_fe fe, int64_t *rowptr, int32_t *col, int flags);
+/* Assemble values (nnz, CSR order of rgm_fe_pattern) and b (n) from u_prev (n). */
+int rgm_fe_assemble(rgm_fe fe, const double *u_prev, double *val, double *b, int flags);
+/* Nodal interpolant of u0 = sum_{j=1..8} a_j sin(j pi x) sin(j pi y), zero on the
+ * boundary.  a8 is a host array of 8 doubles. */
+int rgm_fe_initial_field(rgm_fe fe, const double *a8, double *u0, int flags);
+/* One time step on the device: assemble from u_prev, rgm_set_operator_values,
+ * rgm_solve with x_in as Algorithm 1 prescribes (0 with a recycle space, u_prev
+ * without), then rgm_update_recycle_svd.  u (device, n) holds u_prev on entry
+ * and the new solution on return.  The solver must have been given the FE
+ * pattern by rgm_set_operator_csr. */
+int rgm_fe_time_step(rgm_fe fe, rgm_solver s, double *u_dev, rgm_stats *st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,220 @@
+"""GB300-native recycled GMRES(m) for sequences of convection-diffusion systems.
+
+Thin binding over librgmres (include/rgmres.h).  Every step of the solve runs in
+the library's CUDA kernels; this module only marshals arguments.  Arrays are
+numpy arrays (host; the library copies) or CUDA torch tensors (device pointers,
+used in place on the solver's stream).
+
+Method: Pitton & Heltai, arXiv 1807.09467 -- restarted GMRES (Sec. 3) with a
+recycle space from a thin SVD of previous solutions (Sec. 5.2, Algorithm 1) used
+for deflation (Sec. 3.2, Table 1) or augmentation (Sec. 3.1).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import (AUGMENTED, DEFLATED, FP32_IR, FP64, PLAIN, RGM_DEVICE_PTRS,
+                   RGM_W_NOT_CONVERGED, RGM_W_SINGULAR_COARSE, RgmConfig, RgmError,
+                   RgmStats, check)
+
+MODES = {"plain": PLAIN, "deflated": DEFLATED, "augmented": AUGMENTED}
+PRECISIONS = {"fp64": FP64, "fp32_ir": FP32_IR}
+
+__all__ = ["Solver", "FE", "RgmError", "MODES", "PRECISIONS", "PLAIN", "DEFLATED", "AUGMENTED",
+           "FP64", "FP32_IR", "RGM_W_NOT_CONVERGED", "RGM_W_SINGULAR_COARSE"]
+
+
+def _is_dev(a):
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _ptr(a, dtype):
+    """(pointer, flags, keepalive) for a numpy array or a CUDA torch tensor."""
+    if _is_dev(a):
+        assert a.is_contiguous(), "device tensors must be contiguous"
+        return C.c_void_p(a.data_ptr()), RGM_DEVICE_PTRS, a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return C.c_void_p(arr.ctypes.data), 0, arr
+
+
+def _stats(st: RgmStats):
+    return dict(iters=st.iters, cycles=st.cycles, refinements=st.refinements, k_used=st.k_used,
+                status=st.status, true_relres=st.true_relres)
+
+
+class Solver:
+    """One handle = one sequence of systems of size n (rgm_solver_create)."""
+
+    def __init__(self, n, m=30, k=8, window=16, svd_interval=1, select_smallest=False,
+                 mode="deflated", precision="fp64", start_r=False, maxit=20000, inner_cycles=2,
+                 max_refinements=50, rtol=1e-10, inner_rtol=1e-4, rel_drop=1e-7, stream=None):
+        L = _lib.load()
+        cfg = RgmConfig()
+        L.rgm_config_default(C.byref(cfg))
+        cfg.n, cfg.m, cfg.k, cfg.window = n, m, k, window
+        cfg.svd_interval, cfg.select_smallest = svd_interval, int(select_smallest)
+        cfg.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+        cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        cfg.start_r, cfg.maxit, cfg.inner_cycles = int(start_r), maxit, inner_cycles
+        cfg.max_refinements, cfg.rtol, cfg.inner_rtol, cfg.rel_drop = (
+            max_refinements, rtol, inner_rtol, rel_drop)
+        cfg.cuda_stream = stream
+        self.cfg = cfg
+        self.n = n
+        h = C.c_void_p()
+        check(L.rgm_solver_create(C.byref(h), C.byref(cfg)), "rgm_solver_create")
+        self._h = h
+        self._L = L
+        self.nnz = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.rgm_solver_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_operator_csr(self, rowptr, col, val):
+        rp, f1, k1 = _ptr(rowptr, np.int64)
+        cl, f2, k2 = _ptr(col, np.int32)
+        vl, f3, k3 = _ptr(val, np.float64)
+        assert f1 == f2 == f3, "mix of host and device arrays"
+        nnz = int(len(col))
+        check(self._L.rgm_set_operator_csr(self._h, self.n, nnz, rp, cl, vl, f1),
+              "rgm_set_operator_csr")
+        self.nnz = nnz
+
+    def set_operator_values(self, val):
+        vl, f, k = _ptr(val, np.float64)
+        check(self._L.rgm_set_operator_values(self._h, vl, f), "rgm_set_operator_values")
+
+    def set_recycle_space(self, U):
+        if U is None or np.asarray(U).size == 0:
+            check(self._L.rgm_set_recycle_space(self._h, None, 0, self.n, 0), "set_recycle_space")
+            return
+        Uf = np.asfortranarray(np.asarray(U, dtype=np.float64))
+        check(self._L.rgm_set_recycle_space(self._h, C.c_void_p(Uf.ctypes.data), Uf.shape[1],
+                                            Uf.shape[0], 0), "rgm_set_recycle_space")
+
+    def recycle_space(self):
+        k = C.c_int(0)
+        check(self._L.rgm_get_recycle_space(self._h, None, self.n, C.byref(k), 0), "get_recycle")
+        U = np.zeros((self.n, k.value), order="F")
+        if k.value:
+            check(self._L.rgm_get_recycle_space(self._h, C.c_void_p(U.ctypes.data), self.n,
+                                                C.byref(k), 0), "rgm_get_recycle_space")
+        return U
+
+    def solve(self, b, x=None):
+        """Returns (x, stats).  Host arrays: a new numpy x.  Device tensors: x in place."""
+        st = RgmStats()
+        if _is_dev(b):
+            assert x is not None and _is_dev(x)
+            rc = self._L.rgm_solve(self._h, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()),
+                                   RGM_DEVICE_PTRS, C.byref(st))
+            check(rc, "rgm_solve")
+            return x, _stats(st)
+        bb = np.ascontiguousarray(b, dtype=np.float64)
+        xx = np.zeros(self.n) if x is None else np.array(x, dtype=np.float64, copy=True)
+        rc = self._L.rgm_solve(self._h, C.c_void_p(bb.ctypes.data), C.c_void_p(xx.ctypes.data), 0,
+                               C.byref(st))
+        check(rc, "rgm_solve")
+        return xx, _stats(st)
+
+    def update_recycle_svd(self, x):
+        xp, f, keep = _ptr(x, np.float64)
+        k = C.c_int(0)
+        check(self._L.rgm_update_recycle_svd(self._h, xp, f, C.byref(k)), "rgm_update_recycle_svd")
+        return k.value
+
+    def singular_values(self):
+        out = np.zeros(64)
+        c = C.c_int(0)
+        check(self._L.rgm_get_singular_values(self._h, C.c_void_p(out.ctypes.data), C.byref(c)),
+              "rgm_get_singular_values")
+        return out[: c.value].copy()
+
+    def reset_recycling(self):
+        check(self._L.rgm_reset_recycling(self._h), "rgm_reset_recycling")
+
+    def spmv(self, x):
+        if _is_dev(x):
+            import torch
+            y = torch.empty_like(x)
+            check(self._L.rgm_spmv(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                   RGM_DEVICE_PTRS), "rgm_spmv")
+            return y
+        xx = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.zeros(self.n)
+        check(self._L.rgm_spmv(self._h, C.c_void_p(xx.ctypes.data), C.c_void_p(y.ctypes.data), 0),
+              "rgm_spmv")
+        return y
+
+
+class FE:
+    """The Sec. 6.1 time-step systems built on the device (rgm_fe_*)."""
+
+    def __init__(self, p, N, eps, dt, beta, stream=None):
+        L = _lib.load()
+        h = C.c_void_p()
+        check(L.rgm_fe_create(C.byref(h), p, N, eps, dt, float(beta[0]), float(beta[1]), stream),
+              "rgm_fe_create")
+        self._h, self._L = h, L
+        n, nnz = C.c_int64(), C.c_int64()
+        L.rgm_fe_sizes(h, C.byref(n), C.byref(nnz))
+        self.n, self.nnz = n.value, nnz.value
+        self.p, self.N = p, N
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.rgm_fe_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pattern(self):
+        rp = np.zeros(self.n + 1, dtype=np.int64)
+        cl = np.zeros(self.nnz, dtype=np.int32)
+        check(self._L.rgm_fe_pattern(self._h, C.c_void_p(rp.ctypes.data),
+                                     C.c_void_p(cl.ctypes.data), 0), "rgm_fe_pattern")
+        return rp, cl
+
+    def assemble(self, u_prev):
+        if _is_dev(u_prev):
+            import torch
+            val = torch.empty(self.nnz, dtype=torch.float64, device=u_prev.device)
+            b = torch.empty(self.n, dtype=torch.float64, device=u_prev.device)
+            check(self._L.rgm_fe_assemble(self._h, C.c_void_p(u_prev.data_ptr()),
+                                          C.c_void_p(val.data_ptr()), C.c_void_p(b.data_ptr()),
+                                          RGM_DEVICE_PTRS), "rgm_fe_assemble")
+            return val, b
+        u = np.ascontiguousarray(u_prev, dtype=np.float64)
+        val, b = np.zeros(self.nnz), np.zeros(self.n)
+        check(self._L.rgm_fe_assemble(self._h, C.c_void_p(u.ctypes.data), C.c_void_p(val.ctypes.data),
+                                      C.c_void_p(b.ctypes.data), 0), "rgm_fe_assemble")
+        return val, b
+
+    def initial_field(self, a8):
+        a = np.ascontiguousarray(a8, dtype=np.float64)
+        u0 = np.zeros(self.n)
+        check(self._L.rgm_fe_initial_field(self._h, C.c_void_p(a.ctypes.data),
+                                           C.c_void_p(u0.ctypes.data), 0), "rgm_fe_initial_field")
+        return u0
+
+    def time_step(self, solver: Solver, u_dev):
+        """One step of Algorithm 1 on the device; u_dev (CUDA float64 tensor) is updated."""
+        st = RgmStats()
+        rc = self._L.rgm_fe_time_step(self._h, solver._h, C.c_void_p(u_dev.data_ptr()), C.byref(st))
+        check(rc, "rgm_fe_time_step")
+        return _stats(st)

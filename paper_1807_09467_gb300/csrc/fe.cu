@@ -1,0 +1,408 @@
+// fe.cu -- the Sec. 6.1 time-step systems assembled on the device (the
+// workload the solver is measured on; see include/rgmres.h).
+//
+// Discrete problem (Sec. 6.1, implicit Euler, convection coefficient lagged):
+//   (1/dt)(v, u^n - u^{n-1}) + eps (grad v, grad u^n) + (v, u^{n-1} beta.grad u^n) = (v, 1)
+// on Q_p elements, p = 1..4, with Gauss-Lobatto nodes and (p+1)^2 Gauss points
+// per cell.  Uniform grid => one set of reference tables: the 1D mass M1 and
+// stiffness K1, the load F1, and the reference convection tensor
+//   T[(i),(j),(l)] = sum_q w_q phi_i(q) phi_l(q) (beta . grad_ref phi_j)(q)
+// so that N_ij = h sum_l u_l T[i][j][l] on each cell.  Assembly gathers row by
+// row (one warp per row, one lane per stored entry, cells visited in a fixed
+// order), so it is deterministic and needs no atomics.
+#include "../../include/rgmres.h"
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+extern "C" int rgm_internal_values_ptr(rgm_solver s, double **val, int64_t *nnz);
+extern "C" int rgm_internal_config(rgm_solver s, rgm_config *cfg);
+
+#define CKF(call)                                                            \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess) return (e_ == cudaErrorMemoryAllocation) ? RGM_E_OOM : RGM_E_CUDA; \
+    } while (0)
+
+struct rgm_fe_s {
+    int p = 1, N = 1;
+    double eps = 0, dt = 1, bx = 0, by = 0, h = 1;
+    cudaStream_t st = nullptr;
+    int64_t L = 0, n = 0, nnz = 0;
+    std::vector<int64_t> h_rowptr;
+    std::vector<int32_t> h_col;
+    int64_t *rowptr = nullptr;
+    int32_t *col = nullptr;
+    double *tabs = nullptr;   // M1 | K1 | F1 | T  (device)
+    double *val = nullptr;    // assembly target when not writing into a solver
+    double *b = nullptr;
+    double *x = nullptr;      // solve scratch for rgm_fe_time_step
+};
+
+namespace {
+
+// Gauss-Lobatto nodes on [0,1] for p <= 4 and Gauss-Legendre rules on [0,1]
+// for q <= 5, from their closed forms on [-1,1].
+void gll_closed(int p, double *xi)
+{
+    double t[5];
+    if (p == 1) { t[0] = -1; t[1] = 1; }
+    else if (p == 2) { t[0] = -1; t[1] = 0; t[2] = 1; }
+    else if (p == 3) { t[0] = -1; t[1] = -1 / std::sqrt(5.0); t[2] = -t[1]; t[3] = 1; }
+    else { t[0] = -1; t[1] = -std::sqrt(3.0 / 7.0); t[2] = 0; t[3] = -t[1]; t[4] = 1; }
+    for (int i = 0; i <= p; ++i) xi[i] = 0.5 * (t[i] + 1.0);
+}
+
+void gauss_closed(int q, double *x, double *w)
+{
+    double t[5], c[5];
+    if (q == 2) { t[0] = -1 / std::sqrt(3.0); t[1] = -t[0]; c[0] = c[1] = 1; }
+    else if (q == 3) { t[0] = -std::sqrt(0.6); t[1] = 0; t[2] = -t[0]; c[0] = c[2] = 5.0 / 9; c[1] = 8.0 / 9; }
+    else if (q == 4) {
+        double a = std::sqrt(3.0 / 7 - 2.0 / 7 * std::sqrt(1.2)), b = std::sqrt(3.0 / 7 + 2.0 / 7 * std::sqrt(1.2));
+        double wa = (18 + std::sqrt(30.0)) / 36, wb = (18 - std::sqrt(30.0)) / 36;
+        t[0] = -b; t[1] = -a; t[2] = a; t[3] = b; c[0] = wb; c[1] = wa; c[2] = wa; c[3] = wb;
+    } else {
+        double a = std::sqrt(5 - 2 * std::sqrt(10.0 / 7)) / 3, b = std::sqrt(5 + 2 * std::sqrt(10.0 / 7)) / 3;
+        double wa = (322 + 13 * std::sqrt(70.0)) / 900, wb = (322 - 13 * std::sqrt(70.0)) / 900;
+        t[0] = -b; t[1] = -a; t[2] = 0; t[3] = a; t[4] = b; c[0] = wb; c[1] = wa; c[2] = 128.0 / 225; c[3] = wa; c[4] = wb;
+    }
+    for (int i = 0; i < q; ++i) { x[i] = 0.5 * (t[i] + 1.0); w[i] = 0.5 * c[i]; }
+}
+
+// Lagrange basis on `nodes` and its derivative at x (product rule).
+void basis(int p, const double *nodes, double x, double *phi, double *dphi)
+{
+    for (int a = 0; a <= p; ++a) {
+        double den = 1.0;
+        for (int b = 0; b <= p; ++b) if (b != a) den *= nodes[a] - nodes[b];
+        double num = 1.0;
+        for (int b = 0; b <= p; ++b) if (b != a) num *= x - nodes[b];
+        phi[a] = num / den;
+        double d = 0.0;
+        for (int skip = 0; skip <= p; ++skip) {
+            if (skip == a) continue;
+            double pr = 1.0;
+            for (int b = 0; b <= p; ++b) if (b != a && b != skip) pr *= x - nodes[b];
+            d += pr;
+        }
+        dphi[a] = d / den;
+    }
+}
+
+__device__ __forceinline__ void cell_range(int64_t I, int p, int N, int *c0, int *c1)
+{
+    // cells containing lattice node I along one axis
+    const int64_t c = I / p;
+    if (I % p == 0) { *c0 = (int)(c > 0 ? c - 1 : 0); *c1 = (int)(c < N ? c : N - 1); }
+    else { *c0 = (int)c; *c1 = (int)c; }
+}
+
+__device__ __forceinline__ bool on_bnd(int64_t dof, int64_t L)
+{
+    int64_t ix = dof % L, iy = dof / L;
+    return ix == 0 || iy == 0 || ix == L - 1 || iy == L - 1;
+}
+
+struct FeDev {
+    int p, N, nl;
+    int64_t L, n;
+    double h, inv_dt, eps;
+    const double *M1, *K1, *F1, *T;
+};
+
+// One warp per row: values of A on the Dirichlet pattern.
+__global__ void fe_assemble_kernel(FeDev f, const int64_t *rowptr, const int32_t *col,
+                                   const double *u, double *val)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (row >= f.n) return;
+    const int64_t e0 = rowptr[row], e1 = rowptr[row + 1];
+    if (on_bnd(row, f.L)) {
+        for (int64_t e = e0 + lane; e < e1; e += 32) val[e] = 1.0;
+        return;
+    }
+    const int p = f.p, q1 = p + 1;
+    const int64_t Ix = row % f.L, Iy = row / f.L;
+    int ax0, ax1, ay0, ay1;
+    cell_range(Ix, p, f.N, &ax0, &ax1);
+    cell_range(Iy, p, f.N, &ay0, &ay1);
+    for (int64_t e = e0 + lane; e < e1; e += 32) {
+        const int64_t cj = col[e];
+        const int64_t Jx = cj % f.L, Jy = cj / f.L;
+        int bx0, bx1, by0, by1;
+        cell_range(Jx, p, f.N, &bx0, &bx1);
+        cell_range(Jy, p, f.N, &by0, &by1);
+        double v = 0.0;
+        for (int cy = max(ay0, by0); cy <= min(ay1, by1); ++cy)
+            for (int cx = max(ax0, bx0); cx <= min(ax1, bx1); ++cx) {
+                const int ia = (int)(Ix - (int64_t)cx * p), ib = (int)(Iy - (int64_t)cy * p);
+                const int ja = (int)(Jx - (int64_t)cx * p), jb = (int)(Jy - (int64_t)cy * p);
+                const double mx = f.M1[ia * q1 + ja], my = f.M1[ib * q1 + jb];
+                const double kx = f.K1[ia * q1 + ja], ky = f.K1[ib * q1 + jb];
+                double conv = 0.0;
+                const int il = ib * q1 + ia, jl = jb * q1 + ja;
+                const double *Tij = f.T + ((int64_t)il * f.nl + jl) * f.nl;
+                for (int lb = 0; lb <= p; ++lb) {
+                    const int64_t rowoff = ((int64_t)cy * p + lb) * f.L + (int64_t)cx * p;
+                    for (int la = 0; la <= p; ++la) conv += Tij[lb * q1 + la] * u[rowoff + la];
+                }
+                v += f.h * f.h * mx * my * f.inv_dt + f.eps * (kx * my + mx * ky) + f.h * conv;
+            }
+        val[e] = v;
+    }
+}
+
+// b = M u / dt + F over the full neighbourhood (boundary columns included),
+// then b_i = 0 on Dirichlet rows.  One thread per row.
+__global__ void fe_rhs_kernel(FeDev f, const double *u, double *b)
+{
+    const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (row >= f.n) return;
+    if (on_bnd(row, f.L)) { b[row] = 0.0; return; }
+    const int p = f.p, q1 = p + 1;
+    const int64_t Ix = row % f.L, Iy = row / f.L;
+    int ax0, ax1, ay0, ay1;
+    cell_range(Ix, p, f.N, &ax0, &ax1);
+    cell_range(Iy, p, f.N, &ay0, &ay1);
+    double mu = 0.0, F = 0.0;
+    for (int cy = ay0; cy <= ay1; ++cy)
+        for (int cx = ax0; cx <= ax1; ++cx) {
+            const int ia = (int)(Ix - (int64_t)cx * p), ib = (int)(Iy - (int64_t)cy * p);
+            F += f.h * f.h * f.F1[ia] * f.F1[ib];
+            for (int jb = 0; jb <= p; ++jb)
+                for (int ja = 0; ja <= p; ++ja) {
+                    const int64_t cj = ((int64_t)cy * p + jb) * f.L + (int64_t)cx * p + ja;
+                    mu += f.h * f.h * f.M1[ia * q1 + ja] * f.M1[ib * q1 + jb] * u[cj];
+                }
+        }
+    b[row] = mu * f.inv_dt + F;
+}
+
+__global__ void fe_u0_kernel(int p, int N, int64_t L, double x0, double x1, double x2, double x3,
+                             double x4, const double *a8, double *u0, int64_t n)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (on_bnd(i, L)) { u0[i] = 0.0; return; }
+    const double xi[5] = {x0, x1, x2, x3, x4};
+    const int64_t Ix = i % L, Iy = i / L;
+    const double h = 1.0 / N;
+    const double x = ((double)(Ix / p) + xi[Ix % p]) * h, y = ((double)(Iy / p) + xi[Iy % p]) * h;
+    double s = 0.0;
+    for (int j = 1; j <= 8; ++j) s += a8[j - 1] * sin(j * M_PI * x) * sin(j * M_PI * y);
+    u0[i] = s;
+}
+
+__global__ void fe_select_kernel(double *x, const double *u, int64_t n, int zero)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) x[i] = zero ? 0.0 : u[i];
+}
+
+FeDev dev_view(const rgm_fe_s *fe)
+{
+    const int q1 = fe->p + 1;
+    FeDev f;
+    f.p = fe->p; f.N = fe->N; f.nl = q1 * q1; f.L = fe->L; f.n = fe->n; f.h = fe->h;
+    f.inv_dt = 1.0 / fe->dt; f.eps = fe->eps;
+    f.M1 = fe->tabs; f.K1 = f.M1 + q1 * q1; f.F1 = f.K1 + q1 * q1; f.T = f.F1 + q1;
+    return f;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rgm_fe_create(rgm_fe *out, int p, int N, double eps, double dt, double beta_x, double beta_y,
+                  void *cuda_stream)
+{
+    if (!out || p < 1 || p > 4 || N < 1 || !(dt > 0)) return RGM_E_ARG;
+    *out = nullptr;
+    const int64_t L = (int64_t)p * N + 1;
+    if (L * L > (int64_t)1 << 31) return RGM_E_ARG;
+    rgm_fe_s *fe = new (std::nothrow) rgm_fe_s();
+    if (!fe) return RGM_E_OOM;
+    fe->p = p; fe->N = N; fe->eps = eps; fe->dt = dt; fe->bx = beta_x; fe->by = beta_y;
+    fe->h = 1.0 / N; fe->st = (cudaStream_t)cuda_stream; fe->L = L; fe->n = L * L;
+    // Dirichlet pattern: rows = product of 1D coupling ranges, boundary filtered
+    auto range1 = [&](int64_t I, int64_t *lo, int64_t *hi) {
+        if (I % p == 0) { *lo = I - p < 0 ? 0 : I - p; *hi = I + p > L - 1 ? L - 1 : I + p; }
+        else { *lo = (I / p) * p; *hi = *lo + p; }
+    };
+    auto bnd = [&](int64_t d) { int64_t ix = d % L, iy = d / L; return ix == 0 || iy == 0 || ix == L - 1 || iy == L - 1; };
+    fe->h_rowptr.resize(fe->n + 1);
+    fe->h_rowptr[0] = 0;
+    for (int64_t r = 0; r < fe->n; ++r) {
+        if (bnd(r)) fe->h_col.push_back((int32_t)r);
+        else {
+            int64_t xl, xh, yl, yh;
+            range1(r % L, &xl, &xh);
+            range1(r / L, &yl, &yh);
+            for (int64_t jy = yl; jy <= yh; ++jy)
+                for (int64_t jx = xl; jx <= xh; ++jx) {
+                    int64_t c = jy * L + jx;
+                    if (!bnd(c)) fe->h_col.push_back((int32_t)c);
+                }
+        }
+        fe->h_rowptr[r + 1] = (int64_t)fe->h_col.size();
+    }
+    fe->nnz = (int64_t)fe->h_col.size();
+    // reference tables
+    const int q1 = p + 1, nl = q1 * q1;
+    double xi[5], gx[5], gw[5], ph[5][5], dph[5][5];
+    gll_closed(p, xi);
+    gauss_closed(q1, gx, gw);
+    for (int g = 0; g < q1; ++g) basis(p, xi, gx[g], ph[g], dph[g]);
+    std::vector<double> tab(2 * q1 * q1 + q1 + (size_t)nl * nl * nl, 0.0);
+    double *M1 = tab.data(), *K1 = M1 + q1 * q1, *F1 = K1 + q1 * q1, *T = F1 + q1;
+    for (int a = 0; a <= p; ++a) {
+        for (int c = 0; c <= p; ++c)
+            for (int g = 0; g < q1; ++g) {
+                M1[a * q1 + c] += gw[g] * ph[g][a] * ph[g][c];
+                K1[a * q1 + c] += gw[g] * dph[g][a] * dph[g][c];
+            }
+        for (int g = 0; g < q1; ++g) F1[a] += gw[g] * ph[g][a];
+    }
+    for (int i = 0; i < nl; ++i)
+        for (int j = 0; j < nl; ++j)
+            for (int l = 0; l < nl; ++l) {
+                const int ia = i % q1, ib = i / q1, ja = j % q1, jb = j / q1, la = l % q1, lb = l / q1;
+                double s = 0.0;
+                for (int gy = 0; gy < q1; ++gy)
+                    for (int gxx = 0; gxx < q1; ++gxx) {
+                        double w = gw[gxx] * gw[gy];
+                        double phi_i = ph[gxx][ia] * ph[gy][ib];
+                        double phi_l = ph[gxx][la] * ph[gy][lb];
+                        double bgrad = beta_x * dph[gxx][ja] * ph[gy][jb] + beta_y * ph[gxx][ja] * dph[gy][jb];
+                        s += w * phi_i * phi_l * bgrad;
+                    }
+                T[((int64_t)i * nl + j) * nl + l] = s;
+            }
+    cudaError_t e = cudaMalloc((void **)&fe->rowptr, sizeof(int64_t) * (fe->n + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&fe->col, sizeof(int32_t) * fe->nnz);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&fe->tabs, sizeof(double) * tab.size());
+    if (e == cudaSuccess) e = cudaMalloc((void **)&fe->val, sizeof(double) * fe->nnz);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&fe->b, sizeof(double) * fe->n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&fe->x, sizeof(double) * fe->n);
+    if (e == cudaSuccess) e = cudaMemcpy(fe->rowptr, fe->h_rowptr.data(), sizeof(int64_t) * (fe->n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(fe->col, fe->h_col.data(), sizeof(int32_t) * fe->nnz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(fe->tabs, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        rgm_fe_destroy(fe);
+        return e == cudaErrorMemoryAllocation ? RGM_E_OOM : RGM_E_CUDA;
+    }
+    *out = fe;
+    return RGM_OK;
+}
+
+int rgm_fe_destroy(rgm_fe fe)
+{
+    if (!fe) return RGM_E_ARG;
+    void *p[] = {fe->rowptr, fe->col, fe->tabs, fe->val, fe->b, fe->x};
+    for (void *q : p)
+        if (q) cudaFree(q);
+    delete fe;
+    return RGM_OK;
+}
+
+int rgm_fe_sizes(rgm_fe fe, int64_t *n, int64_t *nnz)
+{
+    if (!fe || !n || !nnz) return RGM_E_ARG;
+    *n = fe->n;
+    *nnz = fe->nnz;
+    return RGM_OK;
+}
+
+int rgm_fe_pattern(rgm_fe fe, int64_t *rowptr, int32_t *col, int flags)
+{
+    if (!fe || !rowptr || !col) return RGM_E_ARG;
+    cudaMemcpyKind k = (flags & RGM_DEVICE_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+    CKF(cudaMemcpy(rowptr, fe->h_rowptr.data(), sizeof(int64_t) * (fe->n + 1), k));
+    CKF(cudaMemcpy(col, fe->h_col.data(), sizeof(int32_t) * fe->nnz, k));
+    return RGM_OK;
+}
+
+static int fe_assemble_dev(rgm_fe fe, const double *u_dev, double *val_dev, double *b_dev)
+{
+    FeDev f = dev_view(fe);
+    const int64_t warps = fe->n;
+    const int tpb = 256;
+    fe_assemble_kernel<<<(unsigned)((warps * 32 + tpb - 1) / tpb), tpb, 0, fe->st>>>(f, fe->rowptr, fe->col, u_dev, val_dev);
+    fe_rhs_kernel<<<(unsigned)((fe->n + tpb - 1) / tpb), tpb, 0, fe->st>>>(f, u_dev, b_dev);
+    CKF(cudaGetLastError());
+    return RGM_OK;
+}
+
+int rgm_fe_assemble(rgm_fe fe, const double *u_prev, double *val, double *b, int flags)
+{
+    if (!fe || !u_prev || !val || !b) return RGM_E_ARG;
+    if (flags & RGM_DEVICE_PTRS) {
+        int rc = fe_assemble_dev(fe, u_prev, val, b);
+        if (rc) return rc;
+        CKF(cudaStreamSynchronize(fe->st));
+        return RGM_OK;
+    }
+    CKF(cudaMemcpyAsync(fe->x, u_prev, sizeof(double) * fe->n, cudaMemcpyHostToDevice, fe->st));
+    int rc = fe_assemble_dev(fe, fe->x, fe->val, fe->b);
+    if (rc) return rc;
+    CKF(cudaMemcpyAsync(val, fe->val, sizeof(double) * fe->nnz, cudaMemcpyDeviceToHost, fe->st));
+    CKF(cudaMemcpyAsync(b, fe->b, sizeof(double) * fe->n, cudaMemcpyDeviceToHost, fe->st));
+    CKF(cudaStreamSynchronize(fe->st));
+    return RGM_OK;
+}
+
+int rgm_fe_initial_field(rgm_fe fe, const double *a8, double *u0, int flags)
+{
+    if (!fe || !a8 || !u0) return RGM_E_ARG;
+    double xi[5] = {0, 0, 0, 0, 0};
+    gll_closed(fe->p, xi);
+    double *a8d = nullptr;
+    CKF(cudaMalloc((void **)&a8d, sizeof(double) * 8));
+    cudaError_t e = cudaMemcpyAsync(a8d, a8, sizeof(double) * 8, cudaMemcpyHostToDevice, fe->st);
+    double *dst = (flags & RGM_DEVICE_PTRS) ? u0 : fe->x;
+    if (e == cudaSuccess) {
+        fe_u0_kernel<<<(unsigned)((fe->n + 255) / 256), 256, 0, fe->st>>>(fe->p, fe->N, fe->L, xi[0], xi[1], xi[2],
+                                                                     xi[3], xi[4], a8d, dst, fe->n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && !(flags & RGM_DEVICE_PTRS))
+        e = cudaMemcpyAsync(u0, fe->x, sizeof(double) * fe->n, cudaMemcpyDeviceToHost, fe->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(fe->st);
+    cudaFree(a8d);
+    return e == cudaSuccess ? RGM_OK : RGM_E_CUDA;
+}
+
+int rgm_fe_time_step(rgm_fe fe, rgm_solver s, double *u_dev, rgm_stats *st)
+{
+    if (!fe || !s || !u_dev) return RGM_E_ARG;
+    double *sval = nullptr;
+    int64_t snnz = 0;
+    int rc = rgm_internal_values_ptr(s, &sval, &snnz);
+    if (rc) return rc;
+    if (snnz != fe->nnz) return RGM_E_STATE;
+    if ((rc = fe_assemble_dev(fe, u_dev, fe->val, fe->b))) return rc;
+    CKF(cudaStreamSynchronize(fe->st));
+    if ((rc = rgm_set_operator_values(s, fe->val, RGM_DEVICE_PTRS))) return rc;
+    int kcur = 0;
+    rgm_get_recycle_space(s, nullptr, 0, &kcur, 0);
+    rgm_config cfg;
+    if ((rc = rgm_internal_config(s, &cfg))) return rc;
+    const int zero = (cfg.mode != RGM_PLAIN && kcur > 0) ? 1 : 0;
+    fe_select_kernel<<<(unsigned)((fe->n + 255) / 256), 256, 0, fe->st>>>(fe->x, u_dev, fe->n, zero);
+    CKF(cudaGetLastError());
+    CKF(cudaStreamSynchronize(fe->st));
+    rc = rgm_solve(s, fe->b, fe->x, RGM_DEVICE_PTRS, st);
+    if (rc < 0) return rc;
+    int rc2 = rgm_update_recycle_svd(s, fe->x, RGM_DEVICE_PTRS, nullptr);
+    if (rc2 < 0) return rc2;
+    CKF(cudaMemcpyAsync(u_dev, fe->x, sizeof(double) * fe->n, cudaMemcpyDeviceToDevice, fe->st));
+    CKF(cudaStreamSynchronize(fe->st));
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,787 @@
+// solver.cu -- librgmres: the C ABI of include/rgmres.h and the host-side
+// orchestration of restarted, recycled GMRES on one GPU.
+//
+// Sec. 3 of the paper defines GMRES as the minimal-residual projection with
+// S_k = K_k(A, r0), C_k = A S_k, computed through the Arnoldi relation; Sec. 1
+// restarts it every m steps; Sec. 3.1 (augmentation), Sec. 3.2 (deflation with
+// P = I - A U E^{-1} U^T) and Table 1 give the recycled variants; Sec. 4.2 the
+// projection initial guess x0 = U E^{-1} U^T b; Sec. 5.2 / Algorithm 1 the
+// recycle space from a thin SVD of a window of previous solutions.
+//
+// Host side: one launch per fused pass, stream-ordered, with all scalar state
+// (Hessenberg matrix, rotations, flags) on the device; the host synchronises
+// once per GMRES cycle to read the residual and decide whether to restart.
+#include "../../include/rgmres.h"
+#include "common.cuh"
+#include "vec_kernels.cuh"
+#include "svd_kernels.cuh"
+
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#define CK(call)                                                             \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess) return (e_ == cudaErrorMemoryAllocation) ? RGM_E_OOM : RGM_E_CUDA; \
+    } while (0)
+
+namespace {
+
+// Per-precision device buffers of the Arnoldi process.
+template <typename T>
+struct Arnoldi {
+    const int64_t *rowptr = nullptr;
+    const int32_t *col = nullptr;
+    const T *val = nullptr;
+    T *V = nullptr;      // n x (m + k + 1), leading dimension ld
+    T *U = nullptr;      // n x kmax
+    T *W = nullptr;      // n x kmax (A U)
+    T *w = nullptr;      // work vector
+    T *r = nullptr;      // residual
+    T *b = nullptr;      // right-hand side of this (inner) solve
+    T *x = nullptr;      // iterate of this (inner) solve
+};
+
+}  // namespace
+
+struct rgm_solver_s {
+    rgm_config cfg;
+    cudaStream_t st = nullptr;
+    int nsm = 0;
+    int64_t n = 0, ld = 0, nnz = 0;
+    int nblocks = 0, rpb = 0, sw = 8;
+    bool have_op = false;
+    // operator
+    int64_t *rowptr = nullptr;
+    int32_t *col = nullptr;
+    double *val = nullptr;
+    float *val32 = nullptr;
+    // binary64 vectors
+    double *V = nullptr, *U = nullptr, *W = nullptr, *w = nullptr, *r = nullptr, *b = nullptr,
+           *x = nullptr;
+    // binary32 vectors (GMRES-IR inner solve)
+    float *V32 = nullptr, *U32 = nullptr, *W32 = nullptr, *w32 = nullptr, *r32 = nullptr,
+          *b32 = nullptr, *x32 = nullptr;
+    // recycling
+    int k_cur = 0;
+    bool coarse_stale = true;
+    double *X = nullptr;          // snapshot window, n x window (ring)
+    int win_count = 0, win_head = 0, updates = 0;
+    double *Ytmp = nullptr;       // n x kmax scratch for the SVD
+    // scratch
+    double *partials = nullptr;
+    unsigned *counter = nullptr;
+    int2 *pairs = nullptr;        // pair list for Gram launches
+    double *gram_out = nullptr;
+    Small *sm = nullptr;
+    Small *hs = nullptr;          // pinned host mirror (header fields)
+    int npairs_max = 0;
+};
+
+static size_t small_header_bytes() { return offsetof(Small, H); }
+
+static int choose_sw(int64_t n, int64_t nnz)
+{
+    double avg = n ? (double)nnz / (double)n : 1.0;
+    if (avg <= 6) return 4;
+    if (avg <= 12) return 8;
+    if (avg <= 28) return 16;
+    return 32;
+}
+
+template <typename T>
+static VecOp<T> base_op(rgm_solver s, const Arnoldi<T> &a)
+{
+    VecOp<T> op;
+    std::memset(&op, 0, sizeof op);
+    op.n = s->n;
+    op.rpb = s->rpb;
+    op.nblocks = s->nblocks;
+    op.src = SRC_NONE;
+    op.rowptr = a.rowptr;
+    op.col = a.col;
+    op.val = a.val;
+    op.xscale = -1;
+    op.U = a.U;
+    op.ldu = s->ld;
+    op.V = a.V;
+    op.ldv = s->ld;
+    op.W = a.W;
+    op.ldw = s->ld;
+    op.partials = s->partials;
+    op.counter = s->counter;
+    op.sm = s->sm;
+    op.fin = FIN_NONE;
+    op.gate = GATE_NONE;
+    return op;
+}
+
+template <typename T>
+static int launch(rgm_solver s, const VecOp<T> &op)
+{
+    const bool spmv = (op.src == SRC_SPMV || op.src == SRC_RES);
+    dim3 g(s->nblocks), bl(RGM_THREADS);
+    if (!spmv) vec_kernel<T, 1><<<g, bl, 0, s->st>>>(op);
+    else if (s->sw == 4) vec_kernel<T, 4><<<g, bl, 0, s->st>>>(op);
+    else if (s->sw == 8) vec_kernel<T, 8><<<g, bl, 0, s->st>>>(op);
+    else if (s->sw == 16) vec_kernel<T, 16><<<g, bl, 0, s->st>>>(op);
+    else vec_kernel<T, 32><<<g, bl, 0, s->st>>>(op);
+    CK(cudaGetLastError());
+    return RGM_OK;
+}
+
+template <typename T>
+static int launch_gram(rgm_solver s, const T *X, int64_t ldx, int nx, const T *Y, int64_t ldy,
+                       const std::vector<int2> &pairs, double *out)
+{
+    if ((int)pairs.size() > s->npairs_max) return RGM_E_ARG;
+    if (pairs.empty()) return RGM_OK;
+    CK(cudaMemcpyAsync(s->pairs, pairs.data(), sizeof(int2) * pairs.size(), cudaMemcpyHostToDevice,
+                       s->st));
+    GramOp<T> op;
+    op.n = s->n;
+    op.rpb = s->rpb;
+    op.nblocks = s->nblocks;
+    op.X = X;
+    op.ldx = ldx;
+    op.nx = nx;
+    op.Y = Y;
+    op.ldy = ldy;
+    op.npairs = (int)pairs.size();
+    op.pairs = s->pairs;
+    op.partials = s->partials;
+    op.counter = s->counter;
+    op.out = out;
+    gram_kernel<T><<<s->nblocks, RGM_THREADS, 0, s->st>>>(op);
+    CK(cudaGetLastError());
+    return RGM_OK;
+}
+
+static int read_header(rgm_solver s)
+{
+    CK(cudaMemcpyAsync(s->hs, s->sm, small_header_bytes(), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return RGM_OK;
+}
+
+__global__ void solve_setup_kernel(Small *s, int maxit, int m, int k)
+{
+    if (threadIdx.x == 0) {
+        s->iters = 0;
+        s->maxit = maxit;
+        s->m = m;
+        s->k = k;
+        s->converged = 0;
+        s->done = 0;
+        s->J = 0;
+        s->nb = 0;
+        s->naug = 0;
+        s->skip = 0;
+        s->breakdown = 0;
+    }
+}
+
+__global__ void set_tol_kernel(Small *s, double rtol)
+{
+    if (threadIdx.x == 0) s->tol_abs = rtol * s->bnorm;
+}
+
+// W = A U and the LU of E = U^T W (binary64), once per (operator, recycle space).
+static int coarse_setup(rgm_solver s)
+{
+    const int k = s->k_cur;
+    Arnoldi<double> a;
+    a.rowptr = s->rowptr; a.col = s->col; a.val = s->val; a.V = s->V; a.U = s->U; a.W = s->W;
+    for (int i = 0; i < k; ++i) {
+        VecOp<double> op = base_op(s, a);
+        op.src = SRC_SPMV;
+        op.x = s->U + (int64_t)i * s->ld;
+        op.out = s->W + (int64_t)i * s->ld;
+        int rc = launch(s, op);
+        if (rc) return rc;
+    }
+    std::vector<int2> pairs;
+    for (int j = 0; j < k; ++j)
+        for (int i = 0; i < k; ++i) pairs.push_back(make_int2(i, k + j));     // E_ij = u_i . w_j
+    for (int i = 0; i < k; ++i) pairs.push_back(make_int2(i, i));
+    for (int i = 0; i < k; ++i) pairs.push_back(make_int2(k + i, k + i));
+    int rc = launch_gram<double>(s, s->U, s->ld, k, s->W, s->ld, pairs, s->gram_out);
+    if (rc) return rc;
+    lu_kernel<<<1, 256, 0, s->st>>>(s->sm, k, s->gram_out, s->gram_out + k * k);
+    CK(cudaGetLastError());
+    rc = read_header(s);
+    if (rc) return rc;
+    // binary32 copies for the GMRES-IR inner solve
+    if (s->cfg.precision == RGM_FP32_IR && k > 0) {
+        convert_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U32, s->U, s->n, s->ld, k);
+        convert_kernel<<<s->nblocks, 256, 0, s->st>>>(s->W32, s->W, s->n, s->ld, k);
+        CK(cudaGetLastError());
+    }
+    s->coarse_stale = false;
+    return RGM_OK;
+}
+
+// One recycled GMRES solve of A x = b on the device buffers of `a`, with the
+// tolerance tol_abs already in Small.  mode: effective mode (PLAIN if no U).
+// Returns the number of cycles through *cycles.
+template <typename T>
+static int gmres_cycles(rgm_solver s, const Arnoldi<T> &a, int mode, int k, int max_cycles,
+                        int *cycles_out)
+{
+    const int m = s->cfg.m;
+    int cycles = 0;
+    double beta_prev = INFINITY;
+    int rc = read_header(s);
+    if (rc) return rc;
+    while (!s->hs->converged && s->hs->iters < s->hs->maxit && cycles < max_cycles) {
+        ++cycles;
+        cycle_reset_kernel<<<1, 256, 0, s->st>>>(s->sm);
+        CK(cudaGetLastError());
+        // start vector: r, or P r for the deflated oblique method (Table 1)
+        if (mode == RGM_DEFLATED) {
+            VecOp<T> op = base_op(s, a);
+            if (!s->cfg.start_r) {
+                op.src = SRC_COPY; op.win = a.r; op.out = a.w; op.ndU = k; op.fin = FIN_START_DEF1;
+                if ((rc = launch(s, op))) return rc;
+                op = base_op(s, a);
+                op.src = SRC_AXPY; op.win = a.w; op.nW = k;
+            } else {
+                op.src = SRC_COPY; op.win = a.r;
+            }
+            op.out = a.V; op.ndW = k; op.dnorm = 1; op.fin = FIN_START_DEF2;
+            if ((rc = launch(s, op))) return rc;
+        } else {
+            VecOp<T> op = base_op(s, a);
+            op.src = SRC_COPY; op.win = a.r; op.out = a.V; op.dnorm = 1; op.fin = FIN_START_PLAIN;
+            if ((rc = launch(s, op))) return rc;
+        }
+        // Arnoldi with CGS2; deflated: operator P A
+        for (int j = 0; j < m; ++j) {
+            VecOp<T> op = base_op(s, a);
+            op.gate = GATE_KRYLOV;
+            op.src = SRC_SPMV; op.x = a.V + (int64_t)j * s->ld; op.xscale = j; op.out = a.w;
+            op.ndU = (mode == RGM_DEFLATED) ? k : 0; op.dnorm = 1; op.dyn = DYN_NDV_NB;
+            op.fin = FIN_ARN1;
+            if ((rc = launch(s, op))) return rc;
+            op = base_op(s, a);
+            op.gate = GATE_KRYLOV;
+            op.src = SRC_AXPY; op.win = a.w; op.out = a.w; op.nW = (mode == RGM_DEFLATED) ? k : 0;
+            op.dyn = DYN_NV_NB | DYN_NDV_NB; op.fin = FIN_ARN2;
+            if ((rc = launch(s, op))) return rc;
+            op = base_op(s, a);
+            op.gate = GATE_KRYLOV;
+            op.src = SRC_AXPY; op.win = a.w; op.dyn = DYN_NV_NB | DYN_OUT_VNB;
+            op.ndW = (mode == RGM_DEFLATED) ? k : 0; op.dnorm = 1; op.fin = FIN_ARN3;
+            if ((rc = launch(s, op))) return rc;
+        }
+        // augmentation: append A u_i to the Arnoldi relation (Sec. 3.1)
+        if (mode == RGM_AUGMENTED) {
+            for (int i = 0; i < k; ++i) {
+                VecOp<T> op = base_op(s, a);
+                op.gate = GATE_APPEND;
+                op.src = SRC_COPY; op.win = a.W + (int64_t)i * s->ld; op.out = a.w;
+                op.dyn = DYN_NDV_NB; op.dnorm = 1; op.fin = FIN_AUG1;
+                if ((rc = launch(s, op))) return rc;
+                op = base_op(s, a);
+                op.gate = GATE_APPEND;
+                op.src = SRC_AXPY; op.win = a.w; op.out = a.w; op.dyn = DYN_NV_NB | DYN_NDV_NB;
+                op.fin = FIN_ARN2;
+                if ((rc = launch(s, op))) return rc;
+                op = base_op(s, a);
+                op.gate = GATE_APPEND;
+                op.src = SRC_AXPY; op.win = a.w; op.dyn = DYN_NV_NB | DYN_OUT_VNB; op.dnorm = 1;
+                op.fin = FIN_AUG3; op.arg = i;
+                if ((rc = launch(s, op))) return rc;
+                clear_skip_kernel<<<1, 32, 0, s->st>>>(s->sm);
+            }
+        }
+        ls_solve_kernel<<<1, 128, 0, s->st>>>(s->sm);
+        CK(cudaGetLastError());
+        {   // x += V y (+ U y_aug)
+            VecOp<T> op = base_op(s, a);
+            op.src = SRC_AXPY; op.win = a.x; op.out = a.x; op.dyn = DYN_NV_J;
+            op.nU = (mode == RGM_AUGMENTED) ? k : 0;
+            if ((rc = launch(s, op))) return rc;
+        }
+        if (mode == RGM_DEFLATED) {   // coarse correction x += U E^{-1} U^T (b - A x)
+            VecOp<T> op = base_op(s, a);
+            op.src = SRC_RES; op.x = a.x; op.b = a.b; op.out = a.r; op.ndU = k; op.fin = FIN_COARSE;
+            if ((rc = launch(s, op))) return rc;
+            op = base_op(s, a);
+            op.src = SRC_AXPY; op.win = a.x; op.out = a.x; op.nU = k;
+            if ((rc = launch(s, op))) return rc;
+        }
+        {
+            VecOp<T> op = base_op(s, a);
+            op.src = SRC_RES; op.x = a.x; op.b = a.b; op.out = a.r; op.dnorm = 1; op.fin = FIN_RESNORM;
+            if ((rc = launch(s, op))) return rc;
+        }
+        if ((rc = read_header(s))) return rc;
+        if (s->hs->J == 0 && !(s->hs->beta < beta_prev)) break;   // stagnation
+        beta_prev = s->hs->beta;
+    }
+    *cycles_out = cycles;
+    return RGM_OK;
+}
+
+// Projection initial guess / coarse correction on (x, b): x += U E^{-1} U^T (b - A x).
+template <typename T>
+static int coarse_correct(rgm_solver s, const Arnoldi<T> &a, int k)
+{
+    VecOp<T> op = base_op(s, a);
+    op.src = SRC_RES; op.x = a.x; op.b = a.b; op.out = a.r; op.ndU = k; op.fin = FIN_COARSE;
+    int rc = launch(s, op);
+    if (rc) return rc;
+    op = base_op(s, a);
+    op.src = SRC_AXPY; op.win = a.x; op.out = a.x; op.nU = k;
+    return launch(s, op);
+}
+
+template <typename T>
+static int residual_norm(rgm_solver s, const Arnoldi<T> &a)
+{
+    VecOp<T> op = base_op(s, a);
+    op.src = SRC_RES; op.x = a.x; op.b = a.b; op.out = a.r; op.dnorm = 1; op.fin = FIN_RESNORM;
+    return launch(s, op);
+}
+
+template <typename T>
+static int norm_of(rgm_solver s, const Arnoldi<T> &a, const T *v, int fin)
+{
+    VecOp<T> op = base_op(s, a);
+    op.src = SRC_COPY; op.win = v; op.out = a.w; op.dnorm = 1; op.fin = fin;
+    return launch(s, op);
+}
+
+static Arnoldi<double> arn64(rgm_solver s)
+{
+    Arnoldi<double> a;
+    a.rowptr = s->rowptr; a.col = s->col; a.val = s->val;
+    a.V = s->V; a.U = s->U; a.W = s->W; a.w = s->w; a.r = s->r; a.b = s->b; a.x = s->x;
+    return a;
+}
+
+static Arnoldi<float> arn32(rgm_solver s)
+{
+    Arnoldi<float> a;
+    a.rowptr = s->rowptr; a.col = s->col; a.val = s->val32;
+    a.V = s->V32; a.U = s->U32; a.W = s->W32; a.w = s->w32; a.r = s->r32; a.b = s->b32; a.x = s->x32;
+    return a;
+}
+
+static int solve_device(rgm_solver s, rgm_stats *out)
+{
+    const rgm_config &c = s->cfg;
+    int status = RGM_OK, rc;
+    int k = (c.mode != RGM_PLAIN) ? s->k_cur : 0;
+    if (k > 0 && s->coarse_stale) {
+        if ((rc = coarse_setup(s))) return rc;
+        if (s->hs->singular) { status = RGM_W_SINGULAR_COARSE; k = 0; }
+    } else if (k > 0 && s->hs->singular) {
+        status = RGM_W_SINGULAR_COARSE; k = 0;
+    }
+    const int mode = k > 0 ? c.mode : RGM_PLAIN;
+    solve_setup_kernel<<<1, 32, 0, s->st>>>(s->sm, c.maxit, c.m, k);
+    CK(cudaGetLastError());
+    Arnoldi<double> a = arn64(s);
+    if ((rc = norm_of(s, a, s->b, FIN_BNORM))) return rc;
+    set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.rtol);
+    if (k > 0 && (rc = coarse_correct(s, a, k))) return rc;     // x0 = x_in + Q (b - A x_in)
+    if ((rc = residual_norm(s, a))) return rc;
+    if ((rc = read_header(s))) return rc;
+    const double bnorm = s->hs->bnorm;
+    int cycles = 0, refinements = 0;
+    if (bnorm == 0.0) {
+        CK(cudaMemsetAsync(s->x, 0, sizeof(double) * s->n, s->st));
+        CK(cudaStreamSynchronize(s->st));
+    } else if (c.precision == RGM_FP64) {
+        if ((rc = gmres_cycles(s, a, mode, k, 1 << 30, &cycles))) return rc;
+    } else {
+        // GMRES-IR: binary64 residual r = b - A x, binary32 recycled GMRES for
+        // A d = r to inner_rtol * ||r||, x += d in binary64.
+        Arnoldi<float> f = arn32(s);
+        int iters_total = 0;
+        while (!s->hs->converged && iters_total < c.maxit && refinements < c.max_refinements) {
+            ++refinements;
+            convert_kernel<<<s->nblocks, 256, 0, s->st>>>(s->b32, s->r, s->n, s->n, 1);
+            CK(cudaMemsetAsync(s->x32, 0, sizeof(float) * s->n, s->st));
+            solve_setup_kernel<<<1, 32, 0, s->st>>>(s->sm, c.maxit - iters_total, c.m, k);
+            if ((rc = norm_of(s, f, s->b32, FIN_BNORM))) return rc;
+            set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.inner_rtol);
+            if (k > 0 && (rc = coarse_correct(s, f, k))) return rc;
+            if ((rc = residual_norm(s, f))) return rc;
+            int cy = 0;
+            if ((rc = gmres_cycles(s, f, mode, k, c.inner_cycles, &cy))) return rc;
+            cycles += cy;
+            iters_total += s->hs->iters;
+            // x += d (binary64), then the true residual
+            add_f32_kernel<<<s->nblocks, 256, 0, s->st>>>(s->x, s->x32, s->n);
+            solve_setup_kernel<<<1, 32, 0, s->st>>>(s->sm, c.maxit, c.m, k);
+            if ((rc = norm_of(s, a, s->b, FIN_BNORM))) return rc;
+            set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.rtol);
+            if ((rc = residual_norm(s, a))) return rc;
+            if ((rc = read_header(s))) return rc;
+            s->hs->iters = iters_total;
+        }
+        s->hs->iters = iters_total;
+    }
+    const double beta = s->hs->beta;
+    const double relres = bnorm > 0.0 ? beta / bnorm : 0.0;
+    if (status == RGM_OK && !(relres <= c.rtol)) status = RGM_W_NOT_CONVERGED;
+    if (out) {
+        out->iters = s->hs->iters;
+        out->cycles = cycles;
+        out->refinements = refinements;
+        out->k_used = k;
+        out->status = status;
+        out->true_relres = relres;
+    }
+    return status;
+}
+
+// ---------------------------------------------------------------- SVD update (Algorithm 1)
+static int svd_update(rgm_solver s, int *k_used)
+{
+    const rgm_config &c = s->cfg;
+    const int cnt = s->win_count;
+    std::vector<int2> pairs;
+    for (int j = 0; j < cnt; ++j)
+        for (int i = 0; i <= j; ++i) pairs.push_back(make_int2(i, j));
+    int rc = launch_gram<double>(s, s->X, s->ld, cnt, s->X, s->ld, pairs, s->gram_out);
+    if (rc) return rc;
+    sym_eig_select_kernel<<<1, 512, EIG_SMEM_BYTES, s->st>>>(s->sm, s->gram_out, cnt, c.k,
+                                                             c.select_smallest, c.rel_drop);
+    CK(cudaGetLastError());
+    if ((rc = read_header(s))) return rc;
+    const int kn = s->hs->k_new;
+    if (kn > 0) {
+        // U = X Phi_k Sigma_k^{-1}, then two CholQR passes
+        combine_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U, s->X, s->sm->evec, cnt, kn, s->n, s->ld,
+                                                      RGM_WMAX);
+        CK(cudaGetLastError());
+        for (int pass = 0; pass < 2; ++pass) {
+            std::vector<int2> up;
+            for (int j = 0; j < kn; ++j)
+                for (int i = 0; i <= j; ++i) up.push_back(make_int2(i, j));
+            if ((rc = launch_gram<double>(s, s->U, s->ld, kn, s->U, s->ld, up, s->gram_out))) return rc;
+            chol_inv_kernel<<<1, 32, 0, s->st>>>(s->sm, s->gram_out, kn);
+            combine_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U, s->U, s->sm->evec, kn, kn, s->n,
+                                                          s->ld, RGM_WMAX);
+            CK(cudaGetLastError());
+        }
+    }
+    s->k_cur = kn;
+    s->coarse_stale = true;
+    if (k_used) *k_used = kn;
+    return RGM_OK;
+}
+
+// ================================================================= C ABI
+extern "C" {
+
+int rgm_config_default(rgm_config *cfg)
+{
+    if (!cfg) return RGM_E_ARG;
+    std::memset(cfg, 0, sizeof *cfg);
+    cfg->m = 30;
+    cfg->k = 8;
+    cfg->window = 16;
+    cfg->svd_interval = 1;
+    cfg->mode = RGM_DEFLATED;
+    cfg->precision = RGM_FP64;
+    cfg->maxit = 20000;
+    cfg->inner_cycles = 2;
+    cfg->max_refinements = 50;
+    cfg->rtol = 1e-10;
+    cfg->inner_rtol = 1e-4;
+    cfg->rel_drop = 1e-7;
+    return RGM_OK;
+}
+
+const char *rgm_status_string(int code)
+{
+    switch (code) {
+    case RGM_OK: return "ok";
+    case RGM_W_NOT_CONVERGED: return "not converged: maxit reached";
+    case RGM_W_SINGULAR_COARSE: return "coarse matrix U^T A U singular: solved without recycling";
+    case RGM_E_ARG: return "invalid argument";
+    case RGM_E_OOM: return "device out of memory";
+    case RGM_E_CUDA: return "CUDA error";
+    case RGM_E_STATE: return "call out of order";
+    case RGM_E_TIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+    }
+}
+
+static void free_all(rgm_solver s)
+{
+    void *dp[] = {s->rowptr, s->col, s->val, s->val32, s->V, s->U, s->W, s->w, s->r, s->b, s->x,
+                  s->V32, s->U32, s->W32, s->w32, s->r32, s->b32, s->x32, s->X, s->Ytmp,
+                  s->partials, s->counter, s->pairs, s->gram_out, s->sm};
+    for (void *p : dp)
+        if (p) cudaFree(p);
+    if (s->hs) cudaFreeHost(s->hs);
+}
+
+int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
+{
+    if (!out || !cfg) return RGM_E_ARG;
+    *out = nullptr;
+    const rgm_config &c = *cfg;
+    if (c.n < 1 || c.m < 1 || c.m > RGM_MMAX || c.k < 0 || c.k > RGM_KMAX || c.window < 1 ||
+        c.window > RGM_WMAX || c.svd_interval < 1 || c.mode < 0 || c.mode > 2 || c.precision < 0 ||
+        c.precision > 1 || c.maxit < 0 || !(c.rtol >= 0) || c.inner_cycles < 1 ||
+        c.max_refinements < 1 || !(c.inner_rtol > 0) || !(c.rel_drop >= 0))
+        return RGM_E_ARG;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RGM_E_CUDA;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return RGM_E_CUDA;
+    if (cudaFuncSetAttribute(sym_eig_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)EIG_SMEM_BYTES) != cudaSuccess)
+        return RGM_E_CUDA;
+    rgm_solver s = new (std::nothrow) rgm_solver_s();
+    if (!s) return RGM_E_OOM;
+    s->cfg = c;
+    s->st = (cudaStream_t)c.cuda_stream;
+    s->nsm = nsm;
+    s->n = c.n;
+    s->ld = (c.n + 31) / 32 * 32;
+    const int64_t want = (s->n + 255) / 256;
+    s->nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, 2 * (int64_t)nsm));
+    s->rpb = (int)((s->n + s->nblocks - 1) / s->nblocks);
+    const int kmax = std::max(c.k, 1);
+    const int64_t ncolV = c.m + c.k + 1;
+    s->npairs_max = RGM_WMAX * (RGM_WMAX + 1) / 2 + RGM_KMAX * RGM_KMAX + 2 * RGM_KMAX;
+    cudaError_t e = cudaSuccess;
+#define ALLOC(p, bytes) if (e == cudaSuccess) e = cudaMalloc((void **)&(p), (bytes))
+    ALLOC(s->V, sizeof(double) * s->ld * ncolV);
+    ALLOC(s->U, sizeof(double) * s->ld * kmax);
+    ALLOC(s->W, sizeof(double) * s->ld * kmax);
+    ALLOC(s->w, sizeof(double) * s->ld);
+    ALLOC(s->r, sizeof(double) * s->ld);
+    ALLOC(s->b, sizeof(double) * s->ld);
+    ALLOC(s->x, sizeof(double) * s->ld);
+    ALLOC(s->X, sizeof(double) * s->ld * c.window);
+    ALLOC(s->partials, sizeof(double) * (size_t)std::max(RGM_MAXDOTS, s->npairs_max) * s->nblocks);
+    ALLOC(s->counter, sizeof(unsigned) * 4);
+    ALLOC(s->pairs, sizeof(int2) * s->npairs_max);
+    ALLOC(s->gram_out, sizeof(double) * s->npairs_max);
+    ALLOC(s->sm, sizeof(Small));
+    if (c.precision == RGM_FP32_IR) {
+        ALLOC(s->V32, sizeof(float) * s->ld * ncolV);
+        ALLOC(s->U32, sizeof(float) * s->ld * kmax);
+        ALLOC(s->W32, sizeof(float) * s->ld * kmax);
+        ALLOC(s->w32, sizeof(float) * s->ld);
+        ALLOC(s->r32, sizeof(float) * s->ld);
+        ALLOC(s->b32, sizeof(float) * s->ld);
+        ALLOC(s->x32, sizeof(float) * s->ld);
+    }
+#undef ALLOC
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&s->hs, sizeof(Small));
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->counter, 0, sizeof(unsigned) * 4, s->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->sm, 0, sizeof(Small), s->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->V, 0, sizeof(double) * s->ld * ncolV, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess) {
+        free_all(s);
+        delete s;
+        return e == cudaErrorMemoryAllocation ? RGM_E_OOM : RGM_E_CUDA;
+    }
+    std::memset(s->hs, 0, sizeof(Small));
+    *out = s;
+    return RGM_OK;
+}
+
+int rgm_solver_destroy(rgm_solver s)
+{
+    if (!s) return RGM_E_ARG;
+    cudaStreamSynchronize(s->st);
+    free_all(s);
+    delete s;
+    return RGM_OK;
+}
+
+static cudaMemcpyKind kind_in(int flags)
+{
+    return (flags & RGM_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+
+static cudaMemcpyKind kind_out(int flags)
+{
+    return (flags & RGM_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+int rgm_set_operator_csr(rgm_solver s, int64_t n, int64_t nnz, const int64_t *rowptr,
+                         const int32_t *col, const double *val, int flags)
+{
+    if (!s || n != s->n || nnz < 0 || !rowptr || (nnz > 0 && (!col || !val))) return RGM_E_ARG;
+    // validate the pattern on the host copy
+    std::vector<int64_t> rp(n + 1);
+    if (cudaMemcpy(rp.data(), rowptr, sizeof(int64_t) * (n + 1), (flags & RGM_DEVICE_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost) != cudaSuccess)
+        return RGM_E_CUDA;
+    if (rp[0] != 0 || rp[n] != nnz) return RGM_E_ARG;
+    for (int64_t i = 0; i < n; ++i)
+        if (rp[i + 1] < rp[i]) return RGM_E_ARG;
+    std::vector<int32_t> cl(nnz);
+    if (nnz && cudaMemcpy(cl.data(), col, sizeof(int32_t) * nnz, (flags & RGM_DEVICE_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost) != cudaSuccess)
+        return RGM_E_CUDA;
+    for (int64_t e = 0; e < nnz; ++e)
+        if (cl[e] < 0 || cl[e] >= n) return RGM_E_ARG;
+    if (nnz != s->nnz || !s->rowptr) {
+        if (s->col) cudaFree(s->col);
+        if (s->val) cudaFree(s->val);
+        if (s->val32) cudaFree(s->val32);
+        if (s->rowptr) cudaFree(s->rowptr);
+        s->col = nullptr; s->val = nullptr; s->val32 = nullptr; s->rowptr = nullptr;
+        CK(cudaMalloc((void **)&s->rowptr, sizeof(int64_t) * (n + 1)));
+        CK(cudaMalloc((void **)&s->col, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+        CK(cudaMalloc((void **)&s->val, sizeof(double) * std::max<int64_t>(nnz, 1)));
+        if (s->cfg.precision == RGM_FP32_IR)
+            CK(cudaMalloc((void **)&s->val32, sizeof(float) * std::max<int64_t>(nnz, 1)));
+    }
+    s->nnz = nnz;
+    CK(cudaMemcpyAsync(s->rowptr, rp.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s->st));
+    if (nnz) CK(cudaMemcpyAsync(s->col, cl.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    s->sw = choose_sw(n, nnz);
+    s->have_op = true;
+    return rgm_set_operator_values(s, val, flags);
+}
+
+int rgm_set_operator_values(rgm_solver s, const double *val, int flags)
+{
+    if (!s || (s->nnz > 0 && !val)) return RGM_E_ARG;
+    if (!s->have_op) return RGM_E_STATE;
+    if (s->nnz) {
+        CK(cudaMemcpyAsync(s->val, val, sizeof(double) * s->nnz, kind_in(flags), s->st));
+        if (s->cfg.precision == RGM_FP32_IR) {
+            convert_kernel<<<s->nblocks, 256, 0, s->st>>>(s->val32, s->val, s->nnz, s->nnz, 1);
+            CK(cudaGetLastError());
+        }
+    }
+    s->coarse_stale = true;
+    if (!(flags & RGM_DEVICE_PTRS)) CK(cudaStreamSynchronize(s->st));
+    return RGM_OK;
+}
+
+int rgm_set_recycle_space(rgm_solver s, const double *U, int k, int64_t ld, int flags)
+{
+    if (!s || k < 0 || k > s->cfg.k || (k > 0 && (!U || ld < s->n))) return RGM_E_ARG;
+    for (int i = 0; i < k; ++i)
+        CK(cudaMemcpyAsync(s->U + (int64_t)i * s->ld, U + (int64_t)i * ld, sizeof(double) * s->n,
+                           kind_in(flags), s->st));
+    CK(cudaStreamSynchronize(s->st));
+    s->k_cur = k;
+    s->coarse_stale = true;
+    return RGM_OK;
+}
+
+int rgm_get_recycle_space(rgm_solver s, double *U, int64_t ld, int *k, int flags)
+{
+    if (!s || !k) return RGM_E_ARG;
+    *k = s->k_cur;
+    if (!U) return RGM_OK;
+    if (ld < s->n) return RGM_E_ARG;
+    for (int i = 0; i < s->k_cur; ++i)
+        CK(cudaMemcpyAsync(U + (int64_t)i * ld, s->U + (int64_t)i * s->ld, sizeof(double) * s->n,
+                           kind_out(flags), s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return RGM_OK;
+}
+
+int rgm_solve(rgm_solver s, const double *b, double *x, int flags, rgm_stats *st)
+{
+    if (!s || !b || !x) return RGM_E_ARG;
+    if (!s->have_op) return RGM_E_STATE;
+    CK(cudaMemcpyAsync(s->b, b, sizeof(double) * s->n, kind_in(flags), s->st));
+    CK(cudaMemcpyAsync(s->x, x, sizeof(double) * s->n, kind_in(flags), s->st));
+    int rc = solve_device(s, st);
+    if (rc < 0) return rc;
+    CK(cudaMemcpyAsync(x, s->x, sizeof(double) * s->n, kind_out(flags), s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return rc;
+}
+
+int rgm_update_recycle_svd(rgm_solver s, const double *x, int flags, int *k_used)
+{
+    if (!s || !x) return RGM_E_ARG;
+    CK(cudaMemcpyAsync(s->X + (int64_t)s->win_head * s->ld, x, sizeof(double) * s->n, kind_in(flags),
+                       s->st));
+    s->win_head = (s->win_head + 1) % s->cfg.window;
+    if (s->win_count < s->cfg.window) ++s->win_count;
+    ++s->updates;
+    if (s->cfg.k > 0 && s->updates % s->cfg.svd_interval == 0) {
+        int rc = svd_update(s, k_used);
+        if (rc) return rc;
+    } else if (k_used) {
+        *k_used = s->k_cur;
+    }
+    CK(cudaStreamSynchronize(s->st));
+    return RGM_OK;
+}
+
+int rgm_get_singular_values(rgm_solver s, double *sigma, int *count)
+{
+    if (!s || !sigma || !count) return RGM_E_ARG;
+    CK(cudaMemcpy(s->hs, s->sm, sizeof(Small), cudaMemcpyDeviceToHost));
+    const int c = s->win_count;
+    for (int i = 0; i < c; ++i) {
+        double l = s->hs->eval[s->hs->ord[i]];
+        sigma[i] = l > 0 ? std::sqrt(l) : 0.0;
+    }
+    *count = c;
+    return RGM_OK;
+}
+
+int rgm_reset_recycling(rgm_solver s)
+{
+    if (!s) return RGM_E_ARG;
+    s->win_count = 0;
+    s->win_head = 0;
+    s->updates = 0;
+    s->k_cur = 0;
+    s->coarse_stale = true;
+    return RGM_OK;
+}
+
+// Library-internal: the solver's device value buffer (for in-library producers
+// such as the FE workload) and a copy of its configuration.
+int rgm_internal_values_ptr(rgm_solver s, double **val, int64_t *nnz)
+{
+    if (!s || !val || !nnz) return RGM_E_ARG;
+    if (!s->have_op) return RGM_E_STATE;
+    *val = s->val;
+    *nnz = s->nnz;
+    return RGM_OK;
+}
+
+int rgm_internal_config(rgm_solver s, rgm_config *cfg)
+{
+    if (!s || !cfg) return RGM_E_ARG;
+    *cfg = s->cfg;
+    return RGM_OK;
+}
+
+int rgm_spmv(rgm_solver s, const double *x, double *y, int flags)
+{
+    if (!s || !x || !y) return RGM_E_ARG;
+    if (!s->have_op) return RGM_E_STATE;
+    CK(cudaMemcpyAsync(s->r, x, sizeof(double) * s->n, kind_in(flags), s->st));
+    Arnoldi<double> a = arn64(s);
+    VecOp<double> op = base_op(s, a);
+    op.src = SRC_SPMV;
+    op.x = s->r;
+    op.out = s->w;
+    int rc = launch(s, op);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(y, s->w, sizeof(double) * s->n, kind_out(flags), s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return RGM_OK;
+}
+
+}  // extern "C"
