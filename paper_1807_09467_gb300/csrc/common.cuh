@@ -18,6 +18,7 @@
 // to the next, the coarse matrix E and its LU factors.  Everything is binary64
 // whatever the vector precision.  Column i of the stored Krylov basis is
 // v_i = colscale[i] * Vraw[:, i] (normalisation is folded into coefficients).
+// The fields before H form the header the host reads back once per cycle.
 struct Small {
     int done;          // Krylov phase of the current cycle finished
     int J;             // Krylov steps taken in the current cycle
@@ -31,6 +32,7 @@ struct Small {
     int breakdown;
     int k;             // recycle columns in use
     int singular;      // E was declared singular
+    int k_new;         // recycle dimension chosen by the last window SVD
     int aug_idx[RGM_KMAX];
     double bnorm, tol_abs, beta, wn0, bs;
     double H[RGM_HLD * RGM_NCOL];         // column-major, leading dimension RGM_HLD
@@ -48,7 +50,6 @@ struct Small {
     double gram[RGM_WMAX * RGM_WMAX];     // last reduced Gram matrix
     double evec[RGM_WMAX * RGM_WMAX];     // eigenvectors of the window Gram matrix
     double eval[RGM_WMAX];
-    int k_new;                            // recycle dimension chosen by the last SVD
     int ord[RGM_WMAX];
     double wn_dummy;
 };

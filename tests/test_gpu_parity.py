@@ -64,7 +64,8 @@ def test_fe_pattern_values_rhs(rg, orc, p, N):
     assert np.all(np.abs(val - oval) <= 1e-13 * scale[rows])
     assert np.all(np.abs(b - ob) <= 1e-13 * (np.abs(ob) + np.abs(b).max()))
     a8, _ = synth.sequence_draws(synth.Q1_32, p)
-    np.testing.assert_allclose(fe.initial_field(a8), orc.u0_field(p, N, a8), rtol=0, atol=1e-15)
+    # node positions (closed form vs Newton) and device sin differ by an ulp or two
+    np.testing.assert_allclose(fe.initial_field(a8), orc.u0_field(p, N, a8), rtol=0, atol=1e-14)
 
 
 # ------------------------------------------------------------------ GMRES (a2-a7)
