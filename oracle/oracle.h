@@ -122,8 +122,11 @@ int orc_gmres_ir(const orc_csr *A, const double *b, double *x, const double *U, 
  * (columns for sigma_i = 0 are left zero).  Householder QR, then one-sided
  * Jacobi on R. */
 int orc_svd_left(int64_t n, int c, const double *X, double *sigma, double *Psi);
+/* Same, also returning the right singular vectors Phi (c x c, column i for sigma_i). */
+int orc_svd_full(int64_t n, int c, const double *X, double *sigma, double *Psi, double *Phi);
 /* Recycle space of Algorithm 1: the k leading left singular vectors of X
- * (or trailing if select_smallest), dropping sigma_i < rel_drop * sigma_1.
+ * (or trailing if select_smallest), dropping sigma_i < rel_drop * sigma_1,
+ * formed as X phi_i / sigma_i and orthonormalised inside their span.
  * Returns k_eff through *k_eff; U is n x k_eff. */
 int orc_recycle_from_window(int64_t n, int c, const double *X, int k, int select_smallest,
                             double rel_drop, double *U, int *k_eff);
@@ -142,6 +145,11 @@ typedef struct {
  * iters/k_used/status (length steps) and relres (length steps) are per step. */
 int orc_sequence(const orc_seq_cfg *cfg, const double *u0, double *x_all, double *x_final,
                  int *iters, int *k_used, double *relres, int *status);
+/* Same, also returning the wall time of each step (assembly + solve + window
+ * update, seconds, CLOCK_MONOTONIC) in step_seconds (length steps). */
+int orc_sequence_timed(const orc_seq_cfg *cfg, const double *u0, double *x_all, double *x_final,
+                       int *iters, int *k_used, double *relres, int *status,
+                       double *step_seconds);
 
 #ifdef __cplusplus
 }

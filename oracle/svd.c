@@ -10,8 +10,16 @@
  *
  * Route (textbook, no LAPACK): Householder QR X = Q R, one-sided (Hestenes)
  * Jacobi on the c x c factor R until every column pair is orthogonal to
- * 1e-15 relative, singular values as the column norms, left singular vectors
- * of X = Q times those of R.  Sorted by descending sigma, ties by index.
+ * 1e-15 relative, accumulating the right singular vectors Phi; singular values
+ * as the column norms, left singular vectors of X = Q times those of R.
+ * Sorted by descending sigma, ties by index.
+ *
+ * The recycle space is formed from the identity psi_i = X phi_i / sigma_i and
+ * then orthonormalised (modified Gram-Schmidt, twice) inside its own span:
+ * Algorithm 1 takes singular modes of X_m, which lie in range(X_m), and this
+ * form keeps V_s there to rounding, whereas Q Psi_R carries the QR's backward
+ * error (relative eps sigma_1 / sigma_i) out of range(X_m) in the trailing
+ * directions.
  */
 #include "oracle.h"
 #include <math.h>
@@ -20,18 +28,25 @@
 
 int orc_svd_left(int64_t n, int c, const double *X, double *sigma, double *Psi)
 {
+    return orc_svd_full(n, c, X, sigma, Psi, NULL);
+}
+
+int orc_svd_full(int64_t n, int c, const double *X, double *sigma, double *Psi, double *Phi)
+{
     if (n < 1 || c < 1 || n < c) return ORC_E_ARG;
     double *A = malloc(sizeof(double) * n * c);       /* working copy, then reflectors */
     double *R = calloc((size_t)c * c, sizeof(double));
     double *B = malloc(sizeof(double) * c * c);
+    double *F = calloc((size_t)c * c, sizeof(double));     /* accumulated rotations */
     double *Y = calloc((size_t)n * c, sizeof(double));
     double *tau = malloc(sizeof(double) * c);
     int *ord = malloc(sizeof(int) * c);
     double *sg = malloc(sizeof(double) * c);
-    if (!A || !R || !B || !Y || !tau || !ord || !sg) {
-        free(A); free(R); free(B); free(Y); free(tau); free(ord); free(sg);
+    if (!A || !R || !B || !F || !Y || !tau || !ord || !sg) {
+        free(A); free(R); free(B); free(F); free(Y); free(tau); free(ord); free(sg);
         return ORC_E_NOMEM;
     }
+    for (int i = 0; i < c; ++i) F[i + i * c] = 1.0;
     memcpy(A, X, sizeof(double) * n * c);
     /* Householder QR: H_j = I - tau_j v_j v_j^T with v_j stored in A[j:, j], v_j[0] = 1 */
     for (int j = 0; j < c; ++j) {
@@ -78,6 +93,9 @@ int orc_svd_left(int64_t n, int c, const double *X, double *sigma, double *Psi)
                     double bp = B[i + p * c], bq = B[i + q * c];
                     B[i + p * c] = cs * bp - sn * bq;
                     B[i + q * c] = sn * bp + cs * bq;
+                    double fp = F[i + p * c], fq = F[i + q * c];
+                    F[i + p * c] = cs * fp - sn * fq;
+                    F[i + q * c] = sn * fp + cs * fq;
                 }
             }
         if (!rotated) break;
@@ -100,6 +118,8 @@ int orc_svd_left(int64_t n, int c, const double *X, double *sigma, double *Psi)
         sigma[jj] = sg[j];
         if (sg[j] > 0.0)
             for (int i = 0; i < c; ++i) Y[i + (int64_t)jj * n] = B[i + j * c] / sg[j];
+        if (Phi)
+            for (int i = 0; i < c; ++i) Phi[i + jj * c] = F[i + j * c];
     }
     for (int j = c - 1; j >= 0; --j) {
         if (tau[j] == 0.0) continue;
@@ -115,7 +135,7 @@ int orc_svd_left(int64_t n, int c, const double *X, double *sigma, double *Psi)
     for (int jj = 0; jj < c; ++jj)
         if (sigma[jj] == 0.0) memset(Y + (int64_t)jj * n, 0, sizeof(double) * n);
     memcpy(Psi, Y, sizeof(double) * n * c);
-    free(A); free(R); free(B); free(Y); free(tau); free(ord); free(sg);
+    free(A); free(R); free(B); free(F); free(Y); free(tau); free(ord); free(sg);
     return ORC_OK;
 }
 
@@ -124,15 +144,41 @@ int orc_recycle_from_window(int64_t n, int c, const double *X, int k, int select
 {
     if (c < 1 || k < 0) { if (k_eff) *k_eff = 0; return c < 1 ? ORC_OK : ORC_E_ARG; }
     double *sigma = malloc(sizeof(double) * c), *Psi = malloc(sizeof(double) * n * c);
-    if (!sigma || !Psi) { free(sigma); free(Psi); return ORC_E_NOMEM; }
-    int rc = orc_svd_left(n, c, X, sigma, Psi);
-    if (rc) { free(sigma); free(Psi); return rc; }
+    double *Phi = malloc(sizeof(double) * c * c);
+    if (!sigma || !Psi || !Phi) { free(sigma); free(Psi); free(Phi); return ORC_E_NOMEM; }
+    int rc = orc_svd_full(n, c, X, sigma, Psi, Phi);
+    if (rc) { free(sigma); free(Psi); free(Phi); return rc; }
     int nz = 0;                                   /* numerically nonzero modes */
     while (nz < c && sigma[nz] > 0.0 && sigma[nz] >= rel_drop * sigma[0]) ++nz;
     int ke = k < nz ? k : nz;
     int first = select_smallest ? nz - ke : 0;
-    memcpy(U, Psi + (int64_t)first * n, sizeof(double) * n * ke);
+    /* psi_l = X phi_l / sigma_l */
+    for (int l = 0; l < ke; ++l) {
+        const double *ph = Phi + (int64_t)(first + l) * c;
+        const double s = sigma[first + l];
+        double *u = U + (int64_t)l * n;
+        for (int64_t i = 0; i < n; ++i) {
+            double acc = 0.0;
+            for (int m = 0; m < c; ++m) acc += X[i + (int64_t)m * n] * ph[m];
+            u[i] = acc / s;
+        }
+    }
+    /* modified Gram-Schmidt, twice, inside span U */
+    for (int pass = 0; pass < 2; ++pass)
+        for (int j = 0; j < ke; ++j) {
+            double *uj = U + (int64_t)j * n;
+            for (int i = 0; i < j; ++i) {
+                const double *ui = U + (int64_t)i * n;
+                double d = 0.0;
+                for (int64_t t = 0; t < n; ++t) d += ui[t] * uj[t];
+                for (int64_t t = 0; t < n; ++t) uj[t] -= d * ui[t];
+            }
+            double nr = 0.0;
+            for (int64_t t = 0; t < n; ++t) nr += uj[t] * uj[t];
+            nr = sqrt(nr);
+            for (int64_t t = 0; t < n; ++t) uj[t] /= nr;
+        }
     *k_eff = ke;
-    free(sigma); free(Psi);
+    free(sigma); free(Psi); free(Phi);
     return ORC_OK;
 }

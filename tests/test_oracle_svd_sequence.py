@@ -110,3 +110,16 @@ def test_sequence_solves_each_system(orc):
     for mode in (1, 2):
         d = np.linalg.norm(results[mode] - results[0], axis=0) / np.linalg.norm(results[0], axis=0)
         assert d.max() < 1e-8
+
+
+def test_recycle_space_lies_in_window_range(orc):
+    """Algorithm 1 keeps singular modes of X_m, so span U is inside range(X_m):
+    with all c modes kept, span U = range(X) even at sigma_c / sigma_1 = 1e-7."""
+    n, c = 3000, 6
+    B = np.linalg.qr(synth.random_matrix(n, c, 60))[0]
+    C = np.linalg.qr(synth.random_matrix(c, c, 61))[0] @ np.diag(np.logspace(0, -7, c))
+    X = B @ C
+    U = orc.recycle_from_window(X, c, rel_drop=1e-9)
+    assert U.shape[1] == c
+    assert np.linalg.norm(U - B @ (B.T @ U)) <= 1e-13
+    np.testing.assert_allclose(U.T @ U, np.eye(c), atol=1e-14)
