@@ -1,0 +1,428 @@
+#!/usr/bin/env python
+"""Benchmark: solves/s of recycled GMRES(m) over a convection-diffusion time-step sequence.
+
+One bench step = one time step of Algorithm 1 on the device: new operator values
+and right-hand side (assembled on the device from the previous solution, outside
+the timed segment), then, timed with CUDA events on the solver's stream,
+rgm_set_operator_values + rgm_solve + rgm_update_recycle_svd.  L2 is flushed
+(256 MiB write) before every timed segment.  Default workload: Q2 elements on a
+128 x 128 grid (66,049 dofs), eps 0.01, dt 0.005, FP64 GMRES(30), rtol 1e-10,
+k = 8 recycle vectors from a window of 16; the headline mode is the deflated
+oblique method, with plain and augmented GMRES measured on the same sequence.
+
+Multi-GPU (torchrun): independent sequences per rank (replicas, no collective
+on the data path); value = all ranks' solves / slowest rank's time.
+--impl reference times the FP64 CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s & HBM GB/s at ‖r‖/‖b‖≤1e-8: recycled vs plain GMRES(m); p99 latency"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12      # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="q2_128x128_eps0.01_dt0.005")
+    ap.add_argument("--mode", default="deflated", choices=["plain", "deflated", "augmented"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_ir"])
+    ap.add_argument("--cpu-steps", type=int, default=0, help="oracle steps for cpu_baseline (0: auto)")
+    ap.add_argument("--quick", action="store_true", help="skip e2e, cpu baseline and side modes")
+    return ap.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def src_digest():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1807_09467_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except Exception:
+        return None
+    ent = rec.get(kernel)
+    if not ent or ent.get("src_sha") != src_digest():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def iters_stats(its):
+    its = [int(i) for i in its]
+    return {"mean": round(statistics.mean(its), 2),
+            "sd": round(statistics.pstdev(its), 2) if len(its) > 1 else 0.0}
+
+
+# ------------------------------------------------------------------ our arm
+def run_sequence(rg, torch, w, seq, mode, precision, warmup, steps, profile=False, keep=None,
+                 flush=None, stream=None):
+    """Runs warmup + steps time steps on the device; returns timing and stats."""
+    a8, beta = seq
+    dev = torch.device("cuda")
+    fe = rg.FE(w.p, w.N, w.eps, w.dt, beta, stream=stream)
+    rp, col = fe.pattern()
+    rtol = w.rtol if precision == "fp64" else 1e-8
+    solver = rg.Solver(fe.n, m=w.m, k=w.k, window=w.window, svd_interval=w.ell, mode=mode,
+                       precision=precision, rtol=rtol, stream=stream)
+    u0 = fe.initial_field(a8)
+    u = torch.tensor(u0, dtype=torch.float64, device=dev)
+    solver.set_operator_csr(rp, col, torch.zeros(len(col), dtype=torch.float64).numpy())
+    x = torch.empty_like(u)
+    cs = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(warmup + steps)]
+    eva = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(warmup + steps)]
+    its, res, kus = [], [], []
+    prof = None
+    for i in range(warmup + steps):
+        if i == warmup and profile:
+            solver.profile(True)
+        eva[i][0].record(cs)
+        val, b = fe.assemble(u)                         # workload step, not timed
+        eva[i][1].record(cs)
+        if keep is not None:
+            keep.append((val.cpu(), b.cpu()))
+        if solver.recycle_dim() > 0 and mode != "plain":
+            x.zero_()
+        else:
+            x.copy_(u)
+        if flush is not None:
+            flush.zero_()
+        ev[i][0].record(cs)
+        solver.set_operator_values(val)
+        _, st = solver.solve(b, x)
+        solver.update_recycle_svd(x)
+        ev[i][1].record(cs)
+        u.copy_(x)
+        its.append(st["iters"])
+        res.append(st["true_relres"])
+        kus.append(st["k_used"])
+    torch.cuda.synchronize()
+    if profile:
+        prof = solver.profile_read()
+        solver.profile(False)
+    seg = [ev[i][0].elapsed_time(ev[i][1]) for i in range(warmup + steps)]
+    asm = [eva[i][0].elapsed_time(eva[i][1]) for i in range(warmup + steps)]
+    solver.close()
+    fe.close()
+    return dict(seg_ms=seg[warmup:], asm_ms=asm[warmup:], iters=its, relres=res, k_used=kus,
+                prof=prof, n=fe.n, nnz=len(col), u_final=u.cpu().numpy())
+
+
+def run_e2e(rg, np, w, seq, mode, precision, warmup, steps, inputs, torch):
+    """Same sequence through the public API with host (pinned) buffers."""
+    a8, beta = seq
+    n = len(inputs[0][1])
+    fe = rg.FE(w.p, w.N, w.eps, w.dt, beta)
+    rp, col = fe.pattern()
+    u = fe.initial_field(a8)
+    fe.close()
+    rtol = w.rtol if precision == "fp64" else 1e-8
+    s = rg.Solver(n, m=w.m, k=w.k, window=w.window, svd_interval=w.ell, mode=mode,
+                  precision=precision, rtol=rtol)
+    s.set_operator_csr(rp, col, np.zeros(len(col)))
+    pin_val = torch.empty(len(col), dtype=torch.float64).pin_memory()
+    pin_b = torch.empty(n, dtype=torch.float64).pin_memory()
+    pin_x = torch.empty(n, dtype=torch.float64).pin_memory()
+    times = []
+    for i in range(warmup + steps):
+        val, b = inputs[i]
+        pin_val.copy_(val)
+        pin_b.copy_(b)
+        if s.recycle_dim() > 0 and mode != "plain":
+            pin_x.zero_()
+        else:
+            pin_x.copy_(torch.from_numpy(u))
+        t0 = time.perf_counter()
+        s.set_operator_values(pin_val.numpy())
+        xx, st = s.solve(pin_b.numpy(), pin_x.numpy())
+        s.update_recycle_svd(xx)
+        t1 = time.perf_counter()
+        u = xx
+        times.append(t1 - t0)
+    s.close()
+    nnz = len(col)
+    return dict(sec=times[warmup:], h2d=8 * nnz + 8 * n * 3, d2h=8 * n)
+
+
+def ours(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as g
+    import paper_1807_09467_gb300 as rg
+    import synth
+
+    ws, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if rank == 0:
+            g.build()
+        dist.barrier()
+    else:
+        g.build()
+    w = synth.WORKLOADS[args.workload]
+    seq = synth.sequence_draws(w, rank)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB
+
+    keep = [] if (rank == 0 and not args.quick) else None
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    t_wall0 = time.perf_counter()
+    main = run_sequence(rg, torch, w, seq, args.mode, args.precision, args.warmup, args.steps,
+                        profile=True, keep=keep, flush=flush)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    clocks = clk.stop()
+    my_sec = sum(main["seg_ms"]) / 1e3
+    tot_sec = my_sec
+    if ws > 1:
+        t = torch.tensor([my_sec], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_sec = float(t.item())
+        dist.barrier()
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+    K = args.steps
+    value = K * ws / tot_sec
+    prof, launches = main["prof"]
+    n, nnz = main["n"], main["nnz"]
+    # dominant kernel by device time
+    kinds = {k: v for k, v in prof.items() if v["launches"] > 0}
+    tot_ms = sum(v["ms"] for v in kinds.values())
+    dom = max(kinds, key=lambda k: kinds[k]["ms"])
+    d = kinds[dom]
+    per_launch_ms = d["ms"] / d["launches"]
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6690.5)
+    if args.precision == "fp64":
+        achieved = d["flops"] / d["launches"] / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+                "peak_source": "FP64 FMA pipe, 152 SMs x 2 FMA/clk x 2.07 GHz (derived)",
+                "achieved_gbs": round(d["bytes"] / d["launches"] / (per_launch_ms * 1e-3) / 1e9, 1)}
+    else:
+        achieved = d["bytes"] / d["launches"] / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "peak_source": "of measured (MEASURED_PEAKS hbm_gbs)"}
+    roof.update({"kernel": dom, "launches": d["launches"], "ms_per_launch": round(per_launch_ms, 5),
+                 "algorithmic_flops_per_launch": d["flops"] / d["launches"],
+                 "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
+                 "traffic": traffic_record(dom)})
+    kernel_share = {k: {"ms": round(v["ms"], 3), "share": round(v["ms"] / tot_ms, 4),
+                        "launches": v["launches"]} for k, v in kinds.items()}
+    seg = main["seg_ms"]
+    all_bytes = sum(v["bytes"] for v in kinds.values())
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": ws, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(tot_sec * 1e3 / K, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "n": n, "nnz": nnz, "p": w.p, "N": w.N, "m": w.m, "k": w.k,
+                   "window": w.window, "svd_interval": w.ell, "mode": args.mode,
+                   "precision": args.precision,
+                   "rtol": w.rtol if args.precision == "fp64" else 1e-8,
+                   "l2": "flushed (256 MiB write) before every timed step",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "hbm_gbs_algorithmic": round(all_bytes / (tot_ms * 1e-3) / 1e9, 1),
+        "latency_ms": {"p50": round(float(np.percentile(seg, 50)), 4),
+                       "p99": round(float(np.percentile(seg, 99)), 4)},
+        "iterations": iters_stats(main["iters"][args.warmup:]),
+        "max_true_relres": max(main["relres"][args.warmup:]),
+        "assembly_ms_per_step": round(statistics.mean(main["asm_ms"]), 4),
+        "roofline": roof, "kernels": kernel_share, "gpu_launches": int(launches),
+        "clocks": clocks, "wall_s": round(t_wall, 3),
+    }
+    if not args.quick:
+        # recycled vs plain on the same sequence
+        side = {}
+        for md in ("plain", "augmented", "deflated"):
+            if md == args.mode:
+                r = main
+            else:
+                r = run_sequence(rg, torch, w, seq, md, args.precision, args.warmup, K, flush=flush)
+            side[md] = {"solves_per_s": round(K / (sum(r["seg_ms"]) / 1e3), 3),
+                        "ms_per_step": round(statistics.mean(r["seg_ms"]), 4),
+                        "iterations": iters_stats(r["iters"][args.warmup:]),
+                        "max_true_relres": max(r["relres"][args.warmup:])}
+        out["modes"] = side
+        # end to end through the public API with host buffers
+        e = run_e2e(rg, np, w, seq, args.mode, args.precision, args.warmup, K, keep, torch)
+        out["e2e"] = {"value": round(K / sum(e["sec"]), 3), "unit": "solves/s",
+                      "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"]}
+        # CPU baseline: the oracle on a bounded sample of the same sequence
+        out["cpu_baseline"], out["parity"] = cpu_baseline(args, w, seq, main, np)
+    print(json.dumps(out))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(args, w, seq, main, np):
+    import oracle as orc
+    orc.build()
+    a8, beta = seq
+    S = args.cpu_steps or min(w.steps, 30 if w.n < 200000 else 3)
+    u0 = orc.u0_field(w.p, w.N, a8)
+    mode = {"plain": 0, "deflated": 1, "augmented": 2}[args.mode]
+    rtol = w.rtol if args.precision == "fp64" else 1e-8
+    r = orc.sequence(w.p, w.N, w.eps, w.dt, beta, S, u0, mode=mode, m=w.m, k=w.k,
+                     window=w.window, ell=w.ell, rtol=rtol, keep_all=False)
+    secs = r["step_seconds"]
+    cb = {"value": round(S / float(secs.sum()), 4), "unit": "solves/s", "cores": 1, "kind": "oracle",
+          "sample": f"first {S} time steps of the same sequence ({w.name}, {args.mode}), "
+                    f"FE assembly + solve + window SVD per step, single thread"}
+    # parity of the last sampled step's iteration count against the device run
+    par = {"oracle_iterations": iters_stats(r["iters"]),
+           "gpu_iterations_same_steps": iters_stats(main["iters"][:S]),
+           "max_abs_iter_diff": int(np.max(np.abs(np.array(main["iters"][:S]) - r["iters"])))
+           if len(main["iters"]) >= S else None}
+    return cb, par
+
+
+# ------------------------------------------------------------------ reference arm
+def reference(args):
+    ws, rank, local = dist_info()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle as orc
+    import synth
+    orc.build()
+    w = synth.WORKLOADS[args.workload]
+    a8, beta = synth.sequence_draws(w, 0)
+    # each bench step is one time step; the oracle is slow, so a step is a
+    # bounded sample (the first warmup+steps steps of the sequence, capped)
+    W, K = args.warmup, args.steps
+    cap = 40 if w.n < 200000 else 4
+    tot = min(W + K, cap)
+    Wc = min(W, max(tot - 1, 0))
+    Kc = tot - Wc
+    mode = {"plain": 0, "deflated": 1, "augmented": 2}[args.mode]
+    rtol = w.rtol if args.precision == "fp64" else 1e-8
+    u0 = orc.u0_field(w.p, w.N, a8)
+    r = orc.sequence(w.p, w.N, w.eps, w.dt, beta, tot, u0, mode=mode, m=w.m, k=w.k,
+                     window=w.window, ell=w.ell, rtol=rtol)
+    secs = r["step_seconds"][Wc:]
+    value = Kc / float(secs.sum())
+    sample = (f"time steps {Wc + 1}..{tot} of the {w.name} sequence ({args.mode}), FP64 oracle, "
+              f"single thread")
+    out = {"metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": args.gpus,
+           "steps": Kc, "warmup": Wc, "ms_per_step": round(1e3 * float(secs.mean()), 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": w.name, "n": w.n, "m": w.m, "k": w.k, "window": w.window,
+                      "mode": args.mode, "precision": "fp64", "rtol": rtol},
+           "iterations": iters_stats(r["iters"][Wc:]),
+           "cpu_baseline": {"value": round(value, 4), "unit": "solves/s", "cores": 1,
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 4), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        reference(a)
+    else:
+        ours(a)

@@ -146,6 +146,32 @@ int rgm_spmv(rgm_solver s, const double *x, double *y, int flags);
 
 const char *rgm_status_string(int code);
 
+/* ------------------------------------------------------------ measurement
+ * Per-launch CUDA-event timing of the solver's kernels on its stream, grouped
+ * by kind, with the algorithmic work of each launch (flops and bytes the
+ * method must compute and move; not the hardware traffic).  Not part of the
+ * method; used to place kernels on the roofline. */
+#define RGM_PROF_ARNOLDI_SPMV 0   /* SpMV A v_j + dots with [U|V] (first pass)   */
+#define RGM_PROF_ARNOLDI_CGS1 1   /* AXPY of the first Gram-Schmidt pass + dots  */
+#define RGM_PROF_ARNOLDI_CGS2 2   /* AXPY of the second pass + norm              */
+#define RGM_PROF_OTHER        3   /* residuals, start vectors, coarse, updates   */
+#define RGM_PROF_GRAM         4   /* Gram matrices (E, snapshot window, CholQR)  */
+#define RGM_PROF_SMALL        5   /* single-block scalar kernels                 */
+#define RGM_PROF_KINDS        6
+
+typedef struct {
+    double ms;          /* summed device time of the launches                */
+    int64_t launches;
+    double flops;       /* summed algorithmic floating-point operations      */
+    double bytes;       /* summed algorithmic bytes read and written         */
+} rgm_kernel_prof;
+
+/* Reset the counters and switch event timing on (1) or off (0). */
+int rgm_profile(rgm_solver s, int enable);
+/* Synchronise the stream and copy the per-kind totals out (nkinds entries);
+ * *launches receives every kernel launch since the last reset. */
+int rgm_profile_read(rgm_solver s, rgm_kernel_prof *out, int nkinds, int64_t *launches);
+
 /* ------------------------------------------------------------ FE workload
  * The time-step systems of Sec. 6.1 built on the device: Q_p Lagrange elements
  * (p = 1..4, Gauss-Lobatto nodes) on a uniform N x N grid of the unit square,

@@ -103,6 +103,9 @@ def lib():
                                                   C.c_double, C.c_void_p, C.POINTER(C.c_int)]
             L.orc_sequence.argtypes = [C.POINTER(_SeqCfg), C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+            L.orc_sequence_timed.argtypes = [C.POINTER(_SeqCfg), C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.c_void_p]
         return _lib
 
 
@@ -327,8 +330,9 @@ def sequence(p, N, eps, dt, beta, steps, u0, mode=PLAIN, m=30, k=8, window=16, e
     k_used = np.zeros(steps, dtype=np.int32)
     relres = np.zeros(steps)
     status = np.zeros(steps, dtype=np.int32)
-    rc = lib().orc_sequence(C.byref(cfg), _p(u0), _p(x_all), _p(x_final), _p(iters), _p(k_used),
-                            _p(relres), _p(status))
+    secs = np.zeros(steps)
+    rc = lib().orc_sequence_timed(C.byref(cfg), _p(u0), _p(x_all), _p(x_final), _p(iters),
+                                  _p(k_used), _p(relres), _p(status), _p(secs))
     assert rc == 0, rc
     return dict(x_final=x_final, x_all=x_all, iters=iters, k_used=k_used, relres=relres,
-                status=status)
+                status=status, step_seconds=secs)

@@ -16,9 +16,24 @@
 #include "oracle.h"
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
+
+static double now_s(void)
+{
+    struct timespec t;
+    clock_gettime(CLOCK_MONOTONIC, &t);
+    return (double)t.tv_sec + 1e-9 * (double)t.tv_nsec;
+}
 
 int orc_sequence(const orc_seq_cfg *cfg, const double *u0, double *x_all, double *x_final,
                  int *iters, int *k_used, double *relres, int *status)
+{
+    return orc_sequence_timed(cfg, u0, x_all, x_final, iters, k_used, relres, status, NULL);
+}
+
+int orc_sequence_timed(const orc_seq_cfg *cfg, const double *u0, double *x_all, double *x_final,
+                       int *iters, int *k_used, double *relres, int *status,
+                       double *step_seconds)
 {
     if (!cfg || !u0 || cfg->steps < 1 || cfg->window < 1) return ORC_E_ARG;
     const int p = cfg->p, N = cfg->N;
@@ -39,6 +54,7 @@ int orc_sequence(const orc_seq_cfg *cfg, const double *u0, double *x_all, double
     memcpy(u, u0, sizeof(double) * n);
     int count = 0, k_eff = 0, rc = ORC_OK;
     for (int i = 1; i <= cfg->steps; ++i) {
+        double t0 = now_s();
         rc = orc_fe_step_system(p, N, cfg->eps, cfg->dt, cfg->bx, cfg->by, u, rowptr, col, val, b);
         if (rc) break;
         int use_u = (cfg->mode != ORC_PLAIN && k_eff > 0);
@@ -66,6 +82,7 @@ int orc_sequence(const orc_seq_cfg *cfg, const double *u0, double *x_all, double
             if (rc) break;
         }
         memcpy(u, x, sizeof(double) * n);
+        if (step_seconds) step_seconds[i - 1] = now_s() - t0;
     }
     if (x_final && rc == ORC_OK) memcpy(x_final, u, sizeof(double) * n);
     free(rowptr); free(col); free(val); free(b); free(u); free(x); free(X); free(U);

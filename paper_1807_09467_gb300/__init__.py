@@ -103,6 +103,12 @@ class Solver:
         check(self._L.rgm_set_recycle_space(self._h, C.c_void_p(Uf.ctypes.data), Uf.shape[1],
                                             Uf.shape[0], 0), "rgm_set_recycle_space")
 
+    def recycle_dim(self):
+        """Number of recycle vectors currently held."""
+        k = C.c_int(0)
+        check(self._L.rgm_get_recycle_space(self._h, None, self.n, C.byref(k), 0), "get_recycle")
+        return k.value
+
     def recycle_space(self):
         k = C.c_int(0)
         check(self._L.rgm_get_recycle_space(self._h, None, self.n, C.byref(k), 0), "get_recycle")
@@ -143,6 +149,20 @@ class Solver:
 
     def reset_recycling(self):
         check(self._L.rgm_reset_recycling(self._h), "rgm_reset_recycling")
+
+    def profile(self, enable=True):
+        """Reset and switch per-launch CUDA-event timing on or off."""
+        check(self._L.rgm_profile(self._h, int(enable)), "rgm_profile")
+
+    def profile_read(self):
+        """{kind: dict(ms, launches, flops, bytes)}, total launches."""
+        n = len(_lib.PROF_KINDS)
+        arr = (_lib.RgmKernelProf * n)()
+        tot = C.c_int64(0)
+        check(self._L.rgm_profile_read(self._h, arr, n, C.byref(tot)), "rgm_profile_read")
+        out = {k: dict(ms=a.ms, launches=a.launches, flops=a.flops, bytes=a.bytes)
+               for k, a in zip(_lib.PROF_KINDS, arr)}
+        return out, tot.value
 
     def spmv(self, x):
         if _is_dev(x):

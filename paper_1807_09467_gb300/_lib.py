@@ -39,6 +39,14 @@ class RgmStats(C.Structure):
                 ("k_used", C.c_int), ("status", C.c_int), ("true_relres", C.c_double)]
 
 
+class RgmKernelProf(C.Structure):
+    _fields_ = [("ms", C.c_double), ("launches", C.c_int64), ("flops", C.c_double),
+                ("bytes", C.c_double)]
+
+
+PROF_KINDS = ["arnoldi_spmv_dots", "arnoldi_cgs1_axpy_dots", "arnoldi_cgs2_axpy_norm", "other_vector",
+              "gram", "small"]
+
 _lib = None
 _lock = threading.Lock()
 
@@ -59,6 +67,9 @@ _SIGS = {
     "rgm_reset_recycling": (C.c_int, [C.c_void_p]),
     "rgm_spmv": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "rgm_status_string": (C.c_char_p, [C.c_int]),
+    "rgm_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "rgm_profile_read": (C.c_int, [C.c_void_p, C.POINTER(RgmKernelProf), C.c_int,
+                                   C.POINTER(C.c_int64)]),
     "rgm_fe_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_double, C.c_double,
                                 C.c_double, C.c_double, C.c_void_p]),
     "rgm_fe_destroy": (C.c_int, [C.c_void_p]),

@@ -32,6 +32,12 @@
 
 namespace {
 
+struct ProfRec {
+    int kind, kry_j;
+    double flops, bytes;
+    cudaEvent_t a, b;
+};
+
 // Per-precision device buffers of the Arnoldi process.
 template <typename T>
 struct Arnoldi {
@@ -81,6 +87,13 @@ struct rgm_solver_s {
     Small *sm = nullptr;
     Small *hs = nullptr;          // pinned host mirror (header fields)
     int npairs_max = 0;
+    // per-launch CUDA-event timing (rgm_profile)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<ProfRec> pending;
+    size_t cycle_rec0 = 0;
+    rgm_kernel_prof acc[RGM_PROF_KINDS];
+    int64_t launches = 0;
 };
 
 static size_t small_header_bytes() { return offsetof(Small, H); }
@@ -121,18 +134,129 @@ static VecOp<T> base_op(rgm_solver s, const Arnoldi<T> &a)
     return op;
 }
 
+static cudaEvent_t pool_event(rgm_solver s)
+{
+    if (!s->ev_pool.empty()) {
+        cudaEvent_t e = s->ev_pool.back();
+        s->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Algorithmic flops and bytes of one fused pass: what the method must read,
+// write and compute (the work vector re-read for the dot pass is not counted).
 template <typename T>
-static int launch(rgm_solver s, const VecOp<T> &op)
+static void op_cost(rgm_solver s, const VecOp<T> &op, int nb, int J, double *flops, double *bytes)
+{
+    const double n = (double)s->n, es = (double)sizeof(T);
+    double f = 0.0, b = 0.0;
+    int nV = op.nV, ndV = op.ndV;
+    if (op.dyn & DYN_NV_NB) nV = nb;
+    if (op.dyn & DYN_NV_J) nV = J;
+    if (op.dyn & DYN_NDV_NB) ndV = nb;
+    if (op.src == SRC_SPMV || op.src == SRC_RES) {
+        b += (double)s->nnz * (es + 4.0) + 8.0 * (n + 1) + 2.0 * es * n;
+        f += 2.0 * (double)s->nnz;
+        if (op.src == SRC_RES) { b += es * n; f += n; }
+    } else if (op.src == SRC_COPY) {
+        b += 2.0 * es * n;
+    } else if (op.src == SRC_AXPY) {
+        const int nc = op.nW + nV + op.nU;
+        b += es * n * (2.0 + nc);
+        f += 2.0 * n * nc;
+    }
+    const int nd = op.ndU + ndV + op.ndW;
+    b += es * n * nd;
+    f += 2.0 * n * (nd + op.dnorm);
+    *flops = f;
+    *bytes = b;
+}
+
+template <typename T>
+static int launch(rgm_solver s, const VecOp<T> &op, int kind = RGM_PROF_OTHER, int kry_j = -1,
+                  int nb_host = 0, int J_host = 0)
 {
     const bool spmv = (op.src == SRC_SPMV || op.src == SRC_RES);
     dim3 g(s->nblocks), bl(RGM_THREADS);
+    ProfRec rec;
+    if (s->prof) {
+        rec.kind = kind;
+        rec.kry_j = kry_j;
+        op_cost(s, op, nb_host, J_host, &rec.flops, &rec.bytes);
+        rec.a = pool_event(s);
+        rec.b = pool_event(s);
+        cudaEventRecord(rec.a, s->st);
+    }
     if (!spmv) vec_kernel<T, 1><<<g, bl, 0, s->st>>>(op);
     else if (s->sw == 4) vec_kernel<T, 4><<<g, bl, 0, s->st>>>(op);
     else if (s->sw == 8) vec_kernel<T, 8><<<g, bl, 0, s->st>>>(op);
     else if (s->sw == 16) vec_kernel<T, 16><<<g, bl, 0, s->st>>>(op);
     else vec_kernel<T, 32><<<g, bl, 0, s->st>>>(op);
+    ++s->launches;
     CK(cudaGetLastError());
+    if (s->prof) {
+        cudaEventRecord(rec.b, s->st);
+        s->pending.push_back(rec);
+    }
     return RGM_OK;
+}
+
+// Launch counting (and optional timing) for the single-block and Gram kernels.
+struct ProfScope {
+    rgm_solver s;
+    ProfRec rec;
+    ProfScope(rgm_solver s_, int kind, double flops = 0.0, double bytes = 0.0) : s(s_)
+    {
+        ++s->launches;
+        if (s->prof) {
+            rec.kind = kind; rec.kry_j = -1; rec.flops = flops; rec.bytes = bytes;
+            rec.a = pool_event(s);
+            rec.b = pool_event(s);
+            cudaEventRecord(rec.a, s->st);
+        }
+    }
+    ~ProfScope()
+    {
+        if (s->prof) {
+            cudaEventRecord(rec.b, s->st);
+            s->pending.push_back(rec);
+        }
+    }
+};
+
+// After a cycle: Krylov passes launched beyond the J steps actually taken
+// returned at once (the device had finished the cycle); book them as overhead.
+static void prof_fix_cycle(rgm_solver s, int J)
+{
+    for (size_t i = s->cycle_rec0; i < s->pending.size(); ++i)
+        if (s->pending[i].kry_j >= J) {
+            s->pending[i].kind = RGM_PROF_OTHER;
+            s->pending[i].flops = 0.0;
+            s->pending[i].bytes = 0.0;
+        }
+    s->cycle_rec0 = s->pending.size();
+}
+
+static void prof_collect(rgm_solver s)
+{
+    if (s->pending.empty()) return;
+    cudaStreamSynchronize(s->st);
+    for (ProfRec &r : s->pending) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        rgm_kernel_prof &a = s->acc[r.kind];
+        a.ms += ms;
+        a.launches += 1;
+        a.flops += r.flops;
+        a.bytes += r.bytes;
+        s->ev_pool.push_back(r.a);
+        s->ev_pool.push_back(r.b);
+    }
+    s->pending.clear();
+    s->cycle_rec0 = 0;
 }
 
 template <typename T>
@@ -157,7 +281,11 @@ static int launch_gram(rgm_solver s, const T *X, int64_t ldx, int nx, const T *Y
     op.partials = s->partials;
     op.counter = s->counter;
     op.out = out;
-    gram_kernel<T><<<s->nblocks, RGM_THREADS, 0, s->st>>>(op);
+    {
+        const double n = (double)s->n, np_ = (double)pairs.size();
+        ProfScope ps(s, RGM_PROF_GRAM, 2.0 * n * np_, (double)sizeof(T) * n * (double)(nx + (X == Y ? 0 : nx)));
+        gram_kernel<T><<<s->nblocks, RGM_THREADS, 0, s->st>>>(op);
+    }
     CK(cudaGetLastError());
     return RGM_OK;
 }
@@ -212,14 +340,14 @@ static int coarse_setup(rgm_solver s)
     for (int i = 0; i < k; ++i) pairs.push_back(make_int2(k + i, k + i));
     int rc = launch_gram<double>(s, s->U, s->ld, k, s->W, s->ld, pairs, s->gram_out);
     if (rc) return rc;
-    lu_kernel<<<1, 256, 0, s->st>>>(s->sm, k, s->gram_out, s->gram_out + k * k);
+    { ProfScope ps_(s, RGM_PROF_SMALL); lu_kernel<<<1, 256, 0, s->st>>>(s->sm, k, s->gram_out, s->gram_out + k * k); }
     CK(cudaGetLastError());
     rc = read_header(s);
     if (rc) return rc;
     // binary32 copies for the GMRES-IR inner solve
     if (s->cfg.precision == RGM_FP32_IR && k > 0) {
-        convert_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U32, s->U, s->n, s->ld, k);
-        convert_kernel<<<s->nblocks, 256, 0, s->st>>>(s->W32, s->W, s->n, s->ld, k);
+        { ProfScope ps_(s, RGM_PROF_OTHER); convert_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U32, s->U, s->n, s->ld, k); }
+        { ProfScope ps_(s, RGM_PROF_OTHER); convert_kernel<<<s->nblocks, 256, 0, s->st>>>(s->W32, s->W, s->n, s->ld, k); }
         CK(cudaGetLastError());
     }
     s->coarse_stale = false;
@@ -240,7 +368,7 @@ static int gmres_cycles(rgm_solver s, const Arnoldi<T> &a, int mode, int k, int 
     if (rc) return rc;
     while (!s->hs->converged && s->hs->iters < s->hs->maxit && cycles < max_cycles) {
         ++cycles;
-        cycle_reset_kernel<<<1, 256, 0, s->st>>>(s->sm);
+        { ProfScope ps_(s, RGM_PROF_SMALL); cycle_reset_kernel<<<1, 256, 0, s->st>>>(s->sm); }
         CK(cudaGetLastError());
         // start vector: r, or P r for the deflated oblique method (Table 1)
         if (mode == RGM_DEFLATED) {
@@ -267,17 +395,17 @@ static int gmres_cycles(rgm_solver s, const Arnoldi<T> &a, int mode, int k, int 
             op.src = SRC_SPMV; op.x = a.V + (int64_t)j * s->ld; op.xscale = j; op.out = a.w;
             op.ndU = (mode == RGM_DEFLATED) ? k : 0; op.dnorm = 1; op.dyn = DYN_NDV_NB;
             op.fin = FIN_ARN1;
-            if ((rc = launch(s, op))) return rc;
+            if ((rc = launch(s, op, RGM_PROF_ARNOLDI_SPMV, j, j + 1))) return rc;
             op = base_op(s, a);
             op.gate = GATE_KRYLOV;
             op.src = SRC_AXPY; op.win = a.w; op.out = a.w; op.nW = (mode == RGM_DEFLATED) ? k : 0;
             op.dyn = DYN_NV_NB | DYN_NDV_NB; op.fin = FIN_ARN2;
-            if ((rc = launch(s, op))) return rc;
+            if ((rc = launch(s, op, RGM_PROF_ARNOLDI_CGS1, j, j + 1))) return rc;
             op = base_op(s, a);
             op.gate = GATE_KRYLOV;
             op.src = SRC_AXPY; op.win = a.w; op.dyn = DYN_NV_NB | DYN_OUT_VNB;
             op.ndW = (mode == RGM_DEFLATED) ? k : 0; op.dnorm = 1; op.fin = FIN_ARN3;
-            if ((rc = launch(s, op))) return rc;
+            if ((rc = launch(s, op, RGM_PROF_ARNOLDI_CGS2, j, j + 1))) return rc;
         }
         // augmentation: append A u_i to the Arnoldi relation (Sec. 3.1)
         if (mode == RGM_AUGMENTED) {
@@ -297,10 +425,10 @@ static int gmres_cycles(rgm_solver s, const Arnoldi<T> &a, int mode, int k, int 
                 op.src = SRC_AXPY; op.win = a.w; op.dyn = DYN_NV_NB | DYN_OUT_VNB; op.dnorm = 1;
                 op.fin = FIN_AUG3; op.arg = i;
                 if ((rc = launch(s, op))) return rc;
-                clear_skip_kernel<<<1, 32, 0, s->st>>>(s->sm);
+                { ProfScope ps_(s, RGM_PROF_SMALL); clear_skip_kernel<<<1, 32, 0, s->st>>>(s->sm); }
             }
         }
-        ls_solve_kernel<<<1, 128, 0, s->st>>>(s->sm);
+        { ProfScope ps_(s, RGM_PROF_SMALL); ls_solve_kernel<<<1, 128, 0, s->st>>>(s->sm); }
         CK(cudaGetLastError());
         {   // x += V y (+ U y_aug)
             VecOp<T> op = base_op(s, a);
@@ -322,6 +450,7 @@ static int gmres_cycles(rgm_solver s, const Arnoldi<T> &a, int mode, int k, int 
             if ((rc = launch(s, op))) return rc;
         }
         if ((rc = read_header(s))) return rc;
+        if (s->prof) prof_fix_cycle(s, s->hs->J);
         if (s->hs->J == 0 && !(s->hs->beta < beta_prev)) break;   // stagnation
         beta_prev = s->hs->beta;
     }
@@ -386,11 +515,11 @@ static int solve_device(rgm_solver s, rgm_stats *out)
         status = RGM_W_SINGULAR_COARSE; k = 0;
     }
     const int mode = k > 0 ? c.mode : RGM_PLAIN;
-    solve_setup_kernel<<<1, 32, 0, s->st>>>(s->sm, c.maxit, c.m, k);
+    { ProfScope ps_(s, RGM_PROF_SMALL); solve_setup_kernel<<<1, 32, 0, s->st>>>(s->sm, c.maxit, c.m, k); }
     CK(cudaGetLastError());
     Arnoldi<double> a = arn64(s);
     if ((rc = norm_of(s, a, s->b, FIN_BNORM))) return rc;
-    set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.rtol);
+    { ProfScope ps_(s, RGM_PROF_SMALL); set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.rtol); }
     if (k > 0 && (rc = coarse_correct(s, a, k))) return rc;     // x0 = x_in + Q (b - A x_in)
     if ((rc = residual_norm(s, a))) return rc;
     if ((rc = read_header(s))) return rc;
@@ -408,11 +537,11 @@ static int solve_device(rgm_solver s, rgm_stats *out)
         int iters_total = 0;
         while (!s->hs->converged && iters_total < c.maxit && refinements < c.max_refinements) {
             ++refinements;
-            convert_kernel<<<s->nblocks, 256, 0, s->st>>>(s->b32, s->r, s->n, s->n, 1);
+            { ProfScope ps_(s, RGM_PROF_OTHER); convert_kernel<<<s->nblocks, 256, 0, s->st>>>(s->b32, s->r, s->n, s->n, 1); }
             CK(cudaMemsetAsync(s->x32, 0, sizeof(float) * s->n, s->st));
-            solve_setup_kernel<<<1, 32, 0, s->st>>>(s->sm, c.maxit - iters_total, c.m, k);
+            { ProfScope ps_(s, RGM_PROF_SMALL); solve_setup_kernel<<<1, 32, 0, s->st>>>(s->sm, c.maxit - iters_total, c.m, k); }
             if ((rc = norm_of(s, f, s->b32, FIN_BNORM))) return rc;
-            set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.inner_rtol);
+            { ProfScope ps_(s, RGM_PROF_SMALL); set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.inner_rtol); }
             if (k > 0 && (rc = coarse_correct(s, f, k))) return rc;
             if ((rc = residual_norm(s, f))) return rc;
             int cy = 0;
@@ -420,10 +549,10 @@ static int solve_device(rgm_solver s, rgm_stats *out)
             cycles += cy;
             iters_total += s->hs->iters;
             // x += d (binary64), then the true residual
-            add_f32_kernel<<<s->nblocks, 256, 0, s->st>>>(s->x, s->x32, s->n);
-            solve_setup_kernel<<<1, 32, 0, s->st>>>(s->sm, c.maxit, c.m, k);
+            { ProfScope ps_(s, RGM_PROF_OTHER); add_f32_kernel<<<s->nblocks, 256, 0, s->st>>>(s->x, s->x32, s->n); }
+            { ProfScope ps_(s, RGM_PROF_SMALL); solve_setup_kernel<<<1, 32, 0, s->st>>>(s->sm, c.maxit, c.m, k); }
             if ((rc = norm_of(s, a, s->b, FIN_BNORM))) return rc;
-            set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.rtol);
+            { ProfScope ps_(s, RGM_PROF_SMALL); set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.rtol); }
             if ((rc = residual_norm(s, a))) return rc;
             if ((rc = read_header(s))) return rc;
             s->hs->iters = iters_total;
@@ -454,24 +583,24 @@ static int svd_update(rgm_solver s, int *k_used)
         for (int i = 0; i <= j; ++i) pairs.push_back(make_int2(i, j));
     int rc = launch_gram<double>(s, s->X, s->ld, cnt, s->X, s->ld, pairs, s->gram_out);
     if (rc) return rc;
-    sym_eig_select_kernel<<<1, 512, EIG_SMEM_BYTES, s->st>>>(s->sm, s->gram_out, cnt, c.k,
-                                                             c.select_smallest, c.rel_drop);
+    { ProfScope ps_(s, RGM_PROF_SMALL); sym_eig_select_kernel<<<1, 512, EIG_SMEM_BYTES, s->st>>>(s->sm, s->gram_out, cnt, c.k,
+                                                             c.select_smallest, c.rel_drop); }
     CK(cudaGetLastError());
     if ((rc = read_header(s))) return rc;
     const int kn = s->hs->k_new;
     if (kn > 0) {
         // U = X Phi_k Sigma_k^{-1}, then two CholQR passes
-        combine_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U, s->X, s->sm->evec, cnt, kn, s->n, s->ld,
-                                                      RGM_WMAX);
+        { ProfScope ps_(s, RGM_PROF_OTHER); combine_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U, s->X, s->sm->evec, cnt, kn, s->n, s->ld,
+                                                      RGM_WMAX); }
         CK(cudaGetLastError());
         for (int pass = 0; pass < 2; ++pass) {
             std::vector<int2> up;
             for (int j = 0; j < kn; ++j)
                 for (int i = 0; i <= j; ++i) up.push_back(make_int2(i, j));
             if ((rc = launch_gram<double>(s, s->U, s->ld, kn, s->U, s->ld, up, s->gram_out))) return rc;
-            chol_inv_kernel<<<1, 32, 0, s->st>>>(s->sm, s->gram_out, kn);
-            combine_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U, s->U, s->sm->evec, kn, kn, s->n,
-                                                          s->ld, RGM_WMAX);
+            { ProfScope ps_(s, RGM_PROF_SMALL); chol_inv_kernel<<<1, 32, 0, s->st>>>(s->sm, s->gram_out, kn); }
+            { ProfScope ps_(s, RGM_PROF_OTHER); combine_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U, s->U, s->sm->evec, kn, kn, s->n,
+                                                          s->ld, RGM_WMAX); }
             CK(cudaGetLastError());
         }
     }
@@ -526,6 +655,8 @@ static void free_all(rgm_solver s)
     for (void *p : dp)
         if (p) cudaFree(p);
     if (s->hs) cudaFreeHost(s->hs);
+    for (ProfRec &r : s->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
 }
 
 int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
@@ -660,7 +791,7 @@ int rgm_set_operator_values(rgm_solver s, const double *val, int flags)
     if (s->nnz) {
         CK(cudaMemcpyAsync(s->val, val, sizeof(double) * s->nnz, kind_in(flags), s->st));
         if (s->cfg.precision == RGM_FP32_IR) {
-            convert_kernel<<<s->nblocks, 256, 0, s->st>>>(s->val32, s->val, s->nnz, s->nnz, 1);
+            { ProfScope ps_(s, RGM_PROF_OTHER); convert_kernel<<<s->nblocks, 256, 0, s->st>>>(s->val32, s->val, s->nnz, s->nnz, 1); }
             CK(cudaGetLastError());
         }
     }
@@ -764,6 +895,25 @@ int rgm_internal_config(rgm_solver s, rgm_config *cfg)
 {
     if (!s || !cfg) return RGM_E_ARG;
     *cfg = s->cfg;
+    return RGM_OK;
+}
+
+int rgm_profile(rgm_solver s, int enable)
+{
+    if (!s) return RGM_E_ARG;
+    prof_collect(s);
+    for (int i = 0; i < RGM_PROF_KINDS; ++i) s->acc[i] = rgm_kernel_prof{0.0, 0, 0.0, 0.0};
+    s->launches = 0;
+    s->prof = enable != 0;
+    return RGM_OK;
+}
+
+int rgm_profile_read(rgm_solver s, rgm_kernel_prof *out, int nkinds, int64_t *launches)
+{
+    if (!s || !out || nkinds < 0 || nkinds > RGM_PROF_KINDS) return RGM_E_ARG;
+    prof_collect(s);
+    for (int i = 0; i < nkinds; ++i) out[i] = s->acc[i];
+    if (launches) *launches = s->launches;
     return RGM_OK;
 }
 
