@@ -18,7 +18,7 @@
 #include <new>
 #include <vector>
 
-extern "C" int rgm_internal_values_ptr(rgm_solver s, double **val, int64_t *nnz);
+extern "C" int rgm_internal_nnz(rgm_solver s, int64_t *nnz);
 extern "C" int rgm_internal_config(rgm_solver s, rgm_config *cfg);
 
 #define CKF(call)                                                            \
@@ -380,9 +380,8 @@ int rgm_fe_initial_field(rgm_fe fe, const double *a8, double *u0, int flags)
 int rgm_fe_time_step(rgm_fe fe, rgm_solver s, double *u_dev, rgm_stats *st)
 {
     if (!fe || !s || !u_dev) return RGM_E_ARG;
-    double *sval = nullptr;
     int64_t snnz = 0;
-    int rc = rgm_internal_values_ptr(s, &sval, &snnz);
+    int rc = rgm_internal_nnz(s, &snnz);
     if (rc) return rc;
     if (snnz != fe->nnz) return RGM_E_STATE;
     if ((rc = fe_assemble_dev(fe, u_dev, fe->val, fe->b))) return rc;

@@ -16,6 +16,7 @@
 #include "vec_kernels.cuh"
 #include "svd_kernels.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -41,9 +42,10 @@ struct ProfRec {
 // Per-precision device buffers of the Arnoldi process.
 template <typename T>
 struct Arnoldi {
-    const int64_t *rowptr = nullptr;
-    const int32_t *col = nullptr;
-    const T *val = nullptr;
+    const int64_t *slice_ptr = nullptr;
+    const int32_t *scol = nullptr;
+    const T *sval = nullptr;
+    const int32_t *perm = nullptr;
     T *V = nullptr;      // n x (m + k + 1), leading dimension ld
     T *U = nullptr;      // n x kmax
     T *W = nullptr;      // n x kmax (A U)
@@ -60,13 +62,15 @@ struct rgm_solver_s {
     cudaStream_t st = nullptr;
     int nsm = 0;
     int64_t n = 0, ld = 0, nnz = 0;
-    int nblocks = 0, rpb = 0, sw = 8;
+    int nblocks = 0, rpb = 0;
     bool have_op = false;
-    // operator
-    int64_t *rowptr = nullptr;
-    int32_t *col = nullptr;
-    double *val = nullptr;
-    float *val32 = nullptr;
+    // operator, sliced ELL (see VecOp); csr2sell maps CSR entry -> ELL slot
+    int64_t nslices = 0, nsell = 0;
+    int64_t *slice_ptr = nullptr;
+    int32_t *scol = nullptr, *perm = nullptr, *csr2sell = nullptr;
+    double *sval = nullptr;
+    float *sval32 = nullptr;
+    double *val_stage = nullptr;  // host values land here before the scatter
     // binary64 vectors
     double *V = nullptr, *U = nullptr, *W = nullptr, *w = nullptr, *r = nullptr, *b = nullptr,
            *x = nullptr;
@@ -98,15 +102,6 @@ struct rgm_solver_s {
 
 static size_t small_header_bytes() { return offsetof(Small, H); }
 
-static int choose_sw(int64_t n, int64_t nnz)
-{
-    double avg = n ? (double)nnz / (double)n : 1.0;
-    if (avg <= 6) return 4;
-    if (avg <= 12) return 8;
-    if (avg <= 28) return 16;
-    return 32;
-}
-
 template <typename T>
 static VecOp<T> base_op(rgm_solver s, const Arnoldi<T> &a)
 {
@@ -116,9 +111,10 @@ static VecOp<T> base_op(rgm_solver s, const Arnoldi<T> &a)
     op.rpb = s->rpb;
     op.nblocks = s->nblocks;
     op.src = SRC_NONE;
-    op.rowptr = a.rowptr;
-    op.col = a.col;
-    op.val = a.val;
+    op.slice_ptr = a.slice_ptr;
+    op.scol = a.scol;
+    op.sval = a.sval;
+    op.perm = a.perm;
     op.xscale = -1;
     op.U = a.U;
     op.ldu = s->ld;
@@ -179,8 +175,9 @@ template <typename T>
 static int launch(rgm_solver s, const VecOp<T> &op, int kind = RGM_PROF_OTHER, int kry_j = -1,
                   int nb_host = 0, int J_host = 0)
 {
-    const bool spmv = (op.src == SRC_SPMV || op.src == SRC_RES);
-    dim3 g(s->nblocks), bl(RGM_THREADS);
+    // largest dot-column count this launch can see
+    const int nb_bound = (kry_j >= 0) ? kry_j + 1 : (nb_host > 0 ? nb_host : s->cfg.m + s->cfg.k + 1);
+    const int nd_max = op.ndU + ((op.dyn & DYN_NDV_NB) ? nb_bound : op.ndV) + op.ndW + op.dnorm;
     ProfRec rec;
     if (s->prof) {
         rec.kind = kind;
@@ -190,13 +187,9 @@ static int launch(rgm_solver s, const VecOp<T> &op, int kind = RGM_PROF_OTHER, i
         rec.b = pool_event(s);
         cudaEventRecord(rec.a, s->st);
     }
-    if (!spmv) vec_kernel<T, 1><<<g, bl, 0, s->st>>>(op);
-    else if (s->sw == 4) vec_kernel<T, 4><<<g, bl, 0, s->st>>>(op);
-    else if (s->sw == 8) vec_kernel<T, 8><<<g, bl, 0, s->st>>>(op);
-    else if (s->sw == 16) vec_kernel<T, 16><<<g, bl, 0, s->st>>>(op);
-    else vec_kernel<T, 32><<<g, bl, 0, s->st>>>(op);
+    const int rc = launch_vec(op, nd_max, s->st);
     ++s->launches;
-    CK(cudaGetLastError());
+    if (rc) return RGM_E_CUDA;
     if (s->prof) {
         cudaEventRecord(rec.b, s->st);
         s->pending.push_back(rec);
@@ -261,9 +254,10 @@ static void prof_collect(rgm_solver s)
 
 template <typename T>
 static int launch_gram(rgm_solver s, const T *X, int64_t ldx, int nx, const T *Y, int64_t ldy,
-                       const std::vector<int2> &pairs, double *out)
+                       int ny, const std::vector<int2> &pairs, double *out)
 {
-    if ((int)pairs.size() > s->npairs_max) return RGM_E_ARG;
+    if ((int)pairs.size() > s->npairs_max || (int)pairs.size() > RGM_GRAM_PMAX * RGM_THREADS)
+        return RGM_E_ARG;
     if (pairs.empty()) return RGM_OK;
     CK(cudaMemcpyAsync(s->pairs, pairs.data(), sizeof(int2) * pairs.size(), cudaMemcpyHostToDevice,
                        s->st));
@@ -276,15 +270,19 @@ static int launch_gram(rgm_solver s, const T *X, int64_t ldx, int nx, const T *Y
     op.nx = nx;
     op.Y = Y;
     op.ldy = ldy;
+    op.ny = ny;
     op.npairs = (int)pairs.size();
     op.pairs = s->pairs;
     op.partials = s->partials;
     op.counter = s->counter;
     op.out = out;
+    const int ncol = nx + ny;
+    op.tile = std::min(256, (int)(48 * 1024 / sizeof(double)) / ncol - 1);
+    const size_t smem = sizeof(double) * (size_t)ncol * (op.tile + 1);
     {
         const double n = (double)s->n, np_ = (double)pairs.size();
-        ProfScope ps(s, RGM_PROF_GRAM, 2.0 * n * np_, (double)sizeof(T) * n * (double)(nx + (X == Y ? 0 : nx)));
-        gram_kernel<T><<<s->nblocks, RGM_THREADS, 0, s->st>>>(op);
+        ProfScope ps(s, RGM_PROF_GRAM, 2.0 * n * np_, (double)sizeof(T) * n * ncol);
+        gram_kernel<T><<<s->nblocks, RGM_THREADS, smem, s->st>>>(op);
     }
     CK(cudaGetLastError());
     return RGM_OK;
@@ -324,7 +322,8 @@ static int coarse_setup(rgm_solver s)
 {
     const int k = s->k_cur;
     Arnoldi<double> a;
-    a.rowptr = s->rowptr; a.col = s->col; a.val = s->val; a.V = s->V; a.U = s->U; a.W = s->W;
+    a.slice_ptr = s->slice_ptr; a.scol = s->scol; a.sval = s->sval; a.perm = s->perm;
+    a.V = s->V; a.U = s->U; a.W = s->W;
     for (int i = 0; i < k; ++i) {
         VecOp<double> op = base_op(s, a);
         op.src = SRC_SPMV;
@@ -338,7 +337,7 @@ static int coarse_setup(rgm_solver s)
         for (int i = 0; i < k; ++i) pairs.push_back(make_int2(i, k + j));     // E_ij = u_i . w_j
     for (int i = 0; i < k; ++i) pairs.push_back(make_int2(i, i));
     for (int i = 0; i < k; ++i) pairs.push_back(make_int2(k + i, k + i));
-    int rc = launch_gram<double>(s, s->U, s->ld, k, s->W, s->ld, pairs, s->gram_out);
+    int rc = launch_gram<double>(s, s->U, s->ld, k, s->W, s->ld, k, pairs, s->gram_out);
     if (rc) return rc;
     { ProfScope ps_(s, RGM_PROF_SMALL); lu_kernel<<<1, 256, 0, s->st>>>(s->sm, k, s->gram_out, s->gram_out + k * k); }
     CK(cudaGetLastError());
@@ -414,17 +413,17 @@ static int gmres_cycles(rgm_solver s, const Arnoldi<T> &a, int mode, int k, int 
                 op.gate = GATE_APPEND;
                 op.src = SRC_COPY; op.win = a.W + (int64_t)i * s->ld; op.out = a.w;
                 op.dyn = DYN_NDV_NB; op.dnorm = 1; op.fin = FIN_AUG1;
-                if ((rc = launch(s, op))) return rc;
+                if ((rc = launch(s, op, RGM_PROF_OTHER, -1, m + 1 + i))) return rc;
                 op = base_op(s, a);
                 op.gate = GATE_APPEND;
                 op.src = SRC_AXPY; op.win = a.w; op.out = a.w; op.dyn = DYN_NV_NB | DYN_NDV_NB;
                 op.fin = FIN_ARN2;
-                if ((rc = launch(s, op))) return rc;
+                if ((rc = launch(s, op, RGM_PROF_OTHER, -1, m + 1 + i))) return rc;
                 op = base_op(s, a);
                 op.gate = GATE_APPEND;
                 op.src = SRC_AXPY; op.win = a.w; op.dyn = DYN_NV_NB | DYN_OUT_VNB; op.dnorm = 1;
                 op.fin = FIN_AUG3; op.arg = i;
-                if ((rc = launch(s, op))) return rc;
+                if ((rc = launch(s, op, RGM_PROF_OTHER, -1, m + 1 + i))) return rc;
                 { ProfScope ps_(s, RGM_PROF_SMALL); clear_skip_kernel<<<1, 32, 0, s->st>>>(s->sm); }
             }
         }
@@ -490,7 +489,7 @@ static int norm_of(rgm_solver s, const Arnoldi<T> &a, const T *v, int fin)
 static Arnoldi<double> arn64(rgm_solver s)
 {
     Arnoldi<double> a;
-    a.rowptr = s->rowptr; a.col = s->col; a.val = s->val;
+    a.slice_ptr = s->slice_ptr; a.scol = s->scol; a.sval = s->sval; a.perm = s->perm;
     a.V = s->V; a.U = s->U; a.W = s->W; a.w = s->w; a.r = s->r; a.b = s->b; a.x = s->x;
     return a;
 }
@@ -498,7 +497,7 @@ static Arnoldi<double> arn64(rgm_solver s)
 static Arnoldi<float> arn32(rgm_solver s)
 {
     Arnoldi<float> a;
-    a.rowptr = s->rowptr; a.col = s->col; a.val = s->val32;
+    a.slice_ptr = s->slice_ptr; a.scol = s->scol; a.sval = s->sval32; a.perm = s->perm;
     a.V = s->V32; a.U = s->U32; a.W = s->W32; a.w = s->w32; a.r = s->r32; a.b = s->b32; a.x = s->x32;
     return a;
 }
@@ -581,7 +580,7 @@ static int svd_update(rgm_solver s, int *k_used)
     std::vector<int2> pairs;
     for (int j = 0; j < cnt; ++j)
         for (int i = 0; i <= j; ++i) pairs.push_back(make_int2(i, j));
-    int rc = launch_gram<double>(s, s->X, s->ld, cnt, s->X, s->ld, pairs, s->gram_out);
+    int rc = launch_gram<double>(s, s->X, s->ld, cnt, s->X, s->ld, 0, pairs, s->gram_out);
     if (rc) return rc;
     { ProfScope ps_(s, RGM_PROF_SMALL); sym_eig_select_kernel<<<1, 512, EIG_SMEM_BYTES, s->st>>>(s->sm, s->gram_out, cnt, c.k,
                                                              c.select_smallest, c.rel_drop); }
@@ -597,8 +596,8 @@ static int svd_update(rgm_solver s, int *k_used)
             std::vector<int2> up;
             for (int j = 0; j < kn; ++j)
                 for (int i = 0; i <= j; ++i) up.push_back(make_int2(i, j));
-            if ((rc = launch_gram<double>(s, s->U, s->ld, kn, s->U, s->ld, up, s->gram_out))) return rc;
-            { ProfScope ps_(s, RGM_PROF_SMALL); chol_inv_kernel<<<1, 32, 0, s->st>>>(s->sm, s->gram_out, kn); }
+            if ((rc = launch_gram<double>(s, s->U, s->ld, kn, s->U, s->ld, 0, up, s->gram_out))) return rc;
+            { ProfScope ps_(s, RGM_PROF_SMALL); chol_inv_kernel<<<1, 64, 0, s->st>>>(s->sm, s->gram_out, kn); }
             { ProfScope ps_(s, RGM_PROF_OTHER); combine_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U, s->U, s->sm->evec, kn, kn, s->n,
                                                           s->ld, RGM_WMAX); }
             CK(cudaGetLastError());
@@ -649,7 +648,7 @@ const char *rgm_status_string(int code)
 
 static void free_all(rgm_solver s)
 {
-    void *dp[] = {s->rowptr, s->col, s->val, s->val32, s->V, s->U, s->W, s->w, s->r, s->b, s->x,
+    void *dp[] = {s->slice_ptr, s->scol, s->perm, s->csr2sell, s->sval, s->sval32, s->val_stage, s->V, s->U, s->W, s->w, s->r, s->b, s->x,
                   s->V32, s->U32, s->W32, s->w32, s->r32, s->b32, s->x32, s->X, s->Ytmp,
                   s->partials, s->counter, s->pairs, s->gram_out, s->sm};
     for (void *p : dp)
@@ -682,9 +681,12 @@ int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
     s->nsm = nsm;
     s->n = c.n;
     s->ld = (c.n + 31) / 32 * 32;
-    const int64_t want = (s->n + 255) / 256;
-    s->nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, 2 * (int64_t)nsm));
-    s->rpb = (int)((s->n + s->nblocks - 1) / s->nblocks);
+    // blocks own whole RGM_TILE-row tiles (the sliced-ELL sorting windows)
+    const int64_t ntile = (s->n + RGM_TILE - 1) / RGM_TILE;
+    const int64_t nb_want = std::max<int64_t>(1, std::min<int64_t>(ntile, 2 * (int64_t)nsm));
+    const int64_t tiles_per_block = (ntile + nb_want - 1) / nb_want;
+    s->rpb = (int)(tiles_per_block * RGM_TILE);
+    s->nblocks = (int)((s->n + s->rpb - 1) / s->rpb);
     const int kmax = std::max(c.k, 1);
     const int64_t ncolV = c.m + c.k + 1;
     s->npairs_max = RGM_WMAX * (RGM_WMAX + 1) / 2 + RGM_KMAX * RGM_KMAX + 2 * RGM_KMAX;
@@ -751,35 +753,81 @@ int rgm_set_operator_csr(rgm_solver s, int64_t n, int64_t nnz, const int64_t *ro
                          const int32_t *col, const double *val, int flags)
 {
     if (!s || n != s->n || nnz < 0 || !rowptr || (nnz > 0 && (!col || !val))) return RGM_E_ARG;
-    // validate the pattern on the host copy
+    // validate the pattern on a host copy
+    const cudaMemcpyKind hk = (flags & RGM_DEVICE_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
     std::vector<int64_t> rp(n + 1);
-    if (cudaMemcpy(rp.data(), rowptr, sizeof(int64_t) * (n + 1), (flags & RGM_DEVICE_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost) != cudaSuccess)
-        return RGM_E_CUDA;
+    if (cudaMemcpy(rp.data(), rowptr, sizeof(int64_t) * (n + 1), hk) != cudaSuccess) return RGM_E_CUDA;
     if (rp[0] != 0 || rp[n] != nnz) return RGM_E_ARG;
     for (int64_t i = 0; i < n; ++i)
         if (rp[i + 1] < rp[i]) return RGM_E_ARG;
     std::vector<int32_t> cl(nnz);
-    if (nnz && cudaMemcpy(cl.data(), col, sizeof(int32_t) * nnz, (flags & RGM_DEVICE_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost) != cudaSuccess)
-        return RGM_E_CUDA;
+    if (nnz && cudaMemcpy(cl.data(), col, sizeof(int32_t) * nnz, hk) != cudaSuccess) return RGM_E_CUDA;
     for (int64_t e = 0; e < nnz; ++e)
         if (cl[e] < 0 || cl[e] >= n) return RGM_E_ARG;
-    if (nnz != s->nnz || !s->rowptr) {
-        if (s->col) cudaFree(s->col);
-        if (s->val) cudaFree(s->val);
-        if (s->val32) cudaFree(s->val32);
-        if (s->rowptr) cudaFree(s->rowptr);
-        s->col = nullptr; s->val = nullptr; s->val32 = nullptr; s->rowptr = nullptr;
-        CK(cudaMalloc((void **)&s->rowptr, sizeof(int64_t) * (n + 1)));
-        CK(cudaMalloc((void **)&s->col, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
-        CK(cudaMalloc((void **)&s->val, sizeof(double) * std::max<int64_t>(nnz, 1)));
-        if (s->cfg.precision == RGM_FP32_IR)
-            CK(cudaMalloc((void **)&s->val32, sizeof(float) * std::max<int64_t>(nnz, 1)));
+    // sliced ELL: inside each tile, rows sorted by length (descending, stable)
+    const int64_t ntile = (n + RGM_TILE - 1) / RGM_TILE, nslices = ntile * (RGM_TILE / 32);
+    std::vector<int32_t> perm(nslices * 32, -1);
+    std::vector<int64_t> sp(nslices + 1, 0);
+    std::vector<int> idx(RGM_TILE);
+    for (int64_t t = 0; t < ntile; ++t) {
+        const int64_t r0 = t * RGM_TILE, cnt = std::min<int64_t>(RGM_TILE, n - r0);
+        for (int i = 0; i < cnt; ++i) idx[i] = i;
+        std::stable_sort(idx.begin(), idx.begin() + cnt, [&](int a, int b) {
+            return rp[r0 + a + 1] - rp[r0 + a] > rp[r0 + b + 1] - rp[r0 + b];
+        });
+        for (int i = 0; i < cnt; ++i) perm[r0 + i] = (int32_t)(r0 + idx[i]);
     }
-    s->nnz = nnz;
-    CK(cudaMemcpyAsync(s->rowptr, rp.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s->st));
-    if (nnz) CK(cudaMemcpyAsync(s->col, cl.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, s->st));
+    for (int64_t sl = 0; sl < nslices; ++sl) {
+        int64_t width = 0;
+        for (int l = 0; l < 32; ++l) {
+            const int32_t r = perm[sl * 32 + l];
+            if (r >= 0) width = std::max<int64_t>(width, rp[r + 1] - rp[r]);
+        }
+        sp[sl + 1] = sp[sl] + 32 * width;
+    }
+    const int64_t nsell = sp[nslices];
+    if (nsell >= ((int64_t)1 << 31)) return RGM_E_ARG;
+    std::vector<int32_t> scol(std::max<int64_t>(nsell, 1));
+    std::vector<int32_t> map(std::max<int64_t>(nnz, 1));
+    for (int64_t sl = 0; sl < nslices; ++sl) {
+        const int64_t width = (sp[sl + 1] - sp[sl]) / 32;
+        for (int l = 0; l < 32; ++l) {
+            const int32_t r = perm[sl * 32 + l];
+            const int64_t len = r >= 0 ? rp[r + 1] - rp[r] : 0;
+            for (int64_t k = 0; k < width; ++k) {
+                const int64_t e = sp[sl] + 32 * k + l;
+                if (k < len) {
+                    scol[e] = cl[rp[r] + k];
+                    map[rp[r] + k] = (int32_t)e;
+                } else {
+                    scol[e] = r >= 0 ? r : 0;       // padding: value 0 on a valid column
+                }
+            }
+        }
+    }
+    void *old[] = {s->slice_ptr, s->scol, s->perm, s->csr2sell, s->sval, s->sval32, s->val_stage};
+    for (void *p : old)
+        if (p) cudaFree(p);
+    s->slice_ptr = nullptr; s->scol = nullptr; s->perm = nullptr; s->csr2sell = nullptr;
+    s->sval = nullptr; s->sval32 = nullptr; s->val_stage = nullptr;
+    CK(cudaMalloc((void **)&s->slice_ptr, sizeof(int64_t) * (nslices + 1)));
+    CK(cudaMalloc((void **)&s->scol, sizeof(int32_t) * std::max<int64_t>(nsell, 1)));
+    CK(cudaMalloc((void **)&s->perm, sizeof(int32_t) * nslices * 32));
+    CK(cudaMalloc((void **)&s->csr2sell, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+    CK(cudaMalloc((void **)&s->sval, sizeof(double) * std::max<int64_t>(nsell, 1)));
+    CK(cudaMalloc((void **)&s->val_stage, sizeof(double) * std::max<int64_t>(nnz, 1)));
+    if (s->cfg.precision == RGM_FP32_IR)
+        CK(cudaMalloc((void **)&s->sval32, sizeof(float) * std::max<int64_t>(nsell, 1)));
+    CK(cudaMemcpyAsync(s->slice_ptr, sp.data(), sizeof(int64_t) * (nslices + 1), cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(s->scol, scol.data(), sizeof(int32_t) * std::max<int64_t>(nsell, 1), cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(s->perm, perm.data(), sizeof(int32_t) * nslices * 32, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(s->csr2sell, map.data(), sizeof(int32_t) * std::max<int64_t>(nnz, 1), cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemsetAsync(s->sval, 0, sizeof(double) * std::max<int64_t>(nsell, 1), s->st));
+    if (s->sval32) CK(cudaMemsetAsync(s->sval32, 0, sizeof(float) * std::max<int64_t>(nsell, 1), s->st));
     CK(cudaStreamSynchronize(s->st));
-    s->sw = choose_sw(n, nnz);
+    s->nnz = nnz;
+    s->nslices = nslices;
+    s->nsell = nsell;
     s->have_op = true;
     return rgm_set_operator_values(s, val, flags);
 }
@@ -789,11 +837,17 @@ int rgm_set_operator_values(rgm_solver s, const double *val, int flags)
     if (!s || (s->nnz > 0 && !val)) return RGM_E_ARG;
     if (!s->have_op) return RGM_E_STATE;
     if (s->nnz) {
-        CK(cudaMemcpyAsync(s->val, val, sizeof(double) * s->nnz, kind_in(flags), s->st));
-        if (s->cfg.precision == RGM_FP32_IR) {
-            { ProfScope ps_(s, RGM_PROF_OTHER); convert_kernel<<<s->nblocks, 256, 0, s->st>>>(s->val32, s->val, s->nnz, s->nnz, 1); }
-            CK(cudaGetLastError());
+        const double *src = val;
+        if (!(flags & RGM_DEVICE_PTRS)) {
+            CK(cudaMemcpyAsync(s->val_stage, val, sizeof(double) * s->nnz, cudaMemcpyHostToDevice, s->st));
+            src = s->val_stage;
         }
+        const int g = (int)std::min<int64_t>((s->nnz + 255) / 256, 8 * (int64_t)s->nsm);
+        {
+            ProfScope ps_(s, RGM_PROF_OTHER);
+            sell_scatter_kernel<double><<<g, 256, 0, s->st>>>(s->sval, s->sval32, src, s->csr2sell, s->nnz);
+        }
+        CK(cudaGetLastError());
     }
     s->coarse_stale = true;
     if (!(flags & RGM_DEVICE_PTRS)) CK(cudaStreamSynchronize(s->st));
@@ -882,11 +936,10 @@ int rgm_reset_recycling(rgm_solver s)
 
 // Library-internal: the solver's device value buffer (for in-library producers
 // such as the FE workload) and a copy of its configuration.
-int rgm_internal_values_ptr(rgm_solver s, double **val, int64_t *nnz)
+int rgm_internal_nnz(rgm_solver s, int64_t *nnz)
 {
-    if (!s || !val || !nnz) return RGM_E_ARG;
+    if (!s || !nnz) return RGM_E_ARG;
     if (!s->have_op) return RGM_E_STATE;
-    *val = s->val;
     *nnz = s->nnz;
     return RGM_OK;
 }

@@ -55,7 +55,19 @@ __global__ void sym_eig_select_kernel(Small *s, const double *gram, int c, int k
         P[i + j * RGM_WMAX] = (i == j) ? 1.0 : 0.0;
     }
     for (int t = threadIdx.x; t < ce; t += blockDim.x) perm[t] = t;
+    __shared__ double gmax;
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int i = 0; i < c; ++i) m = fmax(m, G[i + i * RGM_WMAX]);
+        gmax = m;
+    }
     __syncthreads();
+    // Stop rotating a pair when its coupling is below 1e-15 of its own
+    // diagonal scale (high relative accuracy) or below 1e-20 of the largest
+    // eigenvalue: modes under rel_drop^2 * lambda_1 (1e-14 lambda_1 by default)
+    // are never kept, so the floor costs the kept modes no accuracy and stops
+    // graded windows from sweeping on rounding noise.
+    const double floor_abs = 1e-20 * gmax;
     const int npair = ce / 2;
     for (int sweep = 0; sweep < 40; ++sweep) {
         if (threadIdx.x == 0) any_rot = 0;
@@ -68,7 +80,7 @@ __global__ void sym_eig_select_kernel(Small *s, const double *gram, int c, int k
                 rp[t] = p; rq[t] = q;
                 double app = G[p + p * RGM_WMAX], aqq = G[q + q * RGM_WMAX], apq = G[p + q * RGM_WMAX];
                 double cth = 1.0, sth = 0.0;
-                if (apq != 0.0 && fabs(apq) > 1e-15 * sqrt(fabs(app * aqq))) {
+                if (fabs(apq) > floor_abs && fabs(apq) > 1e-15 * sqrt(fabs(app * aqq))) {
                     double tau = (aqq - app) / (2.0 * apq);
                     double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
                     cth = 1.0 / sqrt(1.0 + tt * tt);
@@ -166,33 +178,44 @@ __global__ void combine_kernel(double *out, const double *in, const double *C, i
 }
 
 // Cholesky factor R of the packed Gram matrix of U (k x k), and its inverse
-// into Small::evec so that U R^{-1} has orthonormal columns.
+// into Small::evec so that U R^{-1} has orthonormal columns.  One block:
+// the factorisation row by row with the trailing updates in parallel, then one
+// thread per column of R^{-1} (back substitution from shared memory).
 __global__ void chol_inv_kernel(Small *s, const double *gram, int k)
 {
-    if (threadIdx.x != 0) return;
-    double R[RGM_KMAX * RGM_KMAX];
-    for (int j = 0; j < k; ++j)
-        for (int i = 0; i < k; ++i) R[i + j * RGM_KMAX] = (i <= j) ? gram[packed_index(i, j)] : 0.0;
-    // upper Cholesky: G = R^T R
-    for (int j = 0; j < k; ++j) {
-        double d = R[j + j * RGM_KMAX];
-        for (int l = 0; l < j; ++l) d -= R[l + j * RGM_KMAX] * R[l + j * RGM_KMAX];
-        d = d > 0.0 ? sqrt(d) : 1.0;
-        R[j + j * RGM_KMAX] = d;
-        for (int i = j + 1; i < k; ++i) {
-            double v = R[j + i * RGM_KMAX];
-            for (int l = 0; l < j; ++l) v -= R[l + j * RGM_KMAX] * R[l + i * RGM_KMAX];
-            R[j + i * RGM_KMAX] = v / d;
-        }
+    __shared__ double R[RGM_KMAX * RGM_KMAX];
+    for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+        const int i = t % k, j = t / k;
+        R[i + j * RGM_KMAX] = (i <= j) ? gram[packed_index(i, j)] : 0.0;
     }
-    // inverse of the upper-triangular R, column by column
+    __syncthreads();
+    // upper Cholesky G = R^T R, right-looking
     for (int j = 0; j < k; ++j) {
-        for (int i = 0; i < k; ++i) s->evec[i + j * RGM_WMAX] = 0.0;
-        s->evec[j + j * RGM_WMAX] = 1.0 / R[j + j * RGM_KMAX];
+        __shared__ double d;
+        if (threadIdx.x == 0) {
+            double v = R[j + j * RGM_KMAX];
+            d = v > 0.0 ? sqrt(v) : 1.0;
+            R[j + j * RGM_KMAX] = d;
+        }
+        __syncthreads();
+        for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) R[j + i * RGM_KMAX] /= d;
+        __syncthreads();
+        for (int t = threadIdx.x; t < (k - j - 1) * (k - j - 1); t += blockDim.x) {
+            const int a = j + 1 + t % (k - j - 1), b = j + 1 + t / (k - j - 1);
+            if (a <= b) R[a + b * RGM_KMAX] -= R[j + a * RGM_KMAX] * R[j + b * RGM_KMAX];
+        }
+        __syncthreads();
+    }
+    // column j of R^{-1}
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        double col[RGM_KMAX];
+        for (int i = 0; i < k; ++i) col[i] = 0.0;
+        col[j] = 1.0 / R[j + j * RGM_KMAX];
         for (int i = j - 1; i >= 0; --i) {
             double v = 0.0;
-            for (int l = i + 1; l <= j; ++l) v += R[i + l * RGM_KMAX] * s->evec[l + j * RGM_WMAX];
-            s->evec[i + j * RGM_WMAX] = -v / R[i + i * RGM_KMAX];
+            for (int l = i + 1; l <= j; ++l) v += R[i + l * RGM_KMAX] * col[l];
+            col[i] = -v / R[i + i * RGM_KMAX];
         }
+        for (int i = 0; i < k; ++i) s->evec[i + j * RGM_WMAX] = col[i];
     }
 }

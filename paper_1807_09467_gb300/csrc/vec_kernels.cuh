@@ -1,5 +1,5 @@
-// vec_kernels.cuh -- the fused vector kernel of the Arnoldi cycle and its
-// finalisation phases (included by solver.cu).
+// vec_kernels.cuh -- the fused vector kernel of the Arnoldi cycle, its
+// finalisation phases and the Gram kernel (included by solver.cu).
 //
 // One launch = one pass over the rows: produce a vector w (SpMV, residual
 // b - A x, copy, or AXPY against [W | Vraw | U]), store it, take its dot
@@ -8,14 +8,22 @@
 // run the scalar step that follows (Gram-Schmidt coefficients, Hessenberg
 // column, Givens rotation, convergence test, ...).  Every scalar decision
 // stays on the device; the host only reads back once per GMRES cycle.
+//
+// Rows are processed in tiles of RGM_TILE: the tile of w is kept in shared
+// memory, and the dot products run one warp per column over the tile, so each
+// warp accumulates its columns across tiles and reduces once at the end.  The
+// last block stages the small state it needs (LU factors, rotations, the new
+// Hessenberg column) in shared memory before the sequential parts.
 #pragma once
 #include "common.cuh"
+
+#define RGM_TILE RGM_THREADS
 
 enum Src { SRC_SPMV = 0, SRC_RES = 1, SRC_COPY = 2, SRC_AXPY = 3, SRC_NONE = 4 };
 enum Gate { GATE_NONE = 0, GATE_KRYLOV = 1, GATE_APPEND = 2 };
 enum Fin {
     FIN_NONE = 0,
-    FIN_BNORM,       // ||b||, tol
+    FIN_BNORM,       // ||b||
     FIN_RESNORM,     // beta = ||r||, converged flag
     FIN_COARSE,      // coefU = E^{-1} (U^T r)
     FIN_START_PLAIN, // v_0 = r / ||r||
@@ -35,9 +43,12 @@ struct VecOp {
     int rpb;                 // rows per block
     int nblocks;
     int src;
-    const int64_t *rowptr;
-    const int32_t *col;
-    const T *val;
+    // operator in sliced ELL: 32-row slices, rows sorted by length inside each
+    // RGM_TILE-row tile; entry k of the slice's lane l at slice_ptr + 32 k + l
+    const int64_t *slice_ptr;
+    const int32_t *scol;
+    const T *sval;
+    const int32_t *perm;     // slice row -> matrix row (-1: padding)
     const T *x;              // SpMV / residual input
     int xscale;              // index into colscale, -1 for none
     const T *b;              // residual right-hand side
@@ -53,7 +64,7 @@ struct VecOp {
     Small *sm;
     int fin;
     int gate;
-    int arg;                 // phase argument (Krylov index j / appended column i)
+    int arg;                 // phase argument (appended column index)
     int dyn;                 // DYN_* bits: counts and output column read from Small
 };
 
@@ -64,187 +75,209 @@ enum Dyn {
     DYN_OUT_VNB = 8   // out = Vraw[:, s->nb]
 };
 
+// Shared scratch of the finalising block.
+struct FinScratch {
+    double LU[RGM_KMAX * RGM_KMAX];
+    int piv[RGM_KMAX];
+    double dd[RGM_KMAX];
+    double col[RGM_HLD + 1];
+    double cs[RGM_HLD], sn[RGM_HLD];
+    double sc[RGM_HLD];
+    int flag;
+};
+
 // ---------------------------------------------------------------- scalar helpers
-__device__ inline void lu_solve_small(int k, const double *LU, const int *piv, double *x)
+__device__ inline void lu_solve_small(int k, const double *LU, int ld, const int *piv, double *x)
 {
     for (int j = 0; j < k; ++j)
         if (piv[j] != j) { double t = x[j]; x[j] = x[piv[j]]; x[piv[j]] = t; }
     for (int i = 0; i < k; ++i)
-        for (int j = 0; j < i; ++j) x[i] -= LU[i + j * RGM_KMAX] * x[j];
+        for (int j = 0; j < i; ++j) x[i] -= LU[i + j * ld] * x[j];
     for (int i = k - 1; i >= 0; --i) {
-        for (int j = i + 1; j < k; ++j) x[i] -= LU[i + j * RGM_KMAX] * x[j];
-        x[i] /= LU[i + i * RGM_KMAX];
+        for (int j = i + 1; j < k; ++j) x[i] -= LU[i + j * ld] * x[j];
+        x[i] /= LU[i + i * ld];
     }
 }
 
-// Apply rotations 0..col-1 to column col of H, then make rotation col.
-__device__ inline void givens_column(Small *s, int col)
+// Stage the k x k LU factors and pivots of E in shared memory (whole block).
+__device__ inline void stage_lu(const Small *s, int k, FinScratch &f)
 {
-    double *hc = s->H + (int64_t)col * RGM_HLD;
-    for (int i = 0; i < col; ++i) {
-        double a = hc[i], b = hc[i + 1];
-        hc[i] = s->cs[i] * a + s->sn[i] * b;
-        hc[i + 1] = -s->sn[i] * a + s->cs[i] * b;
+    for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+        int i = t % k, j = t / k;
+        f.LU[i + j * RGM_KMAX] = s->LU[i + j * RGM_KMAX];
     }
-    double a = hc[col], b = hc[col + 1];
-    double r = hypot(a, b);
-    double c = 1.0, sn = 0.0;
-    if (r != 0.0) { c = a / r; sn = b / r; }
-    s->cs[col] = c;
-    s->sn[col] = sn;
-    hc[col] = r;
-    hc[col + 1] = 0.0;
-    s->g[col + 1] = -sn * s->g[col];
-    s->g[col] = c * s->g[col];
+    for (int t = threadIdx.x; t < k; t += blockDim.x) f.piv[t] = s->piv[t];
 }
 
-// The scalar step after a reduction.  d[] holds the reduced dots in the
-// column order [U | Vraw | W | norm].  Runs on one thread.
+// Rotate column c (in shared memory, rows 0..col+1) by rotations 0..col-1.
+__device__ inline void apply_rotations(double *c, const double *cs, const double *sn, int col)
+{
+    for (int i = 0; i < col; ++i) {
+        double a = c[i], b = c[i + 1];
+        c[i] = cs[i] * a + sn[i] * b;
+        c[i + 1] = -sn[i] * a + cs[i] * b;
+    }
+}
+
+// Finalise one Hessenberg column held in f.col (rows 0..nb, already rotated):
+// make rotation col, update g, write the column and the rotation back.
+__device__ inline void close_column(Small *s, FinScratch &f, int col)
+{
+    if (threadIdx.x == 0) {
+        double a = f.col[col], b = f.col[col + 1];
+        double r = hypot(a, b);
+        double c = 1.0, sn = 0.0;
+        if (r != 0.0) { c = a / r; sn = b / r; }
+        s->cs[col] = c;
+        s->sn[col] = sn;
+        f.col[col] = r;
+        f.col[col + 1] = 0.0;
+        double g0 = s->g[col];
+        s->g[col + 1] = -sn * g0;
+        s->g[col] = c * g0;
+    }
+    __syncthreads();
+    double *hc = s->H + (int64_t)col * RGM_HLD;
+    for (int i = threadIdx.x; i <= col + 1; i += blockDim.x) hc[i] = f.col[i];
+}
+
+// The scalar step after a reduction, run by the whole finalising block.
+// d[] holds the reduced dots in the column order [U | Vraw | W | norm].
 template <typename T>
-__device__ void finalize_scalar(const VecOp<T> &op, const double *d)
+__device__ void finalize_block(const VecOp<T> &op, const double *d, FinScratch &f)
 {
     Small *s = op.sm;
     const double *dU = d, *dV = d + op.ndU, *dW = d + op.ndU + op.ndV;
     const double nrm2 = op.dnorm ? d[op.ndU + op.ndV + op.ndW] : 0.0;
-    const int k = s->k;
+    const int tid = threadIdx.x;
     switch (op.fin) {
     case FIN_BNORM:
-        s->bnorm = sqrt(nrm2);
+        if (tid == 0) s->bnorm = sqrt(nrm2);
         break;
     case FIN_RESNORM:
-        s->beta = sqrt(nrm2);
-        s->converged = (s->beta <= s->tol_abs) ? 1 : 0;
+        if (tid == 0) {
+            s->beta = sqrt(nrm2);
+            s->converged = (s->beta <= s->tol_abs) ? 1 : 0;
+        }
         break;
-    case FIN_COARSE: {
-        double c[RGM_KMAX];
-        for (int i = 0; i < k; ++i) c[i] = dU[i];
-        lu_solve_small(k, s->LU, s->piv, c);
-        for (int i = 0; i < k; ++i) s->coefU[i] = c[i];
-        break;
-    }
-    case FIN_START_PLAIN: {
-        double bs = sqrt(nrm2);
-        s->bs = bs;
-        s->J = 0;
-        s->nb = 1;
-        s->naug = 0;
-        s->g[0] = bs;
-        s->colscale[0] = bs > 0.0 ? 1.0 / bs : 0.0;
-        s->done = (bs > 0.0) ? 0 : 1;
-        s->breakdown = 0;
-        break;
-    }
+    case FIN_COARSE:
     case FIN_START_DEF1: {
-        double c[RGM_KMAX];
-        for (int i = 0; i < k; ++i) c[i] = dU[i];
-        lu_solve_small(k, s->LU, s->piv, c);
-        for (int i = 0; i < k; ++i) s->coefW[i] = -c[i];
+        const int k = op.ndU;
+        stage_lu(s, k, f);
+        __syncthreads();
+        if (tid == 0) {
+            for (int i = 0; i < k; ++i) f.dd[i] = dU[i];
+            lu_solve_small(k, f.LU, RGM_KMAX, f.piv, f.dd);
+        }
+        __syncthreads();
+        for (int i = tid; i < k; i += blockDim.x) {
+            if (op.fin == FIN_COARSE) s->coefU[i] = f.dd[i];
+            else s->coefW[i] = -f.dd[i];
+        }
         break;
     }
+    case FIN_START_PLAIN:
     case FIN_START_DEF2: {
-        double bs = sqrt(nrm2);
-        s->bs = bs;
-        s->J = 0;
-        s->nb = 1;
-        s->naug = 0;
-        s->g[0] = bs;
-        double sc = bs > 0.0 ? 1.0 / bs : 0.0;
-        s->colscale[0] = sc;
-        for (int l = 0; l < op.ndW; ++l) s->VtW[0 + l * RGM_HLD] = dW[l] * sc;
-        s->done = (bs > 0.0) ? 0 : 1;
-        s->breakdown = 0;
+        const double bs = sqrt(nrm2), sc = bs > 0.0 ? 1.0 / bs : 0.0;
+        if (tid == 0) {
+            s->bs = bs;
+            s->J = 0;
+            s->nb = 1;
+            s->naug = 0;
+            s->g[0] = bs;
+            s->colscale[0] = sc;
+            s->done = (bs > 0.0) ? 0 : 1;
+            s->breakdown = 0;
+        }
+        for (int l = tid; l < op.ndW; l += blockDim.x) s->VtW[0 + l * RGM_HLD] = dW[l] * sc;
         break;
     }
-    case FIN_ARN1: {
-        // w = A v_j (unprojected).  Deflated: P w = w - W d, d = E^{-1} U^T w,
-        // and V^T P w = V^T w - (V^T W) d.
-        const int nb = s->nb;
-        s->wn0 = sqrt(nrm2);
-        double dd[RGM_KMAX];
-        int kk = op.ndU;
-        for (int i = 0; i < kk; ++i) dd[i] = dU[i];
-        if (kk) lu_solve_small(kk, s->LU, s->piv, dd);
-        for (int i = 0; i < kk; ++i) s->coefW[i] = -dd[i];
-        for (int i = 0; i < nb; ++i) {
-            double h = dV[i] * s->colscale[i];
-            for (int l = 0; l < kk; ++l) h -= s->VtW[i + l * RGM_HLD] * dd[l];
+    case FIN_ARN1:
+    case FIN_AUG1: {
+        // w = A v_j (or A u_i).  Deflated: P w = w - W d, d = E^{-1} U^T w, and
+        // V^T P w = V^T w - (V^T W) d.
+        const int nb = s->nb, k = op.ndU;
+        if (k) stage_lu(s, k, f);
+        for (int i = tid; i < nb; i += blockDim.x) f.sc[i] = s->colscale[i];
+        __syncthreads();
+        if (tid == 0) {
+            s->wn0 = sqrt(nrm2);
+            if (op.fin == FIN_AUG1) s->skip = (nrm2 == 0.0) ? 1 : 0;
+            for (int i = 0; i < k; ++i) f.dd[i] = dU[i];
+            if (k) lu_solve_small(k, f.LU, RGM_KMAX, f.piv, f.dd);
+        }
+        __syncthreads();
+        for (int i = tid; i < k; i += blockDim.x) s->coefW[i] = -f.dd[i];
+        for (int i = tid; i < nb; i += blockDim.x) {
+            double h = dV[i] * f.sc[i];
+            for (int l = 0; l < k; ++l) h -= s->VtW[i + l * RGM_HLD] * f.dd[l];
             s->hsum[i] = h;
-            s->coefV[i] = -h * s->colscale[i];
+            s->coefV[i] = -h * f.sc[i];
         }
         break;
     }
     case FIN_ARN2: {
         const int nb = s->nb;
-        for (int i = 0; i < nb; ++i) {
-            double h = dV[i] * s->colscale[i];
+        for (int i = tid; i < nb; i += blockDim.x) {
+            const double sc = s->colscale[i];
+            const double h = dV[i] * sc;
             s->hsum[i] += h;
-            s->coefV[i] = -h * s->colscale[i];
+            s->coefV[i] = -h * sc;
         }
         break;
     }
     case FIN_ARN3: {
         const int j = s->J, nb = s->nb;
         const double hn = sqrt(nrm2);
-        double *hc = s->H + (int64_t)j * RGM_HLD;
-        for (int i = 0; i < nb; ++i) hc[i] = s->hsum[i];
-        hc[nb] = hn;
-        givens_column(s, j);
-        s->J = j + 1;
-        s->iters += 1;
-        if (hn <= 1e-14 * s->wn0) {                 // happy breakdown: v_{j+1} := 0
-            s->colscale[nb] = 0.0;
-            for (int l = 0; l < op.ndW; ++l) s->VtW[nb + l * RGM_HLD] = 0.0;
-            s->breakdown = 1;
-            s->done = 1;
-        } else {
-            const double sc = 1.0 / hn;
-            s->colscale[nb] = sc;
-            for (int l = 0; l < op.ndW; ++l) s->VtW[nb + l * RGM_HLD] = dW[l] * sc;
-        }
-        s->nb = nb + 1;
-        if (fabs(s->g[j + 1]) <= s->tol_abs) s->done = 1;
-        if (s->iters >= s->maxit || s->J >= s->m) s->done = 1;
-        break;
-    }
-    case FIN_AUG1: {
-        const int nb = s->nb;
-        s->wn0 = sqrt(nrm2);
-        s->skip = (s->wn0 == 0.0) ? 1 : 0;
-        for (int i = 0; i < nb; ++i) {
-            double h = dV[i] * s->colscale[i];
-            s->hsum[i] = h;
-            s->coefV[i] = -h * s->colscale[i];
+        for (int i = tid; i < nb; i += blockDim.x) f.col[i] = s->hsum[i];
+        for (int i = tid; i < j; i += blockDim.x) { f.cs[i] = s->cs[i]; f.sn[i] = s->sn[i]; }
+        if (tid == 0) f.col[nb] = hn;
+        __syncthreads();
+        if (tid == 0) apply_rotations(f.col, f.cs, f.sn, j);
+        __syncthreads();
+        close_column(s, f, j);
+        const bool brk = hn <= 1e-14 * s->wn0;
+        const double sc = brk ? 0.0 : 1.0 / hn;
+        for (int l = tid; l < op.ndW; l += blockDim.x) s->VtW[nb + l * RGM_HLD] = dW[l] * sc;
+        if (tid == 0) {
+            s->J = j + 1;
+            s->iters += 1;
+            s->colscale[nb] = sc;          // happy breakdown: v_{j+1} := 0
+            if (brk) { s->breakdown = 1; s->done = 1; }
+            s->nb = nb + 1;
+            if (fabs(s->g[j + 1]) <= s->tol_abs) s->done = 1;
+            if (s->iters >= s->maxit || s->J >= s->m) s->done = 1;
         }
         break;
     }
     case FIN_AUG3: {
         const int nb = s->nb, col = s->J + s->naug;
         const double hn = sqrt(nrm2);
-        // the candidate column after the stored rotations
-        double c[RGM_HLD + 1];
-        for (int i = 0; i < nb; ++i) c[i] = s->hsum[i];
-        c[nb] = hn;
-        for (int i = nb + 1; i <= col + 1 && i <= RGM_HLD; ++i) c[i] = 0.0;
-        for (int i = 0; i < col; ++i) {
-            double a = c[i], b = c[i + 1];
-            c[i] = s->cs[i] * a + s->sn[i] * b;
-            c[i + 1] = -s->sn[i] * a + s->cs[i] * b;
+        for (int i = tid; i <= col + 1 && i <= RGM_HLD; i += blockDim.x) f.col[i] = 0.0;
+        __syncthreads();
+        for (int i = tid; i < nb; i += blockDim.x) f.col[i] = s->hsum[i];
+        for (int i = tid; i < col; i += blockDim.x) { f.cs[i] = s->cs[i]; f.sn[i] = s->sn[i]; }
+        if (tid == 0) f.col[nb] = hn;
+        __syncthreads();
+        if (tid == 0) {
+            apply_rotations(f.col, f.cs, f.sn, col);
+            // dependent on the columns already in the relation: drop u_i
+            f.flag = (hypot(f.col[col], f.col[col + 1]) <= 1e-14 * s->wn0) ? 0 : 1;
         }
-        if (hypot(c[col], c[col + 1]) <= 1e-14 * s->wn0) break;    // dependent: drop
-        double *hc = s->H + (int64_t)col * RGM_HLD;
-        for (int i = 0; i < RGM_HLD; ++i) hc[i] = 0.0;
-        for (int i = 0; i < nb; ++i) hc[i] = s->hsum[i];
-        hc[nb] = hn;
-        givens_column(s, col);
-        s->colscale[nb] = (hn <= 1e-14 * s->wn0) ? 0.0 : 1.0 / hn;
-        s->aug_idx[s->naug] = op.arg;
-        s->naug += 1;
-        s->nb = nb + 1;
+        __syncthreads();
+        if (!f.flag) break;
+        close_column(s, f, col);
+        if (tid == 0) {
+            s->colscale[nb] = (hn <= 1e-14 * s->wn0) ? 0.0 : 1.0 / hn;
+            s->aug_idx[s->naug] = op.arg;
+            s->naug += 1;
+            s->nb = nb + 1;
+        }
         break;
     }
     case FIN_DOTS: {
         const int nd = op.ndU + op.ndV + op.ndW + op.dnorm;
-        for (int i = 0; i < nd; ++i) s->dots[i] = d[i];
+        for (int i = tid; i < nd; i += blockDim.x) s->dots[i] = d[i];
         break;
     }
     default:
@@ -264,9 +297,10 @@ __device__ __forceinline__ const T *dot_col(const VecOp<T> &op, int c)
     return op.out;
 }
 
-template <typename T, int SW>
+template <typename T, int QMAX>
 __global__ void __launch_bounds__(RGM_THREADS) vec_kernel(VecOp<T> op)
 {
+    constexpr int NW = RGM_THREADS / 32;      // QMAX * NW >= number of dot columns
     Small *s = op.sm;
     if (op.gate == GATE_KRYLOV && s->done) return;
     if (op.gate == GATE_APPEND && (s->skip || s->J == 0)) return;
@@ -277,8 +311,8 @@ __global__ void __launch_bounds__(RGM_THREADS) vec_kernel(VecOp<T> op)
         if (op.dyn & DYN_OUT_VNB) op.out = const_cast<T *>(op.V) + (int64_t)s->nb * op.ldv;
     }
 
-    __shared__ double red[(RGM_THREADS / 32) * RGM_CHUNK];
     __shared__ T cW[RGM_KMAX], cU[RGM_KMAX], cV[RGM_HLD];
+    __shared__ T ws[RGM_TILE];
     __shared__ double xs;
     if (threadIdx.x == 0) xs = (op.xscale >= 0) ? s->colscale[op.xscale] : 1.0;
     if (op.src == SRC_AXPY) {
@@ -288,72 +322,86 @@ __global__ void __launch_bounds__(RGM_THREADS) vec_kernel(VecOp<T> op)
     }
     __syncthreads();
 
+    const int nd = op.ndU + op.ndV + op.ndW + op.dnorm;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t r0 = (int64_t)blockIdx.x * op.rpb;
     const int64_t r1 = min(op.n, r0 + op.rpb);
-
-    // ---- phase 1: produce and store w on this block's rows
-    if (op.src == SRC_SPMV || op.src == SRC_RES) {
-        // SW lanes per row; the loop bound is uniform across the warp so every
-        // lane reaches the shuffles.
-        const int lane = threadIdx.x % SW;
-        const int grp = threadIdx.x / SW, ngrp = blockDim.x / SW;
-        const T sc = (T)xs;
-        for (int64_t base = r0; base < r1; base += ngrp) {
-            const int64_t r = base + grp;
-            T acc = 0;
-            if (r < r1) {
-                const int64_t e0 = op.rowptr[r], e1 = op.rowptr[r + 1];
-                for (int64_t e = e0 + lane; e < e1; e += SW) acc += op.val[e] * op.x[op.col[e]];
-            }
+    double acc[QMAX];
 #pragma unroll
-            for (int o = SW / 2; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, SW);
-            if (r < r1 && lane == 0) op.out[r] = (op.src == SRC_SPMV) ? acc * sc : op.b[r] - acc;
-        }
-    } else if (op.src == SRC_COPY || op.src == SRC_AXPY) {
-        for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-            T acc = op.win[r];
-            if (op.src == SRC_AXPY) {
-                for (int c = 0; c < op.nW; ++c) acc += cW[c] * op.W[r + (int64_t)c * op.ldw];
-                for (int c = 0; c < op.nV; ++c) acc += cV[c] * op.V[r + (int64_t)c * op.ldv];
-                for (int c = 0; c < op.nU; ++c) acc += cU[c] * op.U[r + (int64_t)c * op.ldu];
+    for (int q = 0; q < QMAX; ++q) acc[q] = 0.0;
+
+    for (int64_t base = r0; base < r1; base += RGM_TILE) {
+        const int nrow = (int)min((int64_t)RGM_TILE, r1 - base);
+        // ---- phase 1: produce and store w on this tile
+        if (op.src == SRC_SPMV || op.src == SRC_RES) {
+            // one warp per 32-row slice of the tile, one lane per row; the
+            // slice's entries are independent loads (unrolled below)
+            const int64_t sl = (base >> 5) + warp;
+            const int64_t p0 = op.slice_ptr[sl], p1 = op.slice_ptr[sl + 1];
+            const T sc = (T)xs;
+            T a = 0;
+#pragma unroll 4
+            for (int64_t e = p0 + lane; e < p1; e += 32) a += op.sval[e] * op.x[op.scol[e]];
+            const int pr = op.perm[(sl << 5) + lane];
+            if (pr >= 0) {
+                const T v = (op.src == SRC_SPMV) ? a * sc : op.b[pr] - a;
+                op.out[pr] = v;
+                ws[pr - base] = v;
             }
-            op.out[r] = acc;
+        } else if (op.src == SRC_COPY || op.src == SRC_AXPY) {
+            const int t = threadIdx.x;
+            if (t < nrow) {
+                const int64_t r = base + t;
+                T a = op.win[r];
+                if (op.src == SRC_AXPY) {
+#pragma unroll 4
+                    for (int c = 0; c < op.nW; ++c) a += cW[c] * op.W[r + (int64_t)c * op.ldw];
+#pragma unroll 8
+                    for (int c = 0; c < op.nV; ++c) a += cV[c] * op.V[r + (int64_t)c * op.ldv];
+#pragma unroll 4
+                    for (int c = 0; c < op.nU; ++c) a += cU[c] * op.U[r + (int64_t)c * op.ldu];
+                }
+                op.out[r] = a;
+                ws[t] = a;
+            }
         }
+        if (nd == 0) continue;
+        __syncthreads();
+        // ---- phase 2: dot products, one warp per column over the tile
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q) {
+            const int c = warp + q * NW;
+            if (c < nd) {
+                const T *cp = dot_col(op, c) + base;
+                const bool self = (c == nd - 1) && op.dnorm;
+                T a = 0;
+                if (self) {
+                    for (int i = lane; i < nrow; i += 32) a += ws[i] * ws[i];
+                } else {
+#pragma unroll 4
+                    for (int i = lane; i < nrow; i += 32) a += cp[i] * ws[i];
+                }
+                acc[q] += (double)a;
+            }
+        }
+        __syncthreads();
     }
-    const int nd = op.ndU + op.ndV + op.ndW + op.dnorm;
     if (nd == 0 && op.fin == FIN_NONE) return;
-    __syncthreads();
-
-    // ---- phase 2: block partial dot products, RGM_CHUNK columns per pass.
-    // Products and per-thread sums in the vector precision T, the reduction
-    // tree across threads and blocks in binary64.
-    for (int c0 = 0; c0 < nd; c0 += RGM_CHUNK) {
-        T acc[RGM_CHUNK];
-        const T *cp[RGM_CHUNK];
+    // per-block partials: one warp reduction per column
 #pragma unroll
-        for (int i = 0; i < RGM_CHUNK; ++i) {
-            acc[i] = 0;
-            cp[i] = (c0 + i < nd) ? dot_col(op, c0 + i) : op.out;
+    for (int q = 0; q < QMAX; ++q) {
+        const int c = warp + q * NW;
+        if (c < nd) {
+            const double v = warp_sum(acc[q]);
+            if (lane == 0) op.partials[(int64_t)c * op.nblocks + blockIdx.x] = v;
         }
-        const int nv = min(RGM_CHUNK, nd - c0);
-        for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-            const T wi = op.out[r];
-#pragma unroll
-            for (int i = 0; i < RGM_CHUNK; ++i)
-                if (i < nv) acc[i] += cp[i][r] * wi;
-        }
-        double accd[RGM_CHUNK];
-#pragma unroll
-        for (int i = 0; i < RGM_CHUNK; ++i) accd[i] = (double)acc[i];
-        block_reduce_store<RGM_CHUNK>(accd, op.partials + (int64_t)c0 * op.nblocks + blockIdx.x, nv,
-                                      op.nblocks, red);
     }
 
-    // ---- phase 3: the last block reduces the partials and runs the scalar step
+    // ---- the last block reduces the partials and runs the scalar step
     if (!last_block(op.counter)) return;
     __shared__ double dsum[RGM_MAXDOTS];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int c = warp; c < nd; c += nw) {
+    __shared__ FinScratch fin;
+    for (int c = warp; c < nd; c += NW) {
         double v = 0.0;
         const double *p = op.partials + (int64_t)c * op.nblocks;
         for (int b = lane; b < op.nblocks; b += 32) v += __ldcg(p + b);
@@ -361,57 +409,104 @@ __global__ void __launch_bounds__(RGM_THREADS) vec_kernel(VecOp<T> op)
         if (lane == 0) dsum[c] = v;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        finalize_scalar(op, dsum);
-        *op.counter = 0u;
+    finalize_block(op, dsum, fin);
+    if (threadIdx.x == 0) *op.counter = 0u;
+}
+
+// Host-side dispatch (vec_f64.cu / vec_f32.cu): the per-warp column tier is
+// chosen from the largest dot-column count the launch can see (nd_max;
+// dynamic counts resolve on the device and never exceed it).
+int launch_vec(const VecOp<double> &op, int nd_max, cudaStream_t st);
+int launch_vec(const VecOp<float> &op, int nd_max, cudaStream_t st);
+
+template <typename T>
+static int launch_vec_impl(const VecOp<T> &op, int nd_max, cudaStream_t st)
+{
+    constexpr int NW = RGM_THREADS / 32;
+    constexpr int QBIG = (RGM_MAXDOTS + NW - 1) / NW;
+    const dim3 g(op.nblocks), b(RGM_THREADS);
+    const int q = (nd_max + NW - 1) / NW;
+    if (q <= 4) vec_kernel<T, 4><<<g, b, 0, st>>>(op);
+    else if (q <= 8) vec_kernel<T, 8><<<g, b, 0, st>>>(op);
+    else vec_kernel<T, QBIG><<<g, b, 0, st>>>(op);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// CSR values -> sliced-ELL positions (binary64 and, when given, binary32 copy).
+template <typename Tin>
+__global__ void sell_scatter_kernel(double *sval, float *sval32, const Tin *val, const int32_t *map,
+                                    int64_t nnz)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)val[e];
+        const int32_t d = map[e];
+        sval[d] = v;
+        if (sval32) sval32[d] = (float)v;
     }
 }
 
+// ---------------------------------------------------------------- Gram matrices
 // Pairwise dot products of columns: out[p] = col(a_p) . col(b_p) for a list of
-// pairs over the combined column list [X | Y]; binary64 accumulation.
+// pairs over the combined column list [X | Y]; binary64 accumulation.  Each
+// block stages a tile of rows of all ncol columns in shared memory (padded
+// stride, conflict-free), and each thread owns pairs p = tid + k * blockDim.
 template <typename T>
 struct GramOp {
     int64_t n;
     int rpb, nblocks;
     const T *X; int64_t ldx; int nx;
-    const T *Y; int64_t ldy;
+    const T *Y; int64_t ldy; int ny;
     int npairs;
     const int2 *pairs;
     double *partials;
     unsigned *counter;
     double *out;
+    int tile;                // rows per tile (tile+1 doubles per column in smem)
 };
 
-template <typename T>
-__device__ __forceinline__ const T *gram_col(const GramOp<T> &op, int c)
-{
-    return c < op.nx ? op.X + (int64_t)c * op.ldx : op.Y + (int64_t)(c - op.nx) * op.ldy;
-}
+#define RGM_GRAM_PMAX 16      // pairs per thread: npairs <= RGM_GRAM_PMAX * RGM_THREADS
 
 template <typename T>
 __global__ void __launch_bounds__(RGM_THREADS) gram_kernel(GramOp<T> op)
 {
-    __shared__ double red[(RGM_THREADS / 32) * RGM_CHUNK];
+    extern __shared__ double gsm[];
+    const int ncol = op.nx + op.ny, ts = op.tile + 1;
     const int64_t r0 = (int64_t)blockIdx.x * op.rpb;
     const int64_t r1 = min(op.n, r0 + op.rpb);
-    for (int p0 = 0; p0 < op.npairs; p0 += RGM_CHUNK) {
-        double acc[RGM_CHUNK];
-        const T *ca[RGM_CHUNK], *cb[RGM_CHUNK];
-        const int nv = min(RGM_CHUNK, op.npairs - p0);
+    double acc[RGM_GRAM_PMAX];
+    int pa[RGM_GRAM_PMAX], pb[RGM_GRAM_PMAX];
 #pragma unroll
-        for (int i = 0; i < RGM_CHUNK; ++i) {
-            acc[i] = 0.0;
-            int2 pr = op.pairs[p0 + (i < nv ? i : 0)];
-            ca[i] = gram_col(op, pr.x);
-            cb[i] = gram_col(op, pr.y);
+    for (int i = 0; i < RGM_GRAM_PMAX; ++i) {
+        acc[i] = 0.0;
+        const int p = threadIdx.x + i * RGM_THREADS;
+        int2 pr = (p < op.npairs) ? op.pairs[p] : make_int2(0, 0);
+        pa[i] = pr.x;
+        pb[i] = pr.y;
+    }
+    for (int64_t base = r0; base < r1; base += op.tile) {
+        const int nrow = (int)min((int64_t)op.tile, r1 - base);
+        for (int t = threadIdx.x; t < nrow * ncol; t += RGM_THREADS) {
+            const int r = t % nrow, c = t / nrow;
+            const T *src = c < op.nx ? op.X + (int64_t)c * op.ldx : op.Y + (int64_t)(c - op.nx) * op.ldy;
+            gsm[c * ts + r] = (double)src[base + r];
         }
-        for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        __syncthreads();
 #pragma unroll
-            for (int i = 0; i < RGM_CHUNK; ++i)
-                if (i < nv) acc[i] += (double)ca[i][r] * (double)cb[i][r];
+        for (int i = 0; i < RGM_GRAM_PMAX; ++i) {
+            if (threadIdx.x + i * RGM_THREADS < op.npairs) {
+                const double *a = gsm + pa[i] * ts, *b = gsm + pb[i] * ts;
+                double s = 0.0;
+                for (int r = 0; r < nrow; ++r) s += a[r] * b[r];
+                acc[i] += s;
+            }
         }
-        block_reduce_store<RGM_CHUNK>(acc, op.partials + (int64_t)p0 * op.nblocks + blockIdx.x, nv,
-                                      op.nblocks, red);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < RGM_GRAM_PMAX; ++i) {
+        const int p = threadIdx.x + i * RGM_THREADS;
+        if (p < op.npairs) op.partials[(int64_t)p * op.nblocks + blockIdx.x] = acc[i];
     }
     if (!last_block(op.counter)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -426,36 +521,43 @@ __global__ void __launch_bounds__(RGM_THREADS) gram_kernel(GramOp<T> op)
 }
 
 // ---------------------------------------------------------------- cycle-end kernels
-// Back substitution R y = g on the rotated (J+naug)^2 block, then the update
-// coefficients of x += Vraw[:, :J] (y * colscale) + U[:, aug] y_aug.
-__global__ void ls_solve_kernel(Small *s)
+// Back substitution R y = g on the rotated (J+naug)^2 block (staged in shared
+// memory), then the update coefficients of x += Vraw[:, :J] (y * colscale)
+// + U[:, aug] y_aug.
+#define RGM_LS_MAX (RGM_NCOL * (RGM_NCOL + 1) / 2)
+static __global__ void ls_solve_kernel(Small *s)
 {
+    __shared__ double R[RGM_LS_MAX];     // packed upper triangle, column j at j(j+1)/2
     __shared__ double g[RGM_HLD];
+    __shared__ double yi;
     const int nc = s->J + s->naug;
+    for (int t = threadIdx.x; t < nc * nc; t += blockDim.x) {
+        const int i = t % nc, j = t / nc;
+        if (i <= j) R[j * (j + 1) / 2 + i] = s->H[i + (int64_t)j * RGM_HLD];
+    }
     for (int i = threadIdx.x; i < nc; i += blockDim.x) g[i] = s->g[i];
     __syncthreads();
     for (int i = nc - 1; i >= 0; --i) {
-        __shared__ double yi;
         if (threadIdx.x == 0) {
-            double d = s->H[i + (int64_t)i * RGM_HLD];
+            const double d = R[i * (i + 1) / 2 + i];
             yi = (d != 0.0) ? g[i] / d : 0.0;
             s->y[i] = yi;
         }
         __syncthreads();
-        for (int t = threadIdx.x; t < i; t += blockDim.x) g[t] -= s->H[t + (int64_t)i * RGM_HLD] * yi;
+        const double y = yi;
+        for (int t = threadIdx.x; t < i; t += blockDim.x) g[t] -= R[i * (i + 1) / 2 + t] * y;
         __syncthreads();
     }
-    for (int i = threadIdx.x; i < RGM_HLD; i += blockDim.x) s->coefV[i] = 0.0;
+    for (int i = threadIdx.x; i < RGM_HLD; i += blockDim.x)
+        s->coefV[i] = (i < s->J) ? s->y[i] * s->colscale[i] : 0.0;
     for (int i = threadIdx.x; i < RGM_KMAX; i += blockDim.x) s->coefU[i] = 0.0;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int c = 0; c < s->J; ++c) s->coefV[c] = s->y[c] * s->colscale[c];
+    if (threadIdx.x == 0)
         for (int a = 0; a < s->naug; ++a) s->coefU[s->aug_idx[a]] += s->y[s->J + a];
-    }
 }
 
 // Reset the per-cycle Hessenberg state (before the start vector kernels).
-__global__ void cycle_reset_kernel(Small *s)
+static __global__ void cycle_reset_kernel(Small *s)
 {
     for (int i = threadIdx.x; i < RGM_HLD * RGM_NCOL; i += blockDim.x) s->H[i] = 0.0;
     for (int i = threadIdx.x; i <= RGM_HLD; i += blockDim.x) s->g[i] = 0.0;
@@ -472,7 +574,7 @@ __global__ void cycle_reset_kernel(Small *s)
 // LU with partial pivoting of E (k x k) in one block; singular when a pivot
 // falls below 1e-13 * max(largest pivot, max_i ||u_i|| ||A u_i||).  colnorm2
 // holds ||u_i||^2 then ||w_i||^2 (2k values).
-__global__ void lu_kernel(Small *s, int k, const double *gram_uw, const double *colnorm2)
+static __global__ void lu_kernel(Small *s, int k, const double *gram_uw, const double *colnorm2)
 {
     __shared__ double M[RGM_KMAX * RGM_KMAX];
     __shared__ int pivrow;
