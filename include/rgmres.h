@@ -172,6 +172,31 @@ int rgm_profile(rgm_solver s, int enable);
  * *launches receives every kernel launch since the last reset. */
 int rgm_profile_read(rgm_solver s, rgm_kernel_prof *out, int nkinds, int64_t *launches);
 
+/* ------------------------------------------------------------ allocation-free check
+ * The paper has no counterpart to this entry point: it serves callers that
+ * cannot allocate device memory (a host framework that owns the allocator, a
+ * latency-critical path that must not synchronise on an allocation, a check
+ * that must run after memory is exhausted) and so cannot create an rgm_solver.
+ *
+ * r = b - A x and norms[0] = ||b - A x||_2, norms[1] = ||b||_2 for an n x n CSR
+ * matrix.  Every pointer is a device pointer of the current device (r may be
+ * NULL); the work is queued on cuda_stream (NULL = legacy default stream) and
+ * the call returns without waiting.  Nothing is allocated: the scratch (per-
+ * block partial sums and a completion counter) is one static device array of
+ * 2 * RGM_NOALLOC_MAX_BLOCKS + 32 doubles that every GPU loading the library
+ * holds until exit.  The first call on a device looks its address up once
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the array: calls that overlap on
+ * the GPU race and give wrong results.  A column index outside [0, n) makes the
+ * norms NaN (it is never dereferenced).
+ * Errors: RGM_E_ARG for a NULL pointer, n < 1 or n > RGM_NOALLOC_MAX_BLOCKS *
+ * RGM_NOALLOC_ROWS_PER_BLOCK (8,388,608 rows); RGM_E_CUDA otherwise. */
+#define RGM_NOALLOC_MAX_BLOCKS 4096
+#define RGM_NOALLOC_ROWS_PER_BLOCK 2048
+int rgm_residual_noalloc(int64_t n, const int64_t *rowptr, const int32_t *col, const double *val,
+                         const double *x, const double *b, double *r, double *norms,
+                         void *cuda_stream);
+
 /* ------------------------------------------------------------ FE workload
  * The time-step systems of Sec. 6.1 built on the device: Q_p Lagrange elements
  * (p = 1..4, Gauss-Lobatto nodes) on a uniform N x N grid of the unit square,

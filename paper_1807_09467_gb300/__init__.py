@@ -23,7 +23,7 @@ from ._lib import (AUGMENTED, DEFLATED, FP32_IR, FP64, PLAIN, RGM_DEVICE_PTRS,
 MODES = {"plain": PLAIN, "deflated": DEFLATED, "augmented": AUGMENTED}
 PRECISIONS = {"fp64": FP64, "fp32_ir": FP32_IR}
 
-__all__ = ["Solver", "FE", "RgmError", "MODES", "PRECISIONS", "PLAIN", "DEFLATED", "AUGMENTED",
+__all__ = ["Solver", "FE", "residual_noalloc", "RgmError", "MODES", "PRECISIONS", "PLAIN", "DEFLATED", "AUGMENTED",
            "FP64", "FP32_IR", "RGM_W_NOT_CONVERGED", "RGM_W_SINGULAR_COARSE"]
 
 
@@ -176,6 +176,20 @@ class Solver:
         check(self._L.rgm_spmv(self._h, C.c_void_p(xx.ctypes.data), C.c_void_p(y.ctypes.data), 0),
               "rgm_spmv")
         return y
+
+
+def residual_noalloc(rowptr, col, val, x, b, r, norms, stream=None):
+    """rgm_residual_noalloc: r = b - A x and norms = [||b - A x||, ||b||] with no
+    device allocation, for callers that cannot allocate (see include/rgmres.h).
+    All arguments are CUDA tensors (int64 rowptr, int32 col, float64 others); r
+    may be None.  Queued on `stream`; the call does not wait."""
+    L = _lib.load()
+    n = rowptr.numel() - 1
+    rp = C.c_void_p(r.data_ptr()) if r is not None else None
+    check(L.rgm_residual_noalloc(n, C.c_void_p(rowptr.data_ptr()), C.c_void_p(col.data_ptr()),
+                                 C.c_void_p(val.data_ptr()), C.c_void_p(x.data_ptr()),
+                                 C.c_void_p(b.data_ptr()), rp, C.c_void_p(norms.data_ptr()), stream),
+          "rgm_residual_noalloc")
 
 
 class FE:

@@ -21,6 +21,7 @@ RGM_E_CUDA = -3
 RGM_E_STATE = -4
 RGM_E_TIMEOUT = -5
 RGM_DEVICE_PTRS = 1
+RGM_NOALLOC_MAX_ROWS = 4096 * 2048
 
 PLAIN, DEFLATED, AUGMENTED = 0, 1, 2
 FP64, FP32_IR = 0, 1
@@ -70,6 +71,8 @@ _SIGS = {
     "rgm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "rgm_profile_read": (C.c_int, [C.c_void_p, C.POINTER(RgmKernelProf), C.c_int,
                                    C.POINTER(C.c_int64)]),
+    "rgm_residual_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rgm_fe_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_double, C.c_double,
                                 C.c_double, C.c_double, C.c_void_p]),
     "rgm_fe_destroy": (C.c_int, [C.c_void_p]),
