@@ -183,7 +183,7 @@ def run_sequence(rg, torch, w, seq, mode, precision, warmup, steps, profile=Fals
         ev[i][0].record(cs)
         solver.set_operator_values(val)
         _, st = solver.solve(b, x)
-        solver.update_recycle_svd(x)
+        solver.update_recycle_svd(x, want_k=False)
         ev[i][1].record(cs)
         u.copy_(x)
         its.append(st["iters"])
@@ -228,7 +228,7 @@ def run_e2e(rg, np, w, seq, mode, precision, warmup, steps, inputs, torch):
         t0 = time.perf_counter()
         s.set_operator_values(pin_val.numpy())
         xx, st = s.solve(pin_b.numpy(), pin_x.numpy())
-        s.update_recycle_svd(xx)
+        s.update_recycle_svd(xx, want_k=False)
         t1 = time.perf_counter()
         u = xx
         times.append(t1 - t0)
@@ -267,10 +267,15 @@ def ours(args):
     clk.start()
     t_wall0 = time.perf_counter()
     main = run_sequence(rg, torch, w, seq, args.mode, args.precision, args.warmup, args.steps,
-                        profile=True, keep=keep, flush=flush)
+                        profile=False, keep=keep, flush=flush)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     clocks = clk.stop()
+    # second pass over the same sequence with per-launch CUDA events on the
+    # solver's stream (events between launches serialise the overlap of
+    # consecutive passes, so this pass is not the headline timing)
+    profd = run_sequence(rg, torch, w, seq, args.mode, args.precision, args.warmup, args.steps,
+                         profile=True, flush=flush)
     my_sec = sum(main["seg_ms"]) / 1e3
     tot_sec = my_sec
     if ws > 1:
@@ -284,7 +289,7 @@ def ours(args):
         return
     K = args.steps
     value = K * ws / tot_sec
-    prof, launches = main["prof"]
+    prof, launches = profd["prof"]
     n, nnz = main["n"], main["nnz"]
     # dominant kernel by device time
     kinds = {k: v for k, v in prof.items() if v["launches"] > 0}
@@ -330,6 +335,7 @@ def ours(args):
         "max_true_relres": max(main["relres"][args.warmup:]),
         "assembly_ms_per_step": round(statistics.mean(main["asm_ms"]), 4),
         "roofline": roof, "kernels": kernel_share, "gpu_launches": int(launches),
+        "profiled_pass_ms_per_step": round(statistics.mean(profd["seg_ms"]), 4),
         "clocks": clocks, "wall_s": round(t_wall, 3),
     }
     if not args.quick:

@@ -132,7 +132,11 @@ int rgm_solve(rgm_solver s, const double *b, double *x, int flags, rgm_stats *st
  * oldest column leaves when `window` are stored); if the number of calls so far
  * is a multiple of svd_interval, replace U by the k leading (or trailing) left
  * singular vectors of the window (Sec. 5.2), dropping singular values below
- * rel_drop * sigma_1.  *k_used (may be NULL) receives the new dimension. */
+ * rel_drop * sigma_1.  *k_used (may be NULL) receives the new dimension, which
+ * makes the call wait for the device; with k_used NULL and RGM_DEVICE_PTRS the
+ * work is only queued on the solver's stream (the next call on the handle
+ * picks up the new dimension).  With host pointers the call returns after x
+ * has been read. */
 int rgm_update_recycle_svd(rgm_solver s, const double *x, int flags, int *k_used);
 /* Singular values of the last window SVD, descending (up to `window` values);
  * *count receives how many are valid. */

@@ -134,11 +134,14 @@ class Solver:
         check(rc, "rgm_solve")
         return xx, _stats(st)
 
-    def update_recycle_svd(self, x):
+    def update_recycle_svd(self, x, want_k=True):
+        """Algorithm 1 window update; returns the new recycle dimension (with
+        want_k=False the call does not wait for the device and returns None)."""
         xp, f, keep = _ptr(x, np.float64)
         k = C.c_int(0)
-        check(self._L.rgm_update_recycle_svd(self._h, xp, f, C.byref(k)), "rgm_update_recycle_svd")
-        return k.value
+        check(self._L.rgm_update_recycle_svd(self._h, xp, f, C.byref(k) if want_k else None),
+              "rgm_update_recycle_svd")
+        return k.value if want_k else None
 
     def singular_values(self):
         out = np.zeros(64)

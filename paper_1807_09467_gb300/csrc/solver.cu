@@ -79,6 +79,7 @@ struct rgm_solver_s {
           *b32 = nullptr, *x32 = nullptr;
     // recycling
     int k_cur = 0;
+    bool k_pending = false;       // a device-side SVD update chose a new k
     bool coarse_stale = true;
     double *X = nullptr;          // snapshot window, n x window (ring)
     int win_count = 0, win_head = 0, updates = 0;
@@ -101,6 +102,7 @@ struct rgm_solver_s {
 };
 
 static size_t small_header_bytes() { return offsetof(Small, H); }
+static int sync_recycle_dim(rgm_solver s);
 
 template <typename T>
 static VecOp<T> base_op(rgm_solver s, const Arnoldi<T> &a)
@@ -252,15 +254,15 @@ static void prof_collect(rgm_solver s)
     s->cycle_rec0 = 0;
 }
 
+// Gram pairs are generated on the device (no host upload, which for pageable
+// memory would synchronise the stream).  nx_dev: optional device count.
 template <typename T>
 static int launch_gram(rgm_solver s, const T *X, int64_t ldx, int nx, const T *Y, int64_t ldy,
-                       int ny, const std::vector<int2> &pairs, double *out)
+                       int mode, const int *nx_dev, int nxmax, double *out)
 {
-    if ((int)pairs.size() > s->npairs_max || (int)pairs.size() > RGM_GRAM_PMAX * RGM_THREADS)
-        return RGM_E_ARG;
-    if (pairs.empty()) return RGM_OK;
-    CK(cudaMemcpyAsync(s->pairs, pairs.data(), sizeof(int2) * pairs.size(), cudaMemcpyHostToDevice,
-                       s->st));
+    if (nxmax <= 0) return RGM_OK;
+    const int npmax = (mode == GRAM_UW) ? nxmax * nxmax + 2 * nxmax : nxmax * (nxmax + 1) / 2;
+    if (npmax > s->npairs_max || npmax > RGM_GRAM_PMAX * RGM_THREADS) return RGM_E_ARG;
     GramOp<T> op;
     op.n = s->n;
     op.rpb = s->rpb;
@@ -270,17 +272,17 @@ static int launch_gram(rgm_solver s, const T *X, int64_t ldx, int nx, const T *Y
     op.nx = nx;
     op.Y = Y;
     op.ldy = ldy;
-    op.ny = ny;
-    op.npairs = (int)pairs.size();
-    op.pairs = s->pairs;
+    op.nx_dev = nx_dev;
+    op.mode = mode;
+    op.nxmax = nxmax;
     op.partials = s->partials;
     op.counter = s->counter;
     op.out = out;
-    const int ncol = nx + ny;
+    const int ncol = (mode == GRAM_UW) ? 2 * nxmax : nxmax;
     op.tile = std::min(256, (int)(48 * 1024 / sizeof(double)) / ncol - 1);
     const size_t smem = sizeof(double) * (size_t)ncol * (op.tile + 1);
     {
-        const double n = (double)s->n, np_ = (double)pairs.size();
+        const double n = (double)s->n, np_ = (double)npmax;
         ProfScope ps(s, RGM_PROF_GRAM, 2.0 * n * np_, (double)sizeof(T) * n * ncol);
         gram_kernel<T><<<s->nblocks, RGM_THREADS, smem, s->st>>>(op);
     }
@@ -332,12 +334,8 @@ static int coarse_setup(rgm_solver s)
         int rc = launch(s, op);
         if (rc) return rc;
     }
-    std::vector<int2> pairs;
-    for (int j = 0; j < k; ++j)
-        for (int i = 0; i < k; ++i) pairs.push_back(make_int2(i, k + j));     // E_ij = u_i . w_j
-    for (int i = 0; i < k; ++i) pairs.push_back(make_int2(i, i));
-    for (int i = 0; i < k; ++i) pairs.push_back(make_int2(k + i, k + i));
-    int rc = launch_gram<double>(s, s->U, s->ld, k, s->W, s->ld, k, pairs, s->gram_out);
+    // E_ij = u_i . w_j, then ||u_i||^2, ||w_i||^2
+    int rc = launch_gram<double>(s, s->U, s->ld, k, s->W, s->ld, GRAM_UW, nullptr, k, s->gram_out);
     if (rc) return rc;
     { ProfScope ps_(s, RGM_PROF_SMALL); lu_kernel<<<1, 256, 0, s->st>>>(s->sm, k, s->gram_out, s->gram_out + k * k); }
     CK(cudaGetLastError());
@@ -506,6 +504,7 @@ static int solve_device(rgm_solver s, rgm_stats *out)
 {
     const rgm_config &c = s->cfg;
     int status = RGM_OK, rc;
+    if ((rc = sync_recycle_dim(s))) return rc;
     int k = (c.mode != RGM_PLAIN) ? s->k_cur : 0;
     if (k > 0 && s->coarse_stale) {
         if ((rc = coarse_setup(s))) return rc;
@@ -573,39 +572,46 @@ static int solve_device(rgm_solver s, rgm_stats *out)
 }
 
 // ---------------------------------------------------------------- SVD update (Algorithm 1)
-static int svd_update(rgm_solver s, int *k_used)
+// Everything stays on the device: the chosen dimension k_new is read by the
+// kernels that need it, and by the host lazily at the next solve.
+static int svd_update(rgm_solver s)
 {
     const rgm_config &c = s->cfg;
     const int cnt = s->win_count;
-    std::vector<int2> pairs;
-    for (int j = 0; j < cnt; ++j)
-        for (int i = 0; i <= j; ++i) pairs.push_back(make_int2(i, j));
-    int rc = launch_gram<double>(s, s->X, s->ld, cnt, s->X, s->ld, 0, pairs, s->gram_out);
+    int rc = launch_gram<double>(s, s->X, s->ld, cnt, s->X, s->ld, GRAM_PACKED, nullptr, cnt,
+                                 s->gram_out);
     if (rc) return rc;
     { ProfScope ps_(s, RGM_PROF_SMALL); sym_eig_select_kernel<<<1, 512, EIG_SMEM_BYTES, s->st>>>(s->sm, s->gram_out, cnt, c.k,
                                                              c.select_smallest, c.rel_drop); }
     CK(cudaGetLastError());
-    if ((rc = read_header(s))) return rc;
-    const int kn = s->hs->k_new;
-    if (kn > 0) {
-        // U = X Phi_k Sigma_k^{-1}, then two CholQR passes
-        { ProfScope ps_(s, RGM_PROF_OTHER); combine_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U, s->X, s->sm->evec, cnt, kn, s->n, s->ld,
-                                                      RGM_WMAX); }
+    const int kmax = std::min(c.k, cnt);
+    const int *kdev = &s->sm->k_new;
+    if (kmax > 0) {
+        // U = X Phi_k Sigma_k^{-1}, then two CholQR passes (k_new read on the device)
+        { ProfScope ps_(s, RGM_PROF_OTHER); combine_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U, s->X, s->sm->evec, cnt, -1, kdev, s->n, s->ld, RGM_WMAX); }
         CK(cudaGetLastError());
         for (int pass = 0; pass < 2; ++pass) {
-            std::vector<int2> up;
-            for (int j = 0; j < kn; ++j)
-                for (int i = 0; i <= j; ++i) up.push_back(make_int2(i, j));
-            if ((rc = launch_gram<double>(s, s->U, s->ld, kn, s->U, s->ld, 0, up, s->gram_out))) return rc;
-            { ProfScope ps_(s, RGM_PROF_SMALL); chol_inv_kernel<<<1, 64, 0, s->st>>>(s->sm, s->gram_out, kn); }
-            { ProfScope ps_(s, RGM_PROF_OTHER); combine_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U, s->U, s->sm->evec, kn, kn, s->n,
-                                                          s->ld, RGM_WMAX); }
+            if ((rc = launch_gram<double>(s, s->U, s->ld, 0, s->U, s->ld, GRAM_PACKED, kdev, kmax, s->gram_out))) return rc;
+            { ProfScope ps_(s, RGM_PROF_SMALL); chol_inv_kernel<<<1, 64, 0, s->st>>>(s->sm, s->gram_out, -1, kdev); }
+            { ProfScope ps_(s, RGM_PROF_OTHER); combine_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U, s->U, s->sm->evec, -1, -1, kdev, s->n, s->ld, RGM_WMAX); }
             CK(cudaGetLastError());
         }
     }
-    s->k_cur = kn;
+    s->k_pending = true;
     s->coarse_stale = true;
-    if (k_used) *k_used = kn;
+    return RGM_OK;
+}
+
+// Pick up the recycle dimension chosen by the last device-side SVD update.
+static int sync_recycle_dim(rgm_solver s)
+{
+    if (!s->k_pending) return RGM_OK;
+    int kn = 0;
+    CK(cudaMemcpyAsync(&s->hs->k_new, &s->sm->k_new, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    kn = s->hs->k_new;
+    s->k_cur = kn;
+    s->k_pending = false;
     return RGM_OK;
 }
 
@@ -862,6 +868,7 @@ int rgm_set_recycle_space(rgm_solver s, const double *U, int k, int64_t ld, int 
                            kind_in(flags), s->st));
     CK(cudaStreamSynchronize(s->st));
     s->k_cur = k;
+    s->k_pending = false;
     s->coarse_stale = true;
     return RGM_OK;
 }
@@ -869,6 +876,8 @@ int rgm_set_recycle_space(rgm_solver s, const double *U, int k, int64_t ld, int 
 int rgm_get_recycle_space(rgm_solver s, double *U, int64_t ld, int *k, int flags)
 {
     if (!s || !k) return RGM_E_ARG;
+    int rc = sync_recycle_dim(s);
+    if (rc) return rc;
     *k = s->k_cur;
     if (!U) return RGM_OK;
     if (ld < s->n) return RGM_E_ARG;
@@ -901,18 +910,23 @@ int rgm_update_recycle_svd(rgm_solver s, const double *x, int flags, int *k_used
     if (s->win_count < s->cfg.window) ++s->win_count;
     ++s->updates;
     if (s->cfg.k > 0 && s->updates % s->cfg.svd_interval == 0) {
-        int rc = svd_update(s, k_used);
+        int rc = svd_update(s);
         if (rc) return rc;
-    } else if (k_used) {
+    }
+    if (k_used) {
+        int rc = sync_recycle_dim(s);
+        if (rc) return rc;
         *k_used = s->k_cur;
     }
-    CK(cudaStreamSynchronize(s->st));
+    // host buffers: the copy must be done before the caller may reuse x
+    if (!(flags & RGM_DEVICE_PTRS)) CK(cudaStreamSynchronize(s->st));
     return RGM_OK;
 }
 
 int rgm_get_singular_values(rgm_solver s, double *sigma, int *count)
 {
     if (!s || !sigma || !count) return RGM_E_ARG;
+    CK(cudaStreamSynchronize(s->st));
     CK(cudaMemcpy(s->hs, s->sm, sizeof(Small), cudaMemcpyDeviceToHost));
     const int c = s->win_count;
     for (int i = 0; i < c; ++i) {
@@ -929,7 +943,9 @@ int rgm_reset_recycling(rgm_solver s)
     s->win_count = 0;
     s->win_head = 0;
     s->updates = 0;
+    CK(cudaStreamSynchronize(s->st));
     s->k_cur = 0;
+    s->k_pending = false;
     s->coarse_stale = true;
     return RGM_OK;
 }

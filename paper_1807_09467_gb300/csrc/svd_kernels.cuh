@@ -63,13 +63,13 @@ __global__ void sym_eig_select_kernel(Small *s, const double *gram, int c, int k
     }
     __syncthreads();
     // Stop rotating a pair when its coupling is below 1e-15 of its own
-    // diagonal scale (high relative accuracy) or below 1e-20 of the largest
-    // eigenvalue: modes under rel_drop^2 * lambda_1 (1e-14 lambda_1 by default)
-    // are never kept, so the floor costs the kept modes no accuracy and stops
-    // graded windows from sweeping on rounding noise.
-    const double floor_abs = 1e-20 * gmax;
+    // diagonal scale or below 2e-16 of the largest eigenvalue.  A rotation of a
+    // pair that couples lambda_max with a tiny eigenvalue reintroduces couplings
+    // of rounding size (about eps * lambda_max), so without this floor graded
+    // windows sweep forever; the floor is the accuracy the Gram matrix carries.
+    const double floor_abs = 2e-16 * gmax;
     const int npair = ce / 2;
-    for (int sweep = 0; sweep < 40; ++sweep) {
+    for (int sweep = 0; sweep < 30; ++sweep) {
         if (threadIdx.x == 0) any_rot = 0;
         __syncthreads();
         for (int step = 0; step < ce - 1; ++step) {
@@ -154,11 +154,15 @@ __global__ void sym_eig_select_kernel(Small *s, const double *gram, int c, int k
 }
 
 // out[:, l] = sum_m in[:, m] C[m + l * ldc] for l < kout; in-place safe
-// (each row's inputs are read before its outputs are written).
+// (each row's inputs are read before its outputs are written).  A negative
+// cin or kout is read from *kdev (the dimension chosen on the device).
 __global__ void combine_kernel(double *out, const double *in, const double *C, int cin, int kout,
-                               int64_t n, int64_t ld, int ldc)
+                               const int *kdev, int64_t n, int64_t ld, int ldc)
 {
     __shared__ double Cs[RGM_WMAX * RGM_KMAX];
+    if (cin < 0) cin = *kdev;
+    if (kout < 0) kout = *kdev;
+    if (kout <= 0) return;
     for (int t = threadIdx.x; t < cin * kout; t += blockDim.x) {
         int m = t % cin, l = t / cin;
         Cs[m + l * RGM_WMAX] = C[m + l * ldc];
@@ -181,9 +185,11 @@ __global__ void combine_kernel(double *out, const double *in, const double *C, i
 // into Small::evec so that U R^{-1} has orthonormal columns.  One block:
 // the factorisation row by row with the trailing updates in parallel, then one
 // thread per column of R^{-1} (back substitution from shared memory).
-__global__ void chol_inv_kernel(Small *s, const double *gram, int k)
+__global__ void chol_inv_kernel(Small *s, const double *gram, int k, const int *kdev)
 {
     __shared__ double R[RGM_KMAX * RGM_KMAX];
+    if (k < 0) k = *kdev;
+    if (k <= 0) return;
     for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
         const int i = t % k, j = t / k;
         R[i + j * RGM_KMAX] = (i <= j) ? gram[packed_index(i, j)] : 0.0;

@@ -301,6 +301,9 @@ template <typename T, int QMAX>
 __global__ void __launch_bounds__(RGM_THREADS) vec_kernel(VecOp<T> op)
 {
     constexpr int NW = RGM_THREADS / 32;      // QMAX * NW >= number of dot columns
+    // programmatic dependent launch: blocks may be scheduled while the previous
+    // pass finishes; nothing it wrote is read before this wait returns
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     Small *s = op.sm;
     if (op.gate == GATE_KRYLOV && s->done) return;
     if (op.gate == GATE_APPEND && (s->skip || s->J == 0)) return;
@@ -323,6 +326,7 @@ __global__ void __launch_bounds__(RGM_THREADS) vec_kernel(VecOp<T> op)
     __syncthreads();
 
     const int nd = op.ndU + op.ndV + op.ndW + op.dnorm;
+    const int ndc_ = op.dnorm ? nd - 1 : -1;          // index of the ||w||^2 column
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t r0 = (int64_t)blockIdx.x * op.rpb;
     const int64_t r1 = min(op.n, r0 + op.rpb);
@@ -368,25 +372,40 @@ __global__ void __launch_bounds__(RGM_THREADS) vec_kernel(VecOp<T> op)
         if (nd == 0) continue;
         __syncthreads();
         // ---- phase 2: dot products, one warp per column over the tile
+        if (nrow == RGM_TILE) {
+            // full tile: every load of the warp's columns is issued up front
+            T wl[RGM_TILE / 32];
 #pragma unroll
-        for (int q = 0; q < QMAX; ++q) {
-            const int c = warp + q * NW;
-            if (c < nd) {
-                const T *cp = dot_col(op, c) + base;
-                const bool self = (c == nd - 1) && op.dnorm;
-                T a = 0;
-                if (self) {
-                    for (int i = lane; i < nrow; i += 32) a += ws[i] * ws[i];
-                } else {
-#pragma unroll 4
-                    for (int i = lane; i < nrow; i += 32) a += cp[i] * ws[i];
+            for (int i = 0; i < RGM_TILE / 32; ++i) wl[i] = ws[lane + 32 * i];
+#pragma unroll
+            for (int q = 0; q < QMAX; ++q) {
+                const int c = warp + q * NW;
+                if (c < nd) {
+                    const T *cp = (c == ndc_) ? ws : dot_col(op, c) + base;
+                    T a = 0;
+#pragma unroll
+                    for (int i = 0; i < RGM_TILE / 32; ++i) a += cp[lane + 32 * i] * wl[i];
+                    acc[q] += (double)a;
                 }
-                acc[q] += (double)a;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < QMAX; ++q) {
+                const int c = warp + q * NW;
+                if (c < nd) {
+                    const T *cp = (c == ndc_) ? ws : dot_col(op, c) + base;
+                    T a = 0;
+                    for (int i = lane; i < nrow; i += 32) a += cp[i] * ws[i];
+                    acc[q] += (double)a;
+                }
             }
         }
         __syncthreads();
     }
-    if (nd == 0 && op.fin == FIN_NONE) return;
+    if (nd == 0 && op.fin == FIN_NONE) {
+        asm volatile("griddepcontrol.launch_dependents;");
+        return;
+    }
     // per-block partials: one warp reduction per column
 #pragma unroll
     for (int q = 0; q < QMAX; ++q) {
@@ -397,16 +416,34 @@ __global__ void __launch_bounds__(RGM_THREADS) vec_kernel(VecOp<T> op)
         }
     }
 
+    // the next pass may start launching; it waits for this grid to complete
+    asm volatile("griddepcontrol.launch_dependents;");
     // ---- the last block reduces the partials and runs the scalar step
     if (!last_block(op.counter)) return;
     __shared__ double dsum[RGM_MAXDOTS];
+    __shared__ double red2[RGM_THREADS];
     __shared__ FinScratch fin;
-    for (int c = warp; c < nd; c += NW) {
-        double v = 0.0;
-        const double *p = op.partials + (int64_t)c * op.nblocks;
-        for (int b = lane; b < op.nblocks; b += 32) v += __ldcg(p + b);
-        v = warp_sum(v);
-        if (lane == 0) dsum[c] = v;
+    if (nd > 0) {
+        // threads split each column's blocks (independent loads); fixed order
+        const int tpc = max(1, RGM_THREADS / nd);
+        const int ncov = RGM_THREADS / tpc;
+        for (int cbase = 0; cbase < nd; cbase += ncov) {
+            const int c = cbase + (int)threadIdx.x / tpc, part = (int)threadIdx.x % tpc;
+            double v = 0.0;
+            if ((int)threadIdx.x < ncov * tpc && c < nd) {
+                const double *p = op.partials + (int64_t)c * op.nblocks;
+#pragma unroll 8
+                for (int b = part; b < op.nblocks; b += tpc) v += __ldcg(p + b);
+            }
+            red2[threadIdx.x] = v;
+            __syncthreads();
+            for (int cc = threadIdx.x; cc < ncov && cbase + cc < nd; cc += blockDim.x) {
+                double t = 0.0;
+                for (int j = 0; j < tpc; ++j) t += red2[cc * tpc + j];
+                dsum[cbase + cc] = t;
+            }
+            __syncthreads();
+        }
     }
     __syncthreads();
     finalize_block(op, dsum, fin);
@@ -419,17 +456,33 @@ __global__ void __launch_bounds__(RGM_THREADS) vec_kernel(VecOp<T> op)
 int launch_vec(const VecOp<double> &op, int nd_max, cudaStream_t st);
 int launch_vec(const VecOp<float> &op, int nd_max, cudaStream_t st);
 
+template <typename T, int Q>
+static cudaError_t launch_vec_pdl(const VecOp<T> &op, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(op.nblocks);
+    cfg.blockDim = dim3(RGM_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, vec_kernel<T, Q>, op);
+}
+
 template <typename T>
 static int launch_vec_impl(const VecOp<T> &op, int nd_max, cudaStream_t st)
 {
     constexpr int NW = RGM_THREADS / 32;
     constexpr int QBIG = (RGM_MAXDOTS + NW - 1) / NW;
-    const dim3 g(op.nblocks), b(RGM_THREADS);
     const int q = (nd_max + NW - 1) / NW;
-    if (q <= 4) vec_kernel<T, 4><<<g, b, 0, st>>>(op);
-    else if (q <= 8) vec_kernel<T, 8><<<g, b, 0, st>>>(op);
-    else vec_kernel<T, QBIG><<<g, b, 0, st>>>(op);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    cudaError_t e;
+    if (q <= 4) e = launch_vec_pdl<T, 4>(op, st);
+    else if (q <= 8) e = launch_vec_pdl<T, 8>(op, st);
+    else e = launch_vec_pdl<T, QBIG>(op, st);
+    return e == cudaSuccess ? 0 : -1;
 }
 
 // CSR values -> sliced-ELL positions (binary64 and, when given, binary32 copy).
@@ -451,14 +504,20 @@ __global__ void sell_scatter_kernel(double *sval, float *sval32, const Tin *val,
 // pairs over the combined column list [X | Y]; binary64 accumulation.  Each
 // block stages a tile of rows of all ncol columns in shared memory (padded
 // stride, conflict-free), and each thread owns pairs p = tid + k * blockDim.
+enum GramMode {
+    GRAM_PACKED = 0,   // all pairs i <= j of the nx columns of X (packed, j-major)
+    GRAM_UW = 1        // E pattern: u_i . w_j (i + j nx), then u_i . u_i, then w_i . w_i
+};
+
 template <typename T>
 struct GramOp {
     int64_t n;
     int rpb, nblocks;
     const T *X; int64_t ldx; int nx;
-    const T *Y; int64_t ldy; int ny;
-    int npairs;
-    const int2 *pairs;
+    const T *Y; int64_t ldy;
+    const int *nx_dev;       // if set, nx is read from the device (dynamic column count)
+    int mode;
+    int nxmax;               // bound on nx (shared-memory sizing)
     double *partials;
     unsigned *counter;
     double *out;
@@ -467,11 +526,23 @@ struct GramOp {
 
 #define RGM_GRAM_PMAX 16      // pairs per thread: npairs <= RGM_GRAM_PMAX * RGM_THREADS
 
+__device__ __forceinline__ void packed_pair(int p, int *i, int *j)
+{
+    int jj = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
+    while ((jj + 1) * (jj + 2) / 2 <= p) ++jj;
+    while (jj * (jj + 1) / 2 > p) --jj;
+    *j = jj;
+    *i = p - jj * (jj + 1) / 2;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(RGM_THREADS) gram_kernel(GramOp<T> op)
 {
     extern __shared__ double gsm[];
-    const int ncol = op.nx + op.ny, ts = op.tile + 1;
+    const int nx = op.nx_dev ? *op.nx_dev : op.nx;
+    const int ny = (op.mode == GRAM_UW) ? nx : 0;
+    const int ncol = nx + ny, ts = op.tile + 1;
+    const int npairs = (op.mode == GRAM_UW) ? nx * nx + 2 * nx : nx * (nx + 1) / 2;
     const int64_t r0 = (int64_t)blockIdx.x * op.rpb;
     const int64_t r1 = min(op.n, r0 + op.rpb);
     double acc[RGM_GRAM_PMAX];
@@ -480,21 +551,33 @@ __global__ void __launch_bounds__(RGM_THREADS) gram_kernel(GramOp<T> op)
     for (int i = 0; i < RGM_GRAM_PMAX; ++i) {
         acc[i] = 0.0;
         const int p = threadIdx.x + i * RGM_THREADS;
-        int2 pr = (p < op.npairs) ? op.pairs[p] : make_int2(0, 0);
-        pa[i] = pr.x;
-        pb[i] = pr.y;
+        int a = 0, b = 0;
+        if (p < npairs) {
+            if (op.mode == GRAM_PACKED) {
+                packed_pair(p, &a, &b);
+            } else if (p < nx * nx) {
+                a = p % nx;
+                b = nx + p / nx;
+            } else if (p < nx * nx + nx) {
+                a = b = p - nx * nx;
+            } else {
+                a = b = nx + (p - nx * nx - nx);
+            }
+        }
+        pa[i] = a;
+        pb[i] = b;
     }
     for (int64_t base = r0; base < r1; base += op.tile) {
         const int nrow = (int)min((int64_t)op.tile, r1 - base);
         for (int t = threadIdx.x; t < nrow * ncol; t += RGM_THREADS) {
             const int r = t % nrow, c = t / nrow;
-            const T *src = c < op.nx ? op.X + (int64_t)c * op.ldx : op.Y + (int64_t)(c - op.nx) * op.ldy;
+            const T *src = c < nx ? op.X + (int64_t)c * op.ldx : op.Y + (int64_t)(c - nx) * op.ldy;
             gsm[c * ts + r] = (double)src[base + r];
         }
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < RGM_GRAM_PMAX; ++i) {
-            if (threadIdx.x + i * RGM_THREADS < op.npairs) {
+            if (threadIdx.x + i * RGM_THREADS < npairs) {
                 const double *a = gsm + pa[i] * ts, *b = gsm + pb[i] * ts;
                 double s = 0.0;
                 for (int r = 0; r < nrow; ++r) s += a[r] * b[r];
@@ -506,11 +589,11 @@ __global__ void __launch_bounds__(RGM_THREADS) gram_kernel(GramOp<T> op)
 #pragma unroll
     for (int i = 0; i < RGM_GRAM_PMAX; ++i) {
         const int p = threadIdx.x + i * RGM_THREADS;
-        if (p < op.npairs) op.partials[(int64_t)p * op.nblocks + blockIdx.x] = acc[i];
+        if (p < npairs) op.partials[(int64_t)p * op.nblocks + blockIdx.x] = acc[i];
     }
     if (!last_block(op.counter)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int c = warp; c < op.npairs; c += nw) {
+    for (int c = warp; c < npairs; c += nw) {
         double v = 0.0;
         const double *p = op.partials + (int64_t)c * op.nblocks;
         for (int b = lane; b < op.nblocks; b += 32) v += __ldcg(p + b);
