@@ -298,7 +298,7 @@ __device__ __forceinline__ const T *dot_col(const VecOp<T> &op, int c)
 }
 
 template <typename T, int QMAX>
-__global__ void __launch_bounds__(RGM_THREADS) vec_kernel(VecOp<T> op)
+__global__ void __launch_bounds__(RGM_THREADS, 4) vec_kernel(VecOp<T> op)
 {
     constexpr int NW = RGM_THREADS / 32;      // QMAX * NW >= number of dot columns
     // programmatic dependent launch: blocks may be scheduled while the previous
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(RGM_THREADS) vec_kernel(VecOp<T> op)
             const int64_t p0 = op.slice_ptr[sl], p1 = op.slice_ptr[sl + 1];
             const T sc = (T)xs;
             T a = 0;
-#pragma unroll 4
+#pragma unroll 8
             for (int64_t e = p0 + lane; e < p1; e += 32) a += op.sval[e] * op.x[op.scol[e]];
             const int pr = op.perm[(sl << 5) + lane];
             if (pr >= 0) {
