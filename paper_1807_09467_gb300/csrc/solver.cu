@@ -689,7 +689,7 @@ int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
     s->ld = (c.n + 31) / 32 * 32;
     // blocks own whole RGM_TILE-row tiles (the sliced-ELL sorting windows)
     const int64_t ntile = (s->n + RGM_TILE - 1) / RGM_TILE;
-    const int64_t nb_want = std::max<int64_t>(1, std::min<int64_t>(ntile, 2 * (int64_t)nsm));
+    const int64_t nb_want = std::max<int64_t>(1, std::min<int64_t>(ntile, 4 * (int64_t)nsm));
     const int64_t tiles_per_block = (ntile + nb_want - 1) / nb_want;
     s->rpb = (int)(tiles_per_block * RGM_TILE);
     s->nblocks = (int)((s->n + s->rpb - 1) / s->rpb);

@@ -334,10 +334,32 @@ __global__ void __launch_bounds__(RGM_THREADS, 4) vec_kernel(VecOp<T> op)
 #pragma unroll
     for (int q = 0; q < QMAX; ++q) acc[q] = 0.0;
 
+    const bool spmv_src = (op.src == SRC_SPMV || op.src == SRC_RES);
+    const int ntiles_blk = (int)((r1 - r0 + RGM_TILE - 1) / RGM_TILE);
+    if (spmv_src && ntiles_blk > 1) {
+        // SpMV over all of the block's slices first.  Inside a tile the slices
+        // are sorted by width (slice 0 widest), so warp w takes slice w of even
+        // tiles and slice NW-1-w of odd ones: every warp gets the same work.
+        const T sc = (T)xs;
+        for (int t = 0; t < ntiles_blk; ++t) {
+            const int64_t base = r0 + (int64_t)t * RGM_TILE;
+            const int slot = (t & 1) ? (NW - 1 - warp) : warp;
+            const int64_t sl = (base >> 5) + slot;
+            const int64_t p0 = op.slice_ptr[sl], p1 = op.slice_ptr[sl + 1];
+            T a = 0;
+#pragma unroll 8
+            for (int64_t e = p0 + lane; e < p1; e += 32) a += op.sval[e] * op.x[op.scol[e]];
+            const int pr = op.perm[(sl << 5) + lane];
+            if (pr >= 0) op.out[pr] = (op.src == SRC_SPMV) ? a * sc : op.b[pr] - a;
+        }
+        __syncthreads();      // the block's own writes are visible to it now
+    }
     for (int64_t base = r0; base < r1; base += RGM_TILE) {
         const int nrow = (int)min((int64_t)RGM_TILE, r1 - base);
         // ---- phase 1: produce and store w on this tile
-        if (op.src == SRC_SPMV || op.src == SRC_RES) {
+        if (spmv_src && ntiles_blk > 1) {
+            if ((int)threadIdx.x < nrow) ws[threadIdx.x] = op.out[base + threadIdx.x];
+        } else if (spmv_src) {
             // one warp per 32-row slice of the tile, one lane per row; the
             // slice's entries are independent loads (unrolled below)
             const int64_t sl = (base >> 5) + warp;
