@@ -22,6 +22,7 @@ _lib = None
 _lock = threading.Lock()
 
 PLAIN, DEFLATED, AUGMENTED = 0, 1, 2
+PROJ_OBLIQUE, PROJ_ORTHOGONAL, PROJ_LS = 0, 1, 2
 OK, W_NOT_CONVERGED, W_SINGULAR_COARSE = 0, 1, 2
 
 
@@ -48,7 +49,7 @@ class _Csr(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("mode", C.c_int), ("m", C.c_int), ("rtol", C.c_double), ("maxit", C.c_int),
-                ("start_r", C.c_int)]
+                ("start_r", C.c_int), ("proj", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -97,6 +98,8 @@ def lib():
                                        C.POINTER(_Stats), C.POINTER(C.c_int)]
             L.orc_apply_oblique.argtypes = [C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                             C.c_void_p, C.c_void_p]
+            L.orc_apply_projector.argtypes = [C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
+                                              C.c_void_p, C.c_void_p]
             L.orc_coarse_setup.argtypes = [C.POINTER(_Csr), C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
             L.orc_svd_left.argtypes = [C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
             L.orc_recycle_from_window.argtypes = [C.c_int64, C.c_int, C.c_void_p, C.c_int, C.c_int,
@@ -238,7 +241,7 @@ def spmv(A: Csr, x):
 
 
 def gmres(A: Csr, b, x_in=None, U=None, mode=PLAIN, m=30, rtol=1e-10, maxit=10000,
-          start_r=False, hist_len=0):
+          start_r=False, hist_len=0, proj=PROJ_OBLIQUE):
     """Returns (x, stats dict, hist)."""
     b = _f64(b)
     x = _f64(x_in).copy() if x_in is not None else np.zeros(A.n)
@@ -247,7 +250,7 @@ def gmres(A: Csr, b, x_in=None, U=None, mode=PLAIN, m=30, rtol=1e-10, maxit=1000
     if U is not None and np.asarray(U).size:
         Uc = _colmajor(U)
         k = Uc.shape[1]
-    o = _Opts(mode, m, rtol, maxit, int(start_r))
+    o = _Opts(mode, m, rtol, maxit, int(start_r), int(proj))
     st = _Stats()
     hist = np.zeros(hist_len) if hist_len else None
     rc = lib().orc_gmres(C.byref(A.s), _p(b), _p(x), _p(Uc), k, C.byref(o), C.byref(st),
@@ -261,14 +264,14 @@ def gmres(A: Csr, b, x_in=None, U=None, mode=PLAIN, m=30, rtol=1e-10, maxit=1000
 
 
 def gmres_ir(A: Csr, b, x_in=None, U=None, mode=PLAIN, m=30, rtol=1e-8, maxit=20000,
-             inner_rtol=1e-5, inner_cycles=2, max_refinements=50):
+             inner_rtol=1e-5, inner_cycles=2, max_refinements=50, proj=PROJ_OBLIQUE):
     b = _f64(b)
     x = _f64(x_in).copy() if x_in is not None else np.zeros(A.n)
     k, Uc = 0, None
     if U is not None and np.asarray(U).size:
         Uc = _colmajor(U)
         k = Uc.shape[1]
-    o = _Opts(mode, m, rtol, maxit, 0)
+    o = _Opts(mode, m, rtol, maxit, 0, int(proj))
     st = _Stats()
     nref = C.c_int(0)
     rc = lib().orc_gmres_ir(C.byref(A.s), _p(b), _p(x), _p(Uc), k, C.byref(o), inner_rtol,
@@ -292,6 +295,16 @@ def apply_oblique(U, W, E, v):
     v = _f64(v)
     out = np.zeros_like(v)
     rc = lib().orc_apply_oblique(Uc.shape[0], Uc.shape[1], _p(Uc), _p(Wc), _p(Ec), _p(v), _p(out))
+    return out, rc
+
+
+def apply_projector(U, W, proj, v):
+    """P v for the projector proj (PROJ_*) of Table 1, W = A U."""
+    Uc, Wc = _colmajor(U), _colmajor(W)
+    v = _f64(v)
+    out = np.zeros_like(v)
+    rc = lib().orc_apply_projector(Uc.shape[0], Uc.shape[1], _p(Uc), _p(Wc), int(proj), _p(v),
+                                   _p(out))
     return out, rc
 
 

@@ -17,13 +17,21 @@
  *    (Table 1 "augmented oblique") the iterates coincide when P r0 = r0.
  *  - Sec. 3.1, Eq. def_aug_S_space / def_aug_C_space: augmented search space
  *    S = K_j(A, r0) + span U and constraint space A S.
+ *  - Sec. 3.3, Table 1 (and Eq. P_A_variant): the other two projectors of the
+ *    deflated family, orthogonal P = I - U (U^T U)^{-1} U^T and least squares
+ *    P = I - A U (U^T A^T A U)^{-1} U^T A^T; Sec. 4.4, Eq. augmented_iterate:
+ *    with the orthogonal projector every cycle starts from the projection guess.
  * Readings where the paper is silent: Arnoldi uses classical Gram-Schmidt with
  * one full re-orthogonalisation (CGS2); the stopping test is the true relative
  * residual ||b - A x|| / ||b|| <= rtol at the end of each cycle, with the
  * Givens estimate |g_{j+1}| ending a cycle early; happy breakdown when
  * h_{j+1,j} <= 1e-14 ||A v_j||; after each deflated cycle the coarse correction
  * x += U E^{-1} U^T (b - A x) is applied (P A x = P b alone does not give
- * A x = b); in augmented mode the k columns A U are appended to the Arnoldi
+ * A x = b); with the least-squares projector the correction is
+ * x += U (W^T W)^{-1} W^T (b - A x), W = A U, for which I - A Q equals P as
+ * U E^{-1} U^T does for the oblique one, so the true residual after the
+ * correction is the minimised one; the orthogonal projector has no such Q and
+ * keeps the oblique correction (the projection guess of the next cycle); in augmented mode the k columns A U are appended to the Arnoldi
  * basis at the end of each cycle and the least-squares problem is solved over
  * K_J(A, r) + span U; E is declared singular when an LU pivot falls below
  * 1e-13 times max(largest pivot, max_i ||u_i|| ||A u_i||), and the solve then
@@ -140,6 +148,40 @@ int orc_apply_oblique(int64_t n, int k, const double *U, const double *W, const 
     return rc;
 }
 
+int orc_apply_projector(int64_t n, int k, const double *U, const double *W, int proj,
+                        const double *v_in, double *v_out)
+{
+    if (n < 1 || k < 1 || !U || !W || !v_in || !v_out || proj < 0 || proj > 2) return ORC_E_ARG;
+    if (proj == ORC_PROJ_OBLIQUE) {
+        double *E = malloc(sizeof(double) * k * k);
+        if (!E) return ORC_E_NOMEM;
+        for (int j = 0; j < k; ++j)
+            for (int i = 0; i < k; ++i) E[i + j * k] = dot(n, U + i * n, W + j * n);
+        int rc = orc_apply_oblique(n, k, U, W, E, v_in, v_out);
+        free(E);
+        return rc;
+    }
+    const double *Y = (proj == ORC_PROJ_LS) ? W : U;
+    double *G = malloc(sizeof(double) * k * k), *cv = malloc(sizeof(double) * k);
+    int *piv = malloc(sizeof(int) * k);
+    if (!G || !cv || !piv) { free(G); free(cv); free(piv); return ORC_E_NOMEM; }
+    double sc = 0.0;
+    for (int j = 0; j < k; ++j) {
+        for (int i = 0; i < k; ++i) G[i + j * k] = dot(n, Y + i * n, Y + j * n);
+        if (G[j + j * k] > sc) sc = G[j + j * k];
+    }
+    int rc = lu_factor(k, G, piv, sc);
+    for (int i = 0; i < k; ++i) cv[i] = dot(n, Y + i * n, v_in);
+    lu_solve(k, G, piv, cv);
+    for (int64_t r = 0; r < n; ++r) {
+        double s = v_in[r];
+        for (int i = 0; i < k; ++i) s -= Y[r + i * n] * cv[i];
+        v_out[r] = s;
+    }
+    free(G); free(cv); free(piv);
+    return rc;
+}
+
 /* ---- the solver core, shared by the FP64 solve and the IR inner solve ---- */
 typedef struct {
     const orc_csr *A;
@@ -147,22 +189,27 @@ typedef struct {
     int f32;                /* round stored vectors to binary32                     */
     int mode, m, start_r, k;
     const double *U, *W;    /* n x k, already rounded when f32                     */
-    const double *LU;       /* LU of E = U^T A U (FP64)                            */
+    const double *LU;       /* LU of E = U^T A U (FP64): projection guess          */
     const int *piv;
+    /* deflated family (Table 1): P w = w - Zp Gp^{-1} Yp^T w, and the cycle-end
+     * correction x += U Gc^{-1} Yc^T (b - A x) */
+    const double *Yp, *Zp, *LUP, *Yc, *LUC;
+    const int *pivP, *pivC;
     int maxit, max_cycles;
     double tol_abs;         /* stop when ||b - A x|| <= tol_abs                     */
     double *hist;
     int hist_len, hist_count;
 } core_t;
 
-/* x <- x + U E^{-1} U^T (b - A x) : the coarse correction / projection guess */
-static void coarse_correct(core_t *c, const double *b, double *x, double *r, double *cv)
+/* x <- x + U G^{-1} Y^T (b - A x) */
+static void correct(core_t *c, const double *Y, const double *LU, const int *piv,
+                    const double *b, double *x, double *r, double *cv)
 {
     const int64_t n = c->A->n;
     spmv_vals(c->A, c->val, x, r, c->f32);
     for (int64_t i = 0; i < n; ++i) r[i] = rd(c->f32, b[i] - r[i]);
-    for (int i = 0; i < c->k; ++i) cv[i] = dot(n, c->U + i * n, r);
-    lu_solve(c->k, c->LU, c->piv, cv);
+    for (int i = 0; i < c->k; ++i) cv[i] = dot(n, Y + i * n, r);
+    lu_solve(c->k, LU, piv, cv);
     for (int64_t i = 0; i < n; ++i) {
         double s = x[i];
         for (int j = 0; j < c->k; ++j) s += c->U[i + j * n] * cv[j];
@@ -170,17 +217,58 @@ static void coarse_correct(core_t *c, const double *b, double *x, double *r, dou
     }
 }
 
-/* w <- P w = w - W E^{-1} U^T w */
+/* x <- x + U E^{-1} U^T (b - A x) : the projection guess (Eq. projection_t_s) */
+static void coarse_correct(core_t *c, const double *b, double *x, double *r, double *cv)
+{
+    correct(c, c->U, c->LU, c->piv, b, x, r, cv);
+}
+
+/* the correction after a deflated cycle */
+static void cycle_correct(core_t *c, const double *b, double *x, double *r, double *cv)
+{
+    correct(c, c->Yc, c->LUC, c->pivC, b, x, r, cv);
+}
+
+/* w <- P w = w - Zp Gp^{-1} Yp^T w */
 static void project(core_t *c, double *w, double *cv)
 {
     const int64_t n = c->A->n;
-    for (int i = 0; i < c->k; ++i) cv[i] = dot(n, c->U + i * n, w);
-    lu_solve(c->k, c->LU, c->piv, cv);
+    for (int i = 0; i < c->k; ++i) cv[i] = dot(n, c->Yp + i * n, w);
+    lu_solve(c->k, c->LUP, c->pivP, cv);
     for (int64_t i = 0; i < n; ++i) {
         double s = w[i];
-        for (int j = 0; j < c->k; ++j) s -= c->W[i + j * n] * cv[j];
+        for (int j = 0; j < c->k; ++j) s -= c->Zp[i + j * n] * cv[j];
         w[i] = rd(c->f32, s);
     }
+}
+
+/* Factor E (in LU on entry) and, for the orthogonal and least-squares
+ * projectors, the Gram matrix G = Y^T Y of Y = U or Y = W into LUP; wire the
+ * projector and the cycle-end correction of the method into c.  Y, Z given to
+ * c are Uv / Wv (the stored, possibly binary32-rounded copies). */
+static int recycle_setup(core_t *c, int64_t n, int k, const double *U, const double *W,
+                         const double *Uv, const double *Wv, int proj, double *LU, int *piv,
+                         double *LUP, int *pivP)
+{
+    if (lu_factor(k, LU, piv, coarse_scale(n, k, U, W)) != ORC_OK) return ORC_W_SINGULAR_COARSE;
+    c->U = Uv; c->W = Wv; c->LU = LU; c->piv = piv; c->k = k;
+    if (proj == ORC_PROJ_ORTHOGONAL || proj == ORC_PROJ_LS) {
+        const double *Y = (proj == ORC_PROJ_LS) ? W : U;
+        double sc = 0.0;
+        for (int j = 0; j < k; ++j) {
+            for (int i = 0; i < k; ++i) LUP[i + j * k] = dot(n, Y + i * n, Y + j * n);
+            if (LUP[j + j * k] > sc) sc = LUP[j + j * k];
+        }
+        if (lu_factor(k, LUP, pivP, sc) != ORC_OK) return ORC_W_SINGULAR_COARSE;
+        const double *Yv = (proj == ORC_PROJ_LS) ? Wv : Uv;
+        c->Yp = Yv; c->Zp = Yv; c->LUP = LUP; c->pivP = pivP;
+        if (proj == ORC_PROJ_LS) { c->Yc = Wv; c->LUC = LUP; c->pivC = pivP; }
+        else { c->Yc = Uv; c->LUC = LU; c->pivC = piv; }
+    } else {
+        c->Yp = Uv; c->Zp = Wv; c->LUP = LU; c->pivP = piv;
+        c->Yc = Uv; c->LUC = LU; c->pivC = piv;
+    }
+    return ORC_OK;
 }
 
 /* classical Gram-Schmidt with one re-orthogonalisation against V[:, 0..nb-1];
@@ -328,7 +416,7 @@ static int core_solve(core_t *c, const double *b, double *x, int *iters_out, int
             for (int a = 0; a < naug; ++a) s += c->U[t + (int64_t)aug_idx[a] * n] * y[J + a];
             x[t] = rd(c->f32, s);
         }
-        if (c->mode == ORC_DEFLATED) coarse_correct(c, b, x, r, cv);
+        if (c->mode == ORC_DEFLATED) cycle_correct(c, b, x, r, cv);
         spmv_vals(c->A, c->val, x, r, c->f32);
         for (int64_t i = 0; i < n; ++i) r[i] = rd(c->f32, b[i] - r[i]);
         double beta_new = nrm2(n, r);
@@ -363,28 +451,30 @@ int orc_gmres(const orc_csr *A, const double *b, double *x, const double *U, int
     c.maxit = o->maxit; c.max_cycles = 1 << 30;
     c.tol_abs = o->rtol * bnorm;
     c.hist = hist; c.hist_len = hist ? hist_len : 0;
-    double *W = NULL, *LU = NULL, *cv = NULL, *r = NULL;
-    int *piv = NULL;
+    double *W = NULL, *LU = NULL, *LUP = NULL, *cv = NULL, *r = NULL;
+    int *piv = NULL, *pivP = NULL;
     int status = ORC_OK;
     if (c.mode != ORC_PLAIN) {
         W = malloc(sizeof(double) * n * k);
         LU = malloc(sizeof(double) * k * k);
+        LUP = malloc(sizeof(double) * k * k);
         piv = malloc(sizeof(int) * k);
+        pivP = malloc(sizeof(int) * k);
         cv = malloc(sizeof(double) * k);
         r = malloc(sizeof(double) * n);
         orc_coarse_setup(A, U, k, W, LU);
-        if (lu_factor(k, LU, piv, coarse_scale(n, k, U, W)) != ORC_OK) {
+        if (recycle_setup(&c, n, k, U, W, U, W, o->proj, LU, piv, LUP, pivP) != ORC_OK) {
             status = ORC_W_SINGULAR_COARSE;
             c.mode = ORC_PLAIN;
+            c.k = 0;
         } else {
-            c.U = U; c.W = W; c.LU = LU; c.piv = piv; c.k = k;
             coarse_correct(&c, b, x, r, cv);     /* projection initial guess */
         }
     }
     int iters, cycles;
     double res;
     int rc = core_solve(&c, b, x, &iters, &cycles, &res);
-    free(W); free(LU); free(piv); free(cv); free(r);
+    free(W); free(LU); free(LUP); free(piv); free(pivP); free(cv); free(r);
     if (rc) return rc;
     if (hist) for (int i = 0; i < c.hist_count; ++i) hist[i] /= bnorm;
     if (status == ORC_OK && res > o->rtol * bnorm) status = ORC_W_NOT_CONVERGED;
@@ -411,8 +501,8 @@ int orc_gmres_ir(const orc_csr *A, const double *b, double *x, const double *U, 
     int mode = (k > 0 && U) ? o->mode : ORC_PLAIN, status = ORC_OK;
     double *Af = malloc(sizeof(double) * nnz), *r = malloc(sizeof(double) * n);
     double *d = malloc(sizeof(double) * n), *tmp = malloc(sizeof(double) * n);
-    double *W = NULL, *LU = NULL, *Uf = NULL, *Wf = NULL, *cv = NULL;
-    int *piv = NULL;
+    double *W = NULL, *LU = NULL, *LUP = NULL, *Uf = NULL, *Wf = NULL, *cv = NULL;
+    int *piv = NULL, *pivP = NULL;
     for (int64_t i = 0; i < nnz; ++i) Af[i] = (double)(float)A->val[i];
     core_t c;
     memset(&c, 0, sizeof c);
@@ -420,13 +510,16 @@ int orc_gmres_ir(const orc_csr *A, const double *b, double *x, const double *U, 
     c.maxit = o->maxit; c.max_cycles = inner_cycles;
     if (mode != ORC_PLAIN) {
         W = malloc(sizeof(double) * n * k); LU = malloc(sizeof(double) * k * k);
+        LUP = malloc(sizeof(double) * k * k); pivP = malloc(sizeof(int) * k);
         piv = malloc(sizeof(int) * k); cv = malloc(sizeof(double) * k);
         Uf = malloc(sizeof(double) * n * k); Wf = malloc(sizeof(double) * n * k);
-        orc_coarse_setup(A, U, k, W, LU);            /* E in FP64 */
-        if (lu_factor(k, LU, piv, coarse_scale(n, k, U, W)) != ORC_OK) { status = ORC_W_SINGULAR_COARSE; mode = ORC_PLAIN; }
-        else {
-            for (int64_t i = 0; i < n * k; ++i) { Uf[i] = (double)(float)U[i]; Wf[i] = (double)(float)W[i]; }
-            c.U = Uf; c.W = Wf; c.LU = LU; c.piv = piv; c.k = k;
+        orc_coarse_setup(A, U, k, W, LU);            /* E (and G) in FP64 */
+        for (int64_t i = 0; i < n * k; ++i) { Uf[i] = (double)(float)U[i]; Wf[i] = (double)(float)W[i]; }
+        if (recycle_setup(&c, n, k, U, W, Uf, Wf, o->proj, LU, piv, LUP, pivP) != ORC_OK) {
+            status = ORC_W_SINGULAR_COARSE;
+            mode = ORC_PLAIN;
+            c.k = 0;
+        } else {
             /* FP64 projection initial guess on the outer iterate */
             core_t c64 = c;
             c64.val = A->val; c64.f32 = 0; c64.U = U; c64.W = W;
@@ -461,6 +554,7 @@ int orc_gmres_ir(const orc_csr *A, const double *b, double *x, const double *U, 
         st->status = status; st->true_relres = res / bnorm;
     }
     if (refinements) *refinements = nref;
-    free(Af); free(r); free(d); free(tmp); free(W); free(LU); free(piv); free(Uf); free(Wf); free(cv);
+    free(Af); free(r); free(d); free(tmp); free(W); free(LU); free(LUP); free(piv); free(pivP);
+    free(Uf); free(Wf); free(cv);
     return status;
 }

@@ -81,13 +81,19 @@ typedef struct {
 #define ORC_DEFLATED   1   /* deflated oblique, Table 1 row 5, + coarse correction */
 #define ORC_AUGMENTED  2   /* Sec. 3.1: S = K_m(A, r) + span U, C = A S            */
 
+/* Projector of the ORC_DEFLATED family (Table 1): the Krylov operator is P A. */
+#define ORC_PROJ_OBLIQUE    0   /* P = I - W E^{-1} U^T, W = A U, E = U^T W            */
+#define ORC_PROJ_ORTHOGONAL 1   /* P = I - U (U^T U)^{-1} U^T (Eq. P_A_variant)       */
+#define ORC_PROJ_LS         2   /* P = I - W (W^T W)^{-1} W^T                          */
+
 typedef struct {
     int mode;          /* ORC_PLAIN / ORC_DEFLATED / ORC_AUGMENTED                  */
     int m;             /* restart length                                           */
     double rtol;       /* stop when ||b - A x|| <= rtol ||b||                       */
     int maxit;         /* cap on Arnoldi steps (operator applications)             */
-    int start_r;       /* DEFLATED only: 1 = start vector r (Table 1 "augmented
-                          oblique"), 0 = P r (Table 1 "deflated oblique")          */
+    int start_r;       /* DEFLATED only: 1 = start vector r (Table 1 "augmented"
+                          rows), 0 = P r (Table 1 "deflated" rows)                 */
+    int proj;          /* DEFLATED only: ORC_PROJ_*                                */
 } orc_opts;
 
 typedef struct {
@@ -104,6 +110,9 @@ int orc_coarse_setup(const orc_csr *A, const double *U, int k, double *W, double
 /* v_out = (I - W E^{-1} U^T) v_in ; returns ORC_W_SINGULAR_COARSE if E is singular. */
 int orc_apply_oblique(int64_t n, int k, const double *U, const double *W, const double *E,
                       const double *v_in, double *v_out);
+/* v_out = P v_in for the projector proj (ORC_PROJ_*), W = A U given. */
+int orc_apply_projector(int64_t n, int k, const double *U, const double *W, int proj,
+                        const double *v_in, double *v_out);
 /* Solve A x = b.  x: in = x_in, out = solution.  U: n x k (k may be 0).
  * hist (optional, length hist_len): relative residual estimate |g_{j+1}|/||b||
  * after every Arnoldi step, in order. */

@@ -254,3 +254,103 @@ def test_gmres_ir_reaches_fp64_residual(orc, mode):
     assert st["status"] == 0 and st["true_relres"] <= 1e-8 and st["refinements"] >= 2
     xs = np.linalg.solve(A.dense(), b)
     assert np.linalg.norm(x - xs) <= 1e-6 * np.linalg.norm(xs)
+
+
+# ------------------------------------------------------------------ Table 1 projector variants
+def _explicit_projectors(A, U):
+    """The three projectors of Table 1 as dense matrices (Eq. P_A_variant for
+    the orthogonal one, so U need not be orthonormal)."""
+    n = A.shape[0]
+    W = A @ U
+    I = np.eye(n)
+    return {0: I - W @ np.linalg.solve(U.T @ W, U.T),
+            1: I - U @ np.linalg.solve(U.T @ U, U.T),
+            2: I - W @ np.linalg.solve(W.T @ W, W.T)}
+
+
+@pytest.mark.parametrize("proj", [0, 1, 2])
+def test_table1_projector_identities(orc, proj):
+    A, _, U = _setup_recycle(30, 4, 100)
+    U = U @ (np.triu(synth.random_matrix(4, 4, 101)) + 2 * np.eye(4))   # not orthonormal
+    W = A @ U
+    v = synth.random_vector(30, 102)
+    Pv, rc = orc.apply_projector(U, W, proj, v)
+    assert rc == 0
+    np.testing.assert_allclose(Pv, _explicit_projectors(A, U)[proj] @ v, atol=1e-11)
+    PPv, _ = orc.apply_projector(U, W, proj, Pv)
+    np.testing.assert_allclose(PPv, Pv, atol=1e-11)                        # P^2 = P
+    killed = {0: W, 1: U, 2: W}[proj]                                       # P kills W or U
+    for i in range(4):
+        Pk, _ = orc.apply_projector(U, W, proj, killed[:, i])
+        assert np.abs(Pk).max() < 1e-11 * np.abs(killed[:, i]).max()
+    if proj in (1, 2):                                                      # orthogonal projectors
+        w2 = synth.random_vector(30, 103)
+        Pw2, _ = orc.apply_projector(U, W, proj, w2)
+        assert abs(Pv @ w2 - v @ Pw2) < 1e-11 * np.linalg.norm(v) * np.linalg.norm(w2)
+
+
+@pytest.mark.parametrize("proj", [1, 2])
+@pytest.mark.parametrize("start_r", [False, True])
+@pytest.mark.parametrize("j", [1, 3, 6])
+def test_table1_variant_fixed_steps_brute_force(orc, proj, start_r, j):
+    """One cycle of j steps of the Table 1 method: x0 = U E^-1 U^T b, Krylov
+    operator P A, start vector P r0 (deflated) or r0 (augmented), y minimising
+    ||s - P A K y|| by numpy least squares over the explicit power basis, then
+    the cycle-end correction x += Q (b - A x) with Q = U (W^T W)^-1 W^T (LS) or
+    U E^-1 U^T (orthogonal)."""
+    A, b, U = _setup_recycle(25, 3, 110 + proj)
+    x, st, _ = orc.gmres(orc.Csr.from_dense(A), b, U=U, mode=1, m=30, rtol=0.0, maxit=j,
+                         start_r=start_r, proj=proj)
+    assert st["iters"] == j and st["k_used"] == 3
+    W = A @ U
+    E = U.T @ W
+    P = _explicit_projectors(A, U)[proj]
+    Qc = U @ np.linalg.solve(W.T @ W, W.T) if proj == 2 else U @ np.linalg.solve(E, U.T)
+    x0 = U @ np.linalg.solve(E, U.T @ b)
+    r0 = b - A @ x0
+    s = r0 if start_r else P @ r0
+    K = _krylov(P @ A, s, j)
+    y, *_ = np.linalg.lstsq(P @ A @ K, s, rcond=None)
+    xk = x0 + K @ y
+    xk = xk + Qc @ (b - A @ xk)
+    np.testing.assert_allclose(x, xk, rtol=1e-9, atol=1e-11)
+
+
+def test_ls_deflated_true_residual_is_the_minimised_one(orc):
+    """Deflated LS (the GCRO inner iteration): after the correction with
+    Q = U (W^T W)^-1 W^T, I - A Q = P, so the true residual of each cycle equals
+    the Givens estimate, as for the oblique projector with Q = U E^-1 U^T."""
+    A, b, U = _setup_recycle(40, 4, 120)
+    Ac = orc.Csr.from_dense(A)
+    for proj in (2, 0):
+        for j in (2, 5, 9):
+            x, st, hist = orc.gmres(Ac, b, U=U, mode=1, m=30, rtol=0.0, maxit=j, proj=proj,
+                                    hist_len=j)
+            assert abs(st["true_relres"] - hist[j - 1]) <= 1e-10 * hist[j - 1] + 1e-14
+
+
+def test_orthogonal_start_vectors_coincide(orc):
+    """With the projection guess the first residual is orthogonal to U
+    (U^T (I - W E^-1 U^T) = 0), so Table 1's augmented and deflated orthogonal
+    methods start from the same vector and give the same iterates."""
+    A, b, U = _setup_recycle(40, 4, 130)
+    Ac = orc.Csr.from_dense(A)
+    for maxit in (3, 10):
+        x1, _, _ = orc.gmres(Ac, b, U=U, mode=1, m=8, rtol=0.0, maxit=maxit, proj=1)
+        x2, _, _ = orc.gmres(Ac, b, U=U, mode=1, m=8, rtol=0.0, maxit=maxit, proj=1, start_r=True)
+        np.testing.assert_allclose(x1, x2, rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("proj", [1, 2])
+def test_table1_variants_solve_fe_step(orc, proj):
+    """Both variants reach the true residual 1e-10 on a Q1 step (restarted)."""
+    w = synth.Q1_32
+    a8, beta = synth.sequence_draws(w, 0)
+    u0 = orc.u0_field(w.p, w.N, a8)
+    rp, col, val, b = orc.step_system(w.p, w.N, w.eps, w.dt, beta, u0)
+    A = orc.Csr(rp, col, val)
+    U = _orth(np.stack([u0, synth.random_vector(len(b), 4), synth.random_vector(len(b), 5)], 1))
+    x, st, _ = orc.gmres(A, b, U=U, mode=1, m=w.m, rtol=1e-10, proj=proj)
+    assert st["status"] == 0 and st["true_relres"] <= 1e-10
+    xs = np.linalg.solve(A.dense(), b)
+    np.testing.assert_allclose(x, xs, rtol=0, atol=1e-8 * np.abs(xs).max())
