@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_ir"])
     ap.add_argument("--cpu-steps", type=int, default=0, help="oracle steps for cpu_baseline (0: auto)")
     ap.add_argument("--quick", action="store_true", help="skip e2e, cpu baseline and side modes")
+    ap.add_argument("--launch-policy", default="auto", choices=["auto", "per_pass"],
+                    help="Arnoldi steps of a cycle in one cooperative launch (auto) or one launch per pass")
     return ap.parse_args()
 
 
@@ -154,7 +156,7 @@ def run_sequence(rg, torch, w, seq, mode, precision, warmup, steps, profile=Fals
     rp, col = fe.pattern()
     rtol = w.rtol if precision == "fp64" else 1e-8
     solver = rg.Solver(fe.n, m=w.m, k=w.k, window=w.window, svd_interval=w.ell, mode=mode,
-                       precision=precision, rtol=rtol, stream=stream)
+                       precision=precision, rtol=rtol, stream=stream, launch_policy=LAUNCH_POLICY[0])
     u0 = fe.initial_field(a8)
     u = torch.tensor(u0, dtype=torch.float64, device=dev)
     solver.set_operator_csr(rp, col, torch.zeros(len(col), dtype=torch.float64).numpy())
@@ -211,6 +213,7 @@ def run_e2e(rg, np, w, seq, mode, precision, warmup, steps, inputs, torch):
     fe.close()
     rtol = w.rtol if precision == "fp64" else 1e-8
     s = rg.Solver(n, m=w.m, k=w.k, window=w.window, svd_interval=w.ell, mode=mode,
+                  launch_policy=LAUNCH_POLICY[0],
                   precision=precision, rtol=rtol)
     s.set_operator_csr(rp, col, np.zeros(len(col)))
     pin_val = torch.empty(len(col), dtype=torch.float64).pin_memory()
@@ -237,7 +240,11 @@ def run_e2e(rg, np, w, seq, mode, precision, warmup, steps, inputs, torch):
     return dict(sec=times[warmup:], h2d=8 * nnz + 8 * n * 3, d2h=8 * n)
 
 
+LAUNCH_POLICY = ["auto"]
+
+
 def ours(args):
+    LAUNCH_POLICY[0] = args.launch_policy
     import numpy as np
     import torch
 
@@ -324,7 +331,7 @@ def ours(args):
         "data": "synthetic",
         "config": {"workload": w.name, "n": n, "nnz": nnz, "p": w.p, "N": w.N, "m": w.m, "k": w.k,
                    "window": w.window, "svd_interval": w.ell, "mode": args.mode,
-                   "precision": args.precision,
+                   "precision": args.precision, "launch_policy": args.launch_policy,
                    "rtol": w.rtol if args.precision == "fp64" else 1e-8,
                    "l2": "flushed (256 MiB write) before every timed step",
                    "parallelism": "replicas" if ws > 1 else "single"},

@@ -64,6 +64,13 @@ typedef enum {
                             refinement loop (residual, Hessenberg, E and SVD stay binary64)  */
 } rgm_precision;
 
+typedef enum {
+    RGM_LAUNCH_AUTO = 0,     /* the Arnoldi steps of a cycle run in one cooperative launch
+                                (grid barriers between the fused passes) when the grid fits
+                                on the device at once; otherwise one launch per pass        */
+    RGM_LAUNCH_PER_PASS = 1  /* one launch per fused pass (same arithmetic)                 */
+} rgm_launch_policy;
+
 typedef struct {
     int64_t n;            /* system size (fixed for the handle's life)                      */
     int m;                /* restart length, 1..64                                          */
@@ -77,6 +84,7 @@ typedef struct {
     int maxit;            /* cap on Arnoldi steps per solve                                 */
     int inner_cycles;     /* FP32_IR: GMRES cycles per refinement                           */
     int max_refinements;  /* FP32_IR: cap on refinement steps                               */
+    int launch_policy;    /* rgm_launch_policy                                              */
     double rtol;          /* converged when ||b - A x||_2 <= rtol ||b||_2                   */
     double inner_rtol;    /* FP32_IR: inner solve to inner_rtol * ||r||                     */
     double rel_drop;      /* drop singular values below rel_drop * sigma_1                 */
@@ -97,6 +105,12 @@ typedef struct rgm_solver_s *rgm_solver;
 /* Fill *cfg with defaults: m 30, k 8, window 16, ell 1, deflated, FP64,
  * rtol 1e-10, maxit 20000, inner_rtol 1e-4, inner_cycles 2, rel_drop 1e-7. */
 int rgm_config_default(rgm_config *cfg);
+
+/* Text of the CUDA error behind the last RGM_E_CUDA or RGM_E_OOM returned on
+ * the calling thread (error name, message, failing call); "" if none.  The
+ * string belongs to the library and stays valid until the thread's next
+ * failing call. */
+const char *rgm_last_error(void);
 
 /* Create a solver for systems of size cfg->n on the current device.  Allocates
  * the Krylov basis (n x (m+k+1)), the recycle space and the snapshot window.
@@ -145,6 +159,25 @@ int rgm_get_singular_values(rgm_solver s, double *sigma, int *count);
 /* Clear the snapshot window and the recycle space. */
 int rgm_reset_recycling(rgm_solver s);
 
+/* Checkpoint / resume of the recycling state that Algorithm 1 carries from
+ * one system of the sequence to the next: the snapshot window (its stored
+ * columns, ring position and update count) and the recycle space U.  Not
+ * described in the paper; it lets a sequence continue in a new handle or a
+ * new process with results identical to the uninterrupted run.  The operator
+ * is not part of the state (each step sets its own), nor are the singular
+ * values of the last update.
+ *
+ * rgm_export_state: with buf == NULL, *bytes receives the size needed; else
+ * *bytes must hold buf's capacity, the state is written to buf (host memory,
+ * native byte order) and *bytes receives the size written.  Waits for the
+ * handle's stream.  RGM_E_ARG if the capacity is too small.
+ * rgm_import_state: buf/bytes as written by rgm_export_state for a handle
+ * with the same n, window and k >= the stored recycle dimension; RGM_E_ARG
+ * otherwise (the handle is then unchanged).  The next solve rebuilds
+ * W = A U and E from the operator it is given. */
+int rgm_export_state(rgm_solver s, void *buf, size_t *bytes);
+int rgm_import_state(rgm_solver s, const void *buf, size_t bytes);
+
 /* y = A x with the solver's operator (the SpMV of every Arnoldi step). */
 int rgm_spmv(rgm_solver s, const double *x, double *y, int flags);
 
@@ -161,7 +194,9 @@ const char *rgm_status_string(int code);
 #define RGM_PROF_OTHER        3   /* residuals, start vectors, coarse, updates   */
 #define RGM_PROF_GRAM         4   /* Gram matrices (E, snapshot window, CholQR)  */
 #define RGM_PROF_SMALL        5   /* single-block scalar kernels                 */
-#define RGM_PROF_KINDS        6
+#define RGM_PROF_ARNOLDI_CYCLE 6  /* all Arnoldi steps of a cycle in one cooperative
+                                     launch (RGM_LAUNCH_AUTO)                       */
+#define RGM_PROF_KINDS        7
 
 typedef struct {
     double ms;          /* summed device time of the launches                */
@@ -175,6 +210,20 @@ int rgm_profile(rgm_solver s, int enable);
 /* Synchronise the stream and copy the per-kind totals out (nkinds entries);
  * *launches receives every kernel launch since the last reset. */
 int rgm_profile_read(rgm_solver s, rgm_kernel_prof *out, int nkinds, int64_t *launches);
+
+/* ------------------------------------------------------------ bounded-wait self-test
+ * Not part of the method.  The cooperative cycle kernel (RGM_LAUNCH_AUTO)
+ * separates its passes by grid barriers whose waits are bounded: a block that
+ * waits longer than its limit sets a fault flag and returns, and the solve
+ * reports RGM_E_TIMEOUT instead of hanging.  This call exercises exactly that
+ * path on the current device: it launches two blocks that wait at such a
+ * barrier for a generation nothing ever publishes, with the wait limit
+ * limit_ns (1e3 .. 1e9 ns), synchronises, and sets *blocks_gave_up (blocks
+ * whose wait ended without the release: 2 when the limit works) and
+ * *fault_flag (the device-side fault flag: 1).  Allocates and frees a few
+ * hundred KB of device memory; RGM_E_ARG for bad arguments, RGM_E_CUDA on a
+ * CUDA error. */
+int rgm_wait_selftest(int64_t limit_ns, int *blocks_gave_up, int *fault_flag);
 
 /* ------------------------------------------------------------ allocation-free check
  * The paper has no counterpart to this entry point: it serves callers that

@@ -22,6 +22,7 @@ from ._lib import (AUGMENTED, DEFLATED, FP32_IR, FP64, PLAIN, RGM_DEVICE_PTRS,
 
 MODES = {"plain": PLAIN, "deflated": DEFLATED, "augmented": AUGMENTED}
 PRECISIONS = {"fp64": FP64, "fp32_ir": FP32_IR}
+LAUNCH_POLICIES = {"auto": 0, "per_pass": 1}
 
 __all__ = ["Solver", "FE", "residual_noalloc", "RgmError", "MODES", "PRECISIONS", "PLAIN", "DEFLATED", "AUGMENTED",
            "FP64", "FP32_IR", "RGM_W_NOT_CONVERGED", "RGM_W_SINGULAR_COARSE"]
@@ -50,7 +51,8 @@ class Solver:
 
     def __init__(self, n, m=30, k=8, window=16, svd_interval=1, select_smallest=False,
                  mode="deflated", precision="fp64", start_r=False, maxit=20000, inner_cycles=2,
-                 max_refinements=50, rtol=1e-10, inner_rtol=1e-4, rel_drop=1e-7, stream=None):
+                 max_refinements=50, rtol=1e-10, inner_rtol=1e-4, rel_drop=1e-7, stream=None,
+                 launch_policy="auto"):
         L = _lib.load()
         cfg = RgmConfig()
         L.rgm_config_default(C.byref(cfg))
@@ -61,6 +63,8 @@ class Solver:
         cfg.start_r, cfg.maxit, cfg.inner_cycles = int(start_r), maxit, inner_cycles
         cfg.max_refinements, cfg.rtol, cfg.inner_rtol, cfg.rel_drop = (
             max_refinements, rtol, inner_rtol, rel_drop)
+        cfg.launch_policy = LAUNCH_POLICIES[launch_policy] if isinstance(launch_policy, str) \
+            else int(launch_policy)
         cfg.cuda_stream = stream
         self.cfg = cfg
         self.n = n
@@ -153,6 +157,19 @@ class Solver:
     def reset_recycling(self):
         check(self._L.rgm_reset_recycling(self._h), "rgm_reset_recycling")
 
+    def export_state(self):
+        """rgm_export_state: the recycling state (window, U) as bytes."""
+        n = C.c_size_t()
+        check(self._L.rgm_export_state(self._h, None, C.byref(n)), "rgm_export_state")
+        buf = C.create_string_buffer(n.value)
+        check(self._L.rgm_export_state(self._h, buf, C.byref(n)), "rgm_export_state")
+        return buf.raw[:n.value]
+
+    def import_state(self, data):
+        """rgm_import_state: resume from bytes written by export_state."""
+        buf = C.create_string_buffer(bytes(data), len(data))
+        check(self._L.rgm_import_state(self._h, buf, C.c_size_t(len(data))), "rgm_import_state")
+
     def profile(self, enable=True):
         """Reset and switch per-launch CUDA-event timing on or off."""
         check(self._L.rgm_profile(self._h, int(enable)), "rgm_profile")
@@ -179,6 +196,16 @@ class Solver:
         check(self._L.rgm_spmv(self._h, C.c_void_p(xx.ctypes.data), C.c_void_p(y.ctypes.data), 0),
               "rgm_spmv")
         return y
+
+
+def wait_selftest(limit_ns):
+    """rgm_wait_selftest: two blocks wait at a grid barrier that is never
+    released, with the given wait limit.  Returns (blocks that gave up, device
+    fault flag); (2, 1) when the bounded wait works."""
+    L = _lib.load()
+    g, f = C.c_int(), C.c_int()
+    check(L.rgm_wait_selftest(int(limit_ns), C.byref(g), C.byref(f)), "rgm_wait_selftest")
+    return g.value, f.value
 
 
 def residual_noalloc(rowptr, col, val, x, b, r, norms, stream=None):

@@ -31,7 +31,8 @@ class RgmConfig(C.Structure):
     _fields_ = [("n", C.c_int64), ("m", C.c_int), ("k", C.c_int), ("window", C.c_int),
                 ("svd_interval", C.c_int), ("select_smallest", C.c_int), ("mode", C.c_int),
                 ("precision", C.c_int), ("start_r", C.c_int), ("maxit", C.c_int),
-                ("inner_cycles", C.c_int), ("max_refinements", C.c_int), ("rtol", C.c_double),
+                ("inner_cycles", C.c_int), ("max_refinements", C.c_int), ("launch_policy", C.c_int),
+                ("rtol", C.c_double),
                 ("inner_rtol", C.c_double), ("rel_drop", C.c_double), ("cuda_stream", C.c_void_p)]
 
 
@@ -46,7 +47,7 @@ class RgmKernelProf(C.Structure):
 
 
 PROF_KINDS = ["arnoldi_spmv_dots", "arnoldi_cgs1_axpy_dots", "arnoldi_cgs2_axpy_norm", "other_vector",
-              "gram", "small"]
+              "gram", "small", "arnoldi_cycle"]
 
 _lib = None
 _lock = threading.Lock()
@@ -62,6 +63,10 @@ _SIGS = {
     "rgm_set_recycle_space": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_int]),
     "rgm_get_recycle_space": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int),
                                         C.c_int]),
+    "rgm_export_state": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
+    "rgm_import_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "rgm_last_error": (C.c_char_p, []),
+    "rgm_wait_selftest": (C.c_int, [C.c_int64, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "rgm_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(RgmStats)]),
     "rgm_update_recycle_svd": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "rgm_get_singular_values": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
@@ -106,7 +111,12 @@ def load():
 
 class RgmError(RuntimeError):
     def __init__(self, code, what):
-        msg = load().rgm_status_string(code).decode()
+        L = load()
+        msg = L.rgm_status_string(code).decode()
+        if code in (RGM_E_CUDA, RGM_E_OOM):
+            detail = L.rgm_last_error().decode()
+            if detail:
+                msg += f": {detail}"
         super().__init__(f"{what}: {msg} ({code})")
         self.code = code
 

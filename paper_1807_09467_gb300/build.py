@@ -59,7 +59,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".{os.getpid()}.tmp"
-        run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
+        run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-ldl"])
         os.replace(tmp, LIB)
     return LIB
 

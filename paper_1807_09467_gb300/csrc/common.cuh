@@ -33,6 +33,8 @@ struct Small {
     int k;             // recycle columns in use
     int singular;      // E was declared singular
     int k_new;         // recycle dimension chosen by the last window SVD
+    unsigned gen;      // grid-barrier generation of the persistent cycle kernel
+    unsigned fault;    // a bounded device wait gave up (cleared per solve)
     int aug_idx[RGM_KMAX];
     double bnorm, tol_abs, beta, wn0, bs;
     double H[RGM_HLD * RGM_NCOL];         // column-major, leading dimension RGM_HLD
@@ -113,6 +115,29 @@ __device__ __forceinline__ double warp_sum(double v)
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Record the CUDA error behind an RGM_E_CUDA / RGM_E_OOM return (solver.cu).
+void rgm_note_cuda_error(int err, const char *what, int line);
+
+// Scoped memory operations for the grid barrier of the persistent kernel.
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 // Last-block-done: every block calls this after writing its partials; returns

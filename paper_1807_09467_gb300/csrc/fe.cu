@@ -18,13 +18,18 @@
 #include <new>
 #include <vector>
 
+void rgm_note_cuda_error(int err, const char *what, int line);   // solver.cu
+
 extern "C" int rgm_internal_nnz(rgm_solver s, int64_t *nnz);
 extern "C" int rgm_internal_config(rgm_solver s, rgm_config *cfg);
 
 #define CKF(call)                                                            \
     do {                                                                     \
         cudaError_t e_ = (call);                                             \
-        if (e_ != cudaSuccess) return (e_ == cudaErrorMemoryAllocation) ? RGM_E_OOM : RGM_E_CUDA; \
+        if (e_ != cudaSuccess) {                                             \
+            rgm_note_cuda_error((int)e_, #call, __LINE__);                   \
+            return (e_ == cudaErrorMemoryAllocation) ? RGM_E_OOM : RGM_E_CUDA; \
+        }                                                                    \
     } while (0)
 
 struct rgm_fe_s {

@@ -16,6 +16,8 @@
 #include "vec_kernels.cuh"
 #include "svd_kernels.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
@@ -25,10 +27,24 @@
 #include <new>
 #include <vector>
 
+// The CUDA error behind the last RGM_E_CUDA / RGM_E_OOM of this thread
+// (rgm_last_error).
+static thread_local char g_last_error[320] = "";
+
+void rgm_note_cuda_error(int err, const char *what, int line)
+{
+    const cudaError_t e = (cudaError_t)err;
+    std::snprintf(g_last_error, sizeof g_last_error, "%s (%s) in %s [line %d]", cudaGetErrorName(e),
+                  cudaGetErrorString(e), what, line);
+}
+
 #define CK(call)                                                             \
     do {                                                                     \
         cudaError_t e_ = (call);                                             \
-        if (e_ != cudaSuccess) return (e_ == cudaErrorMemoryAllocation) ? RGM_E_OOM : RGM_E_CUDA; \
+        if (e_ != cudaSuccess) {                                             \
+            rgm_note_cuda_error((int)e_, #call, __LINE__);                   \
+            return (e_ == cudaErrorMemoryAllocation) ? RGM_E_OOM : RGM_E_CUDA; \
+        }                                                                    \
     } while (0)
 
 namespace {
@@ -99,6 +115,10 @@ struct rgm_solver_s {
     size_t cycle_rec0 = 0;
     rgm_kernel_prof acc[RGM_PROF_KINDS];
     int64_t launches = 0;
+    std::vector<double> cyc_flops, cyc_bytes;   // cost of the first j steps of a cycle launch
+    // co-resident capacity of cycle_kernel per precision and dot-column bound
+    // (-1: not queried yet)
+    int cycle_cap[2][RGM_MAXDOTS + 2];
 };
 
 static size_t small_header_bytes() { return offsetof(Small, H); }
@@ -173,6 +193,12 @@ static void op_cost(rgm_solver s, const VecOp<T> &op, int nb, int J, double *flo
     *bytes = b;
 }
 
+// NVTX range names, one per profiling kind (a profiler can select or rename
+// launches by them; with no tool attached a range push is a no-op call).
+static const char *const kNvtxKind[RGM_PROF_KINDS] = {
+    "arnoldi_spmv_dots", "arnoldi_cgs1_axpy_dots", "arnoldi_cgs2_axpy_norm", "other_vector", "gram", "small",
+    "arnoldi_cycle"};
+
 template <typename T>
 static int launch(rgm_solver s, const VecOp<T> &op, int kind = RGM_PROF_OTHER, int kry_j = -1,
                   int nb_host = 0, int J_host = 0)
@@ -189,9 +215,14 @@ static int launch(rgm_solver s, const VecOp<T> &op, int kind = RGM_PROF_OTHER, i
         rec.b = pool_event(s);
         cudaEventRecord(rec.a, s->st);
     }
+    nvtxRangePushA(kNvtxKind[kind]);
     const int rc = launch_vec(op, nd_max, s->st);
+    nvtxRangePop();
     ++s->launches;
-    if (rc) return RGM_E_CUDA;
+    if (rc) {
+        rgm_note_cuda_error(rc, "vec_kernel launch", __LINE__);
+        return RGM_E_CUDA;
+    }
     if (s->prof) {
         cudaEventRecord(rec.b, s->st);
         s->pending.push_back(rec);
@@ -206,6 +237,7 @@ struct ProfScope {
     ProfScope(rgm_solver s_, int kind, double flops = 0.0, double bytes = 0.0) : s(s_)
     {
         ++s->launches;
+        nvtxRangePushA(kNvtxKind[kind]);
         if (s->prof) {
             rec.kind = kind; rec.kry_j = -1; rec.flops = flops; rec.bytes = bytes;
             rec.a = pool_event(s);
@@ -215,6 +247,7 @@ struct ProfScope {
     }
     ~ProfScope()
     {
+        nvtxRangePop();
         if (s->prof) {
             cudaEventRecord(rec.b, s->st);
             s->pending.push_back(rec);
@@ -227,7 +260,11 @@ struct ProfScope {
 static void prof_fix_cycle(rgm_solver s, int J)
 {
     for (size_t i = s->cycle_rec0; i < s->pending.size(); ++i)
-        if (s->pending[i].kry_j >= J) {
+        if (s->pending[i].kind == RGM_PROF_ARNOLDI_CYCLE) {
+            const size_t jj = std::min<size_t>((size_t)std::max(J, 0), s->cyc_flops.size() - 1);
+            s->pending[i].flops = s->cyc_flops[jj];
+            s->pending[i].bytes = s->cyc_bytes[jj];
+        } else if (s->pending[i].kry_j >= J) {
             s->pending[i].kind = RGM_PROF_OTHER;
             s->pending[i].flops = 0.0;
             s->pending[i].bytes = 0.0;
@@ -279,7 +316,17 @@ static int launch_gram(rgm_solver s, const T *X, int64_t ldx, int nx, const T *Y
     op.counter = s->counter;
     op.out = out;
     const int ncol = (mode == GRAM_UW) ? 2 * nxmax : nxmax;
-    op.tile = std::min(256, (int)(48 * 1024 / sizeof(double)) / ncol - 1);
+    // the row tile of all ncol columns (tile + 1 doubles each) in dynamic shared
+    // memory, within the 48 KB a launch may use without opting in, less the
+    // kernel's static shared memory
+    static size_t static_smem = (size_t)-1;
+    if (static_smem == (size_t)-1) {
+        cudaFuncAttributes fa;
+        CK(cudaFuncGetAttributes(&fa, gram_kernel<T>));
+        static_smem = fa.sharedSizeBytes;
+    }
+    const int budget = (int)((48 * 1024 - static_smem) / sizeof(double));
+    op.tile = std::min(256, budget / ncol - 1);
     const size_t smem = sizeof(double) * (size_t)ncol * (op.tile + 1);
     {
         const double n = (double)s->n, np_ = (double)npmax;
@@ -294,6 +341,13 @@ static int read_header(rgm_solver s)
 {
     CK(cudaMemcpyAsync(s->hs, s->sm, small_header_bytes(), cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
+    if (s->hs->fault) {
+        // blocks that gave up left the completion counter mid-count: clear it
+        // so that the handle's next solve starts from a clean state
+        CK(cudaMemsetAsync(s->counter, 0, sizeof(unsigned) * 4, s->st));
+        CK(cudaStreamSynchronize(s->st));
+        return RGM_E_TIMEOUT;
+    }
     return RGM_OK;
 }
 
@@ -311,6 +365,8 @@ __global__ void solve_setup_kernel(Small *s, int maxit, int m, int k)
         s->naug = 0;
         s->skip = 0;
         s->breakdown = 0;
+        s->gen = 0u;
+        s->fault = 0u;
     }
 }
 
@@ -351,6 +407,84 @@ static int coarse_setup(rgm_solver s)
     return RGM_OK;
 }
 
+// The three fused passes of an Arnoldi step with CGS2 (operator P A when kdef
+// recycle columns deflate): A v_j and its dots with [U | V], the first
+// Gram-Schmidt update and the dots of the second pass, the second update with
+// ||w|| and the Givens step.  Step j's input column and scale are set per step.
+template <typename T>
+static void arnoldi_passes(rgm_solver s, const Arnoldi<T> &a, int kdef, CycleOp<T> &c)
+{
+    VecOp<T> op = base_op(s, a);
+    op.src = SRC_SPMV; op.x = a.V; op.xscale = 0; op.out = a.w;
+    op.ndU = kdef; op.dnorm = 1; op.dyn = DYN_NDV_NB; op.fin = FIN_ARN1;
+    c.pass[0] = op;
+    op = base_op(s, a);
+    op.src = SRC_AXPY; op.win = a.w; op.out = a.w; op.nW = kdef;
+    op.dyn = DYN_NV_NB | DYN_NDV_NB; op.fin = FIN_ARN2;
+    c.pass[1] = op;
+    op = base_op(s, a);
+    op.src = SRC_AXPY; op.win = a.w; op.dyn = DYN_NV_NB | DYN_OUT_VNB;
+    op.ndW = kdef; op.dnorm = 1; op.fin = FIN_ARN3;
+    c.pass[2] = op;
+    c.m = s->cfg.m;
+}
+
+// The cooperative cycle launch applies when the policy allows it and every
+// block of the grid can be resident at once (checked by occupancy; the
+// cooperative launch itself also refuses a grid that does not fit).
+template <typename T>
+static bool use_cycle_kernel(rgm_solver s, const CycleOp<T> &c, int nd_max)
+{
+    if (s->cfg.launch_policy != RGM_LAUNCH_AUTO || nd_max > RGM_MAXDOTS) return false;
+    int &cap = s->cycle_cap[sizeof(T) == 4 ? 1 : 0][nd_max];
+    if (cap < 0) cap = cycle_capacity(c, nd_max);
+    return s->nblocks <= cap;
+}
+
+template <typename T>
+static int launch_cycle_prof(rgm_solver s, const CycleOp<T> &c, int nd_max)
+{
+    ProfRec rec;
+    if (s->prof) {
+        // algorithmic cost of the first j steps, j = 0..m (booked once J is known)
+        const int m = c.m;
+        s->cyc_flops.assign(m + 1, 0.0);
+        s->cyc_bytes.assign(m + 1, 0.0);
+        for (int j = 0; j < m; ++j) {
+            double f = 0.0, b = 0.0, ft, bt;
+            for (int p = 0; p < 3; ++p) {
+                op_cost(s, c.pass[p], j + 1, j + 1, &ft, &bt);
+                f += ft;
+                b += bt;
+            }
+            s->cyc_flops[j + 1] = s->cyc_flops[j] + f;
+            s->cyc_bytes[j + 1] = s->cyc_bytes[j] + b;
+        }
+        rec.kind = RGM_PROF_ARNOLDI_CYCLE;
+        rec.kry_j = -1;
+        rec.flops = rec.bytes = 0.0;
+        rec.a = pool_event(s);
+        rec.b = pool_event(s);
+        cudaEventRecord(rec.a, s->st);
+    }
+    nvtxRangePushA(kNvtxKind[RGM_PROF_ARNOLDI_CYCLE]);
+    const int rc = launch_cycle(c, nd_max, s->st);
+    nvtxRangePop();
+    ++s->launches;
+    if (rc) {
+        char what[96];
+        std::snprintf(what, sizeof what, "cycle_kernel cooperative launch (%d blocks, capacity %d)",
+                      c.pass[0].nblocks, s->cycle_cap[sizeof(T) == 4 ? 1 : 0][nd_max]);
+        rgm_note_cuda_error(rc, what, __LINE__);
+        return RGM_E_CUDA;
+    }
+    if (s->prof) {
+        cudaEventRecord(rec.b, s->st);
+        s->pending.push_back(rec);
+    }
+    return RGM_OK;
+}
+
 // One recycled GMRES solve of A x = b on the device buffers of `a`, with the
 // tolerance tol_abs already in Small.  mode: effective mode (PLAIN if no U).
 // Returns the number of cycles through *cycles.
@@ -386,23 +520,25 @@ static int gmres_cycles(rgm_solver s, const Arnoldi<T> &a, int mode, int k, int 
             if ((rc = launch(s, op))) return rc;
         }
         // Arnoldi with CGS2; deflated: operator P A
-        for (int j = 0; j < m; ++j) {
-            VecOp<T> op = base_op(s, a);
-            op.gate = GATE_KRYLOV;
-            op.src = SRC_SPMV; op.x = a.V + (int64_t)j * s->ld; op.xscale = j; op.out = a.w;
-            op.ndU = (mode == RGM_DEFLATED) ? k : 0; op.dnorm = 1; op.dyn = DYN_NDV_NB;
-            op.fin = FIN_ARN1;
-            if ((rc = launch(s, op, RGM_PROF_ARNOLDI_SPMV, j, j + 1))) return rc;
-            op = base_op(s, a);
-            op.gate = GATE_KRYLOV;
-            op.src = SRC_AXPY; op.win = a.w; op.out = a.w; op.nW = (mode == RGM_DEFLATED) ? k : 0;
-            op.dyn = DYN_NV_NB | DYN_NDV_NB; op.fin = FIN_ARN2;
-            if ((rc = launch(s, op, RGM_PROF_ARNOLDI_CGS1, j, j + 1))) return rc;
-            op = base_op(s, a);
-            op.gate = GATE_KRYLOV;
-            op.src = SRC_AXPY; op.win = a.w; op.dyn = DYN_NV_NB | DYN_OUT_VNB;
-            op.ndW = (mode == RGM_DEFLATED) ? k : 0; op.dnorm = 1; op.fin = FIN_ARN3;
-            if ((rc = launch(s, op, RGM_PROF_ARNOLDI_CGS2, j, j + 1))) return rc;
+        const int kdef = (mode == RGM_DEFLATED) ? k : 0;
+        CycleOp<T> cyc;
+        arnoldi_passes(s, a, kdef, cyc);
+        if (use_cycle_kernel(s, cyc, kdef + m + 1)) {
+            if ((rc = launch_cycle_prof(s, cyc, kdef + m + 1))) return rc;
+        } else {
+            for (int j = 0; j < m; ++j) {
+                VecOp<T> op = cyc.pass[0];
+                op.gate = GATE_KRYLOV;
+                op.x = a.V + (int64_t)j * s->ld;
+                op.xscale = j;
+                if ((rc = launch(s, op, RGM_PROF_ARNOLDI_SPMV, j, j + 1))) return rc;
+                op = cyc.pass[1];
+                op.gate = GATE_KRYLOV;
+                if ((rc = launch(s, op, RGM_PROF_ARNOLDI_CGS1, j, j + 1))) return rc;
+                op = cyc.pass[2];
+                op.gate = GATE_KRYLOV;
+                if ((rc = launch(s, op, RGM_PROF_ARNOLDI_CGS2, j, j + 1))) return rc;
+            }
         }
         // augmentation: append A u_i to the Arnoldi relation (Sec. 3.1)
         if (mode == RGM_AUGMENTED) {
@@ -637,6 +773,8 @@ int rgm_config_default(rgm_config *cfg)
     return RGM_OK;
 }
 
+const char *rgm_last_error(void) { return g_last_error; }
+
 const char *rgm_status_string(int code)
 {
     switch (code) {
@@ -672,7 +810,8 @@ int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
     if (c.n < 1 || c.m < 1 || c.m > RGM_MMAX || c.k < 0 || c.k > RGM_KMAX || c.window < 1 ||
         c.window > RGM_WMAX || c.svd_interval < 1 || c.mode < 0 || c.mode > 2 || c.precision < 0 ||
         c.precision > 1 || c.maxit < 0 || !(c.rtol >= 0) || c.inner_cycles < 1 ||
-        c.max_refinements < 1 || !(c.inner_rtol > 0) || !(c.rel_drop >= 0))
+        c.max_refinements < 1 || !(c.inner_rtol > 0) || !(c.rel_drop >= 0) ||
+        c.launch_policy < RGM_LAUNCH_AUTO || c.launch_policy > RGM_LAUNCH_PER_PASS)
         return RGM_E_ARG;
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RGM_E_CUDA;
@@ -682,6 +821,8 @@ int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
         return RGM_E_CUDA;
     rgm_solver s = new (std::nothrow) rgm_solver_s();
     if (!s) return RGM_E_OOM;
+    for (auto &row : s->cycle_cap)
+        for (int &v : row) v = -1;
     s->cfg = c;
     s->st = (cudaStream_t)c.cuda_stream;
     s->nsm = nsm;
@@ -947,6 +1088,106 @@ int rgm_reset_recycling(rgm_solver s)
     s->k_cur = 0;
     s->k_pending = false;
     s->coarse_stale = true;
+    return RGM_OK;
+}
+
+// Checkpoint layout: StateHeader, then win_used window columns (ring slots
+// 0..win_used-1, n doubles each), then k_cur columns of U.
+namespace {
+struct StateHeader {
+    uint32_t magic, version;
+    int64_t n;
+    int32_t window, k_cur, win_count, win_head;
+    int64_t updates;
+};
+const uint32_t kStateMagic = 0x314d4752u;   // bytes "RGM1" in little-endian order
+}  // namespace
+
+int rgm_export_state(rgm_solver s, void *buf, size_t *bytes)
+{
+    if (!s || !bytes) return RGM_E_ARG;
+    int rc = sync_recycle_dim(s);
+    if (rc) return rc;
+    const int win_used = s->win_count;   // ring slots 0..win_count-1 hold data
+    const size_t need = sizeof(StateHeader) + sizeof(double) * (size_t)s->n * (win_used + s->k_cur);
+    if (!buf) { *bytes = need; return RGM_OK; }
+    if (*bytes < need) return RGM_E_ARG;
+    StateHeader h;
+    h.magic = kStateMagic;
+    h.version = 1;
+    h.n = s->n;
+    h.window = s->cfg.window;
+    h.k_cur = s->k_cur;
+    h.win_count = s->win_count;
+    h.win_head = s->win_head;
+    h.updates = s->updates;
+    std::memcpy(buf, &h, sizeof h);
+    double *d = reinterpret_cast<double *>(static_cast<char *>(buf) + sizeof h);
+    for (int i = 0; i < win_used; ++i)
+        CK(cudaMemcpyAsync(d + (size_t)i * s->n, s->X + (int64_t)i * s->ld, sizeof(double) * s->n,
+                           cudaMemcpyDeviceToHost, s->st));
+    d += (size_t)win_used * s->n;
+    for (int i = 0; i < s->k_cur; ++i)
+        CK(cudaMemcpyAsync(d + (size_t)i * s->n, s->U + (int64_t)i * s->ld, sizeof(double) * s->n,
+                           cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    *bytes = need;
+    return RGM_OK;
+}
+
+int rgm_import_state(rgm_solver s, const void *buf, size_t bytes)
+{
+    if (!s || !buf || bytes < sizeof(StateHeader)) return RGM_E_ARG;
+    StateHeader h;
+    std::memcpy(&h, buf, sizeof h);
+    if (h.magic != kStateMagic || h.version != 1 || h.n != s->n || h.window != s->cfg.window ||
+        h.k_cur < 0 || h.k_cur > s->cfg.k || h.win_count < 0 || h.win_count > h.window ||
+        h.win_head < 0 || h.win_head >= h.window || h.updates < h.win_count)
+        return RGM_E_ARG;
+    const size_t need = sizeof(StateHeader) + sizeof(double) * (size_t)s->n * (h.win_count + h.k_cur);
+    if (bytes != need) return RGM_E_ARG;
+    CK(cudaStreamSynchronize(s->st));
+    const double *d = reinterpret_cast<const double *>(static_cast<const char *>(buf) + sizeof h);
+    for (int i = 0; i < h.win_count; ++i)
+        CK(cudaMemcpyAsync(s->X + (int64_t)i * s->ld, d + (size_t)i * s->n, sizeof(double) * s->n,
+                           cudaMemcpyHostToDevice, s->st));
+    d += (size_t)h.win_count * s->n;
+    for (int i = 0; i < h.k_cur; ++i)
+        CK(cudaMemcpyAsync(s->U + (int64_t)i * s->ld, d + (size_t)i * s->n, sizeof(double) * s->n,
+                           cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    s->win_count = h.win_count;
+    s->win_head = h.win_head;
+    s->updates = (int)h.updates;
+    s->k_cur = h.k_cur;
+    s->k_pending = false;
+    s->coarse_stale = true;
+    return RGM_OK;
+}
+
+int rgm_wait_selftest(int64_t limit_ns, int *blocks_gave_up, int *fault_flag)
+{
+    if (limit_ns < 1000 || limit_ns > 1000000000 || !blocks_gave_up || !fault_flag) return RGM_E_ARG;
+    Small *sm = nullptr;
+    int *cnt = nullptr;
+    cudaError_t e = cudaMalloc((void **)&sm, sizeof(Small));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&cnt, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(sm, 0, sizeof(Small));
+    if (e == cudaSuccess) e = cudaMemset(cnt, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        wait_selftest_kernel<<<2, RGM_THREADS>>>(sm, (unsigned long long)limit_ns, cnt);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    Small h;
+    int c = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&c, cnt, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, sm, offsetof(Small, H), cudaMemcpyDeviceToHost);
+    cudaFree(sm);
+    cudaFree(cnt);
+    if (e != cudaSuccess) return RGM_E_CUDA;
+    *blocks_gave_up = c;
+    *fault_flag = h.fault ? 1 : 0;
     return RGM_OK;
 }
 

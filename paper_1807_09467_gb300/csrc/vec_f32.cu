@@ -6,3 +6,13 @@ int launch_vec(const VecOp<float> &op, int nd_max, cudaStream_t st)
 {
     return launch_vec_impl(op, nd_max, st);
 }
+
+int cycle_capacity(const CycleOp<float> &, int nd_max)
+{
+    return cycle_capacity_impl<float>(nd_max);
+}
+
+int launch_cycle(const CycleOp<float> &c, int nd_max, cudaStream_t st)
+{
+    return launch_cycle_impl(c, nd_max, st);
+}

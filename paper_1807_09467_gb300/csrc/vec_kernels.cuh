@@ -297,16 +297,20 @@ __device__ __forceinline__ const T *dot_col(const VecOp<T> &op, int c)
     return op.out;
 }
 
-template <typename T, int QMAX>
-__global__ void __launch_bounds__(RGM_THREADS, 4) vec_kernel(VecOp<T> op)
+// What one block did in a pass: left without touching the completion counter
+// (gated off, or nothing to reduce), arrived, or arrived last and finalised.
+enum PassResult { PASS_SKIPPED = 0, PASS_ARRIVED = 1, PASS_LAST = 2 };
+
+// One fused pass over the block's rows (body of vec_kernel and of each phase
+// of cycle_kernel).  PDL: signal programmatic dependents once the partials
+// are written.
+template <typename T, int QMAX, bool PDL>
+__device__ __forceinline__ int vec_pass(VecOp<T> op)
 {
     constexpr int NW = RGM_THREADS / 32;      // QMAX * NW >= number of dot columns
-    // programmatic dependent launch: blocks may be scheduled while the previous
-    // pass finishes; nothing it wrote is read before this wait returns
-    asm volatile("griddepcontrol.wait;" ::: "memory");
     Small *s = op.sm;
-    if (op.gate == GATE_KRYLOV && s->done) return;
-    if (op.gate == GATE_APPEND && (s->skip || s->J == 0)) return;
+    if (op.gate == GATE_KRYLOV && s->done) return PASS_SKIPPED;
+    if (op.gate == GATE_APPEND && (s->skip || s->J == 0)) return PASS_SKIPPED;
     if (op.dyn) {
         if (op.dyn & DYN_NDV_NB) op.ndV = s->nb;
         if (op.dyn & DYN_NV_NB) op.nV = s->nb;
@@ -425,8 +429,8 @@ __global__ void __launch_bounds__(RGM_THREADS, 4) vec_kernel(VecOp<T> op)
         __syncthreads();
     }
     if (nd == 0 && op.fin == FIN_NONE) {
-        asm volatile("griddepcontrol.launch_dependents;");
-        return;
+        if (PDL) asm volatile("griddepcontrol.launch_dependents;");
+        return PASS_SKIPPED;
     }
     // per-block partials: one warp reduction per column
 #pragma unroll
@@ -439,9 +443,9 @@ __global__ void __launch_bounds__(RGM_THREADS, 4) vec_kernel(VecOp<T> op)
     }
 
     // the next pass may start launching; it waits for this grid to complete
-    asm volatile("griddepcontrol.launch_dependents;");
+    if (PDL) asm volatile("griddepcontrol.launch_dependents;");
     // ---- the last block reduces the partials and runs the scalar step
-    if (!last_block(op.counter)) return;
+    if (!last_block(op.counter)) return PASS_ARRIVED;
     __shared__ double dsum[RGM_MAXDOTS];
     __shared__ double red2[RGM_THREADS];
     __shared__ FinScratch fin;
@@ -470,13 +474,108 @@ __global__ void __launch_bounds__(RGM_THREADS, 4) vec_kernel(VecOp<T> op)
     __syncthreads();
     finalize_block(op, dsum, fin);
     if (threadIdx.x == 0) *op.counter = 0u;
+    return PASS_LAST;
+}
+
+template <typename T, int QMAX>
+__global__ void __launch_bounds__(RGM_THREADS, 4) vec_kernel(VecOp<T> op)
+{
+    // programmatic dependent launch: blocks may be scheduled while the previous
+    // pass finishes; nothing it wrote is read before this wait returns
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    vec_pass<T, QMAX, true>(op);
+}
+
+// ---------------------------------------------------------------- persistent cycle
+// All Arnoldi steps of one GMRES cycle in one cooperative launch.  The three
+// fused passes of a step run back to back in every block, separated by a grid
+// barrier that the block finishing a pass last -- the one that reduced the
+// partials and ran the scalar step -- releases.  Every block reads the cycle
+// state after a barrier, so all of them leave the loop at the same step, and
+// the arithmetic is that of the per-pass launches (same code, same reduction
+// order).  Waits are bounded: a block that waits longer than RGM_GRID_WAIT_NS
+// (or sees Small::fault set) sets Small::fault and returns, the others follow
+// at their next wait, and the host reports RGM_E_TIMEOUT.
+#define RGM_GRID_WAIT_NS 1000000000ull
+
+template <typename T>
+struct CycleOp {
+    VecOp<T> pass[3];    // A v_j + dots (first CGS pass), second CGS pass, norm + Givens
+    int m;               // Arnoldi steps at most
+};
+
+// After a pass: the last block publishes generation `target`, the others wait
+// for it, at most limit_ns.  False when the wait gave up.
+__device__ __forceinline__ bool grid_barrier(int pass_rc, Small *s, unsigned target,
+                                             unsigned long long limit_ns = RGM_GRID_WAIT_NS)
+{
+    __shared__ int ok;
+    if (pass_rc == PASS_LAST) {
+        __syncthreads();                  // the scalar step is complete
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release_gpu(&s->gen, target);
+        }
+        return true;
+    }
+    if (threadIdx.x == 0) {
+        int good = 1;
+        const unsigned long long t0 = globaltimer_ns();
+        // a second bound that holds even if the timer stalled: one poll is an
+        // L2 round trip (hundreds of ns), so this cap is far above limit_ns
+        const unsigned long long cap = limit_ns / 16ull + 1024ull;
+        for (unsigned long long it = 1; ld_acquire_gpu(&s->gen) < target; ++it) {
+            if ((it & 63ull) == 0 && (ld_acquire_gpu(&s->fault) != 0u || it > cap ||
+                                      globaltimer_ns() - t0 > limit_ns)) {
+                atomicExch(&s->fault, 1u);
+                good = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <typename T, int QMAX>
+__global__ void __launch_bounds__(RGM_THREADS, 4) cycle_kernel(CycleOp<T> c)
+{
+    Small *s = c.pass[0].sm;
+    unsigned gen = 0;
+    for (int j = 0; j < c.m; ++j) {
+        if (*(volatile int *)&s->done) break;       // same value in every block
+        VecOp<T> op = c.pass[0];
+        op.x = op.V + (int64_t)j * op.ldv;
+        op.xscale = j;
+        if (!grid_barrier(vec_pass<T, QMAX, false>(op), s, ++gen)) return;
+        if (!grid_barrier(vec_pass<T, QMAX, false>(c.pass[1]), s, ++gen)) return;
+        if (!grid_barrier(vec_pass<T, QMAX, false>(c.pass[2]), s, ++gen)) return;
+    }
+}
+
+// Self-test of the bounded wait: no block ever finishes a pass last, so the
+// generation these blocks wait for is never published; each block records in
+// *gave_up whether its wait ended by the limit (or by another block's fault).
+static __global__ void wait_selftest_kernel(Small *s, unsigned long long limit_ns, int *gave_up)
+{
+    const bool ok = grid_barrier(PASS_ARRIVED, s, 1u, limit_ns);
+    if (threadIdx.x == 0 && !ok) atomicAdd(gave_up, 1);
 }
 
 // Host-side dispatch (vec_f64.cu / vec_f32.cu): the per-warp column tier is
 // chosen from the largest dot-column count the launch can see (nd_max;
 // dynamic counts resolve on the device and never exceed it).
+// Return the cudaError_t of the launch (0 = success).
 int launch_vec(const VecOp<double> &op, int nd_max, cudaStream_t st);
 int launch_vec(const VecOp<float> &op, int nd_max, cudaStream_t st);
+// cycle_kernel: blocks that can be resident at once for this column bound
+// (0 if the device cannot launch it cooperatively), and the launch itself.
+int cycle_capacity(const CycleOp<double> &c, int nd_max);
+int cycle_capacity(const CycleOp<float> &c, int nd_max);
+int launch_cycle(const CycleOp<double> &c, int nd_max, cudaStream_t st);
+int launch_cycle(const CycleOp<float> &c, int nd_max, cudaStream_t st);
 
 template <typename T, int Q>
 static cudaError_t launch_vec_pdl(const VecOp<T> &op, cudaStream_t st)
@@ -504,7 +603,61 @@ static int launch_vec_impl(const VecOp<T> &op, int nd_max, cudaStream_t st)
     if (q <= 4) e = launch_vec_pdl<T, 4>(op, st);
     else if (q <= 8) e = launch_vec_pdl<T, 8>(op, st);
     else e = launch_vec_pdl<T, QBIG>(op, st);
-    return e == cudaSuccess ? 0 : -1;
+    return (int)e;          // cudaSuccess == 0
+}
+
+template <typename T, int Q>
+static int cycle_capacity_q(int dev)
+{
+    int coop = 0, nsm = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cycle_kernel<T, Q>, RGM_THREADS, 0) !=
+        cudaSuccess)
+        return 0;
+    return per_sm * nsm;
+}
+
+template <typename T>
+static int cycle_capacity_impl(int nd_max)
+{
+    constexpr int NW = RGM_THREADS / 32;
+    constexpr int QBIG = (RGM_MAXDOTS + NW - 1) / NW;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    const int q = (nd_max + NW - 1) / NW;
+    if (q <= 4) return cycle_capacity_q<T, 4>(dev);
+    if (q <= 8) return cycle_capacity_q<T, 8>(dev);
+    return cycle_capacity_q<T, QBIG>(dev);
+}
+
+template <typename T, int Q>
+static cudaError_t launch_cycle_q(const CycleOp<T> &c, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c.pass[0].nblocks);
+    cfg.blockDim = dim3(RGM_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;   // all blocks resident, or the launch fails
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, cycle_kernel<T, Q>, c);
+}
+
+template <typename T>
+static int launch_cycle_impl(const CycleOp<T> &c, int nd_max, cudaStream_t st)
+{
+    constexpr int NW = RGM_THREADS / 32;
+    constexpr int QBIG = (RGM_MAXDOTS + NW - 1) / NW;
+    const int q = (nd_max + NW - 1) / NW;
+    cudaError_t e;
+    if (q <= 4) e = launch_cycle_q<T, 4>(c, st);
+    else if (q <= 8) e = launch_cycle_q<T, 8>(c, st);
+    else e = launch_cycle_q<T, QBIG>(c, st);
+    return (int)e;          // cudaSuccess == 0
 }
 
 // CSR values -> sliced-ELL positions (binary64 and, when given, binary32 copy).
@@ -673,6 +826,7 @@ static __global__ void cycle_reset_kernel(Small *s)
         s->skip = 0;
         s->done = 0;
         s->breakdown = 0;
+        s->gen = 0u;          // grid-barrier generations restart with each cycle
     }
 }
 

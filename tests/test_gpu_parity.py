@@ -293,3 +293,31 @@ def test_q4_256_residual_property(rg, orc):
     x, st = s.solve(b, u0)
     r = ob - orc.spmv(orc.Csr(orp, ocol, oval), x)
     assert np.linalg.norm(r) / np.linalg.norm(ob) <= 1.5e-10
+
+
+@pytest.mark.parametrize("mode", ["deflated", "augmented"])
+def test_maximum_dimensions(rg, orc, mode):
+    """The library's limits at once: m = 64, k = 32 (E from a 2k-column Gram
+    tile), window = 64 (the window SVD on 64 snapshots), several row tiles and a
+    ragged tail; x and iterations against the oracle."""
+    n = 5000 + 37
+    rp, col, val, b = _random_system(n, 17)
+    A = orc.Csr(rp, col, val)
+    U = _orth(synth.random_matrix(n, 32, 18))
+    s = rg.Solver(n, m=64, k=32, window=64, mode=mode, rtol=1e-10)
+    s.set_operator_csr(rp, col, val)
+    s.set_recycle_space(U)
+    x, st = s.solve(b)
+    xo, so, _ = orc.gmres(A, b, U=U, mode=rg.MODES[mode], m=64, rtol=1e-10)
+    assert st["status"] == 0 and st["k_used"] == 32
+    assert abs(st["iters"] - so["iters"]) <= 1, (st, so)
+    assert _rel(x, xo) <= 1e-9
+    # window SVD over 64 snapshots keeps k = 32 columns inside range(X)
+    X = synth.random_matrix(n, 64, 19)
+    for i in range(64):
+        k_new = s.update_recycle_svd(X[:, i])
+    assert k_new == 32
+    Ug = s.recycle_space()
+    np.testing.assert_allclose(Ug.T @ Ug, np.eye(32), atol=1e-12)
+    Q = np.linalg.qr(X)[0]
+    assert np.linalg.norm(Ug - Q @ (Q.T @ Ug)) <= 1e-10
