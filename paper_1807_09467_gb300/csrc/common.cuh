@@ -47,7 +47,9 @@ struct Small {
     double VtW[RGM_HLD * RGM_KMAX];       // v_i^T W_l at [i + l * RGM_HLD]
     double E[RGM_KMAX * RGM_KMAX];
     double LU[RGM_KMAX * RGM_KMAX];
-    int piv[RGM_KMAX];
+    double LUrd[RGM_KMAX];                // reciprocals of the U pivots of LU
+    int piv[RGM_KMAX];                    // row swaps of the LU, in order
+    int LUperm[RGM_KMAX];                 // the same swaps as one permutation
     double dots[RGM_MAXDOTS];             // last reduced dot products
     double gram[RGM_WMAX * RGM_WMAX];     // last reduced Gram matrix
     double evec[RGM_WMAX * RGM_WMAX];     // eigenvectors of the window Gram matrix
@@ -140,19 +142,28 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
     return t;
 }
 
-// Last-block-done: every block calls this after writing its partials; returns
-// true in exactly one block (the last to arrive), which then sees all partials.
-// No block waits for another, so nothing can spin.
-__device__ __forceinline__ bool last_block(unsigned *counter)
+// Fetch-and-add with acquire-release semantics at GPU scope: the caller's
+// earlier writes (and, through a preceding __syncthreads, those of its whole
+// block) are visible to whoever observes the new value, and the caller sees
+// everything released by the earlier adds it observes.
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned *p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// Last-of-n: every one of n blocks calls this once (after writing what the
+// last one will read); returns true in exactly the block that arrives last,
+// which then sees everything the others wrote before arriving.  Nothing spins.
+__device__ __forceinline__ bool last_of(unsigned *counter, unsigned n)
 {
     __shared__ bool am_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned t = atomicAdd(counter, 1u);
-        am_last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (am_last) __threadfence();
+    __syncthreads();                    // the block's writes precede thread 0's release
+    if (threadIdx.x == 0) am_last = (atom_add_acq_rel_gpu(counter, 1u) == n - 1u);
+    __syncthreads();                    // and its acquire precedes the block's reads
     return am_last;
 }
+
+// Last-block-done over the whole grid (see last_of).
+__device__ __forceinline__ bool last_block(unsigned *counter) { return last_of(counter, gridDim.x); }

@@ -102,7 +102,9 @@ struct rgm_solver_s {
     double *Ytmp = nullptr;       // n x kmax scratch for the SVD
     // scratch
     double *partials = nullptr;
-    unsigned *counter = nullptr;
+    unsigned *counter = nullptr;  // [0..3] completion counters, then one per reduction group
+    double *gpart = nullptr;      // per-group dot sums (RGM_MAXDOTS x ngroups)
+    int ngroups = 0;
     int2 *pairs = nullptr;        // pair list for Gram launches
     double *gram_out = nullptr;
     Small *sm = nullptr;
@@ -146,6 +148,9 @@ static VecOp<T> base_op(rgm_solver s, const Arnoldi<T> &a)
     op.ldw = s->ld;
     op.partials = s->partials;
     op.counter = s->counter;
+    op.gcount = s->counter + 4;
+    op.gpart = s->gpart;
+    op.ngroups = s->ngroups;
     op.sm = s->sm;
     op.fin = FIN_NONE;
     op.gate = GATE_NONE;
@@ -344,7 +349,7 @@ static int read_header(rgm_solver s)
     if (s->hs->fault) {
         // blocks that gave up left the completion counter mid-count: clear it
         // so that the handle's next solve starts from a clean state
-        CK(cudaMemsetAsync(s->counter, 0, sizeof(unsigned) * 4, s->st));
+        CK(cudaMemsetAsync(s->counter, 0, sizeof(unsigned) * (4 + s->ngroups), s->st));
         CK(cudaStreamSynchronize(s->st));
         return RGM_E_TIMEOUT;
     }
@@ -794,7 +799,7 @@ static void free_all(rgm_solver s)
 {
     void *dp[] = {s->slice_ptr, s->scol, s->perm, s->csr2sell, s->sval, s->sval32, s->val_stage, s->V, s->U, s->W, s->w, s->r, s->b, s->x,
                   s->V32, s->U32, s->W32, s->w32, s->r32, s->b32, s->x32, s->X, s->Ytmp,
-                  s->partials, s->counter, s->pairs, s->gram_out, s->sm};
+                  s->partials, s->counter, s->gpart, s->pairs, s->gram_out, s->sm};
     for (void *p : dp)
         if (p) cudaFree(p);
     if (s->hs) cudaFreeHost(s->hs);
@@ -848,7 +853,9 @@ int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
     ALLOC(s->x, sizeof(double) * s->ld);
     ALLOC(s->X, sizeof(double) * s->ld * c.window);
     ALLOC(s->partials, sizeof(double) * (size_t)std::max(RGM_MAXDOTS, s->npairs_max) * s->nblocks);
-    ALLOC(s->counter, sizeof(unsigned) * 4);
+    s->ngroups = (s->nblocks + RGM_RGROUP - 1) / RGM_RGROUP;
+    ALLOC(s->counter, sizeof(unsigned) * (4 + s->ngroups));
+    ALLOC(s->gpart, sizeof(double) * (size_t)RGM_MAXDOTS * s->ngroups);
     ALLOC(s->pairs, sizeof(int2) * s->npairs_max);
     ALLOC(s->gram_out, sizeof(double) * s->npairs_max);
     ALLOC(s->sm, sizeof(Small));
@@ -863,7 +870,7 @@ int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
     }
 #undef ALLOC
     if (e == cudaSuccess) e = cudaMallocHost((void **)&s->hs, sizeof(Small));
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->counter, 0, sizeof(unsigned) * 4, s->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->counter, 0, sizeof(unsigned) * (4 + s->ngroups), s->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->sm, 0, sizeof(Small), s->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->V, 0, sizeof(double) * s->ld * ncolV, s->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);

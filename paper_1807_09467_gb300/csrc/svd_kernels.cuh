@@ -44,8 +44,6 @@ __global__ void sym_eig_select_kernel(Small *s, const double *gram, int c, int k
     double *G = eig_smem, *P = eig_smem + RGM_WMAX * RGM_WMAX;
     __shared__ double rc[RGM_WMAX / 2], rs[RGM_WMAX / 2];
     __shared__ int rp[RGM_WMAX / 2], rq[RGM_WMAX / 2];
-    __shared__ int perm[RGM_WMAX];
-    __shared__ int any_rot;
     const int ce = c + (c & 1);                 // even size for the tournament
     for (int t = threadIdx.x; t < ce * ce; t += blockDim.x) {
         int i = t % ce, j = t / ce;
@@ -54,7 +52,6 @@ __global__ void sym_eig_select_kernel(Small *s, const double *gram, int c, int k
         G[i + j * RGM_WMAX] = v;
         P[i + j * RGM_WMAX] = (i == j) ? 1.0 : 0.0;
     }
-    for (int t = threadIdx.x; t < ce; t += blockDim.x) perm[t] = t;
     __shared__ double gmax;
     if (threadIdx.x == 0) {
         double m = 0.0;
@@ -68,60 +65,86 @@ __global__ void sym_eig_select_kernel(Small *s, const double *gram, int c, int k
     // of rounding size (about eps * lambda_max), so without this floor graded
     // windows sweep forever; the floor is the accuracy the Gram matrix carries.
     const double floor_abs = 2e-16 * gmax;
-    const int npair = ce / 2;
+    const double floor2 = floor_abs * floor_abs;
+    const int npair = ce / 2, nround = ce - 1;
+    __shared__ double rt[RGM_WMAX / 2];
+    __shared__ int rot_flag[2];
+    if (threadIdx.x == 0) rot_flag[0] = 0;
+    __syncthreads();
     for (int sweep = 0; sweep < 30; ++sweep) {
-        if (threadIdx.x == 0) any_rot = 0;
-        __syncthreads();
-        for (int step = 0; step < ce - 1; ++step) {
-            // pairs of this round: (perm[i], perm[ce-1-i])
+        const int fl = sweep & 1;
+        for (int round = 0; round < nround; ++round) {
+            // round-robin pairs (circle method): (round, ce-1) and
+            // ((round + i) mod (ce-1), (round - i) mod (ce-1)), i = 1 .. npair-1
             for (int t = threadIdx.x; t < npair; t += blockDim.x) {
-                int p = perm[t], q = perm[ce - 1 - t];
-                if (p > q) { int tmp = p; p = q; q = tmp; }
+                int a = round, b = ce - 1;
+                if (t > 0) { a = (round + t) % nround; b = (round - t + nround) % nround; }
+                const int p = min(a, b), q = max(a, b);
                 rp[t] = p; rq[t] = q;
-                double app = G[p + p * RGM_WMAX], aqq = G[q + q * RGM_WMAX], apq = G[p + q * RGM_WMAX];
-                double cth = 1.0, sth = 0.0;
-                if (fabs(apq) > floor_abs && fabs(apq) > 1e-15 * sqrt(fabs(app * aqq))) {
-                    double tau = (aqq - app) / (2.0 * apq);
-                    double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                    cth = 1.0 / sqrt(1.0 + tt * tt);
+                const double app = G[p + p * RGM_WMAX], aqq = G[q + q * RGM_WMAX], apq = G[p + q * RGM_WMAX];
+                double cth = 1.0, sth = 0.0, tt = 0.0;
+                const double apq2 = apq * apq;
+                if (apq2 > floor2 && apq2 > 1e-30 * fabs(app * aqq)) {
+                    // t = sgn(tau) / (|tau| + sqrt(1 + tau^2)), tau = (aqq - app) / (2 apq),
+                    // written as 2|apq| sgn(tau) / (|d| + sqrt(d^2 + 4 apq^2)), d = aqq - app
+                    const double d = aqq - app;
+                    const double h = fma(d, d, 4.0 * apq2);
+                    const double num = (d > 0.0) ? 2.0 * apq : (d < 0.0) ? -2.0 * apq : 2.0 * fabs(apq);
+                    tt = num / (fabs(d) + h * rsqrt(h));
+                    cth = rsqrt(fma(tt, tt, 1.0));
                     sth = tt * cth;
-                    any_rot = 1;
+                    rot_flag[fl] = 1;
                 }
-                rc[t] = cth; rs[t] = sth;
+                rc[t] = cth; rs[t] = sth; rt[t] = tt;
             }
             __syncthreads();
-            // G <- J^T G (rows p, q), then G <- G J (columns p, q), Phi <- Phi J
-            for (int t = threadIdx.x; t < npair * ce; t += blockDim.x) {
-                int pr = t / ce, col = t % ce;
-                int p = rp[pr], q = rq[pr];
-                double cth = rc[pr], sth = rs[pr];
-                double gp = G[p + col * RGM_WMAX], gq = G[q + col * RGM_WMAX];
-                G[p + col * RGM_WMAX] = cth * gp - sth * gq;
-                G[q + col * RGM_WMAX] = sth * gp + cth * gq;
-            }
-            __syncthreads();
-            for (int t = threadIdx.x; t < npair * ce; t += blockDim.x) {
-                int pr = t / ce, row = t % ce;
-                int p = rp[pr], q = rq[pr];
-                double cth = rc[pr], sth = rs[pr];
-                double gp = G[row + p * RGM_WMAX], gq = G[row + q * RGM_WMAX];
-                G[row + p * RGM_WMAX] = cth * gp - sth * gq;
-                G[row + q * RGM_WMAX] = sth * gp + cth * gq;
-                double vp = P[row + p * RGM_WMAX], vq = P[row + q * RGM_WMAX];
-                P[row + p * RGM_WMAX] = cth * vp - sth * vq;
-                P[row + q * RGM_WMAX] = sth * vp + cth * vq;
-            }
-            __syncthreads();
-            // rotate the tournament: keep perm[0], shift the rest
-            if (threadIdx.x == 0) {
-                int last = perm[ce - 1];
-                for (int i = ce - 1; i > 1; --i) perm[i] = perm[i - 1];
-                perm[1] = last;
+            // clear the next sweep's flag: every thread has read it (end of the
+            // previous sweep) before this barrier, and it is next written in the
+            // next sweep
+            if (round == 0 && threadIdx.x == 0) rot_flag[fl ^ 1] = 0;
+            // G <- J^T G J: every 2 x 2 block (pair a rows, pair b columns) with
+            // a <= b in one thread (two-sided), mirrored; Phi <- Phi J
+            const int nblk = npair * npair;
+            for (int x = threadIdx.x; x < nblk + npair * ce; x += blockDim.x) {
+                if (x < nblk) {
+                    const int ia = x % npair, ib = x / npair;
+                    if (ia > ib) continue;
+                    const int p1 = rp[ia], q1 = rq[ia];
+                    if (ia == ib) {
+                        const double tt = rt[ia];
+                        if (tt != 0.0) {
+                            const double apq = G[p1 + q1 * RGM_WMAX];
+                            G[p1 + p1 * RGM_WMAX] -= tt * apq;
+                            G[q1 + q1 * RGM_WMAX] += tt * apq;
+                            G[p1 + q1 * RGM_WMAX] = 0.0;
+                            G[q1 + p1 * RGM_WMAX] = 0.0;
+                        }
+                        continue;
+                    }
+                    const int p2 = rp[ib], q2 = rq[ib];
+                    const double c1 = rc[ia], s1 = rs[ia], c2 = rc[ib], s2 = rs[ib];
+                    const double b00 = G[p1 + p2 * RGM_WMAX], b01 = G[p1 + q2 * RGM_WMAX];
+                    const double b10 = G[q1 + p2 * RGM_WMAX], b11 = G[q1 + q2 * RGM_WMAX];
+                    const double r00 = c1 * b00 - s1 * b10, r01 = c1 * b01 - s1 * b11;
+                    const double r10 = s1 * b00 + c1 * b10, r11 = s1 * b01 + c1 * b11;
+                    const double n00 = c2 * r00 - s2 * r01, n01 = s2 * r00 + c2 * r01;
+                    const double n10 = c2 * r10 - s2 * r11, n11 = s2 * r10 + c2 * r11;
+                    G[p1 + p2 * RGM_WMAX] = n00; G[p2 + p1 * RGM_WMAX] = n00;
+                    G[p1 + q2 * RGM_WMAX] = n01; G[q2 + p1 * RGM_WMAX] = n01;
+                    G[q1 + p2 * RGM_WMAX] = n10; G[p2 + q1 * RGM_WMAX] = n10;
+                    G[q1 + q2 * RGM_WMAX] = n11; G[q2 + q1 * RGM_WMAX] = n11;
+                } else {
+                    const int y = x - nblk, pr = y / ce, row = y % ce;
+                    const int p = rp[pr], q = rq[pr];
+                    const double cth = rc[pr], sth = rs[pr];
+                    const double vp = P[row + p * RGM_WMAX], vq = P[row + q * RGM_WMAX];
+                    P[row + p * RGM_WMAX] = cth * vp - sth * vq;
+                    P[row + q * RGM_WMAX] = sth * vp + cth * vq;
+                }
             }
             __syncthreads();
         }
-        if (!any_rot) break;
-        __syncthreads();
+        if (!rot_flag[fl]) break;
     }
     if (threadIdx.x == 0) {
         // eigenvalues (clamped at 0), stable descending order

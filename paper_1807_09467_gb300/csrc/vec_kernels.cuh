@@ -18,6 +18,7 @@
 #include "common.cuh"
 
 #define RGM_TILE RGM_THREADS
+#define RGM_RGROUP 32            // blocks per group of the two-level dot reduction
 
 enum Src { SRC_SPMV = 0, SRC_RES = 1, SRC_COPY = 2, SRC_AXPY = 3, SRC_NONE = 4 };
 enum Gate { GATE_NONE = 0, GATE_KRYLOV = 1, GATE_APPEND = 2 };
@@ -59,8 +60,11 @@ struct VecOp {
     const T *V; int64_t ldv;
     const T *W; int64_t ldw;
     int ndU, ndV, ndW, dnorm;  // dot columns: U[0..ndU), Vraw[0..ndV), W[0..ndW), ||w||^2
-    double *partials;
-    unsigned *counter;
+    double *partials;        // per-block dot partials, column c at c * nblocks
+    unsigned *counter;       // completion counter of the groups
+    unsigned *gcount;        // per-group completion counters (RGM_RGROUP blocks a group)
+    double *gpart;           // per-group sums, column c at c * ngroups
+    int ngroups;
     Small *sm;
     int fin;
     int gate;
@@ -83,11 +87,18 @@ struct FinScratch {
     double col[RGM_HLD + 1];
     double cs[RGM_HLD], sn[RGM_HLD];
     double sc[RGM_HLD];
+    double rd[RGM_KMAX];                      // reciprocals of the U pivots
+    int perm[RGM_KMAX];                       // composite row permutation of the LU
+    double vtw[(RGM_MMAX + 1) * RGM_KMAX];    // V^T W rows 0..nb-1 (leading dim RGM_MMAX+1)
     int flag;
 };
+#define RGM_VTW_LD (RGM_MMAX + 1)
 
 // ---------------------------------------------------------------- scalar helpers
-__device__ inline void lu_solve_small(int k, const double *LU, int ld, const int *piv, double *x)
+// Solve with the LU factors of a k x k matrix (row swaps piv, unit lower L,
+// upper U with its pivots' reciprocals rd): no divisions on the serial path.
+__device__ inline void lu_solve_small(int k, const double *LU, int ld, const int *piv, const double *rd,
+                                      double *x)
 {
     for (int j = 0; j < k; ++j)
         if (piv[j] != j) { double t = x[j]; x[j] = x[piv[j]]; x[piv[j]] = t; }
@@ -95,18 +106,75 @@ __device__ inline void lu_solve_small(int k, const double *LU, int ld, const int
         for (int j = 0; j < i; ++j) x[i] -= LU[i + j * ld] * x[j];
     for (int i = k - 1; i >= 0; --i) {
         for (int j = i + 1; j < k; ++j) x[i] -= LU[i + j * ld] * x[j];
-        x[i] /= LU[i + i * ld];
+        x[i] *= rd[i];
     }
 }
 
-// Stage the k x k LU factors and pivots of E in shared memory (whole block).
+// Stage the k x k LU factors, pivots and pivot reciprocals of E in shared
+// memory (whole block).
 __device__ inline void stage_lu(const Small *s, int k, FinScratch &f)
 {
     for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
         int i = t % k, j = t / k;
         f.LU[i + j * RGM_KMAX] = s->LU[i + j * RGM_KMAX];
     }
-    for (int t = threadIdx.x; t < k; t += blockDim.x) f.piv[t] = s->piv[t];
+    for (int t = threadIdx.x; t < k; t += blockDim.x) {
+        f.piv[t] = s->piv[t];
+        f.rd[t] = s->LUrd[t];
+        f.perm[t] = s->LUperm[t];
+    }
+}
+
+// Warp-parallel solve with the staged LU factors (k <= 32): lane i enters with
+// b[perm[i]] and leaves with x_i.  3k binary64 warp instructions instead of a
+// k^2 chain in one thread.
+__device__ __forceinline__ double warp_lu_solve(int k, const FinScratch &f, double x)
+{
+    const int lane = threadIdx.x & 31;
+    for (int j = 0; j < k - 1; ++j) {
+        const double xj = __shfl_sync(0xffffffffu, x, j);
+        if (lane > j && lane < k) x = fma(-f.LU[lane + j * RGM_KMAX], xj, x);
+    }
+    for (int j = k - 1; j >= 0; --j) {
+        if (lane == j) x *= f.rd[j];
+        const double xj = __shfl_sync(0xffffffffu, x, j);
+        if (lane < j) x = fma(-f.LU[lane + j * RGM_KMAX], xj, x);
+    }
+    return x;
+}
+
+// The new Hessenberg column after the stored rotations, as an affine scan.
+// Rotation i maps (t_i, h_{i+1}) to (cs_i t_i + sn_i h_{i+1}, t_{i+1}) with
+// t_{i+1} = -sn_i t_i + cs_i h_{i+1}, t_0 = h_0; the recurrence for t is
+// composed over the warp in log2(32) steps (chunks of 32 rotations in turn).
+// One warp; on return col[0..j-1] hold the rotated entries and the return
+// value is t_j (entry j before the new rotation).  h: col on entry.
+__device__ __forceinline__ double warp_rotate_column(double *col, const double *cs, const double *sn, int j)
+{
+    const int lane = threadIdx.x & 31;
+    double tin = col[0];
+    for (int base = 0; base < j; base += 32) {
+        const int i = base + lane;
+        const bool ok = i < j;
+        const double c = ok ? cs[i] : 1.0, sg = ok ? sn[i] : 0.0, h1 = ok ? col[i + 1] : 0.0;
+        double A = ok ? -sg : 1.0, B = ok ? c * h1 : 0.0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double A1 = __shfl_up_sync(0xffffffffu, A, o), B1 = __shfl_up_sync(0xffffffffu, B, o);
+            if (lane >= o) {
+                B = fma(A, B1, B);
+                A = A * A1;
+            }
+        }
+        const double tnext = fma(A, tin, B);                   // t_{i+1}
+        double tcur = __shfl_up_sync(0xffffffffu, tnext, 1);   // t_i
+        if (lane == 0) tcur = tin;
+        __syncwarp();
+        if (ok) col[i] = fma(c, tcur, sg * h1);
+        tin = __shfl_sync(0xffffffffu, tnext, min(31, j - 1 - base));
+        __syncwarp();
+    }
+    return tin;
 }
 
 // Rotate column c (in shared memory, rows 0..col+1) by rotations 0..col-1.
@@ -141,6 +209,49 @@ __device__ inline void close_column(Small *s, FinScratch &f, int col)
     for (int i = threadIdx.x; i <= col + 1; i += blockDim.x) hc[i] = f.col[i];
 }
 
+// Loads of the small state the scalar step needs, issued by the finalising
+// block together with the loads of the partial sums (one round trip for both).
+// Counts come from the pass itself: nb = op.ndV for the first and second CGS
+// passes (DYN_NDV_NB), op.nV for the third (DYN_NV_NB).
+template <typename T>
+__device__ void fin_stage(const VecOp<T> &op, FinScratch &f)
+{
+    const Small *s = op.sm;
+    const int tid = threadIdx.x;
+    switch (op.fin) {
+    case FIN_COARSE:
+    case FIN_START_DEF1:
+        stage_lu(s, op.ndU, f);
+        break;
+    case FIN_ARN1:
+    case FIN_AUG1: {
+        const int nb = op.ndV, k = op.ndU;
+        if (k) stage_lu(s, k, f);
+        for (int i = tid; i < nb; i += blockDim.x) f.sc[i] = s->colscale[i];
+        for (int t = tid; t < nb * k; t += blockDim.x) {
+            const int i = t % nb, l = t / nb;
+            f.vtw[i + l * RGM_VTW_LD] = s->VtW[i + l * RGM_HLD];
+        }
+        break;
+    }
+    case FIN_ARN2:
+        for (int i = tid; i < op.ndV; i += blockDim.x) {
+            f.sc[i] = s->colscale[i];
+            f.col[i] = s->hsum[i];
+        }
+        break;
+    case FIN_ARN3:
+        for (int i = tid; i < op.nV; i += blockDim.x) {
+            f.col[i] = s->hsum[i];
+            f.cs[i] = s->cs[i];
+            f.sn[i] = s->sn[i];
+        }
+        break;
+    default:
+        break;
+    }
+}
+
 // The scalar step after a reduction, run by the whole finalising block.
 // d[] holds the reduced dots in the column order [U | Vraw | W | norm].
 template <typename T>
@@ -162,12 +273,10 @@ __device__ void finalize_block(const VecOp<T> &op, const double *d, FinScratch &
         break;
     case FIN_COARSE:
     case FIN_START_DEF1: {
-        const int k = op.ndU;
-        stage_lu(s, k, f);
-        __syncthreads();
-        if (tid == 0) {
-            for (int i = 0; i < k; ++i) f.dd[i] = dU[i];
-            lu_solve_small(k, f.LU, RGM_KMAX, f.piv, f.dd);
+        const int k = op.ndU;           // LU staged by fin_stage
+        if (tid < 32) {
+            const double x = warp_lu_solve(k, f, tid < k ? dU[f.perm[tid]] : 0.0);
+            if (tid < k) f.dd[tid] = x;
         }
         __syncthreads();
         for (int i = tid; i < k; i += blockDim.x) {
@@ -196,58 +305,76 @@ __device__ void finalize_block(const VecOp<T> &op, const double *d, FinScratch &
     case FIN_AUG1: {
         // w = A v_j (or A u_i).  Deflated: P w = w - W d, d = E^{-1} U^T w, and
         // V^T P w = V^T w - (V^T W) d.
-        const int nb = s->nb, k = op.ndU;
-        if (k) stage_lu(s, k, f);
-        for (int i = tid; i < nb; i += blockDim.x) f.sc[i] = s->colscale[i];
-        __syncthreads();
-        if (tid == 0) {
+        // LU, colscale and V^T W staged by fin_stage (nb = op.ndV)
+        const int nb = op.ndV, k = op.ndU;
+        if (tid < 32 && k) {
+            const double x = warp_lu_solve(k, f, tid < k ? dU[f.perm[tid]] : 0.0);
+            if (tid < k) f.dd[tid] = x;
+        }
+        if (tid == 32) {
             s->wn0 = sqrt(nrm2);
             if (op.fin == FIN_AUG1) s->skip = (nrm2 == 0.0) ? 1 : 0;
-            for (int i = 0; i < k; ++i) f.dd[i] = dU[i];
-            if (k) lu_solve_small(k, f.LU, RGM_KMAX, f.piv, f.dd);
         }
         __syncthreads();
         for (int i = tid; i < k; i += blockDim.x) s->coefW[i] = -f.dd[i];
         for (int i = tid; i < nb; i += blockDim.x) {
             double h = dV[i] * f.sc[i];
-            for (int l = 0; l < k; ++l) h -= s->VtW[i + l * RGM_HLD] * f.dd[l];
+            for (int l = 0; l < k; ++l) h -= f.vtw[i + l * RGM_VTW_LD] * f.dd[l];
             s->hsum[i] = h;
             s->coefV[i] = -h * f.sc[i];
         }
         break;
     }
     case FIN_ARN2: {
-        const int nb = s->nb;
+        // colscale and hsum staged by fin_stage (nb = op.ndV)
+        const int nb = op.ndV;
         for (int i = tid; i < nb; i += blockDim.x) {
-            const double sc = s->colscale[i];
+            const double sc = f.sc[i];
             const double h = dV[i] * sc;
-            s->hsum[i] += h;
+            s->hsum[i] = f.col[i] + h;
             s->coefV[i] = -h * sc;
         }
         break;
     }
     case FIN_ARN3: {
-        const int j = s->J, nb = s->nb;
-        const double hn = sqrt(nrm2);
-        for (int i = tid; i < nb; i += blockDim.x) f.col[i] = s->hsum[i];
-        for (int i = tid; i < j; i += blockDim.x) { f.cs[i] = s->cs[i]; f.sn[i] = s->sn[i]; }
-        if (tid == 0) f.col[nb] = hn;
-        __syncthreads();
-        if (tid == 0) apply_rotations(f.col, f.cs, f.sn, j);
-        __syncthreads();
-        close_column(s, f, j);
-        const bool brk = hn <= 1e-14 * s->wn0;
-        const double sc = brk ? 0.0 : 1.0 / hn;
-        for (int l = tid; l < op.ndW; l += blockDim.x) s->VtW[nb + l * RGM_HLD] = dW[l] * sc;
-        if (tid == 0) {
-            s->J = j + 1;
-            s->iters += 1;
-            s->colscale[nb] = sc;          // happy breakdown: v_{j+1} := 0
-            if (brk) { s->breakdown = 1; s->done = 1; }
-            s->nb = nb + 1;
-            if (fabs(s->g[j + 1]) <= s->tol_abs) s->done = 1;
-            if (s->iters >= s->maxit || s->J >= s->m) s->done = 1;
+        // hsum, cs and sn staged by fin_stage (nb = op.nV = J + 1)
+        const int nb = op.nV, j = nb - 1;
+        __shared__ double sc_sh;
+        if (tid < 32) {
+            // rotated column (warp 0), then the new rotation from (t_j, ||w||)
+            const double a = warp_rotate_column(f.col, f.cs, f.sn, j);
+            if (tid == 0) {
+                const double inv_hn = (nrm2 > 0.0) ? rsqrt(nrm2) : 0.0;
+                const double hn = nrm2 * inv_hn;
+                const double r2 = fma(a, a, nrm2);
+                const double inv_r = (r2 > 0.0) ? rsqrt(r2) : 0.0;
+                const double c = (r2 > 0.0) ? a * inv_r : 1.0, sn = hn * inv_r;
+                f.col[j] = r2 * inv_r;
+                f.col[j + 1] = 0.0;
+                s->cs[j] = c;
+                s->sn[j] = sn;
+                const double g0 = s->g[j], g1 = -sn * g0;
+                s->g[j + 1] = g1;
+                s->g[j] = c * g0;
+                const bool brk = hn <= 1e-14 * s->wn0;
+                const double sc = brk ? 0.0 : inv_hn;
+                sc_sh = sc;
+                s->J = j + 1;
+                const int it = s->iters + 1;
+                s->iters = it;
+                s->colscale[nb] = sc;          // happy breakdown: v_{j+1} := 0
+                int done = 0;
+                if (brk) { s->breakdown = 1; done = 1; }
+                s->nb = nb + 1;
+                if (fabs(g1) <= s->tol_abs || it >= s->maxit || j + 1 >= s->m) done = 1;
+                if (done) s->done = 1;
+            }
         }
+        __syncthreads();
+        double *hc = s->H + (int64_t)j * RGM_HLD;
+        for (int i = tid; i <= j + 1; i += blockDim.x) hc[i] = f.col[i];
+        const double sc = sc_sh;
+        for (int l = tid; l < op.ndW; l += blockDim.x) s->VtW[nb + l * RGM_HLD] = dW[l] * sc;
         break;
     }
     case FIN_AUG3: {
@@ -282,6 +409,32 @@ __device__ void finalize_block(const VecOp<T> &op, const double *d, FinScratch &
     }
     default:
         break;
+    }
+}
+
+// Warp sums of the QMAX per-lane values v[q] (column warp + q * NW of a pass);
+// store(c, sum) is called once per column c < nd by one lane.  For power-of-2
+// QMAX the butterfly halves the live values at each step (QMAX-1 + 5 -
+// log2 QMAX binary64 adds per warp instead of 5 QMAX: the FP64 pipe is narrow).
+template <int QMAX, typename Store>
+__device__ __forceinline__ void warp_sums_store(double (&v)[QMAX], int nd, Store store)
+{
+    constexpr int NW = RGM_THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if constexpr ((QMAX & (QMAX - 1)) == 0 && QMAX <= 32) {
+        warp_multi_reduce<QMAX>(v);
+        const int sh = warp_multi_owner_shift<QMAX>();
+        const int c = warp + (lane >> sh) * NW;
+        if ((lane & ((1 << sh) - 1)) == 0 && c < nd) store(c, v[0]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q) {
+            const int c = warp + q * NW;
+            if (c < nd) {
+                const double t = warp_sum(v[q]);
+                if (lane == 0) store(c, t);
+            }
+        }
     }
 }
 
@@ -432,48 +585,55 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op)
         if (PDL) asm volatile("griddepcontrol.launch_dependents;");
         return PASS_SKIPPED;
     }
-    // per-block partials: one warp reduction per column
-#pragma unroll
-    for (int q = 0; q < QMAX; ++q) {
-        const int c = warp + q * NW;
-        if (c < nd) {
-            const double v = warp_sum(acc[q]);
-            if (lane == 0) op.partials[(int64_t)c * op.nblocks + blockIdx.x] = v;
-        }
+    // per-block partials
+    {
+        double *pp = op.partials + blockIdx.x;
+        const int64_t nbk = op.nblocks;
+        warp_sums_store<QMAX>(acc, nd, [&](int c, double t) { pp[(int64_t)c * nbk] = t; });
     }
 
     // the next pass may start launching; it waits for this grid to complete
     if (PDL) asm volatile("griddepcontrol.launch_dependents;");
-    // ---- the last block reduces the partials and runs the scalar step
-    if (!last_block(op.counter)) return PASS_ARRIVED;
+    // ---- two-level reduction, deterministic (fixed lane order and trees):
+    // the last block of each group of RGM_RGROUP blocks adds the group's
+    // partials (one warp per column, one lane per block); the last group adds
+    // the group sums and runs the scalar step.  No block waits for another.
     __shared__ double dsum[RGM_MAXDOTS];
-    __shared__ double red2[RGM_THREADS];
     __shared__ FinScratch fin;
-    if (nd > 0) {
-        // threads split each column's blocks (independent loads); fixed order
-        const int tpc = max(1, RGM_THREADS / nd);
-        const int ncov = RGM_THREADS / tpc;
-        for (int cbase = 0; cbase < nd; cbase += ncov) {
-            const int c = cbase + (int)threadIdx.x / tpc, part = (int)threadIdx.x % tpc;
+    const int g = blockIdx.x / RGM_RGROUP, gb0 = g * RGM_RGROUP;
+    const int gn = min(RGM_RGROUP, op.nblocks - gb0);
+    if (!last_of(op.gcount + g, (unsigned)gn)) return PASS_ARRIVED;
+    const bool single = (op.ngroups == 1);
+    if (single) fin_stage(op, fin);
+#pragma unroll
+    for (int q = 0; q < QMAX; ++q) {
+        const int c = warp + q * NW;
+        acc[q] = (c < nd && lane < gn) ? __ldcg(op.partials + (int64_t)c * op.nblocks + gb0 + lane) : 0.0;
+    }
+    if (single) {
+        warp_sums_store<QMAX>(acc, nd, [&](int c, double t) { dsum[c] = t; });
+    } else {
+        double *gp = op.gpart + g;
+        const int64_t ng = op.ngroups;
+        warp_sums_store<QMAX>(acc, nd, [&](int c, double t) { gp[(int64_t)c * ng] = t; });
+    }
+    if (threadIdx.x == 0) op.gcount[g] = 0u;
+    if (!single) {
+        if (!last_of(op.counter, (unsigned)op.ngroups)) return PASS_ARRIVED;
+        fin_stage(op, fin);
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q) {
+            const int c = warp + q * NW;
             double v = 0.0;
-            if ((int)threadIdx.x < ncov * tpc && c < nd) {
-                const double *p = op.partials + (int64_t)c * op.nblocks;
-#pragma unroll 8
-                for (int b = part; b < op.nblocks; b += tpc) v += __ldcg(p + b);
-            }
-            red2[threadIdx.x] = v;
-            __syncthreads();
-            for (int cc = threadIdx.x; cc < ncov && cbase + cc < nd; cc += blockDim.x) {
-                double t = 0.0;
-                for (int j = 0; j < tpc; ++j) t += red2[cc * tpc + j];
-                dsum[cbase + cc] = t;
-            }
-            __syncthreads();
+            if (c < nd)
+                for (int gg = lane; gg < op.ngroups; gg += 32) v += __ldcg(op.gpart + (int64_t)c * op.ngroups + gg);
+            acc[q] = v;
         }
+        warp_sums_store<QMAX>(acc, nd, [&](int c, double t) { dsum[c] = t; });
     }
     __syncthreads();
     finalize_block(op, dsum, fin);
-    if (threadIdx.x == 0) *op.counter = 0u;
+    if (threadIdx.x == 0 && !single) *op.counter = 0u;
     return PASS_LAST;
 }
 
@@ -512,10 +672,7 @@ __device__ __forceinline__ bool grid_barrier(int pass_rc, Small *s, unsigned tar
     __shared__ int ok;
     if (pass_rc == PASS_LAST) {
         __syncthreads();                  // the scalar step is complete
-        if (threadIdx.x == 0) {
-            __threadfence();
-            st_release_gpu(&s->gen, target);
-        }
+        if (threadIdx.x == 0) st_release_gpu(&s->gen, target);
         return true;
     }
     if (threadIdx.x == 0) {
@@ -531,7 +688,7 @@ __device__ __forceinline__ bool grid_barrier(int pass_rc, Small *s, unsigned tar
                 good = 0;
                 break;
             }
-            __nanosleep(64);
+            if (it > 256) __nanosleep(64);     // spin first: the release is usually close
         }
         ok = good;
     }
@@ -877,6 +1034,20 @@ static __global__ void lu_kernel(Small *s, int k, const double *gram_uw, const d
         __syncthreads();
     }
     for (int i = threadIdx.x; i < RGM_KMAX * RGM_KMAX; i += blockDim.x) s->LU[i] = M[i];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const double d = M[i + i * RGM_KMAX];
+        s->LUrd[i] = (d != 0.0) ? 1.0 / d : 0.0;
+    }
+    if (threadIdx.x == 0) {
+        // the row swaps as one permutation: (P b)_i = b[perm_i]
+        int pm[RGM_KMAX];
+        for (int i = 0; i < k; ++i) pm[i] = i;
+        for (int j = 0; j < k; ++j) {
+            const int p = s->piv[j];
+            const int t = pm[j]; pm[j] = pm[p]; pm[p] = t;
+        }
+        for (int i = 0; i < k; ++i) s->LUperm[i] = pm[i];
+    }
     if (threadIdx.x == 0) {
         int sing = (k > 0 && (minp == 0.0 || minp < 1e-13 * maxp)) ? 1 : 0;
         s->singular = sing;
