@@ -161,7 +161,8 @@ int rgm_reset_recycling(rgm_solver s);
 
 /* Checkpoint / resume of the recycling state that Algorithm 1 carries from
  * one system of the sequence to the next: the snapshot window (its stored
- * columns, ring position and update count) and the recycle space U.  Not
+ * columns, ring position, update count and the window Gram matrix that the
+ * next update extends by one column) and the recycle space U.  Not
  * described in the paper; it lets a sequence continue in a new handle or a
  * new process with results identical to the uninterrupted run.  The operator
  * is not part of the state (each step sets its own), nor are the singular

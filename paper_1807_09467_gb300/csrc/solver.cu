@@ -99,7 +99,10 @@ struct rgm_solver_s {
     bool coarse_stale = true;
     double *X = nullptr;          // snapshot window, n x window (ring)
     int win_count = 0, win_head = 0, updates = 0;
-    double *Ytmp = nullptr;       // n x kmax scratch for the SVD
+    double *Urow = nullptr;       // row-major copy of U (n x kmax) for the SpMM W = A U
+    double *gwin = nullptr;       // window Gram matrix X^T X kept between updates (WMAX^2)
+    bool gwin_valid = false;      // gwin matches the stored columns
+    int win_last = -1;            // ring slot written by the last update
     // scratch
     double *partials = nullptr;
     unsigned *counter = nullptr;  // [0..3] completion counters, then one per reduction group
@@ -300,10 +303,11 @@ static void prof_collect(rgm_solver s)
 // memory would synchronise the stream).  nx_dev: optional device count.
 template <typename T>
 static int launch_gram(rgm_solver s, const T *X, int64_t ldx, int nx, const T *Y, int64_t ldy,
-                       int mode, const int *nx_dev, int nxmax, double *out)
+                       int mode, const int *nx_dev, int nxmax, double *out, int col = 0)
 {
     if (nxmax <= 0) return RGM_OK;
-    const int npmax = (mode == GRAM_UW) ? nxmax * nxmax + 2 * nxmax : nxmax * (nxmax + 1) / 2;
+    const int npmax = (mode == GRAM_UW) ? nxmax * nxmax + 2 * nxmax
+                      : (mode == GRAM_COL) ? nxmax : nxmax * (nxmax + 1) / 2;
     if (npmax > s->npairs_max || npmax > RGM_GRAM_PMAX * RGM_THREADS) return RGM_E_ARG;
     GramOp<T> op;
     op.n = s->n;
@@ -317,6 +321,7 @@ static int launch_gram(rgm_solver s, const T *X, int64_t ldx, int nx, const T *Y
     op.nx_dev = nx_dev;
     op.mode = mode;
     op.nxmax = nxmax;
+    op.col = col;
     op.partials = s->partials;
     op.counter = s->counter;
     op.out = out;
@@ -384,17 +389,20 @@ __global__ void set_tol_kernel(Small *s, double rtol)
 static int coarse_setup(rgm_solver s)
 {
     const int k = s->k_cur;
-    Arnoldi<double> a;
-    a.slice_ptr = s->slice_ptr; a.scol = s->scol; a.sval = s->sval; a.perm = s->perm;
-    a.V = s->V; a.U = s->U; a.W = s->W;
-    for (int i = 0; i < k; ++i) {
-        VecOp<double> op = base_op(s, a);
-        op.src = SRC_SPMV;
-        op.x = s->U + (int64_t)i * s->ld;
-        op.out = s->W + (int64_t)i * s->ld;
-        int rc = launch(s, op);
-        if (rc) return rc;
+    if (k > 0) {   // W = A U, one pass over the operator
+        {
+            ProfScope ps_(s, RGM_PROF_OTHER, 0.0, 16.0 * (double)s->n * k);
+            urow_kernel<<<(unsigned)((s->n + RGM_UROW_ROWS - 1) / RGM_UROW_ROWS), 256, 0, s->st>>>(
+                s->Urow, s->U, s->n, s->ld, k);
+        }
+        const int grid = (int)std::min<int64_t>((s->nslices + 7) / 8, 8 * (int64_t)s->nsm);
+        const double flops = 2.0 * (double)s->nnz * k;
+        const double bytes = 12.0 * (double)s->nnz + 8.0 * (double)s->n * (2.0 * k + 1.0);
+        ProfScope ps_(s, RGM_PROF_OTHER, flops, bytes);
+        spmm_kernel<<<grid, 256, 0, s->st>>>(s->slice_ptr, s->scol, s->sval, s->perm, s->nslices, s->Urow,
+                                             k, s->W, s->ld);
     }
+    CK(cudaGetLastError());
     // E_ij = u_i . w_j, then ||u_i||^2, ||w_i||^2
     int rc = launch_gram<double>(s, s->U, s->ld, k, s->W, s->ld, GRAM_UW, nullptr, k, s->gram_out);
     if (rc) return rc;
@@ -719,10 +727,21 @@ static int svd_update(rgm_solver s)
 {
     const rgm_config &c = s->cfg;
     const int cnt = s->win_count;
-    int rc = launch_gram<double>(s, s->X, s->ld, cnt, s->X, s->ld, GRAM_PACKED, nullptr, cnt,
-                                 s->gram_out);
-    if (rc) return rc;
-    { ProfScope ps_(s, RGM_PROF_SMALL); sym_eig_select_kernel<<<1, 512, EIG_SMEM_BYTES, s->st>>>(s->sm, s->gram_out, cnt, c.k,
+    int rc;
+    if (s->gwin_valid) {
+        // only the new snapshot's row and column of X^T X change
+        if ((rc = launch_gram<double>(s, s->X, s->ld, cnt, s->X, s->ld, GRAM_COL, nullptr, cnt, s->gram_out,
+                                      s->win_last)))
+            return rc;
+        { ProfScope ps_(s, RGM_PROF_SMALL); gram_insert_kernel<<<1, 64, 0, s->st>>>(s->gwin, s->gram_out, s->win_last, cnt); }
+    } else {
+        if ((rc = launch_gram<double>(s, s->X, s->ld, cnt, s->X, s->ld, GRAM_PACKED, nullptr, cnt, s->gram_out)))
+            return rc;
+        { ProfScope ps_(s, RGM_PROF_SMALL); gram_unpack_kernel<<<1, 256, 0, s->st>>>(s->gwin, s->gram_out, cnt); }
+    }
+    CK(cudaGetLastError());
+    s->gwin_valid = true;
+    { ProfScope ps_(s, RGM_PROF_SMALL); sym_eig_select_kernel<<<1, 512, EIG_SMEM_BYTES, s->st>>>(s->sm, s->gwin, cnt, c.k,
                                                              c.select_smallest, c.rel_drop); }
     CK(cudaGetLastError());
     const int kmax = std::min(c.k, cnt);
@@ -798,7 +817,7 @@ const char *rgm_status_string(int code)
 static void free_all(rgm_solver s)
 {
     void *dp[] = {s->slice_ptr, s->scol, s->perm, s->csr2sell, s->sval, s->sval32, s->val_stage, s->V, s->U, s->W, s->w, s->r, s->b, s->x,
-                  s->V32, s->U32, s->W32, s->w32, s->r32, s->b32, s->x32, s->X, s->Ytmp,
+                  s->V32, s->U32, s->W32, s->w32, s->r32, s->b32, s->x32, s->X, s->Urow, s->gwin,
                   s->partials, s->counter, s->gpart, s->pairs, s->gram_out, s->sm};
     for (void *p : dp)
         if (p) cudaFree(p);
@@ -852,6 +871,8 @@ int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
     ALLOC(s->b, sizeof(double) * s->ld);
     ALLOC(s->x, sizeof(double) * s->ld);
     ALLOC(s->X, sizeof(double) * s->ld * c.window);
+    ALLOC(s->Urow, sizeof(double) * s->ld * kmax);
+    ALLOC(s->gwin, sizeof(double) * RGM_WMAX * RGM_WMAX);
     ALLOC(s->partials, sizeof(double) * (size_t)std::max(RGM_MAXDOTS, s->npairs_max) * s->nblocks);
     s->ngroups = (s->nblocks + RGM_RGROUP - 1) / RGM_RGROUP;
     ALLOC(s->counter, sizeof(unsigned) * (4 + s->ngroups));
@@ -1054,6 +1075,11 @@ int rgm_update_recycle_svd(rgm_solver s, const double *x, int flags, int *k_used
     if (!s || !x) return RGM_E_ARG;
     CK(cudaMemcpyAsync(s->X + (int64_t)s->win_head * s->ld, x, sizeof(double) * s->n, kind_in(flags),
                        s->st));
+    // the resident window Gram matrix tracks one new column per update; a
+    // column stored without an update (svd_interval > 1) invalidates it
+    if (s->win_last >= 0 && !(s->cfg.k > 0 && (s->updates + 1) % s->cfg.svd_interval == 0))
+        s->gwin_valid = false;
+    s->win_last = s->win_head;
     s->win_head = (s->win_head + 1) % s->cfg.window;
     if (s->win_count < s->cfg.window) ++s->win_count;
     ++s->updates;
@@ -1091,6 +1117,8 @@ int rgm_reset_recycling(rgm_solver s)
     s->win_count = 0;
     s->win_head = 0;
     s->updates = 0;
+    s->gwin_valid = false;
+    s->win_last = -1;
     CK(cudaStreamSynchronize(s->st));
     s->k_cur = 0;
     s->k_pending = false;
@@ -1099,13 +1127,15 @@ int rgm_reset_recycling(rgm_solver s)
 }
 
 // Checkpoint layout: StateHeader, then win_used window columns (ring slots
-// 0..win_used-1, n doubles each), then k_cur columns of U.
+// 0..win_used-1, n doubles each), k_cur columns of U, and (gram set) the
+// win_used x win_used window Gram matrix the next update builds on.
 namespace {
 struct StateHeader {
     uint32_t magic, version;
     int64_t n;
     int32_t window, k_cur, win_count, win_head;
     int64_t updates;
+    int32_t gram, reserved;
 };
 const uint32_t kStateMagic = 0x314d4752u;   // bytes "RGM1" in little-endian order
 }  // namespace
@@ -1116,18 +1146,22 @@ int rgm_export_state(rgm_solver s, void *buf, size_t *bytes)
     int rc = sync_recycle_dim(s);
     if (rc) return rc;
     const int win_used = s->win_count;   // ring slots 0..win_count-1 hold data
-    const size_t need = sizeof(StateHeader) + sizeof(double) * (size_t)s->n * (win_used + s->k_cur);
+    const int with_gram = s->gwin_valid ? 1 : 0;
+    const size_t need = sizeof(StateHeader) + sizeof(double) * ((size_t)s->n * (win_used + s->k_cur) +
+                                                                (size_t)with_gram * win_used * win_used);
     if (!buf) { *bytes = need; return RGM_OK; }
     if (*bytes < need) return RGM_E_ARG;
     StateHeader h;
     h.magic = kStateMagic;
-    h.version = 1;
+    h.version = 2;
     h.n = s->n;
     h.window = s->cfg.window;
     h.k_cur = s->k_cur;
     h.win_count = s->win_count;
     h.win_head = s->win_head;
     h.updates = s->updates;
+    h.gram = with_gram;
+    h.reserved = 0;
     std::memcpy(buf, &h, sizeof h);
     double *d = reinterpret_cast<double *>(static_cast<char *>(buf) + sizeof h);
     for (int i = 0; i < win_used; ++i)
@@ -1137,6 +1171,10 @@ int rgm_export_state(rgm_solver s, void *buf, size_t *bytes)
     for (int i = 0; i < s->k_cur; ++i)
         CK(cudaMemcpyAsync(d + (size_t)i * s->n, s->U + (int64_t)i * s->ld, sizeof(double) * s->n,
                            cudaMemcpyDeviceToHost, s->st));
+    d += (size_t)s->k_cur * s->n;
+    for (int j = 0; j < win_used && with_gram; ++j)
+        CK(cudaMemcpyAsync(d + (size_t)j * win_used, s->gwin + (int64_t)j * RGM_WMAX,
+                           sizeof(double) * win_used, cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
     *bytes = need;
     return RGM_OK;
@@ -1147,11 +1185,12 @@ int rgm_import_state(rgm_solver s, const void *buf, size_t bytes)
     if (!s || !buf || bytes < sizeof(StateHeader)) return RGM_E_ARG;
     StateHeader h;
     std::memcpy(&h, buf, sizeof h);
-    if (h.magic != kStateMagic || h.version != 1 || h.n != s->n || h.window != s->cfg.window ||
+    if (h.magic != kStateMagic || h.version != 2 || h.n != s->n || h.window != s->cfg.window ||
         h.k_cur < 0 || h.k_cur > s->cfg.k || h.win_count < 0 || h.win_count > h.window ||
-        h.win_head < 0 || h.win_head >= h.window || h.updates < h.win_count)
+        h.win_head < 0 || h.win_head >= h.window || h.updates < h.win_count || h.gram < 0 || h.gram > 1)
         return RGM_E_ARG;
-    const size_t need = sizeof(StateHeader) + sizeof(double) * (size_t)s->n * (h.win_count + h.k_cur);
+    const size_t need = sizeof(StateHeader) + sizeof(double) * ((size_t)s->n * (h.win_count + h.k_cur) +
+                                                                (size_t)h.gram * h.win_count * h.win_count);
     if (bytes != need) return RGM_E_ARG;
     CK(cudaStreamSynchronize(s->st));
     const double *d = reinterpret_cast<const double *>(static_cast<const char *>(buf) + sizeof h);
@@ -1162,7 +1201,13 @@ int rgm_import_state(rgm_solver s, const void *buf, size_t bytes)
     for (int i = 0; i < h.k_cur; ++i)
         CK(cudaMemcpyAsync(s->U + (int64_t)i * s->ld, d + (size_t)i * s->n, sizeof(double) * s->n,
                            cudaMemcpyHostToDevice, s->st));
+    d += (size_t)h.k_cur * s->n;
+    for (int j = 0; j < h.win_count && h.gram; ++j)
+        CK(cudaMemcpyAsync(s->gwin + (int64_t)j * RGM_WMAX, d + (size_t)j * h.win_count,
+                           sizeof(double) * h.win_count, cudaMemcpyHostToDevice, s->st));
     CK(cudaStreamSynchronize(s->st));
+    s->gwin_valid = h.gram != 0;
+    s->win_last = -1;
     s->win_count = h.win_count;
     s->win_head = h.win_head;
     s->updates = (int)h.updates;

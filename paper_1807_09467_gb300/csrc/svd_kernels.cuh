@@ -30,6 +30,84 @@ __global__ void clear_skip_kernel(Small *s)
     if (threadIdx.x == 0) s->skip = 0;
 }
 
+// Row-major copy of the k columns of U (row r at Urow + r k) for the SpMM
+// gather, through a shared-memory tile of RGM_UROW_ROWS rows (coalesced on
+// both sides).
+#define RGM_UROW_ROWS 128
+__global__ void __launch_bounds__(256) urow_kernel(double *__restrict__ Urow, const double *__restrict__ U,
+                                                   int64_t n, int64_t ld, int k)
+{
+    __shared__ double t[RGM_UROW_ROWS * (RGM_KMAX + 1)];
+    const int64_t r0 = (int64_t)blockIdx.x * RGM_UROW_ROWS;
+    const int nr = (int)min((int64_t)RGM_UROW_ROWS, n - r0);
+    for (int i = threadIdx.x; i < RGM_UROW_ROWS * k; i += blockDim.x) {
+        const int r = i % RGM_UROW_ROWS, c = i / RGM_UROW_ROWS;
+        if (r < nr) t[r * (RGM_KMAX + 1) + c] = U[r0 + r + (int64_t)c * ld];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nr * k; i += blockDim.x) {
+        const int r = i / k, c = i % k;
+        Urow[(r0 + r) * k + c] = t[r * (RGM_KMAX + 1) + c];
+    }
+}
+
+// W = A U for k columns in one pass over the sliced-ELL operator (the operator
+// is read once per RGM_SPMM_KB columns instead of once per column): one warp
+// per 32-row slice, one lane per row, RGM_SPMM_KB accumulators per lane; the
+// gathered rows of U come from the row-major copy (contiguous per entry).
+#define RGM_SPMM_KB 8
+__global__ void __launch_bounds__(256) spmm_kernel(const int64_t *__restrict__ slice_ptr,
+                                                   const int32_t *__restrict__ scol,
+                                                   const double *__restrict__ sval,
+                                                   const int32_t *__restrict__ perm, int64_t nslices,
+                                                   const double *__restrict__ Urow, int k,
+                                                   double *__restrict__ W, int64_t ldw)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < nslices; sl += nwarps) {
+        const int64_t p0 = slice_ptr[sl], p1 = slice_ptr[sl + 1];
+        const int pr = perm[(sl << 5) + lane];
+        for (int c0 = 0; c0 < k; c0 += RGM_SPMM_KB) {
+            double acc[RGM_SPMM_KB];
+#pragma unroll
+            for (int c = 0; c < RGM_SPMM_KB; ++c) acc[c] = 0.0;
+            for (int64_t e = p0 + lane; e < p1; e += 32) {
+                const double a = sval[e];
+                const double *u = Urow + (int64_t)scol[e] * k + c0;
+#pragma unroll
+                for (int c = 0; c < RGM_SPMM_KB; ++c)
+                    if (c0 + c < k) acc[c] = fma(a, u[c], acc[c]);
+            }
+            if (pr >= 0) {
+#pragma unroll
+                for (int c = 0; c < RGM_SPMM_KB; ++c)
+                    if (c0 + c < k) W[pr + (int64_t)(c0 + c) * ldw] = acc[c];
+            }
+        }
+    }
+}
+
+// The window Gram matrix kept between updates (full, leading dimension
+// RGM_WMAX): a new snapshot in ring slot `slot` replaces row and column slot
+// with its dots against the c stored columns (col[j] = x_slot . x_j).
+__global__ void gram_insert_kernel(double *gwin, const double *col, int slot, int c)
+{
+    for (int j = threadIdx.x; j < c; j += blockDim.x) {
+        gwin[slot + j * RGM_WMAX] = col[j];
+        gwin[j + slot * RGM_WMAX] = col[j];
+    }
+}
+
+// Full window Gram matrix from the packed pair list (rebuild after a reset).
+__global__ void gram_unpack_kernel(double *gwin, const double *packed, int c)
+{
+    for (int t = threadIdx.x; t < c * c; t += blockDim.x) {
+        const int i = t % c, j = t / c;
+        gwin[i + j * RGM_WMAX] = packed[i <= j ? j * (j + 1) / 2 + i : i * (i + 1) / 2 + j];
+    }
+}
+
 // Unpack the Gram matrix of columns 0..c-1 from the pair list (i <= j, j-major).
 __device__ inline int packed_index(int i, int j) { return j * (j + 1) / 2 + i; }
 
@@ -39,6 +117,7 @@ __device__ inline int packed_index(int i, int j) { return j * (j + 1) / 2 + i; }
 #define EIG_SMEM_BYTES (2 * RGM_WMAX * RGM_WMAX * sizeof(double))
 __global__ void sym_eig_select_kernel(Small *s, const double *gram, int c, int k,
                                       int select_smallest, double rel_drop)
+// gram: the full c x c window Gram matrix, leading dimension RGM_WMAX
 {
     extern __shared__ double eig_smem[];       // G and Phi, RGM_WMAX x RGM_WMAX each
     double *G = eig_smem, *P = eig_smem + RGM_WMAX * RGM_WMAX;
@@ -48,7 +127,7 @@ __global__ void sym_eig_select_kernel(Small *s, const double *gram, int c, int k
     for (int t = threadIdx.x; t < ce * ce; t += blockDim.x) {
         int i = t % ce, j = t / ce;
         double v = 0.0;
-        if (i < c && j < c) v = gram[i <= j ? packed_index(i, j) : packed_index(j, i)];
+        if (i < c && j < c) v = gram[i + j * RGM_WMAX];
         G[i + j * RGM_WMAX] = v;
         P[i + j * RGM_WMAX] = (i == j) ? 1.0 : 0.0;
     }
@@ -146,33 +225,43 @@ __global__ void sym_eig_select_kernel(Small *s, const double *gram, int c, int k
         }
         if (!rot_flag[fl]) break;
     }
+    // eigenvalues, stable descending order by rank counting (ties by index)
+    __shared__ double lam[RGM_WMAX], isg[RGM_WMAX];
+    __shared__ int ord[RGM_WMAX];
+    __shared__ int sel[2];                       // k_new, first selected rank
+    for (int i = threadIdx.x; i < c; i += blockDim.x) lam[i] = G[i + i * RGM_WMAX];
+    __syncthreads();
+    for (int i = threadIdx.x; i < c; i += blockDim.x) {
+        const double li = lam[i];
+        int r = 0;
+        for (int j = 0; j < c; ++j) r += (lam[j] > li || (lam[j] == li && j < i)) ? 1 : 0;
+        ord[r] = i;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        // eigenvalues (clamped at 0), stable descending order
-        int ord[RGM_WMAX];
-        double lam[RGM_WMAX];
-        for (int i = 0; i < c; ++i) { lam[i] = G[i + i * RGM_WMAX]; ord[i] = i; }
-        for (int i = 1; i < c; ++i) {
-            int o = ord[i], j = i - 1;
-            while (j >= 0 && lam[ord[j]] < lam[o]) { ord[j + 1] = ord[j]; --j; }
-            ord[j + 1] = o;
-        }
-        for (int i = 0; i < c; ++i) { s->eval[i] = lam[i]; s->ord[i] = ord[i]; }
-        const double s1 = lam[ord[0]] > 0 ? sqrt(lam[ord[0]]) : 0.0;
+        // keep sigma_i = sqrt(lambda_i) > 0 with sigma_i >= rel_drop sigma_1
+        // (compared as squares)
+        const double l1 = lam[ord[0]];
+        const double thr = (l1 > 0.0) ? rel_drop * rel_drop * l1 : INFINITY;
         int nz = 0;
-        while (nz < c) {
-            double l = lam[ord[nz]];
-            double sg = l > 0 ? sqrt(l) : 0.0;
-            if (!(sg > 0.0 && sg >= rel_drop * s1)) break;
-            ++nz;
-        }
+        while (nz < c && lam[ord[nz]] > 0.0 && lam[ord[nz]] >= thr) ++nz;
         const int kn = k < nz ? k : nz;
-        const int first = select_smallest ? nz - kn : 0;
-        for (int l = 0; l < kn; ++l) {
-            int e = ord[first + l];
-            double sg = sqrt(lam[e]);
-            for (int m = 0; m < c; ++m) s->evec[m + l * RGM_WMAX] = P[m + e * RGM_WMAX] / sg;
-        }
+        sel[0] = kn;
+        sel[1] = select_smallest ? nz - kn : 0;
         s->k_new = kn;
+    }
+    __syncthreads();
+    const int kn = sel[0], first = sel[1];
+    for (int i = threadIdx.x; i < c; i += blockDim.x) {
+        s->eval[i] = lam[i];
+        s->ord[i] = ord[i];
+    }
+    for (int l = threadIdx.x; l < kn; l += blockDim.x) isg[l] = rsqrt(lam[ord[first + l]]);
+    __syncthreads();
+    // evec[:, l] = phi_e / sigma_e for the selected modes e
+    for (int t = threadIdx.x; t < kn * c; t += blockDim.x) {
+        const int l = t / c, m = t % c, e = ord[first + l];
+        s->evec[m + l * RGM_WMAX] = P[m + e * RGM_WMAX] * isg[l];
     }
 }
 

@@ -838,7 +838,8 @@ __global__ void sell_scatter_kernel(double *sval, float *sval32, const Tin *val,
 // stride, conflict-free), and each thread owns pairs p = tid + k * blockDim.
 enum GramMode {
     GRAM_PACKED = 0,   // all pairs i <= j of the nx columns of X (packed, j-major)
-    GRAM_UW = 1        // E pattern: u_i . w_j (i + j nx), then u_i . u_i, then w_i . w_i
+    GRAM_UW = 1,       // E pattern: u_i . w_j (i + j nx), then u_i . u_i, then w_i . w_i
+    GRAM_COL = 2       // one column against all: x_col . x_j, j < nx
 };
 
 template <typename T>
@@ -850,6 +851,7 @@ struct GramOp {
     const int *nx_dev;       // if set, nx is read from the device (dynamic column count)
     int mode;
     int nxmax;               // bound on nx (shared-memory sizing)
+    int col;                 // GRAM_COL: the column dotted with all others
     double *partials;
     unsigned *counter;
     double *out;
@@ -874,7 +876,7 @@ __global__ void __launch_bounds__(RGM_THREADS) gram_kernel(GramOp<T> op)
     const int nx = op.nx_dev ? *op.nx_dev : op.nx;
     const int ny = (op.mode == GRAM_UW) ? nx : 0;
     const int ncol = nx + ny, ts = op.tile + 1;
-    const int npairs = (op.mode == GRAM_UW) ? nx * nx + 2 * nx : nx * (nx + 1) / 2;
+    const int npairs = (op.mode == GRAM_UW) ? nx * nx + 2 * nx : (op.mode == GRAM_COL) ? nx : nx * (nx + 1) / 2;
     const int64_t r0 = (int64_t)blockIdx.x * op.rpb;
     const int64_t r1 = min(op.n, r0 + op.rpb);
     double acc[RGM_GRAM_PMAX];
@@ -887,6 +889,9 @@ __global__ void __launch_bounds__(RGM_THREADS) gram_kernel(GramOp<T> op)
         if (p < npairs) {
             if (op.mode == GRAM_PACKED) {
                 packed_pair(p, &a, &b);
+            } else if (op.mode == GRAM_COL) {
+                a = op.col;
+                b = p;
             } else if (p < nx * nx) {
                 a = p % nx;
                 b = nx + p / nx;
