@@ -72,14 +72,14 @@ def src_digest():
     return h.hexdigest()[:16]
 
 
-def traffic_record(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources; else None."""
+def traffic_record(workload, precision, kernel):
+    """DRAM bytes per launch of `kernel` on this workload from the committed
+    ncu summary, if it was taken on the current kernel sources; else None."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
     except Exception:
         return None
-    ent = rec.get(kernel)
+    ent = rec.get(f"{workload}/{precision}/{kernel}")
     if not ent or ent.get("src_sha") != src_digest():
         return None
     return ent.get("dram_bytes_per_launch")
@@ -319,7 +319,7 @@ def ours(args):
     roof.update({"kernel": dom, "launches": d["launches"], "ms_per_launch": round(per_launch_ms, 5),
                  "algorithmic_flops_per_launch": d["flops"] / d["launches"],
                  "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
-                 "traffic": traffic_record(dom)})
+                 "traffic": traffic_record(w.name, args.precision, dom)})
     kernel_share = {k: {"ms": round(v["ms"], 3), "share": round(v["ms"] / tot_ms, 4),
                         "launches": v["launches"]} for k, v in kinds.items()}
     seg = main["seg_ms"]
