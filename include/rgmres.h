@@ -65,6 +65,15 @@ typedef enum {
 } rgm_precision;
 
 typedef enum {
+    RGM_PROJ_OBLIQUE = 0,    /* P = I - W E^{-1} U^T, W = A U, E = U^T W (Table 1 oblique)      */
+    RGM_PROJ_ORTHOGONAL = 1, /* P = I - U (U^T U)^{-1} U^T (Table 1 orthogonal, Eq. P_A_variant);
+                                each cycle ends with the projection correction
+                                x += U E^{-1} U^T (b - A x) (Eq. augmented_iterate)           */
+    RGM_PROJ_LS = 2          /* P = I - W (W^T W)^{-1} W^T (Table 1 LS); cycle-end correction
+                                x += U (W^T W)^{-1} W^T (b - A x), so I - A Q = P            */
+} rgm_projector;
+
+typedef enum {
     RGM_LAUNCH_AUTO = 0,     /* the Arnoldi steps of a cycle run in one cooperative launch
                                 (grid barriers between the fused passes) when the grid fits
                                 on the device at once; otherwise one launch per pass        */
@@ -85,6 +94,7 @@ typedef struct {
     int inner_cycles;     /* FP32_IR: GMRES cycles per refinement                           */
     int max_refinements;  /* FP32_IR: cap on refinement steps                               */
     int launch_policy;    /* rgm_launch_policy                                              */
+    int proj;             /* deflated mode: rgm_projector of the Krylov operator P A       */
     double rtol;          /* converged when ||b - A x||_2 <= rtol ||b||_2                   */
     double inner_rtol;    /* FP32_IR: inner solve to inner_rtol * ||r||                     */
     double rel_drop;      /* drop singular values below rel_drop * sigma_1                 */

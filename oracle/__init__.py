@@ -27,7 +27,7 @@ OK, W_NOT_CONVERGED, W_SINGULAR_COARSE = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle C sources with gcc (plain -O2, no fast-math)."""
+    """Compile the oracle C sources with gcc (plain -O2, no fast-math, no FMA contraction)."""
     srcs = [os.path.join(_HERE, s) for s in _SRCS]
     hdr = os.path.join(_HERE, "oracle.h")
     if not force and os.path.exists(_LIB_PATH):
@@ -36,7 +36,9 @@ def build(force: bool = False) -> str:
             return _LIB_PATH
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fno-fast-math",
+    # -ffp-contract=off: every operation rounds as written (no fused multiply-add
+    # on targets where the compiler would contract), so results agree across hosts
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
            "-o", tmp] + srcs + ["-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)

@@ -50,6 +50,10 @@ struct Small {
     double LUrd[RGM_KMAX];                // reciprocals of the U pivots of LU
     int piv[RGM_KMAX];                    // row swaps of the LU, in order
     int LUperm[RGM_KMAX];                 // the same swaps as one permutation
+    double LUP[RGM_KMAX * RGM_KMAX];      // LU of the projector's Gram matrix Y^T Y
+    double LUPrd[RGM_KMAX];               //   (orthogonal: Y = U, least squares: Y = A U)
+    int pivP[RGM_KMAX];
+    int LUPperm[RGM_KMAX];
     double dots[RGM_MAXDOTS];             // last reduced dot products
     double gram[RGM_WMAX * RGM_WMAX];     // last reduced Gram matrix
     double evec[RGM_WMAX * RGM_WMAX];     // eigenvectors of the window Gram matrix

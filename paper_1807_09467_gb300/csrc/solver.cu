@@ -157,6 +157,9 @@ static VecOp<T> base_op(rgm_solver s, const Arnoldi<T> &a)
     op.sm = s->sm;
     op.fin = FIN_NONE;
     op.gate = GATE_NONE;
+    op.arg = 0;
+    op.lu_sel = 0;
+    op.dyn = 0;
     return op;
 }
 
@@ -406,8 +409,15 @@ static int coarse_setup(rgm_solver s)
     // E_ij = u_i . w_j, then ||u_i||^2, ||w_i||^2
     int rc = launch_gram<double>(s, s->U, s->ld, k, s->W, s->ld, GRAM_UW, nullptr, k, s->gram_out);
     if (rc) return rc;
-    { ProfScope ps_(s, RGM_PROF_SMALL); lu_kernel<<<1, 256, 0, s->st>>>(s->sm, k, s->gram_out, s->gram_out + k * k); }
+    { ProfScope ps_(s, RGM_PROF_SMALL); lu_kernel<<<1, 256, 0, s->st>>>(s->sm, k, s->gram_out, s->gram_out + k * k, 0); }
     CK(cudaGetLastError());
+    if (s->cfg.proj != RGM_PROJ_OBLIQUE && k > 0) {
+        // Gram matrix of the projector's columns: U (orthogonal) or W = A U (least squares)
+        const double *Y = (s->cfg.proj == RGM_PROJ_LS) ? s->W : s->U;
+        if ((rc = launch_gram<double>(s, Y, s->ld, k, Y, s->ld, GRAM_PACKED, nullptr, k, s->gram_out))) return rc;
+        { ProfScope ps_(s, RGM_PROF_SMALL); lu_kernel<<<1, 256, 0, s->st>>>(s->sm, k, s->gram_out, nullptr, 1); }
+        CK(cudaGetLastError());
+    }
     rc = read_header(s);
     if (rc) return rc;
     // binary32 copies for the GMRES-IR inner solve
@@ -420,6 +430,30 @@ static int coarse_setup(rgm_solver s)
     return RGM_OK;
 }
 
+// Columns of the deflation projector P w = w - Zp Gp^{-1} Yp^T w (Table 1) and
+// of the cycle-end correction x += U Gc^{-1} Yc^T (b - A x), W = A U:
+// oblique Yp = U, Zp = W, Gp = E; orthogonal Yp = Zp = U, Gp = U^T U;
+// least squares Yp = Zp = W, Gp = W^T W.  The correction uses Yc = U, Gc = E
+// except for least squares (Yc = W, Gc = W^T W, so that I - A Q = P).
+template <typename T>
+struct ProjCols {
+    const T *Yp, *Zp, *Yc;
+    int psel, csel;      // LU factors: 0 = E's, 1 = the projector's Gram matrix
+};
+
+template <typename T>
+static ProjCols<T> proj_cols(rgm_solver s, const Arnoldi<T> &a)
+{
+    ProjCols<T> p;
+    const int pj = s->cfg.proj;
+    p.Yp = (pj == RGM_PROJ_LS) ? a.W : a.U;
+    p.Zp = (pj == RGM_PROJ_ORTHOGONAL) ? a.U : a.W;
+    p.Yc = (pj == RGM_PROJ_LS) ? a.W : a.U;
+    p.psel = (pj != RGM_PROJ_OBLIQUE) ? 1 : 0;
+    p.csel = (pj == RGM_PROJ_LS) ? 1 : 0;
+    return p;
+}
+
 // The three fused passes of an Arnoldi step with CGS2 (operator P A when kdef
 // recycle columns deflate): A v_j and its dots with [U | V], the first
 // Gram-Schmidt update and the dots of the second pass, the second update with
@@ -427,16 +461,18 @@ static int coarse_setup(rgm_solver s)
 template <typename T>
 static void arnoldi_passes(rgm_solver s, const Arnoldi<T> &a, int kdef, CycleOp<T> &c)
 {
+    const ProjCols<T> pc = proj_cols(s, a);
     VecOp<T> op = base_op(s, a);
     op.src = SRC_SPMV; op.x = a.V; op.xscale = 0; op.out = a.w;
+    op.U = pc.Yp; op.lu_sel = pc.psel;
     op.ndU = kdef; op.dnorm = 1; op.dyn = DYN_NDV_NB; op.fin = FIN_ARN1;
     c.pass[0] = op;
     op = base_op(s, a);
-    op.src = SRC_AXPY; op.win = a.w; op.out = a.w; op.nW = kdef;
+    op.src = SRC_AXPY; op.win = a.w; op.out = a.w; op.nW = kdef; op.W = pc.Zp;
     op.dyn = DYN_NV_NB | DYN_NDV_NB; op.fin = FIN_ARN2;
     c.pass[1] = op;
     op = base_op(s, a);
-    op.src = SRC_AXPY; op.win = a.w; op.dyn = DYN_NV_NB | DYN_OUT_VNB;
+    op.src = SRC_AXPY; op.win = a.w; op.dyn = DYN_NV_NB | DYN_OUT_VNB; op.W = pc.Zp;
     op.ndW = kdef; op.dnorm = 1; op.fin = FIN_ARN3;
     c.pass[2] = op;
     c.m = s->cfg.m;
@@ -516,15 +552,18 @@ static int gmres_cycles(rgm_solver s, const Arnoldi<T> &a, int mode, int k, int 
         CK(cudaGetLastError());
         // start vector: r, or P r for the deflated oblique method (Table 1)
         if (mode == RGM_DEFLATED) {
+            const ProjCols<T> pc = proj_cols(s, a);
             VecOp<T> op = base_op(s, a);
             if (!s->cfg.start_r) {
                 op.src = SRC_COPY; op.win = a.r; op.out = a.w; op.ndU = k; op.fin = FIN_START_DEF1;
+                op.U = pc.Yp; op.lu_sel = pc.psel;
                 if ((rc = launch(s, op))) return rc;
                 op = base_op(s, a);
                 op.src = SRC_AXPY; op.win = a.w; op.nW = k;
             } else {
                 op.src = SRC_COPY; op.win = a.r;
             }
+            op.W = pc.Zp;
             op.out = a.V; op.ndW = k; op.dnorm = 1; op.fin = FIN_START_DEF2;
             if ((rc = launch(s, op))) return rc;
         } else {
@@ -582,9 +621,11 @@ static int gmres_cycles(rgm_solver s, const Arnoldi<T> &a, int mode, int k, int 
             op.nU = (mode == RGM_AUGMENTED) ? k : 0;
             if ((rc = launch(s, op))) return rc;
         }
-        if (mode == RGM_DEFLATED) {   // coarse correction x += U E^{-1} U^T (b - A x)
+        if (mode == RGM_DEFLATED) {   // cycle-end correction x += U Gc^{-1} Yc^T (b - A x)
+            const ProjCols<T> pc = proj_cols(s, a);
             VecOp<T> op = base_op(s, a);
             op.src = SRC_RES; op.x = a.x; op.b = a.b; op.out = a.r; op.ndU = k; op.fin = FIN_COARSE;
+            op.U = pc.Yc; op.lu_sel = pc.csel;
             if ((rc = launch(s, op))) return rc;
             op = base_op(s, a);
             op.src = SRC_AXPY; op.win = a.x; op.out = a.x; op.nU = k;
@@ -835,7 +876,8 @@ int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
         c.window > RGM_WMAX || c.svd_interval < 1 || c.mode < 0 || c.mode > 2 || c.precision < 0 ||
         c.precision > 1 || c.maxit < 0 || !(c.rtol >= 0) || c.inner_cycles < 1 ||
         c.max_refinements < 1 || !(c.inner_rtol > 0) || !(c.rel_drop >= 0) ||
-        c.launch_policy < RGM_LAUNCH_AUTO || c.launch_policy > RGM_LAUNCH_PER_PASS)
+        c.launch_policy < RGM_LAUNCH_AUTO || c.launch_policy > RGM_LAUNCH_PER_PASS ||
+        c.proj < RGM_PROJ_OBLIQUE || c.proj > RGM_PROJ_LS)
         return RGM_E_ARG;
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RGM_E_CUDA;

@@ -69,6 +69,7 @@ struct VecOp {
     int fin;
     int gate;
     int arg;                 // phase argument (appended column index)
+    int lu_sel;              // small solves with E's LU (0) or the projector's (1)
     int dyn;                 // DYN_* bits: counts and output column read from Small
 };
 
@@ -112,16 +113,18 @@ __device__ inline void lu_solve_small(int k, const double *LU, int ld, const int
 
 // Stage the k x k LU factors, pivots and pivot reciprocals of E in shared
 // memory (whole block).
-__device__ inline void stage_lu(const Small *s, int k, FinScratch &f)
+__device__ inline void stage_lu(const Small *s, int k, FinScratch &f, int sel)
 {
+    const double *LU = sel ? s->LUP : s->LU, *rd = sel ? s->LUPrd : s->LUrd;
+    const int *piv = sel ? s->pivP : s->piv, *pm = sel ? s->LUPperm : s->LUperm;
     for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
         int i = t % k, j = t / k;
-        f.LU[i + j * RGM_KMAX] = s->LU[i + j * RGM_KMAX];
+        f.LU[i + j * RGM_KMAX] = LU[i + j * RGM_KMAX];
     }
     for (int t = threadIdx.x; t < k; t += blockDim.x) {
-        f.piv[t] = s->piv[t];
-        f.rd[t] = s->LUrd[t];
-        f.perm[t] = s->LUperm[t];
+        f.piv[t] = piv[t];
+        f.rd[t] = rd[t];
+        f.perm[t] = pm[t];
     }
 }
 
@@ -221,12 +224,12 @@ __device__ void fin_stage(const VecOp<T> &op, FinScratch &f)
     switch (op.fin) {
     case FIN_COARSE:
     case FIN_START_DEF1:
-        stage_lu(s, op.ndU, f);
+        stage_lu(s, op.ndU, f, op.lu_sel);
         break;
     case FIN_ARN1:
     case FIN_AUG1: {
         const int nb = op.ndV, k = op.ndU;
-        if (k) stage_lu(s, k, f);
+        if (k) stage_lu(s, k, f, op.lu_sel);
         for (int i = tid; i < nb; i += blockDim.x) f.sc[i] = s->colscale[i];
         for (int t = tid; t < nb * k; t += blockDim.x) {
             const int i = t % nb, l = t / nb;
@@ -992,21 +995,37 @@ static __global__ void cycle_reset_kernel(Small *s)
     }
 }
 
-// LU with partial pivoting of E (k x k) in one block; singular when a pivot
-// falls below 1e-13 * max(largest pivot, max_i ||u_i|| ||A u_i||).  colnorm2
-// holds ||u_i||^2 then ||w_i||^2 (2k values).
-static __global__ void lu_kernel(Small *s, int k, const double *gram_uw, const double *colnorm2)
+// LU with partial pivoting of a k x k matrix in one block (singular when a
+// pivot < 1e-13 * max(largest pivot, scale)).  which = 0: E = U^T W from the
+// GRAM_UW output (k x k column-major, then the squared column norms of U and
+// W; scale max ||u_i|| ||w_i||) into E, LU, LUrd, piv, LUperm.  which = 1: the
+// Gram matrix G = Y^T Y of the orthogonal / least-squares projector from a
+// packed pair list (scale max G_ii) into LUP, LUPrd, pivP, LUPperm.  Either
+// one singular sets Small::singular and k = 0 (the solve runs without
+// recycling).
+static __global__ void lu_kernel(Small *s, int k, const double *in, const double *colnorm2, int which)
 {
     __shared__ double M[RGM_KMAX * RGM_KMAX];
     __shared__ int pivrow;
     for (int i = threadIdx.x; i < k * k; i += blockDim.x) {
-        int r = i % k, c = i / k;
-        M[r + c * RGM_KMAX] = gram_uw[i];
-        s->E[r + c * RGM_KMAX] = gram_uw[i];
+        const int r = i % k, c = i / k;
+        double v;
+        if (which == 0) {
+            v = in[i];
+            s->E[r + c * RGM_KMAX] = v;
+        } else {
+            v = in[r <= c ? c * (c + 1) / 2 + r : r * (r + 1) / 2 + c];
+        }
+        M[r + c * RGM_KMAX] = v;
     }
     __syncthreads();
     double scale = 0.0;
-    for (int i = 0; i < k; ++i) scale = fmax(scale, sqrt(colnorm2[i] * colnorm2[k + i]));
+    if (which == 0)
+        for (int i = 0; i < k; ++i) scale = fmax(scale, sqrt(colnorm2[i] * colnorm2[k + i]));
+    else
+        for (int i = 0; i < k; ++i) scale = fmax(scale, M[i + i * RGM_KMAX]);
+    double *LUo = which ? s->LUP : s->LU, *rdo = which ? s->LUPrd : s->LUrd;
+    int *pvo = which ? s->pivP : s->piv, *pmo = which ? s->LUPperm : s->LUperm;
     double maxp = scale, minp = INFINITY;
     for (int j = 0; j < k; ++j) {
         if (threadIdx.x == 0) {
@@ -1014,7 +1033,7 @@ static __global__ void lu_kernel(Small *s, int k, const double *gram_uw, const d
             for (int i = j + 1; i < k; ++i)
                 if (fabs(M[i + j * RGM_KMAX]) > fabs(M[p + j * RGM_KMAX])) p = i;
             pivrow = p;
-            s->piv[j] = p;
+            pvo[j] = p;
         }
         __syncthreads();
         const int p = pivrow;
@@ -1038,24 +1057,27 @@ static __global__ void lu_kernel(Small *s, int k, const double *gram_uw, const d
         }
         __syncthreads();
     }
-    for (int i = threadIdx.x; i < RGM_KMAX * RGM_KMAX; i += blockDim.x) s->LU[i] = M[i];
+    for (int i = threadIdx.x; i < RGM_KMAX * RGM_KMAX; i += blockDim.x) LUo[i] = M[i];
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
         const double d = M[i + i * RGM_KMAX];
-        s->LUrd[i] = (d != 0.0) ? 1.0 / d : 0.0;
+        rdo[i] = (d != 0.0) ? 1.0 / d : 0.0;
     }
     if (threadIdx.x == 0) {
         // the row swaps as one permutation: (P b)_i = b[perm_i]
         int pm[RGM_KMAX];
         for (int i = 0; i < k; ++i) pm[i] = i;
         for (int j = 0; j < k; ++j) {
-            const int p = s->piv[j];
+            const int p = pvo[j];
             const int t = pm[j]; pm[j] = pm[p]; pm[p] = t;
         }
-        for (int i = 0; i < k; ++i) s->LUperm[i] = pm[i];
-    }
-    if (threadIdx.x == 0) {
-        int sing = (k > 0 && (minp == 0.0 || minp < 1e-13 * maxp)) ? 1 : 0;
-        s->singular = sing;
-        s->k = sing ? 0 : k;
+        for (int i = 0; i < k; ++i) pmo[i] = pm[i];
+        const int sing = (k > 0 && (minp == 0.0 || minp < 1e-13 * maxp)) ? 1 : 0;
+        if (which == 0) {
+            s->singular = sing;
+            s->k = sing ? 0 : k;
+        } else if (sing) {
+            s->singular = 1;
+            s->k = 0;
+        }
     }
 }
