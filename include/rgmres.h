@@ -133,8 +133,24 @@ int rgm_solver_destroy(rgm_solver s);
  * must lie in [0, n); rows need not be sorted.  Errors: RGM_E_ARG, RGM_E_OOM. */
 int rgm_set_operator_csr(rgm_solver s, int64_t n, int64_t nnz, const int64_t *rowptr,
                          const int32_t *col, const double *val, int flags);
+/* Operator A (n x n) in the library's own layout, sliced ELL with 32-row slices
+ * (SELL-32-sigma with sorting windows inside 256-row tiles), as the kernels read
+ * it.  nslices = 8 * ceil(n / 256); slice q holds slice rows 32q .. 32q + 31.
+ *  - perm (nslices * 32 int32): matrix row of each slice row, or -1 for padding;
+ *    every matrix row appears exactly once, and the slice rows of tile t
+ *    (slices 8t .. 8t + 7) map to matrix rows 256t .. 256t + 255.
+ *  - slice_ptr (nslices + 1 int64): slice_ptr[0] = 0, each slice's size a
+ *    multiple of 32; entry j of lane l of slice q sits at slice_ptr[q] + 32 j + l.
+ *  - col, val (nsell = slice_ptr[nslices] entries): padding entries need a
+ *    column in [0, n) and value 0.
+ * Slices sorted by width inside a tile run fastest (the kernels balance warps on
+ * that order).  After this call rgm_set_operator_values takes nsell values in
+ * this layout.  Errors: RGM_E_ARG (any rule above), RGM_E_OOM, RGM_E_CUDA. */
+int rgm_set_operator_sell(rgm_solver s, int64_t n, int64_t nslices, const int64_t *slice_ptr,
+                          const int32_t *perm, const int32_t *col, const double *val, int flags);
 /* New values on the pattern of the last rgm_set_operator_csr (nnz doubles, same
- * order).  This is the per-time-step call of Sec. 2: A_i = A(t_i, x_{i-1}). */
+ * order) or rgm_set_operator_sell (nsell doubles, that layout).  This is the
+ * per-time-step call of Sec. 2: A_i = A(t_i, x_{i-1}). */
 int rgm_set_operator_values(rgm_solver s, const double *val, int flags);
 
 /* Recycle space U (n x k, leading dimension ld >= n) set by the caller instead

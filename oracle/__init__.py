@@ -64,7 +64,7 @@ class _SeqCfg(C.Structure):
                 ("bx", C.c_double), ("by", C.c_double), ("steps", C.c_int), ("mode", C.c_int),
                 ("m", C.c_int), ("k", C.c_int), ("window", C.c_int), ("ell", C.c_int),
                 ("select_smallest", C.c_int), ("rtol", C.c_double), ("maxit", C.c_int),
-                ("rel_drop", C.c_double)]
+                ("rel_drop", C.c_double), ("guess", C.c_int)]
 
 
 SCALAR_FN = C.CFUNCTYPE(C.c_double, C.c_double, C.c_double, C.c_void_p)
@@ -102,6 +102,7 @@ def lib():
                                             C.c_void_p, C.c_void_p]
             L.orc_apply_projector.argtypes = [C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
                                               C.c_void_p, C.c_void_p]
+            L.orc_extrapolate.argtypes = [C.c_int64, C.c_int, C.c_void_p, C.c_int64, C.c_void_p]
             L.orc_coarse_setup.argtypes = [C.POINTER(_Csr), C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
             L.orc_svd_left.argtypes = [C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
             L.orc_recycle_from_window.argtypes = [C.c_int64, C.c_int, C.c_void_p, C.c_int, C.c_int,
@@ -300,6 +301,16 @@ def apply_oblique(U, W, E, v):
     return out, rc
 
 
+def extrapolate(P):
+    """Eq. ext2-ext4: column j of P is x_{i-1-j}; returns x0 (order P.shape[1]-1)."""
+    Pc = _colmajor(P)
+    n, s = Pc.shape
+    out = np.zeros(n)
+    rc = lib().orc_extrapolate(n, s, _p(Pc), n, _p(out))
+    assert rc == 0, rc
+    return out
+
+
 def apply_projector(U, W, proj, v):
     """P v for the projector proj (PROJ_*) of Table 1, W = A U."""
     Uc, Wc = _colmajor(U), _colmajor(W)
@@ -334,10 +345,11 @@ def recycle_from_window(X, k, select_smallest=False, rel_drop=1e-7):
 
 # ---------------------------------------------------------------- Algorithm 1 (sequence.c)
 def sequence(p, N, eps, dt, beta, steps, u0, mode=PLAIN, m=30, k=8, window=16, ell=1,
-             rtol=1e-10, maxit=20000, select_smallest=False, rel_drop=1e-7, keep_all=False):
+             rtol=1e-10, maxit=20000, select_smallest=False, rel_drop=1e-7, keep_all=False,
+             guess=0):
     n = ndofs(p, N)
     cfg = _SeqCfg(p, N, eps, dt, beta[0], beta[1], steps, mode, m, k, window, ell,
-                  int(select_smallest), rtol, maxit, rel_drop)
+                  int(select_smallest), rtol, maxit, rel_drop, int(guess))
     u0 = _f64(u0)
     x_all = np.zeros((n, steps), order="F") if keep_all else None
     x_final = np.zeros(n)

@@ -140,6 +140,12 @@ int orc_svd_full(int64_t n, int c, const double *X, double *sigma, double *Psi, 
 int orc_recycle_from_window(int64_t n, int c, const double *X, int k, int select_smallest,
                             double rel_drop, double *U, int *k_eff);
 
+/* Extrapolated initial guess (Sec. 4.1, Eq. ext2 / ext3 / ext4): the polynomial
+ * of degree s-1 through the s most recent solutions, evaluated one time step
+ * ahead: x0 = sum_{j=1..s} (-1)^(j+1) C(s, j) x_{i-j}.  Column j-1 of P (leading
+ * dimension ldp) is x_{i-j}.  s = 1..4. */
+int orc_extrapolate(int64_t n, int s, const double *P, int64_t ldp, double *x0);
+
 /* ---------------- Algorithm 1 over the Sec. 6.1 sequence (sequence.c) ---------------- */
 typedef struct {
     int p, N;
@@ -149,6 +155,9 @@ typedef struct {
     double rtol;
     int maxit;
     double rel_drop;
+    int guess;         /* 0: previous solution (plain) / zero (recycled) as x_in;
+                          g = 1..3: extrapolation of order g from the g+1 most recent
+                          solutions (Eq. ext2-ext4) once that many are stored    */
 } orc_seq_cfg;
 /* u0: initial nodal field.  x_all (optional): n x steps solutions.
  * iters/k_used/status (length steps) and relres (length steps) are per step. */

@@ -12,6 +12,8 @@
  * singular values below rel_drop * sigma_1 are dropped; step 1 runs plain;
  * with a recycle space the solve starts from x_in = 0 (so the initial guess is
  * the paper's x0 = U E^{-1} U^T b), without one from the previous solution.
+ * With cfg->guess = g > 0, x_in is instead the extrapolation of order g
+ * (Sec. 4.1) once g+1 solutions are stored (the window must hold them).
  */
 #include "oracle.h"
 #include <stdlib.h>
@@ -60,6 +62,15 @@ int orc_sequence_timed(const orc_seq_cfg *cfg, const double *u0, double *x_all, 
         int use_u = (cfg->mode != ORC_PLAIN && k_eff > 0);
         if (use_u) memset(x, 0, sizeof(double) * n);
         else memcpy(x, u, sizeof(double) * n);
+        if (cfg->guess > 0 && count >= cfg->guess + 1) {
+            /* x_{i-1}, x_{i-2}, ... are window columns count-1, count-2, ... */
+            double *P = malloc(sizeof(double) * n * (cfg->guess + 1));
+            if (!P) { rc = ORC_E_NOMEM; break; }
+            for (int j = 0; j <= cfg->guess; ++j)
+                memcpy(P + (int64_t)j * n, X + (int64_t)(count - 1 - j) * n, sizeof(double) * n);
+            orc_extrapolate(n, cfg->guess + 1, P, n, x);
+            free(P);
+        }
         orc_opts o = {cfg->mode, cfg->m, cfg->rtol, cfg->maxit, 0};
         orc_stats st;
         int s = orc_gmres(&A, b, x, use_u ? U : NULL, use_u ? k_eff : 0, &o, &st, NULL, 0);
@@ -87,4 +98,22 @@ int orc_sequence_timed(const orc_seq_cfg *cfg, const double *u0, double *x_all, 
     if (x_final && rc == ORC_OK) memcpy(x_final, u, sizeof(double) * n);
     free(rowptr); free(col); free(val); free(b); free(u); free(x); free(X); free(U);
     return rc;
+}
+
+int orc_extrapolate(int64_t n, int s, const double *P, int64_t ldp, double *x0)
+{
+    if (n < 0 || s < 1 || s > 4 || !P || !x0) return ORC_E_ARG;
+    /* binomial coefficients C(s, j) with alternating signs */
+    double c[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    double binom = 1.0;
+    for (int j = 1; j <= s; ++j) {
+        binom = binom * (double)(s - j + 1) / (double)j;
+        c[j] = (j % 2 == 1) ? binom : -binom;
+    }
+    for (int64_t r = 0; r < n; ++r) {
+        double acc = 0.0;
+        for (int j = 1; j <= s; ++j) acc += c[j] * P[r + (int64_t)(j - 1) * ldp];
+        x0[r] = acc;
+    }
+    return ORC_OK;
 }

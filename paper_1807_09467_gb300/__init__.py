@@ -97,6 +97,20 @@ class Solver:
               "rgm_set_operator_csr")
         self.nnz = nnz
 
+    def set_operator_sell(self, slice_ptr, perm, col, val):
+        """rgm_set_operator_sell: the operator in the library's sliced-ELL layout
+        (see include/rgmres.h); later set_operator_values calls take values in
+        that layout."""
+        sp, f1, k1 = _ptr(slice_ptr, np.int64)
+        pm, f2, k2 = _ptr(perm, np.int32)
+        cl, f3, k3 = _ptr(col, np.int32)
+        vl, f4, k4 = _ptr(val, np.float64)
+        assert f1 == f2 == f3 == f4, "mix of host and device arrays"
+        nslices = int(len(slice_ptr)) - 1
+        check(self._L.rgm_set_operator_sell(self._h, self.n, nslices, sp, pm, cl, vl, f1),
+              "rgm_set_operator_sell")
+        self.nnz = int(len(col))
+
     def set_operator_values(self, val):
         vl, f, k = _ptr(val, np.float64)
         check(self._L.rgm_set_operator_values(self._h, vl, f), "rgm_set_operator_values")

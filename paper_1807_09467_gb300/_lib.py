@@ -61,6 +61,8 @@ _SIGS = {
     "rgm_set_operator_csr": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_int]),
     "rgm_set_operator_values": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "rgm_set_operator_sell": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_int]),
     "rgm_set_recycle_space": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_int]),
     "rgm_get_recycle_space": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int),
                                         C.c_int]),

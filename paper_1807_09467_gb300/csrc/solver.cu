@@ -1049,6 +1049,67 @@ int rgm_set_operator_csr(rgm_solver s, int64_t n, int64_t nnz, const int64_t *ro
     return rgm_set_operator_values(s, val, flags);
 }
 
+int rgm_set_operator_sell(rgm_solver s, int64_t n, int64_t nslices, const int64_t *slice_ptr,
+                          const int32_t *perm, const int32_t *col, const double *val, int flags)
+{
+    if (!s || n != s->n || !slice_ptr || !perm) return RGM_E_ARG;
+    const int64_t ntile = (n + RGM_TILE - 1) / RGM_TILE;
+    if (nslices != ntile * (RGM_TILE / 32)) return RGM_E_ARG;
+    // validate the layout on host copies
+    const cudaMemcpyKind hk = (flags & RGM_DEVICE_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    std::vector<int64_t> sp(nslices + 1);
+    std::vector<int32_t> pm(nslices * 32);
+    if (cudaMemcpy(sp.data(), slice_ptr, sizeof(int64_t) * (nslices + 1), hk) != cudaSuccess) return RGM_E_CUDA;
+    if (cudaMemcpy(pm.data(), perm, sizeof(int32_t) * nslices * 32, hk) != cudaSuccess) return RGM_E_CUDA;
+    if (sp[0] != 0) return RGM_E_ARG;
+    for (int64_t q = 0; q < nslices; ++q)
+        if (sp[q + 1] < sp[q] || (sp[q + 1] - sp[q]) % 32 != 0) return RGM_E_ARG;
+    const int64_t nsell = sp[nslices];
+    if (nsell >= ((int64_t)1 << 31) || (nsell > 0 && (!col || !val))) return RGM_E_ARG;
+    std::vector<char> seen(n, 0);
+    for (int64_t i = 0; i < nslices * 32; ++i) {
+        const int32_t r = pm[i];
+        if (r < 0) continue;
+        const int64_t t = i / RGM_TILE;
+        if (r >= n || r < t * RGM_TILE || r >= (t + 1) * RGM_TILE || seen[r]) return RGM_E_ARG;
+        seen[r] = 1;
+    }
+    for (int64_t r = 0; r < n; ++r)
+        if (!seen[r]) return RGM_E_ARG;
+    std::vector<int32_t> cl(std::max<int64_t>(nsell, 1));
+    if (nsell && cudaMemcpy(cl.data(), col, sizeof(int32_t) * nsell, hk) != cudaSuccess) return RGM_E_CUDA;
+    for (int64_t e = 0; e < nsell; ++e)
+        if (cl[e] < 0 || cl[e] >= n) return RGM_E_ARG;
+    // values arrive in this layout: the scatter map is the identity
+    std::vector<int32_t> map(std::max<int64_t>(nsell, 1));
+    for (int64_t e = 0; e < nsell; ++e) map[e] = (int32_t)e;
+    void *old[] = {s->slice_ptr, s->scol, s->perm, s->csr2sell, s->sval, s->sval32, s->val_stage};
+    for (void *p : old)
+        if (p) cudaFree(p);
+    s->slice_ptr = nullptr; s->scol = nullptr; s->perm = nullptr; s->csr2sell = nullptr;
+    s->sval = nullptr; s->sval32 = nullptr; s->val_stage = nullptr;
+    const int64_t ne = std::max<int64_t>(nsell, 1);
+    CK(cudaMalloc((void **)&s->slice_ptr, sizeof(int64_t) * (nslices + 1)));
+    CK(cudaMalloc((void **)&s->scol, sizeof(int32_t) * ne));
+    CK(cudaMalloc((void **)&s->perm, sizeof(int32_t) * nslices * 32));
+    CK(cudaMalloc((void **)&s->csr2sell, sizeof(int32_t) * ne));
+    CK(cudaMalloc((void **)&s->sval, sizeof(double) * ne));
+    CK(cudaMalloc((void **)&s->val_stage, sizeof(double) * ne));
+    if (s->cfg.precision == RGM_FP32_IR) CK(cudaMalloc((void **)&s->sval32, sizeof(float) * ne));
+    CK(cudaMemcpyAsync(s->slice_ptr, sp.data(), sizeof(int64_t) * (nslices + 1), cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(s->scol, cl.data(), sizeof(int32_t) * ne, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(s->perm, pm.data(), sizeof(int32_t) * nslices * 32, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(s->csr2sell, map.data(), sizeof(int32_t) * ne, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemsetAsync(s->sval, 0, sizeof(double) * ne, s->st));
+    if (s->sval32) CK(cudaMemsetAsync(s->sval32, 0, sizeof(float) * ne, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    s->nnz = nsell;
+    s->nslices = nslices;
+    s->nsell = nsell;
+    s->have_op = true;
+    return rgm_set_operator_values(s, val, flags);
+}
+
 int rgm_set_operator_values(rgm_solver s, const double *val, int flags)
 {
     if (!s || (s->nnz > 0 && !val)) return RGM_E_ARG;
