@@ -95,6 +95,10 @@ typedef struct {
     int max_refinements;  /* FP32_IR: cap on refinement steps                               */
     int launch_policy;    /* rgm_launch_policy                                              */
     int proj;             /* deflated mode: rgm_projector of the Krylov operator P A       */
+    int guess;            /* 0: solve from the x passed in; g = 1..3: replace it by the
+                             extrapolation of order g (Sec. 4.1, Eq. ext2..ext4) from the
+                             g+1 most recent window snapshots once the window holds them
+                             (needs window >= g+1); recycling then adds its projection  */
     double rtol;          /* converged when ||b - A x||_2 <= rtol ||b||_2                   */
     double inner_rtol;    /* FP32_IR: inner solve to inner_rtol * ||r||                     */
     double rel_drop;      /* drop singular values below rel_drop * sigma_1                 */

@@ -703,6 +703,12 @@ static int solve_device(rgm_solver s, rgm_stats *out)
         status = RGM_W_SINGULAR_COARSE; k = 0;
     }
     const int mode = k > 0 ? c.mode : RGM_PLAIN;
+    if (c.guess > 0 && s->win_count >= c.guess + 1) {
+        // extrapolation from the most recent snapshots replaces the x passed in
+        const int newest = (s->win_head - 1 + c.window) % c.window;
+        ProfScope ps_(s, RGM_PROF_OTHER, 2.0 * (c.guess + 1) * (double)s->n, 8.0 * (c.guess + 2) * (double)s->n);
+        extrap_kernel<<<s->nblocks, 256, 0, s->st>>>(s->x, s->X, s->ld, c.guess + 1, newest, c.window, s->n);
+    }
     { ProfScope ps_(s, RGM_PROF_SMALL); solve_setup_kernel<<<1, 32, 0, s->st>>>(s->sm, c.maxit, c.m, k); }
     CK(cudaGetLastError());
     Arnoldi<double> a = arn64(s);
@@ -877,7 +883,8 @@ int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
         c.precision > 1 || c.maxit < 0 || !(c.rtol >= 0) || c.inner_cycles < 1 ||
         c.max_refinements < 1 || !(c.inner_rtol > 0) || !(c.rel_drop >= 0) ||
         c.launch_policy < RGM_LAUNCH_AUTO || c.launch_policy > RGM_LAUNCH_PER_PASS ||
-        c.proj < RGM_PROJ_OBLIQUE || c.proj > RGM_PROJ_LS)
+        c.proj < RGM_PROJ_OBLIQUE || c.proj > RGM_PROJ_LS || c.guess < 0 || c.guess > 3 ||
+        (c.guess > 0 && c.window < c.guess + 1))
         return RGM_E_ARG;
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RGM_E_CUDA;

@@ -30,6 +30,27 @@ __global__ void clear_skip_kernel(Small *s)
     if (threadIdx.x == 0) s->skip = 0;
 }
 
+// Extrapolated initial guess (Sec. 4.1, Eq. ext2 / ext3 / ext4): x = sum over
+// j = 1..s of (-1)^(j+1) C(s, j) x_{i-j}, where x_{i-j} sits in ring slot
+// (newest - j + 1) mod window of the snapshot window X.
+__global__ void extrap_kernel(double *__restrict__ x, const double *__restrict__ X, int64_t ld, int s,
+                              int newest, int window, int64_t n)
+{
+    double c[4];
+    int64_t off[4];
+    double binom = 1.0;
+    for (int j = 1; j <= s; ++j) {
+        binom = binom * (double)(s - j + 1) / (double)j;
+        c[j - 1] = (j % 2 == 1) ? binom : -binom;
+        off[j - 1] = (int64_t)((newest - (j - 1) + window) % window) * ld;
+    }
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int j = 0; j < s; ++j) acc += c[j] * X[r + off[j]];
+        x[r] = acc;
+    }
+}
+
 // Row-major copy of the k columns of U (row r at Urow + r k) for the SpMM
 // gather, through a shared-memory tile of RGM_UROW_ROWS rows (coalesced on
 // both sides).
