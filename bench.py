@@ -57,6 +57,20 @@ def dist_info():
     return ws, rank, local
 
 
+def replica_sequence(rank):
+    """Replicas (no data-path collective): rank r solves sequence r of the
+    workload, an independent problem with its own seeded draws."""
+    return rank
+
+
+def aggregate_replicas(my_sec, steps, ws, reduce_max):
+    """Whole-job throughput of ws replicas that each ran `steps` timed solves:
+    the job lasts as long as the slowest rank (max over ranks through
+    reduce_max), and all ranks' solves count.  Returns (value, job seconds)."""
+    tot = reduce_max(my_sec) if ws > 1 else my_sec
+    return steps * ws / tot, tot
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -263,7 +277,7 @@ def ours(args):
     else:
         g.build()
     w = synth.WORKLOADS[args.workload]
-    seq = synth.sequence_draws(w, rank)
+    seq = synth.sequence_draws(w, replica_sequence(rank))
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB
 
     keep = [] if (rank == 0 and not args.quick) else None
@@ -284,18 +298,20 @@ def ours(args):
     profd = run_sequence(rg, torch, w, seq, args.mode, args.precision, args.warmup, args.steps,
                          profile=True, flush=flush)
     my_sec = sum(main["seg_ms"]) / 1e3
-    tot_sec = my_sec
-    if ws > 1:
-        t = torch.tensor([my_sec], device="cuda", dtype=torch.float64)
+
+    def reduce_max(x):
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_sec = float(t.item())
+        return float(t.item())
+
+    K = args.steps
+    value, tot_sec = aggregate_replicas(my_sec, K, ws, reduce_max)
+    if ws > 1:
         dist.barrier()
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
         return
-    K = args.steps
-    value = K * ws / tot_sec
     prof, launches = profd["prof"]
     n, nnz = main["n"], main["nnz"]
     # dominant kernel by device time
