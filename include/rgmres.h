@@ -182,6 +182,19 @@ int rgm_solve(rgm_solver s, const double *b, double *x, int flags, rgm_stats *st
  * picks up the new dimension).  With host pointers the call returns after x
  * has been read. */
 int rgm_update_recycle_svd(rgm_solver s, const double *x, int flags, int *k_used);
+
+/* Batched solve: nsys independent systems, system i on handle handles[i], solved
+ * concurrently (survey: batched / served forms; the sequences of a batch are
+ * independent problems).  Each handle's work is queued on its own stream from a
+ * pool of host threads, one launch per fused pass (the cooperative cycle
+ * kernel is not used inside a batch: cooperative grids on concurrent streams
+ * are not guaranteed to be resident together).  Handles must be distinct and
+ * should have distinct streams (solves on one stream serialise).  b[i], x[i]
+ * and flags as in rgm_solve; st (optional) receives nsys entries.  Returns the
+ * first error if any solve failed (rgm_last_error then describes it), else
+ * the largest warning, else RGM_OK. */
+int rgm_batch_solve(rgm_solver *handles, int nsys, const double *const *b, double *const *x, int flags,
+                    rgm_stats *st);
 /* Singular values of the last window SVD, descending (up to `window` values);
  * *count receives how many are valid. */
 int rgm_get_singular_values(rgm_solver s, double *sigma, int *count);

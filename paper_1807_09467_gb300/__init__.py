@@ -215,6 +215,23 @@ class Solver:
         return y
 
 
+def batch_solve(solvers, bs, xs):
+    """rgm_batch_solve: solves system i on solvers[i] with right-hand side bs[i]
+    and initial guess / result xs[i] (CUDA tensors, updated in place),
+    concurrently.  Returns the list of stats dicts."""
+    L = _lib.load()
+    n = len(solvers)
+    assert len(bs) == n and len(xs) == n
+    for b, x in zip(bs, xs):
+        assert _is_dev(b) and _is_dev(x) and b.is_contiguous() and x.is_contiguous()
+    H = (C.c_void_p * n)(*[s._h.value for s in solvers])
+    B = (C.c_void_p * n)(*[b.data_ptr() for b in bs])
+    X = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+    st = (RgmStats * n)()
+    check(L.rgm_batch_solve(H, n, B, X, RGM_DEVICE_PTRS, st), "rgm_batch_solve")
+    return [_stats(st[i]) for i in range(n)]
+
+
 def wait_selftest(limit_ns):
     """rgm_wait_selftest: two blocks wait at a grid barrier that is never
     released, with the given wait limit.  Returns (blocks that gave up, device

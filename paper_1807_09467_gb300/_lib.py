@@ -71,6 +71,8 @@ _SIGS = {
     "rgm_last_error": (C.c_char_p, []),
     "rgm_wait_selftest": (C.c_int, [C.c_int64, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "rgm_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(RgmStats)]),
+    "rgm_batch_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
+                                  C.c_void_p]),
     "rgm_update_recycle_svd": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "rgm_get_singular_values": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
     "rgm_reset_recycling": (C.c_int, [C.c_void_p]),

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librgmres.so")
 SOURCES = ["solver.cu", "vec_f64.cu", "vec_f32.cu", "fe.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread",
          "-I", os.path.join(ROOT, "include")]
 
 
@@ -59,7 +59,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".{os.getpid()}.tmp"
-        run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-ldl"])
+        run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-ldl", "-lpthread"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -19,6 +19,10 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <thread>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -124,6 +128,7 @@ struct rgm_solver_s {
     // co-resident capacity of cycle_kernel per precision and dot-column bound
     // (-1: not queried yet)
     int cycle_cap[2][RGM_MAXDOTS + 2];
+    bool in_batch = false;        // solving inside rgm_batch_solve: no cooperative launch
 };
 
 static size_t small_header_bytes() { return offsetof(Small, H); }
@@ -484,7 +489,7 @@ static void arnoldi_passes(rgm_solver s, const Arnoldi<T> &a, int kdef, CycleOp<
 template <typename T>
 static bool use_cycle_kernel(rgm_solver s, const CycleOp<T> &c, int nd_max)
 {
-    if (s->cfg.launch_policy != RGM_LAUNCH_AUTO || nd_max > RGM_MAXDOTS) return false;
+    if (s->cfg.launch_policy != RGM_LAUNCH_AUTO || s->in_batch || nd_max > RGM_MAXDOTS) return false;
     int &cap = s->cycle_cap[sizeof(T) == 4 ? 1 : 0][nd_max];
     if (cap < 0) cap = cycle_capacity(c, nd_max);
     return s->nblocks <= cap;
@@ -1178,6 +1183,52 @@ int rgm_solve(rgm_solver s, const double *b, double *x, int flags, rgm_stats *st
     CK(cudaMemcpyAsync(x, s->x, sizeof(double) * s->n, kind_out(flags), s->st));
     CK(cudaStreamSynchronize(s->st));
     return rc;
+}
+
+int rgm_batch_solve(rgm_solver *handles, int nsys, const double *const *b, double *const *x, int flags,
+                    rgm_stats *st)
+{
+    if (nsys < 0 || (nsys > 0 && (!handles || !b || !x))) return RGM_E_ARG;
+    {
+        std::vector<rgm_solver> hs(handles, handles + nsys);
+        std::sort(hs.begin(), hs.end());
+        for (int i = 0; i < nsys; ++i)
+            if (!hs[i] || !b[i] || !x[i] || (i > 0 && hs[i] == hs[i - 1])) return RGM_E_ARG;
+    }
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::vector<int> rc(nsys, RGM_OK);
+    std::atomic<int> next(0);
+    std::mutex mu;
+    std::string first_error;
+    auto work = [&]() {
+        if (cudaSetDevice(dev) != cudaSuccess) return;
+        for (;;) {
+            const int i = next.fetch_add(1);
+            if (i >= nsys) break;
+            rgm_solver s = handles[i];
+            s->in_batch = true;
+            rc[i] = rgm_solve(s, b[i], x[i], flags, st ? &st[i] : nullptr);
+            s->in_batch = false;
+            if (rc[i] < 0) {
+                std::lock_guard<std::mutex> lk(mu);
+                if (first_error.empty()) first_error = g_last_error;
+            }
+        }
+    };
+    const int nthr = std::max(1, std::min<int>(nsys, (int)std::max(1u, std::thread::hardware_concurrency())));
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nthr; ++t) pool.emplace_back(work);
+    work();
+    for (auto &th : pool) th.join();
+    if (next.load() < nsys) return RGM_E_CUDA;            // a worker could not select the device
+    int worst = RGM_OK;
+    for (int r : rc) {
+        if (r < 0) { if (worst >= 0) worst = r; }
+        else if (worst >= 0 && r > worst) worst = r;
+    }
+    if (!first_error.empty()) std::snprintf(g_last_error, sizeof g_last_error, "%s", first_error.c_str());
+    return worst;
 }
 
 int rgm_update_recycle_svd(rgm_solver s, const double *x, int flags, int *k_used)

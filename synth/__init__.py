@@ -86,6 +86,26 @@ def sequence_draws(w: Workload, seq_index: int = 0):
     return a8, beta
 
 
+def batch_sequences(count: int = 64, steps: int = 20, seed_index: int = 0, n_lo: int = 32,
+                    n_hi: int = 192):
+    """Independent sequences of uneven size for the batched form: per sequence
+    p ~ U{1..4}, N ~ U{n_lo..n_hi}, eps = 10^U(-3, -1), then the u0 amplitudes
+    a_1..a_8 ~ U(-0.5, 0.5) and theta ~ U(0, 2 pi) of that sequence; dt 0.005,
+    GMRES(30), k 8 from a window of 16, true residual 1e-8.  Returns a list of
+    (Workload, a8, beta)."""
+    g = SplitMix64(BASE_SEED + 0x4000 + seed_index)
+    out = []
+    for i in range(count):
+        p = g.randint(1, 4)
+        N = g.randint(n_lo, n_hi)
+        eps = 10.0 ** g.uniform(-3.0, -1.0)
+        a8 = np.array([g.uniform(-0.5, 0.5) for _ in range(8)])
+        theta = g.uniform(0.0, 2.0 * math.pi)
+        w = Workload(f"batch{i}_q{p}_{N}x{N}", p, N, eps, 0.005, steps, 30, 8, 16, 1e-8)
+        out.append((w, a8, (math.cos(theta), math.sin(theta))))
+    return out
+
+
 def random_vector(n: int, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
     g = SplitMix64(seed)
     return np.array([g.uniform(lo, hi) for _ in range(n)])
