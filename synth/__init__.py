@@ -106,6 +106,29 @@ def batch_sequences(count: int = 64, steps: int = 20, seed_index: int = 0, n_lo:
     return out
 
 
+def serve_stream(count: int = 512, rate_per_s: float = 100.0, n_lo: int = 16, n_hi: int = 256,
+                 steps_lo: int = 10, steps_hi: int = 100, seed_index: int = 0):
+    """A seeded arrival stream for the served form: inter-arrival gaps
+    Exp(rate_per_s) (inverse transform of a uniform draw), then per sequence
+    p ~ U{1..4}, N ~ U{n_lo..n_hi}, eps = 10^U(-3, -1), steps ~ U{steps_lo..
+    steps_hi}, the u0 amplitudes and theta.  dt 0.005, GMRES(30), k 8 of 16,
+    true residual 1e-8.  Returns dicts (keys of serve.Request)."""
+    g = SplitMix64(BASE_SEED + 0x5000 + seed_index)
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += -math.log(1.0 - g.uniform()) / rate_per_s
+        p = g.randint(1, 4)
+        N = g.randint(n_lo, n_hi)
+        eps = 10.0 ** g.uniform(-3.0, -1.0)
+        steps = g.randint(steps_lo, steps_hi)
+        a8 = np.array([g.uniform(-0.5, 0.5) for _ in range(8)])
+        theta = g.uniform(0.0, 2.0 * math.pi)
+        out.append(dict(rid=i, arrival_s=t, p=p, N=N, eps=eps, dt=0.005, steps=steps, a8=a8,
+                        beta=(math.cos(theta), math.sin(theta))))
+    return out
+
+
 def random_vector(n: int, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
     g = SplitMix64(seed)
     return np.array([g.uniform(lo, hi) for _ in range(n)])
