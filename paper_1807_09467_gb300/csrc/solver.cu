@@ -189,6 +189,7 @@ static void op_cost(rgm_solver s, const VecOp<T> &op, int nb, int J, double *flo
     double f = 0.0, b = 0.0;
     int nV = op.nV, ndV = op.ndV;
     if (op.dyn & DYN_NV_NB) nV = nb;
+    if (op.dyn & DYN_NV_NBM1) nV = nb;     // nb here is the basis size the step started with
     if (op.dyn & DYN_NV_J) nV = J;
     if (op.dyn & DYN_NDV_NB) ndV = nb;
     if (op.src == SRC_SPMV || op.src == SRC_RES) {
@@ -474,13 +475,15 @@ static void arnoldi_passes(rgm_solver s, const Arnoldi<T> &a, int kdef, CycleOp<
     c.pass[0] = op;
     op = base_op(s, a);
     op.src = SRC_AXPY; op.win = a.w; op.out = a.w; op.nW = kdef; op.W = pc.Zp;
-    op.dyn = DYN_NV_NB | DYN_NDV_NB; op.fin = FIN_ARN2;
+    op.ndW = kdef; op.dnorm = 1;
+    op.dyn = DYN_NV_NB | DYN_NDV_NB; op.fin = FIN_ARN2H;
     c.pass[1] = op;
     op = base_op(s, a);
-    op.src = SRC_AXPY; op.win = a.w; op.dyn = DYN_NV_NB | DYN_OUT_VNB; op.W = pc.Zp;
-    op.ndW = kdef; op.dnorm = 1; op.fin = FIN_ARN3;
+    op.src = SRC_AXPY; op.win = a.w; op.dyn = DYN_NV_NBM1 | DYN_OUT_VNBM1; op.W = pc.Zp;
+    op.fin = FIN_NONE;
     c.pass[2] = op;
     c.m = s->cfg.m;
+    c.arrive = s->counter + 1;
 }
 
 // The cooperative cycle launch applies when the policy allows it and every
@@ -593,7 +596,8 @@ static int gmres_cycles(rgm_solver s, const Arnoldi<T> &a, int mode, int k, int 
                 op.gate = GATE_KRYLOV;
                 if ((rc = launch(s, op, RGM_PROF_ARNOLDI_CGS1, j, j + 1))) return rc;
                 op = cyc.pass[2];
-                op.gate = GATE_KRYLOV;
+                op.gate = GATE_STEP;        // also after the step that ended the cycle
+                op.arg = j + 1;
                 if ((rc = launch(s, op, RGM_PROF_ARNOLDI_CGS2, j, j + 1))) return rc;
             }
         }

@@ -21,7 +21,12 @@
 #define RGM_RGROUP 32            // blocks per group of the two-level dot reduction
 
 enum Src { SRC_SPMV = 0, SRC_RES = 1, SRC_COPY = 2, SRC_AXPY = 3, SRC_NONE = 4 };
-enum Gate { GATE_NONE = 0, GATE_KRYLOV = 1, GATE_APPEND = 2 };
+enum Gate {
+    GATE_NONE = 0,
+    GATE_KRYLOV = 1,   // skip once the cycle's Krylov phase is done
+    GATE_APPEND = 2,   // skip a dropped appended column
+    GATE_STEP = 3      // run only if Arnoldi step arg - 1 completed (s->J == arg)
+};
 enum Fin {
     FIN_NONE = 0,
     FIN_BNORM,       // ||b||
@@ -31,7 +36,9 @@ enum Fin {
     FIN_START_DEF1,  // coefW = -E^{-1} U^T r  (start vector P r)
     FIN_START_DEF2,  // v_0 = P r / ||P r||, VtW row 0
     FIN_ARN1,        // first CGS pass coefficients (with the oblique projection)
-    FIN_ARN2,        // second CGS pass coefficients
+    FIN_ARN2,        // second CGS pass coefficients (appended columns)
+    FIN_ARN2H,       // second CGS pass with ||w - V h2|| from the same reduction:
+                     // Hessenberg column, Givens, flags (the third pass is a plain update)
     FIN_ARN3,        // Hessenberg column, Givens, flags
     FIN_AUG1,        // appended column: first pass
     FIN_AUG3,        // appended column: accept / drop, Givens
@@ -77,7 +84,9 @@ enum Dyn {
     DYN_NDV_NB = 1,   // ndV = s->nb
     DYN_NV_NB = 2,    // nV  = s->nb
     DYN_NV_J = 4,     // nV  = s->J
-    DYN_OUT_VNB = 8   // out = Vraw[:, s->nb]
+    DYN_OUT_VNB = 8,  // out = Vraw[:, s->nb]
+    DYN_NV_NBM1 = 16, // nV  = s->nb - 1 (after a scalar step that stored column nb)
+    DYN_OUT_VNBM1 = 32 // out = Vraw[:, s->nb - 1]
 };
 
 // Shared scratch of the finalising block.
@@ -88,6 +97,7 @@ struct FinScratch {
     double col[RGM_HLD + 1];
     double cs[RGM_HLD], sn[RGM_HLD];
     double sc[RGM_HLD];
+    double h2[RGM_HLD];                       // second-pass coefficients
     double rd[RGM_KMAX];                      // reciprocals of the U pivots
     int perm[RGM_KMAX];                       // composite row permutation of the LU
     double vtw[(RGM_MMAX + 1) * RGM_KMAX];    // V^T W rows 0..nb-1 (leading dim RGM_MMAX+1)
@@ -243,6 +253,20 @@ __device__ void fin_stage(const VecOp<T> &op, FinScratch &f)
             f.col[i] = s->hsum[i];
         }
         break;
+    case FIN_ARN2H: {
+        const int nb = op.ndV, k = op.ndW;
+        for (int i = tid; i < nb; i += blockDim.x) {
+            f.sc[i] = s->colscale[i];
+            f.col[i] = s->hsum[i];
+            f.cs[i] = s->cs[i];
+            f.sn[i] = s->sn[i];
+        }
+        for (int t = tid; t < nb * k; t += blockDim.x) {
+            const int i = t % nb, l = t / nb;
+            f.vtw[i + l * RGM_VTW_LD] = s->VtW[i + l * RGM_HLD];
+        }
+        break;
+    }
     case FIN_ARN3:
         for (int i = tid; i < op.nV; i += blockDim.x) {
             f.col[i] = s->hsum[i];
@@ -336,6 +360,66 @@ __device__ void finalize_block(const VecOp<T> &op, const double *d, FinScratch &
             const double h = dV[i] * sc;
             s->hsum[i] = f.col[i] + h;
             s->coefV[i] = -h * sc;
+        }
+        break;
+    }
+    case FIN_ARN2H: {
+        // w1 = w after the first CGS pass; d: [V^T w1 | W^T w1 | ||w1||^2].  The
+        // second pass removes h2 = V^T w1, and since V is orthonormal
+        // ||w1 - V h2||^2 = ||w1||^2 - ||h2||^2 (no cancellation: w1 is already
+        // orthogonal to V up to rounding); v_{j+1}^T W follows from W^T w1 and
+        // the stored rows of V^T W.  Staged: colscale, hsum, cs, sn, V^T W.
+        const int nb = op.ndV, j = nb - 1, kw = op.ndW;
+        __shared__ double sc_h;
+        for (int i = tid; i < nb; i += blockDim.x) {
+            const double sc = f.sc[i], h = dV[i] * sc;
+            f.h2[i] = h;
+            f.col[i] += h;                     // the Hessenberg column h1 + h2
+            s->coefV[i] = -h * sc;
+        }
+        __syncthreads();
+        if (tid < 32) {
+            double q = 0.0;
+            for (int i = tid; i < nb; i += 32) q = fma(f.h2[i], f.h2[i], q);
+            q = warp_sum(q);
+            const double hn2 = fmax(nrm2 - q, 0.0);
+            // rotated column (warp 0), then the new rotation from (t_j, hn)
+            const double a = warp_rotate_column(f.col, f.cs, f.sn, j);
+            if (tid == 0) {
+                const double inv_hn = (hn2 > 0.0) ? rsqrt(hn2) : 0.0;
+                const double hn = hn2 * inv_hn;
+                const double r2 = fma(a, a, hn2);
+                const double inv_r = (r2 > 0.0) ? rsqrt(r2) : 0.0;
+                const double c = (r2 > 0.0) ? a * inv_r : 1.0, sn = hn * inv_r;
+                f.col[j] = r2 * inv_r;
+                f.col[j + 1] = 0.0;
+                s->cs[j] = c;
+                s->sn[j] = sn;
+                const double g0 = s->g[j], g1 = -sn * g0;
+                s->g[j + 1] = g1;
+                s->g[j] = c * g0;
+                const bool brk = hn <= 1e-14 * s->wn0;
+                const double sc = brk ? 0.0 : inv_hn;
+                sc_h = sc;
+                s->J = j + 1;
+                const int it = s->iters + 1;
+                s->iters = it;
+                s->colscale[nb] = sc;          // happy breakdown: v_{j+1} := 0
+                int done = 0;
+                if (brk) { s->breakdown = 1; done = 1; }
+                s->nb = nb + 1;
+                if (fabs(g1) <= s->tol_abs || it >= s->maxit || j + 1 >= s->m) done = 1;
+                if (done) s->done = 1;
+            }
+        }
+        __syncthreads();
+        double *hc = s->H + (int64_t)j * RGM_HLD;
+        for (int i = tid; i <= j + 1; i += blockDim.x) hc[i] = f.col[i];
+        const double sc = sc_h;
+        for (int l = tid; l < kw; l += blockDim.x) {
+            double v = dW[l];
+            for (int i = 0; i < nb; ++i) v = fma(-f.h2[i], f.vtw[i + l * RGM_VTW_LD], v);
+            s->VtW[nb + l * RGM_HLD] = v * sc;
         }
         break;
     }
@@ -467,11 +551,14 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op)
     Small *s = op.sm;
     if (op.gate == GATE_KRYLOV && s->done) return PASS_SKIPPED;
     if (op.gate == GATE_APPEND && (s->skip || s->J == 0)) return PASS_SKIPPED;
+    if (op.gate == GATE_STEP && s->J != op.arg) return PASS_SKIPPED;
     if (op.dyn) {
         if (op.dyn & DYN_NDV_NB) op.ndV = s->nb;
         if (op.dyn & DYN_NV_NB) op.nV = s->nb;
         if (op.dyn & DYN_NV_J) op.nV = s->J;
         if (op.dyn & DYN_OUT_VNB) op.out = const_cast<T *>(op.V) + (int64_t)s->nb * op.ldv;
+        if (op.dyn & DYN_NV_NBM1) op.nV = s->nb - 1;
+        if (op.dyn & DYN_OUT_VNBM1) op.out = const_cast<T *>(op.V) + (int64_t)(s->nb - 1) * op.ldv;
     }
 
     __shared__ T cW[RGM_KMAX], cU[RGM_KMAX], cV[RGM_HLD];
@@ -663,8 +750,10 @@ __global__ void __launch_bounds__(RGM_THREADS, 4) vec_kernel(VecOp<T> op)
 
 template <typename T>
 struct CycleOp {
-    VecOp<T> pass[3];    // A v_j + dots (first CGS pass), second CGS pass, norm + Givens
+    VecOp<T> pass[3];    // A v_j + dots (first CGS pass), second CGS pass with the norm and
+                         // the Givens step, the plain update that stores v_{j+1}
     int m;               // Arnoldi steps at most
+    unsigned *arrive;    // arrival counter of the plain barrier
 };
 
 // After a pass: the last block publishes generation `target`, the others wait
@@ -699,6 +788,24 @@ __device__ __forceinline__ bool grid_barrier(int pass_rc, Small *s, unsigned tar
     return ok != 0;
 }
 
+// Barrier after a pass with no reduction: the last of the n blocks to arrive
+// clears the counter and publishes generation `target`; the others wait.
+__device__ __forceinline__ bool grid_barrier_arrive(Small *s, unsigned *counter, unsigned n, unsigned target)
+{
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        last = (atom_add_acq_rel_gpu(counter, 1u) == n - 1u) ? 1 : 0;
+        if (last) {
+            *counter = 0u;
+            st_release_gpu(&s->gen, target);
+        }
+    }
+    __syncthreads();
+    if (last) return true;
+    return grid_barrier(PASS_ARRIVED, s, target);
+}
+
 template <typename T, int QMAX>
 __global__ void __launch_bounds__(RGM_THREADS, 4) cycle_kernel(CycleOp<T> c)
 {
@@ -711,7 +818,10 @@ __global__ void __launch_bounds__(RGM_THREADS, 4) cycle_kernel(CycleOp<T> c)
         op.xscale = j;
         if (!grid_barrier(vec_pass<T, QMAX, false>(op), s, ++gen)) return;
         if (!grid_barrier(vec_pass<T, QMAX, false>(c.pass[1]), s, ++gen)) return;
-        if (!grid_barrier(vec_pass<T, QMAX, false>(c.pass[2]), s, ++gen)) return;
+        // plain update storing v_{j+1} (also after the last step: the augmented
+        // relation orthogonalises against it)
+        vec_pass<T, QMAX, false>(c.pass[2]);
+        if (!grid_barrier_arrive(s, c.arrive, (unsigned)c.pass[2].nblocks, ++gen)) return;
     }
 }
 
