@@ -152,6 +152,7 @@ __global__ void sym_eig_select_kernel(Small *s, const double *gram, int c, int k
         G[i + j * RGM_WMAX] = v;
         P[i + j * RGM_WMAX] = (i == j) ? 1.0 : 0.0;
     }
+    __syncthreads();                            // G complete before its diagonal is read
     __shared__ double gmax;
     if (threadIdx.x == 0) {
         double m = 0.0;
