@@ -163,14 +163,9 @@ __device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned *p, unsigned v
 __device__ __forceinline__ bool last_of(unsigned *counter, unsigned n)
 {
     __shared__ bool am_last;
-    // every thread makes its own writes visible at GPU scope before the block
-    // arrives (a release by thread 0 alone, ordered after the others' writes
-    // only through the block barrier, let a reducer read stale partials)
-    __threadfence();
-    __syncthreads();
+    __syncthreads();                    // the block's writes precede thread 0's release
     if (threadIdx.x == 0) am_last = (atom_add_acq_rel_gpu(counter, 1u) == n - 1u);
-    __syncthreads();
-    if (am_last) __threadfence();       // and every thread of the last block acquires
+    __syncthreads();                    // and its acquire precedes the block's reads
     return am_last;
 }
 

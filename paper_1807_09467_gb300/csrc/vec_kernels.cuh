@@ -587,28 +587,17 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op)
         // SpMV over all of the block's slices first.  Inside a tile the slices
         // are sorted by width (slice 0 widest), so warp w takes slice w of even
         // tiles and slice NW-1-w of odd ones: every warp gets the same work.
-        // Two tiles at a time: each warp streams its slice of tile t and its
-        // slice of tile t+1 together (twice the independent loads in flight).
         const T sc = (T)xs;
-        for (int t = 0; t < ntiles_blk; t += 2) {
-            const bool two = t + 1 < ntiles_blk;
-            const int64_t slA = ((r0 + (int64_t)t * RGM_TILE) >> 5) + warp;
-            const int64_t slB = two ? ((r0 + (int64_t)(t + 1) * RGM_TILE) >> 5) + (NW - 1 - warp) : slA;
-            const int64_t pA = op.slice_ptr[slA], la = op.slice_ptr[slA + 1] - pA;
-            const int64_t pB = op.slice_ptr[slB], lb = two ? op.slice_ptr[slB + 1] - pB : 0;
-            const int64_t lm = max(la, lb);
-            T a = 0, b = 0;
-#pragma unroll 4
-            for (int64_t o = lane; o < lm; o += 32) {
-                if (o < la) a += op.sval[pA + o] * op.x[op.scol[pA + o]];
-                if (o < lb) b += op.sval[pB + o] * op.x[op.scol[pB + o]];
-            }
-            const int prA = op.perm[(slA << 5) + lane];
-            if (prA >= 0) op.out[prA] = (op.src == SRC_SPMV) ? a * sc : op.b[prA] - a;
-            if (two) {
-                const int prB = op.perm[(slB << 5) + lane];
-                if (prB >= 0) op.out[prB] = (op.src == SRC_SPMV) ? b * sc : op.b[prB] - b;
-            }
+        for (int t = 0; t < ntiles_blk; ++t) {
+            const int64_t base = r0 + (int64_t)t * RGM_TILE;
+            const int slot = (t & 1) ? (NW - 1 - warp) : warp;
+            const int64_t sl = (base >> 5) + slot;
+            const int64_t p0 = op.slice_ptr[sl], p1 = op.slice_ptr[sl + 1];
+            T a = 0;
+#pragma unroll 8
+            for (int64_t e = p0 + lane; e < p1; e += 32) a += op.sval[e] * op.x[op.scol[e]];
+            const int pr = op.perm[(sl << 5) + lane];
+            if (pr >= 0) op.out[pr] = (op.src == SRC_SPMV) ? a * sc : op.b[pr] - a;
         }
         __syncthreads();      // the block's own writes are visible to it now
     }
@@ -774,7 +763,6 @@ __device__ __forceinline__ bool grid_barrier(int pass_rc, Small *s, unsigned tar
 {
     __shared__ int ok;
     if (pass_rc == PASS_LAST) {
-        __threadfence();                  // each thread's part of the scalar step
         __syncthreads();                  // the scalar step is complete
         if (threadIdx.x == 0) st_release_gpu(&s->gen, target);
         return true;
@@ -797,7 +785,6 @@ __device__ __forceinline__ bool grid_barrier(int pass_rc, Small *s, unsigned tar
         ok = good;
     }
     __syncthreads();
-    __threadfence();                      // every thread reads after the acquire
     return ok != 0;
 }
 
@@ -806,7 +793,6 @@ __device__ __forceinline__ bool grid_barrier(int pass_rc, Small *s, unsigned tar
 __device__ __forceinline__ bool grid_barrier_arrive(Small *s, unsigned *counter, unsigned n, unsigned target)
 {
     __shared__ int last;
-    __threadfence();                      // each thread's rows visible before the arrival
     __syncthreads();
     if (threadIdx.x == 0) {
         last = (atom_add_acq_rel_gpu(counter, 1u) == n - 1u) ? 1 : 0;
@@ -816,10 +802,7 @@ __device__ __forceinline__ bool grid_barrier_arrive(Small *s, unsigned *counter,
         }
     }
     __syncthreads();
-    if (last) {
-        __threadfence();
-        return true;
-    }
+    if (last) return true;
     return grid_barrier(PASS_ARRIVED, s, target);
 }
 
