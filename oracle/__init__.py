@@ -23,6 +23,7 @@ _lock = threading.Lock()
 
 PLAIN, DEFLATED, AUGMENTED = 0, 1, 2
 PROJ_OBLIQUE, PROJ_ORTHOGONAL, PROJ_LS = 0, 1, 2
+PRECOND_NONE, PRECOND_JACOBI = 0, 1
 OK, W_NOT_CONVERGED, W_SINGULAR_COARSE = 0, 1, 2
 
 
@@ -51,7 +52,7 @@ class _Csr(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("mode", C.c_int), ("m", C.c_int), ("rtol", C.c_double), ("maxit", C.c_int),
-                ("start_r", C.c_int), ("proj", C.c_int)]
+                ("start_r", C.c_int), ("proj", C.c_int), ("precond", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -244,7 +245,7 @@ def spmv(A: Csr, x):
 
 
 def gmres(A: Csr, b, x_in=None, U=None, mode=PLAIN, m=30, rtol=1e-10, maxit=10000,
-          start_r=False, hist_len=0, proj=PROJ_OBLIQUE):
+          start_r=False, hist_len=0, proj=PROJ_OBLIQUE, precond=0):
     """Returns (x, stats dict, hist)."""
     b = _f64(b)
     x = _f64(x_in).copy() if x_in is not None else np.zeros(A.n)
@@ -253,7 +254,7 @@ def gmres(A: Csr, b, x_in=None, U=None, mode=PLAIN, m=30, rtol=1e-10, maxit=1000
     if U is not None and np.asarray(U).size:
         Uc = _colmajor(U)
         k = Uc.shape[1]
-    o = _Opts(mode, m, rtol, maxit, int(start_r), int(proj))
+    o = _Opts(mode, m, rtol, maxit, int(start_r), int(proj), int(precond))
     st = _Stats()
     hist = np.zeros(hist_len) if hist_len else None
     rc = lib().orc_gmres(C.byref(A.s), _p(b), _p(x), _p(Uc), k, C.byref(o), C.byref(st),
@@ -274,7 +275,7 @@ def gmres_ir(A: Csr, b, x_in=None, U=None, mode=PLAIN, m=30, rtol=1e-8, maxit=20
     if U is not None and np.asarray(U).size:
         Uc = _colmajor(U)
         k = Uc.shape[1]
-    o = _Opts(mode, m, rtol, maxit, 0, int(proj))
+    o = _Opts(mode, m, rtol, maxit, 0, int(proj), 0)
     st = _Stats()
     nref = C.c_int(0)
     rc = lib().orc_gmres_ir(C.byref(A.s), _p(b), _p(x), _p(Uc), k, C.byref(o), inner_rtol,

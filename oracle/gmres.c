@@ -17,6 +17,8 @@
  *    (Table 1 "augmented oblique") the iterates coincide when P r0 = r0.
  *  - Sec. 3.1, Eq. def_aug_S_space / def_aug_C_space: augmented search space
  *    S = K_j(A, r0) + span U and constraint space A S.
+ *  - Left Jacobi preconditioning (not the paper's SSOR, which is sequential):
+ *    GMRES on D^{-1} A x = D^{-1} b with the true-residual stopping test.
  *  - Sec. 3.3, Table 1 (and Eq. P_A_variant): the other two projectors of the
  *    deflated family, orthogonal P = I - U (U^T U)^{-1} U^T and least squares
  *    P = I - A U (U^T A^T A U)^{-1} U^T A^T; Sec. 4.4, Eq. augmented_iterate:
@@ -182,6 +184,30 @@ int orc_apply_projector(int64_t n, int k, const double *U, const double *W, int 
     return rc;
 }
 
+/* ||w .* r|| (w NULL: ||r||) */
+static double wnrm2(int64_t n, const double *r, const double *w)
+{
+    if (!w) return nrm2(n, r);
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += (w[i] * r[i]) * (w[i] * r[i]);
+    return sqrt(s);
+}
+
+/* Left Jacobi: d_i = A_ii (1 where the diagonal is absent or zero), the row-
+ * scaled values D^{-1} A into vs and b / d into bs. */
+static void jacobi_scale(const orc_csr *A, const double *b, double *vs, double *bs, double *d)
+{
+    for (int64_t i = 0; i < A->n; ++i) {
+        double di = 0.0;
+        for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e)
+            if (A->col[e] == i) di += A->val[e];
+        if (di == 0.0) di = 1.0;
+        d[i] = di;
+        for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) vs[e] = A->val[e] / di;
+        bs[i] = b[i] / di;
+    }
+}
+
 /* ---- the solver core, shared by the FP64 solve and the IR inner solve ---- */
 typedef struct {
     const orc_csr *A;
@@ -197,6 +223,9 @@ typedef struct {
     const int *pivP, *pivC;
     int maxit, max_cycles;
     double tol_abs;         /* stop when ||b - A x|| <= tol_abs                     */
+    double tol_in;          /* in-cycle exit: |g_{j+1}| <= tol_in                    */
+    const double *wts;      /* true residual = wts .* (residual of the solved
+                               system) (left Jacobi: wts = diag(A)), or NULL      */
     double *hist;
     int hist_len, hist_count;
 } core_t;
@@ -332,7 +361,7 @@ static int core_solve(core_t *c, const double *b, double *x, int *iters_out, int
     int iters = 0, cycles = 0;
     spmv_vals(c->A, c->val, x, r, c->f32);
     for (int64_t i = 0; i < n; ++i) r[i] = rd(c->f32, b[i] - r[i]);
-    double beta = nrm2(n, r);
+    double beta = wnrm2(n, r, c->wts);
 
     while (beta > c->tol_abs && iters < c->maxit && cycles < c->max_cycles) {
         ++cycles;
@@ -364,7 +393,7 @@ static int core_solve(core_t *c, const double *b, double *x, int *iters_out, int
                     break;
                 }
                 for (int64_t i = 0; i < n; ++i) V[i + (int64_t)(j + 1) * n] = rd(c->f32, w[i] / hn);
-                if (fabs(g[j + 1]) <= c->tol_abs) break;
+                if (fabs(g[j + 1]) <= c->tol_in) break;
             }
         }
         /* augmentation: append A u_i as extra columns of the Arnoldi relation */
@@ -419,7 +448,7 @@ static int core_solve(core_t *c, const double *b, double *x, int *iters_out, int
         if (c->mode == ORC_DEFLATED) cycle_correct(c, b, x, r, cv);
         spmv_vals(c->A, c->val, x, r, c->f32);
         for (int64_t i = 0; i < n; ++i) r[i] = rd(c->f32, b[i] - r[i]);
-        double beta_new = nrm2(n, r);
+        double beta_new = wnrm2(n, r, c->wts);
         if (J == 0 && !(beta_new < beta)) { beta = beta_new; break; }   /* stagnation */
         beta = beta_new;
     }
@@ -443,6 +472,21 @@ int orc_gmres(const orc_csr *A, const double *b, double *x, const double *U, int
         if (st) *st = s0;
         return ORC_OK;
     }
+    /* left Jacobi: solve D^-1 A x = D^-1 b (the true residual is D times its residual) */
+    orc_csr As = *A;
+    double *vs = NULL, *bs = NULL, *dw = NULL;
+    const double *bb = b;
+    if (o->precond == ORC_PRECOND_JACOBI) {
+        const int64_t nnz = A->rowptr[n];
+        vs = malloc(sizeof(double) * (nnz + 1));
+        bs = malloc(sizeof(double) * n);
+        dw = malloc(sizeof(double) * n);
+        if (!vs || !bs || !dw) { free(vs); free(bs); free(dw); return ORC_E_NOMEM; }
+        jacobi_scale(A, b, vs, bs, dw);
+        As.val = vs;
+        bb = bs;
+        A = &As;
+    }
     core_t c;
     memset(&c, 0, sizeof c);
     c.A = A; c.val = A->val; c.f32 = 0;
@@ -450,6 +494,8 @@ int orc_gmres(const orc_csr *A, const double *b, double *x, const double *U, int
     c.m = o->m; c.start_r = o->start_r; c.k = 0;
     c.maxit = o->maxit; c.max_cycles = 1 << 30;
     c.tol_abs = o->rtol * bnorm;
+    c.tol_in = dw ? o->rtol * nrm2(n, bb) : c.tol_abs;
+    c.wts = dw;
     c.hist = hist; c.hist_len = hist ? hist_len : 0;
     double *W = NULL, *LU = NULL, *LUP = NULL, *cv = NULL, *r = NULL;
     int *piv = NULL, *pivP = NULL;
@@ -468,13 +514,14 @@ int orc_gmres(const orc_csr *A, const double *b, double *x, const double *U, int
             c.mode = ORC_PLAIN;
             c.k = 0;
         } else {
-            coarse_correct(&c, b, x, r, cv);     /* projection initial guess */
+            coarse_correct(&c, bb, x, r, cv);     /* projection initial guess */
         }
     }
     int iters, cycles;
     double res;
-    int rc = core_solve(&c, b, x, &iters, &cycles, &res);
+    int rc = core_solve(&c, bb, x, &iters, &cycles, &res);
     free(W); free(LU); free(LUP); free(piv); free(pivP); free(cv); free(r);
+    free(vs); free(bs); free(dw);
     if (rc) return rc;
     if (hist) for (int i = 0; i < c.hist_count; ++i) hist[i] /= bnorm;
     if (status == ORC_OK && res > o->rtol * bnorm) status = ORC_W_NOT_CONVERGED;
@@ -490,6 +537,7 @@ int orc_gmres_ir(const orc_csr *A, const double *b, double *x, const double *U, 
                  int max_refinements, orc_stats *st, int *refinements)
 {
     if (!A || !b || !x || !o || o->m < 1 || k < 0) return ORC_E_ARG;
+    if (o->precond != ORC_PRECOND_NONE) return ORC_E_ARG;   /* Jacobi: binary64 solves only */
     const int64_t n = A->n, nnz = A->rowptr[n];
     double bnorm = nrm2(n, b);
     if (bnorm == 0.0) {

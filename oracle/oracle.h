@@ -94,7 +94,16 @@ typedef struct {
     int start_r;       /* DEFLATED only: 1 = start vector r (Table 1 "augmented"
                           rows), 0 = P r (Table 1 "deflated" rows)                 */
     int proj;          /* DEFLATED only: ORC_PROJ_*                                */
+    int precond;       /* ORC_PRECOND_NONE / ORC_PRECOND_JACOBI                    */
 } orc_opts;
+
+/* Left Jacobi preconditioning (survey "next": a GPU-friendly preconditioner in
+ * place of the paper's SSOR): GMRES on D^{-1} A x = D^{-1} b, D = diag(A) (rows
+ * without a nonzero diagonal keep weight 1).  The in-cycle exit compares the
+ * Givens estimate of the preconditioned residual with rtol ||D^{-1} b||; the
+ * stopping test stays on the true residual ||b - A x|| <= rtol ||b||. */
+#define ORC_PRECOND_NONE    0
+#define ORC_PRECOND_JACOBI  1
 
 typedef struct {
     int iters;           /* Arnoldi steps summed over cycles                       */

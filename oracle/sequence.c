@@ -71,7 +71,7 @@ int orc_sequence_timed(const orc_seq_cfg *cfg, const double *u0, double *x_all, 
             orc_extrapolate(n, cfg->guess + 1, P, n, x);
             free(P);
         }
-        orc_opts o = {cfg->mode, cfg->m, cfg->rtol, cfg->maxit, 0};
+        orc_opts o = {cfg->mode, cfg->m, cfg->rtol, cfg->maxit, 0, 0, 0};
         orc_stats st;
         int s = orc_gmres(&A, b, x, use_u ? U : NULL, use_u ? k_eff : 0, &o, &st, NULL, 0);
         if (s < 0) { rc = s; break; }

@@ -354,3 +354,81 @@ def test_table1_variants_solve_fe_step(orc, proj):
     assert st["status"] == 0 and st["true_relres"] <= 1e-10
     xs = np.linalg.solve(A.dense(), b)
     np.testing.assert_allclose(x, xs, rtol=0, atol=1e-8 * np.abs(xs).max())
+
+
+# ------------------------------------------------------------------ left Jacobi preconditioning
+def _jacobi(A):
+    d = np.diag(A).copy()
+    d[d == 0] = 1.0
+    return d
+
+
+def test_jacobi_diagonal_matrix_one_step(orc):
+    n = 12
+    A = np.diag(np.arange(1.0, n + 1))
+    b = synth.random_vector(n, 200)
+    x0, s0, _ = orc.gmres(orc.Csr.from_dense(A), b, m=n, rtol=1e-12)
+    x1, s1, _ = orc.gmres(orc.Csr.from_dense(A), b, m=n, rtol=1e-12, precond=orc.PRECOND_JACOBI)
+    assert s1["iters"] == 1 and s0["iters"] == n               # D^-1 A = I
+    np.testing.assert_allclose(x1, b / np.diag(A), rtol=1e-14)
+
+
+@pytest.mark.parametrize("j", [1, 3, 6])
+def test_jacobi_fixed_steps_brute_force(orc, j):
+    """x = x0 + K y, K = K_j(D^-1 A, D^-1 r0), y minimising ||D^-1 (r0 - A K y)||."""
+    n = 18
+    A, b = _rand_system(n, 210)
+    A += np.diag(synth.random_vector(n, 211, 1.0, 5.0))          # uneven diagonal
+    x0 = synth.random_vector(n, 212)
+    x, st, _ = orc.gmres(orc.Csr.from_dense(A), b, x_in=x0, m=30, rtol=0.0, maxit=j,
+                         precond=orc.PRECOND_JACOBI)
+    assert st["iters"] == j
+    Di = np.diag(1.0 / _jacobi(A))
+    r0 = Di @ (b - A @ x0)
+    K = _krylov(Di @ A, r0, j)
+    y, *_ = np.linalg.lstsq(Di @ A @ K, r0, rcond=None)
+    np.testing.assert_allclose(x, x0 + K @ y, rtol=1e-9, atol=1e-11)
+
+
+@pytest.mark.parametrize("j", [1, 4])
+def test_jacobi_deflated_fixed_steps_brute_force(orc, j):
+    """Deflation on the preconditioned operator: A~ = D^-1 A, W = A~ U,
+    P = I - W (U^T W)^-1 U^T, start P r~0 from the projection guess."""
+    A, b, U = _setup_recycle(25, 3, 220)
+    A += np.diag(synth.random_vector(25, 221, 1.0, 4.0))
+    x, st, _ = orc.gmres(orc.Csr.from_dense(A), b, U=U, mode=1, m=30, rtol=0.0, maxit=j,
+                         precond=orc.PRECOND_JACOBI)
+    Di = np.diag(1.0 / _jacobi(A))
+    At, bt = Di @ A, Di @ b
+    E = U.T @ At @ U
+    Q = U @ np.linalg.solve(E, U.T)
+    P = np.eye(25) - At @ Q
+    xk0 = Q @ bt
+    r0 = bt - At @ xk0
+    K = _krylov(P @ At, P @ r0, j)
+    y, *_ = np.linalg.lstsq(P @ At @ K, P @ r0, rcond=None)
+    xk = xk0 + K @ y
+    xk = xk + Q @ (bt - At @ xk)
+    np.testing.assert_allclose(x, xk, rtol=1e-9, atol=1e-11)
+
+
+def test_jacobi_converges_on_true_residual_and_unit_diagonal_is_neutral(orc):
+    w = synth.Q1_32
+    a8, beta = synth.sequence_draws(w, 0)
+    u0 = orc.u0_field(w.p, w.N, a8)
+    rp, col, val, b = orc.step_system(w.p, w.N, w.eps, w.dt, beta, u0)
+    A = orc.Csr(rp, col, val)
+    for mode, U in ((0, None), (1, _orth(np.stack([u0, synth.random_vector(len(b), 4)], 1)))):
+        x, st, _ = orc.gmres(A, b, U=U, mode=mode, m=w.m, rtol=1e-10, precond=orc.PRECOND_JACOBI)
+        assert st["status"] == 0 and st["true_relres"] <= 1e-10
+        r = b - orc.spmv(A, x)
+        assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-9)
+    # unit diagonal: scaling by 1 changes nothing, bit for bit
+    Ad = A.dense()
+    Ad[np.diag_indices_from(Ad)] = 1.0
+    Au = orc.Csr.from_dense(Ad)
+    xa, sa, _ = orc.gmres(Au, b, m=10, rtol=1e-8, maxit=40)
+    xb, sb, _ = orc.gmres(Au, b, m=10, rtol=1e-8, maxit=40, precond=orc.PRECOND_JACOBI)
+    np.testing.assert_array_equal(xa, xb)
+    assert sa["iters"] == sb["iters"]
+
