@@ -74,6 +74,15 @@ typedef enum {
 } rgm_projector;
 
 typedef enum {
+    RGM_PRECOND_NONE = 0,
+    RGM_PRECOND_JACOBI = 1   /* left Jacobi, M = diag(A): GMRES on D^{-1} A x = D^{-1} b (a
+                                rows without a nonzero diagonal keep weight 1); the in-cycle
+                                exit compares the preconditioned estimate with
+                                rtol ||D^{-1} b||, the stopping test stays on the true
+                                residual ||b - A x|| <= rtol ||b||.  Binary64 solves only. */
+} rgm_precond;
+
+typedef enum {
     RGM_LAUNCH_AUTO = 0,     /* the Arnoldi steps of a cycle run in one cooperative launch
                                 (grid barriers between the fused passes) when the grid fits
                                 on the device at once; otherwise one launch per pass        */
@@ -99,6 +108,7 @@ typedef struct {
                              extrapolation of order g (Sec. 4.1, Eq. ext2..ext4) from the
                              g+1 most recent window snapshots once the window holds them
                              (needs window >= g+1); recycling then adds its projection  */
+    int precond;          /* rgm_precond (not with RGM_FP32_IR)                              */
     double rtol;          /* converged when ||b - A x||_2 <= rtol ||b||_2                   */
     double inner_rtol;    /* FP32_IR: inner solve to inner_rtol * ||r||                     */
     double rel_drop;      /* drop singular values below rel_drop * sigma_1                 */

@@ -24,6 +24,7 @@ MODES = {"plain": PLAIN, "deflated": DEFLATED, "augmented": AUGMENTED}
 PRECISIONS = {"fp64": FP64, "fp32_ir": FP32_IR}
 LAUNCH_POLICIES = {"auto": 0, "per_pass": 1}
 PROJECTORS = {"oblique": 0, "orthogonal": 1, "ls": 2}
+PRECONDS = {"none": 0, "jacobi": 1}
 
 __all__ = ["Solver", "FE", "residual_noalloc", "RgmError", "MODES", "PRECISIONS", "PLAIN", "DEFLATED", "AUGMENTED",
            "FP64", "FP32_IR", "RGM_W_NOT_CONVERGED", "RGM_W_SINGULAR_COARSE"]
@@ -53,7 +54,7 @@ class Solver:
     def __init__(self, n, m=30, k=8, window=16, svd_interval=1, select_smallest=False,
                  mode="deflated", precision="fp64", start_r=False, maxit=20000, inner_cycles=2,
                  max_refinements=50, rtol=1e-10, inner_rtol=1e-4, rel_drop=1e-7, stream=None,
-                 launch_policy="auto", proj="oblique", guess=0):
+                 launch_policy="auto", proj="oblique", guess=0, precond="none"):
         L = _lib.load()
         cfg = RgmConfig()
         L.rgm_config_default(C.byref(cfg))
@@ -68,6 +69,7 @@ class Solver:
             else int(launch_policy)
         cfg.proj = PROJECTORS[proj] if isinstance(proj, str) else int(proj)
         cfg.guess = int(guess)
+        cfg.precond = PRECONDS[precond] if isinstance(precond, str) else int(precond)
         cfg.cuda_stream = stream
         self.cfg = cfg
         self.n = n

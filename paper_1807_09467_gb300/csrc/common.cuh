@@ -37,6 +37,7 @@ struct Small {
     unsigned fault;    // a bounded device wait gave up (cleared per solve)
     int aug_idx[RGM_KMAX];
     double bnorm, tol_abs, beta, wn0, bs;
+    double bnorm_p, tol_in;  // preconditioned ||D^{-1} b|| and the in-cycle tolerance
     double H[RGM_HLD * RGM_NCOL];         // column-major, leading dimension RGM_HLD
     double cs[RGM_HLD], sn[RGM_HLD], g[RGM_HLD + 1], y[RGM_HLD];
     double hsum[RGM_HLD];                 // Gram-Schmidt coefficients of the current column

@@ -91,6 +91,7 @@ struct rgm_solver_s {
     double *sval = nullptr;
     float *sval32 = nullptr;
     double *val_stage = nullptr;  // host values land here before the scatter
+    double *dvec = nullptr;       // left Jacobi: diag(A) of the unscaled operator
     // binary64 vectors
     double *V = nullptr, *U = nullptr, *W = nullptr, *w = nullptr, *r = nullptr, *b = nullptr,
            *x = nullptr;
@@ -389,9 +390,14 @@ __global__ void solve_setup_kernel(Small *s, int maxit, int m, int k)
     }
 }
 
-__global__ void set_tol_kernel(Small *s, double rtol)
+// tol_abs bounds the true residual; tol_in the in-cycle Givens estimate, which
+// with left Jacobi measures the residual of D^{-1} A x = D^{-1} b.
+__global__ void set_tol_kernel(Small *s, double rtol, int precond)
 {
-    if (threadIdx.x == 0) s->tol_abs = rtol * s->bnorm;
+    if (threadIdx.x == 0) {
+        s->tol_abs = rtol * s->bnorm;
+        s->tol_in = precond ? rtol * s->bnorm_p : s->tol_abs;
+    }
 }
 
 // W = A U and the LU of E = U^T W (binary64), once per (operator, recycle space).
@@ -542,6 +548,11 @@ static int launch_cycle_prof(rgm_solver s, const CycleOp<T> &c, int nd_max)
     return RGM_OK;
 }
 
+// Weights of the true-residual norm: with left Jacobi the stored residual is
+// D^{-1} (b - A x), so ||b - A x|| = ||d .* r||.  binary64 solves only.
+static const double *res_weights(rgm_solver s, const Arnoldi<double> &) { return s->dvec; }
+static const float *res_weights(rgm_solver, const Arnoldi<float> &) { return nullptr; }
+
 // One recycled GMRES solve of A x = b on the device buffers of `a`, with the
 // tolerance tol_abs already in Small.  mode: effective mode (PLAIN if no U).
 // Returns the number of cycles through *cycles.
@@ -643,6 +654,7 @@ static int gmres_cycles(rgm_solver s, const Arnoldi<T> &a, int mode, int k, int 
         {
             VecOp<T> op = base_op(s, a);
             op.src = SRC_RES; op.x = a.x; op.b = a.b; op.out = a.r; op.dnorm = 1; op.fin = FIN_RESNORM;
+            op.wvec = res_weights(s, a);
             if ((rc = launch(s, op))) return rc;
         }
         if ((rc = read_header(s))) return rc;
@@ -672,6 +684,7 @@ static int residual_norm(rgm_solver s, const Arnoldi<T> &a)
 {
     VecOp<T> op = base_op(s, a);
     op.src = SRC_RES; op.x = a.x; op.b = a.b; op.out = a.r; op.dnorm = 1; op.fin = FIN_RESNORM;
+    op.wvec = res_weights(s, a);
     return launch(s, op);
 }
 
@@ -721,8 +734,15 @@ static int solve_device(rgm_solver s, rgm_stats *out)
     { ProfScope ps_(s, RGM_PROF_SMALL); solve_setup_kernel<<<1, 32, 0, s->st>>>(s->sm, c.maxit, c.m, k); }
     CK(cudaGetLastError());
     Arnoldi<double> a = arn64(s);
+    const int pre = s->dvec != nullptr;
     if ((rc = norm_of(s, a, s->b, FIN_BNORM))) return rc;
-    { ProfScope ps_(s, RGM_PROF_SMALL); set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.rtol); }
+    if (pre) {   // left Jacobi: b := D^{-1} b, ||D^{-1} b|| for the in-cycle tolerance
+        { ProfScope ps_(s, RGM_PROF_OTHER, (double)s->n, 24.0 * (double)s->n);
+          diag_apply_kernel<<<s->nblocks, 256, 0, s->st>>>(s->b, s->dvec, s->n, 1); }
+        CK(cudaGetLastError());
+        if ((rc = norm_of(s, a, s->b, FIN_BNORMP))) return rc;
+    }
+    { ProfScope ps_(s, RGM_PROF_SMALL); set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.rtol, pre); }
     if (k > 0 && (rc = coarse_correct(s, a, k))) return rc;     // x0 = x_in + Q (b - A x_in)
     if ((rc = residual_norm(s, a))) return rc;
     if ((rc = read_header(s))) return rc;
@@ -744,7 +764,7 @@ static int solve_device(rgm_solver s, rgm_stats *out)
             CK(cudaMemsetAsync(s->x32, 0, sizeof(float) * s->n, s->st));
             { ProfScope ps_(s, RGM_PROF_SMALL); solve_setup_kernel<<<1, 32, 0, s->st>>>(s->sm, c.maxit - iters_total, c.m, k); }
             if ((rc = norm_of(s, f, s->b32, FIN_BNORM))) return rc;
-            { ProfScope ps_(s, RGM_PROF_SMALL); set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.inner_rtol); }
+            { ProfScope ps_(s, RGM_PROF_SMALL); set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.inner_rtol, 0); }
             if (k > 0 && (rc = coarse_correct(s, f, k))) return rc;
             if ((rc = residual_norm(s, f))) return rc;
             int cy = 0;
@@ -755,7 +775,7 @@ static int solve_device(rgm_solver s, rgm_stats *out)
             { ProfScope ps_(s, RGM_PROF_OTHER); add_f32_kernel<<<s->nblocks, 256, 0, s->st>>>(s->x, s->x32, s->n); }
             { ProfScope ps_(s, RGM_PROF_SMALL); solve_setup_kernel<<<1, 32, 0, s->st>>>(s->sm, c.maxit, c.m, k); }
             if ((rc = norm_of(s, a, s->b, FIN_BNORM))) return rc;
-            { ProfScope ps_(s, RGM_PROF_SMALL); set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.rtol); }
+            { ProfScope ps_(s, RGM_PROF_SMALL); set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.rtol, 0); }
             if ((rc = residual_norm(s, a))) return rc;
             if ((rc = read_header(s))) return rc;
             s->hs->iters = iters_total;
@@ -874,7 +894,7 @@ static void free_all(rgm_solver s)
 {
     void *dp[] = {s->slice_ptr, s->scol, s->perm, s->csr2sell, s->sval, s->sval32, s->val_stage, s->V, s->U, s->W, s->w, s->r, s->b, s->x,
                   s->V32, s->U32, s->W32, s->w32, s->r32, s->b32, s->x32, s->X, s->Urow, s->gwin,
-                  s->partials, s->counter, s->gpart, s->pairs, s->gram_out, s->sm};
+                  s->dvec, s->partials, s->counter, s->gpart, s->pairs, s->gram_out, s->sm};
     for (void *p : dp)
         if (p) cudaFree(p);
     if (s->hs) cudaFreeHost(s->hs);
@@ -893,7 +913,8 @@ int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
         c.max_refinements < 1 || !(c.inner_rtol > 0) || !(c.rel_drop >= 0) ||
         c.launch_policy < RGM_LAUNCH_AUTO || c.launch_policy > RGM_LAUNCH_PER_PASS ||
         c.proj < RGM_PROJ_OBLIQUE || c.proj > RGM_PROJ_LS || c.guess < 0 || c.guess > 3 ||
-        (c.guess > 0 && c.window < c.guess + 1))
+        (c.guess > 0 && c.window < c.guess + 1) || c.precond < RGM_PRECOND_NONE ||
+        c.precond > RGM_PRECOND_JACOBI || (c.precond != RGM_PRECOND_NONE && c.precision != RGM_FP64))
         return RGM_E_ARG;
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RGM_E_CUDA;
@@ -938,6 +959,7 @@ int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
     ALLOC(s->pairs, sizeof(int2) * s->npairs_max);
     ALLOC(s->gram_out, sizeof(double) * s->npairs_max);
     ALLOC(s->sm, sizeof(Small));
+    if (c.precond == RGM_PRECOND_JACOBI) ALLOC(s->dvec, sizeof(double) * s->ld);
     if (c.precision == RGM_FP32_IR) {
         ALLOC(s->V32, sizeof(float) * s->ld * ncolV);
         ALLOC(s->U32, sizeof(float) * s->ld * kmax);
@@ -1141,6 +1163,13 @@ int rgm_set_operator_values(rgm_solver s, const double *val, int flags)
             ProfScope ps_(s, RGM_PROF_OTHER);
             sell_scatter_kernel<double><<<g, 256, 0, s->st>>>(s->sval, s->sval32, src, s->csr2sell, s->nnz);
         }
+        CK(cudaGetLastError());
+    }
+    if (s->dvec) {   // left Jacobi: keep D^{-1} A, remember D
+        const int g = (int)std::min<int64_t>((s->nslices + 7) / 8, 8 * (int64_t)s->nsm);
+        ProfScope ps_(s, RGM_PROF_OTHER);
+        jacobi_scale_kernel<<<std::max(g, 1), 256, 0, s->st>>>(s->sval, s->scol, s->slice_ptr, s->perm,
+                                                              s->nslices, s->dvec);
         CK(cudaGetLastError());
     }
     s->coarse_stale = true;
@@ -1456,6 +1485,11 @@ int rgm_spmv(rgm_solver s, const double *x, double *y, int flags)
     op.out = s->w;
     int rc = launch(s, op);
     if (rc) return rc;
+    if (s->dvec) {   // the stored operator is D^{-1} A
+        ProfScope ps_(s, RGM_PROF_OTHER, (double)s->n, 24.0 * (double)s->n);
+        diag_apply_kernel<<<s->nblocks, 256, 0, s->st>>>(s->w, s->dvec, s->n, 0);
+        CK(cudaGetLastError());
+    }
     CK(cudaMemcpyAsync(y, s->w, sizeof(double) * s->n, kind_out(flags), s->st));
     CK(cudaStreamSynchronize(s->st));
     return RGM_OK;

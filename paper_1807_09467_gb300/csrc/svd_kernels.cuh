@@ -30,6 +30,37 @@ __global__ void clear_skip_kernel(Small *s)
     if (threadIdx.x == 0) s->skip = 0;
 }
 
+// Left Jacobi (M = diag(A)) on the sliced-ELL operator: one warp per slice,
+// one lane per row; d = sum of the row's entries in column i (padding entries
+// hold 0 and add nothing), 1 if that sum is 0; the row's values are divided
+// by d.  Rows of a slice are interleaved: entry e of the slice belongs to the
+// row in lane e mod 32.
+__global__ void jacobi_scale_kernel(double *__restrict__ sval, const int32_t *__restrict__ scol,
+                                    const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ perm,
+                                    int64_t nslices, double *__restrict__ dvec)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < nslices; sl += nwarps) {
+        const int pr = perm[(sl << 5) + lane];
+        if (pr < 0) continue;
+        const int64_t p0 = slice_ptr[sl], p1 = slice_ptr[sl + 1];
+        double d = 0.0;
+        for (int64_t e = p0 + lane; e < p1; e += 32)
+            if (scol[e] == pr) d += sval[e];
+        if (d == 0.0) d = 1.0;
+        dvec[pr] = d;
+        for (int64_t e = p0 + lane; e < p1; e += 32) sval[e] = sval[e] / d;
+    }
+}
+
+// v = v ./ d (div = 1) or v .* d (div = 0)
+__global__ void diag_apply_kernel(double *v, const double *d, int64_t n, int div)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = div ? v[i] / d[i] : v[i] * d[i];
+}
+
 // Extrapolated initial guess (Sec. 4.1, Eq. ext2 / ext3 / ext4): x = sum over
 // j = 1..s of (-1)^(j+1) C(s, j) x_{i-j}, where x_{i-j} sits in ring slot
 // (newest - j + 1) mod window of the snapshot window X.

@@ -30,6 +30,7 @@ enum Gate {
 enum Fin {
     FIN_NONE = 0,
     FIN_BNORM,       // ||b||
+    FIN_BNORMP,      // ||D^{-1} b|| (left Jacobi)
     FIN_RESNORM,     // beta = ||r||, converged flag
     FIN_COARSE,      // coefU = E^{-1} (U^T r)
     FIN_START_PLAIN, // v_0 = r / ||r||
@@ -67,6 +68,7 @@ struct VecOp {
     const T *V; int64_t ldv;
     const T *W; int64_t ldw;
     int ndU, ndV, ndW, dnorm;  // dot columns: U[0..ndU), Vraw[0..ndV), W[0..ndW), ||w||^2
+    const T *wvec;           // if set, the norm column is ||wvec .* w||^2 (true residual)
     double *partials;        // per-block dot partials, column c at c * nblocks
     unsigned *counter;       // completion counter of the groups
     unsigned *gcount;        // per-group completion counters (RGM_RGROUP blocks a group)
@@ -292,6 +294,9 @@ __device__ void finalize_block(const VecOp<T> &op, const double *d, FinScratch &
     case FIN_BNORM:
         if (tid == 0) s->bnorm = sqrt(nrm2);
         break;
+    case FIN_BNORMP:
+        if (tid == 0) s->bnorm_p = sqrt(nrm2);
+        break;
     case FIN_RESNORM:
         if (tid == 0) {
             s->beta = sqrt(nrm2);
@@ -408,7 +413,7 @@ __device__ void finalize_block(const VecOp<T> &op, const double *d, FinScratch &
                 int done = 0;
                 if (brk) { s->breakdown = 1; done = 1; }
                 s->nb = nb + 1;
-                if (fabs(g1) <= s->tol_abs || it >= s->maxit || j + 1 >= s->m) done = 1;
+                if (fabs(g1) <= s->tol_in || it >= s->maxit || j + 1 >= s->m) done = 1;
                 if (done) s->done = 1;
             }
         }
@@ -453,7 +458,7 @@ __device__ void finalize_block(const VecOp<T> &op, const double *d, FinScratch &
                 int done = 0;
                 if (brk) { s->breakdown = 1; done = 1; }
                 s->nb = nb + 1;
-                if (fabs(g1) <= s->tol_abs || it >= s->maxit || j + 1 >= s->m) done = 1;
+                if (fabs(g1) <= s->tol_in || it >= s->maxit || j + 1 >= s->m) done = 1;
                 if (done) s->done = 1;
             }
         }
@@ -650,10 +655,18 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op)
             for (int q = 0; q < QMAX; ++q) {
                 const int c = warp + q * NW;
                 if (c < nd) {
-                    const T *cp = (c == ndc_) ? ws : dot_col(op, c) + base;
                     T a = 0;
+                    if (c == ndc_ && op.wvec) {          // weighted norm: ||wvec .* w||^2
 #pragma unroll
-                    for (int i = 0; i < RGM_TILE / 32; ++i) a += cp[lane + 32 * i] * wl[i];
+                        for (int i = 0; i < RGM_TILE / 32; ++i) {
+                            const T v = wl[i] * op.wvec[base + lane + 32 * i];
+                            a += v * v;
+                        }
+                    } else {
+                        const T *cp = (c == ndc_) ? ws : dot_col(op, c) + base;
+#pragma unroll
+                        for (int i = 0; i < RGM_TILE / 32; ++i) a += cp[lane + 32 * i] * wl[i];
+                    }
                     acc[q] += (double)a;
                 }
             }
@@ -662,9 +675,16 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op)
             for (int q = 0; q < QMAX; ++q) {
                 const int c = warp + q * NW;
                 if (c < nd) {
-                    const T *cp = (c == ndc_) ? ws : dot_col(op, c) + base;
                     T a = 0;
-                    for (int i = lane; i < nrow; i += 32) a += cp[i] * ws[i];
+                    if (c == ndc_ && op.wvec) {
+                        for (int i = lane; i < nrow; i += 32) {
+                            const T v = ws[i] * op.wvec[base + i];
+                            a += v * v;
+                        }
+                    } else {
+                        const T *cp = (c == ndc_) ? ws : dot_col(op, c) + base;
+                        for (int i = lane; i < nrow; i += 32) a += cp[i] * ws[i];
+                    }
                     acc[q] += (double)a;
                 }
             }
