@@ -164,18 +164,39 @@ def iters_stats(its):
             "sd": round(statistics.pstdev(its), 2) if len(its) > 1 else 0.0}
 
 
+# ------------------------------------------------------------------ workloads
+def workload_fe(rg, w, beta, stream=None):
+    """The workload's FE handle (Sec. 6.1's cellular velocity when it asks)."""
+    fe = rg.FE(w.p, w.N, w.eps, w.dt, beta, stream=stream)
+    if w.velocity == "cellular":
+        fe.set_velocity("cellular")
+    return fe
+
+
+def workload_u0(np, fe, w, a8):
+    return np.zeros(fe.n) if w.u0 == "zero" else fe.initial_field(a8)
+
+
+def workload_seq(synth, w, index, steps):
+    """(a8, beta, forcing rows or None) of one sequence."""
+    a8, beta = synth.sequence_draws(w, index)
+    forcing = synth.forcing_draws(w, steps, index) if w.forcing_modes else None
+    return a8, beta, forcing
+
+
 # ------------------------------------------------------------------ our arm
 def run_sequence(rg, torch, w, seq, mode, precision, warmup, steps, profile=False, keep=None,
                  flush=None, stream=None):
     """Runs warmup + steps time steps on the device; returns timing and stats."""
-    a8, beta = seq
+    import numpy as np
+    a8, beta, forcing = seq
     dev = torch.device("cuda")
-    fe = rg.FE(w.p, w.N, w.eps, w.dt, beta, stream=stream)
+    fe = workload_fe(rg, w, beta, stream=stream)
     rp, col = fe.pattern()
     rtol = w.rtol if precision == "fp64" else 1e-8
     solver = rg.Solver(fe.n, m=w.m, k=w.k, window=w.window, svd_interval=w.ell, mode=mode,
                        precision=precision, rtol=rtol, stream=stream, launch_policy=LAUNCH_POLICY[0])
-    u0 = fe.initial_field(a8)
+    u0 = workload_u0(np, fe, w, a8)
     u = torch.tensor(u0, dtype=torch.float64, device=dev)
     solver.set_operator_csr(rp, col, torch.zeros(len(col), dtype=torch.float64).numpy())
     x = torch.empty_like(u)
@@ -189,6 +210,8 @@ def run_sequence(rg, torch, w, seq, mode, precision, warmup, steps, profile=Fals
     for i in range(warmup + steps):
         if i == warmup and profile:
             solver.profile(True)
+        if forcing is not None:
+            fe.set_forcing(forcing[i], w.forcing_C)
         eva[i][0].record(cs)
         val, b = fe.assemble(u)                         # workload step, not timed
         eva[i][1].record(cs)
@@ -223,11 +246,11 @@ def run_sequence(rg, torch, w, seq, mode, precision, warmup, steps, profile=Fals
 
 def run_e2e(rg, np, w, seq, mode, precision, warmup, steps, inputs, torch):
     """Same sequence through the public API with host (pinned) buffers."""
-    a8, beta = seq
+    a8, beta, _ = seq
     n = len(inputs[0][1])
-    fe = rg.FE(w.p, w.N, w.eps, w.dt, beta)
+    fe = workload_fe(rg, w, beta)
     rp, col = fe.pattern()
-    u = fe.initial_field(a8)
+    u = workload_u0(np, fe, w, a8)
     fe.close()
     rtol = w.rtol if precision == "fp64" else 1e-8
     s = rg.Solver(n, m=w.m, k=w.k, window=w.window, svd_interval=w.ell, mode=mode,
@@ -281,7 +304,7 @@ def ours(args):
     else:
         g.build()
     w = synth.WORKLOADS[args.workload]
-    seq = synth.sequence_draws(w, replica_sequence(rank))
+    seq = workload_seq(synth, w, replica_sequence(rank), max(w.steps, args.warmup + args.steps))
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB
 
     keep = [] if (rank == 0 and not args.quick) else None
@@ -351,6 +374,7 @@ def ours(args):
         "data": "synthetic",
         "config": {"workload": w.name, "n": n, "nnz": nnz, "p": w.p, "N": w.N, "m": w.m, "k": w.k,
                    "window": w.window, "svd_interval": w.ell, "mode": args.mode,
+                   "velocity": w.velocity, "forcing_modes": w.forcing_modes, "u0": w.u0,
                    "precision": args.precision, "launch_policy": args.launch_policy,
                    "rtol": w.rtol if args.precision == "fp64" else 1e-8,
                    "l2": "flushed (256 MiB write) before every timed step",
@@ -524,13 +548,15 @@ def run_serve(args):
 def cpu_baseline(args, w, seq, main, np):
     import oracle as orc
     orc.build()
-    a8, beta = seq
+    a8, beta, forcing = seq
     S = args.cpu_steps or min(w.steps, 30 if w.n < 200000 else 3)
-    u0 = orc.u0_field(w.p, w.N, a8)
+    u0 = np.zeros(w.n) if w.u0 == "zero" else orc.u0_field(w.p, w.N, a8)
     mode = {"plain": 0, "deflated": 1, "augmented": 2}[args.mode]
     rtol = w.rtol if args.precision == "fp64" else 1e-8
     r = orc.sequence(w.p, w.N, w.eps, w.dt, beta, S, u0, mode=mode, m=w.m, k=w.k,
-                     window=w.window, ell=w.ell, rtol=rtol, keep_all=False)
+                     window=w.window, ell=w.ell, rtol=rtol, keep_all=False,
+                     velocity=int(w.velocity == "cellular"), forcing=forcing,
+                     forcing_C=w.forcing_C)
     secs = r["step_seconds"]
     cb = {"value": round(S / float(secs.sum()), 4), "unit": "solves/s", "cores": 1, "kind": "oracle",
           "sample": f"first {S} time steps of the same sequence ({w.name}, {args.mode}), "
@@ -554,7 +580,7 @@ def reference(args):
     import synth
     orc.build()
     w = synth.WORKLOADS[args.workload]
-    a8, beta = synth.sequence_draws(w, 0)
+    a8, beta, forcing = workload_seq(synth, w, 0, max(w.steps, args.warmup + args.steps))
     # each bench step is one time step; the oracle is slow, so a step is a
     # bounded sample (the first warmup+steps steps of the sequence, capped)
     W, K = args.warmup, args.steps
@@ -564,9 +590,11 @@ def reference(args):
     Kc = tot - Wc
     mode = {"plain": 0, "deflated": 1, "augmented": 2}[args.mode]
     rtol = w.rtol if args.precision == "fp64" else 1e-8
-    u0 = orc.u0_field(w.p, w.N, a8)
+    u0 = np.zeros(w.n) if w.u0 == "zero" else orc.u0_field(w.p, w.N, a8)
     r = orc.sequence(w.p, w.N, w.eps, w.dt, beta, tot, u0, mode=mode, m=w.m, k=w.k,
-                     window=w.window, ell=w.ell, rtol=rtol)
+                     window=w.window, ell=w.ell, rtol=rtol,
+                     velocity=int(w.velocity == "cellular"), forcing=forcing,
+                     forcing_C=w.forcing_C)
     secs = r["step_seconds"][Wc:]
     value = Kc / float(secs.sum())
     sample = (f"time steps {Wc + 1}..{tot} of the {w.name} sequence ({args.mode}), FP64 oracle, "

@@ -310,7 +310,9 @@ int rgm_residual_noalloc(int64_t n, const int64_t *rowptr, const int32_t *col, c
  * (p+1)^2 Gauss points per cell, implicit Euler with the convection coefficient
  * lagged one step,
  *   A = M/dt + eps K + N(u_prev; beta),  b = M u_prev / dt + F(f = 1),
- * N_ij = (u_prev beta . grad phi_j, phi_i), homogeneous Dirichlet rows
+ * N_ij = (u_prev beta . grad phi_j, phi_i) (beta constant, or the paper's
+ * cellular field, rgm_fe_set_velocity; f = 1 or the paper's random modes,
+ * rgm_fe_set_forcing), homogeneous Dirichlet rows
  * (identity, b_i = 0), boundary columns dropped from interior rows.
  * Dofs are numbered lexicographically (x fastest) on the (pN+1)^2 lattice.
  * This is the workload the solver is measured on, not part of the method.  */
@@ -325,6 +327,24 @@ int rgm_fe_sizes(rgm_fe fe, int64_t *n, int64_t *nnz);
 int rgm_fe_pattern(rgm_fe fe, int64_t *rowptr, int32_t *col, int flags);
 /* Assemble values (nnz, CSR order of rgm_fe_pattern) and b (n) from u_prev (n). */
 int rgm_fe_assemble(rgm_fe fe, const double *u_prev, double *val, double *b, int flags);
+/* Velocity of the convection term (Sec. 6.1).  RGM_FE_VELOCITY_CONSTANT: the
+ * (beta_x, beta_y) given at creation.  RGM_FE_VELOCITY_CELLULAR: the paper's
+ * solenoidal field b = (-sin(pi x) cos(pi y), cos(pi x) sin(pi y)) through its
+ * nodal interpolant (P_{V_h} b), N_ij = (u_prev b_h . grad phi_j, phi_i).
+ * Returns RGM_E_ARG for another kind; device memory for the field (3 vectors
+ * of the cell quadrature size) is owned by the handle.  Synchronises. */
+typedef enum { RGM_FE_VELOCITY_CONSTANT = 0, RGM_FE_VELOCITY_CELLULAR = 1 } rgm_fe_velocity;
+int rgm_fe_set_velocity(rgm_fe fe, int kind);
+/* Forcing of the load (v, f) (Sec. 6.1):
+ *   f = (C/2) sum_{j=1..nmodes} c_j exp(-j^2/20) sin(2 j pi x) sin(2 j pi y)
+ * through its nodal interpolant f_h, so the load is M f_h (the paper: C = 0.1,
+ * 16 modes, c_1 = 1 and c_2..c_16 drawn from U[-1, 1] at every step).  c: nmodes
+ * coefficients (c[0] = c_1), host or device memory by flags; with
+ * RGM_DEVICE_PTRS the call is asynchronous on the handle's stream.  nmodes = 0
+ * restores f = 1.  RGM_E_ARG for nmodes outside 0..RGM_FE_MAX_MODES or a null c.
+ * The forcing applies to every later assembly until changed. */
+#define RGM_FE_MAX_MODES 64
+int rgm_fe_set_forcing(rgm_fe fe, int nmodes, const double *c, double C, int flags);
 /* Nodal interpolant of u0 = sum_{j=1..8} a_j sin(j pi x) sin(j pi y), zero on the
  * boundary.  a8 is a host array of 8 doubles. */
 int rgm_fe_initial_field(rgm_fe fe, const double *a8, double *u0, int flags);

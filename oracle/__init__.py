@@ -65,7 +65,9 @@ class _SeqCfg(C.Structure):
                 ("bx", C.c_double), ("by", C.c_double), ("steps", C.c_int), ("mode", C.c_int),
                 ("m", C.c_int), ("k", C.c_int), ("window", C.c_int), ("ell", C.c_int),
                 ("select_smallest", C.c_int), ("rtol", C.c_double), ("maxit", C.c_int),
-                ("rel_drop", C.c_double), ("guess", C.c_int)]
+                ("rel_drop", C.c_double), ("guess", C.c_int), ("velocity", C.c_int),
+                ("nmodes", C.c_int), ("fC", C.c_double), ("forcing", C.c_void_p),
+                ("proj", C.c_int), ("precond", C.c_int)]
 
 
 SCALAR_FN = C.CFUNCTYPE(C.c_double, C.c_double, C.c_double, C.c_void_p)
@@ -94,6 +96,15 @@ def lib():
             L.orc_fe_step_system.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                              C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                              C.c_void_p, C.c_void_p]
+            L.orc_fe_assemble_field.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double,
+                                                C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                                C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+            L.orc_fe_step_system_field.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double,
+                                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+            L.orc_fe_paper_velocity.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_void_p]
+            L.orc_fe_paper_forcing.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_double,
+                                               C.c_void_p]
             L.orc_gmres.argtypes = [C.POINTER(_Csr), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                     C.POINTER(_Opts), C.POINTER(_Stats), C.c_void_p, C.c_int]
             L.orc_gmres_ir.argtypes = [C.POINTER(_Csr), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
@@ -196,6 +207,48 @@ def step_system(p, N, eps, dt, beta, u_prev, pat=None):
     u = _f64(u_prev)
     rc = lib().orc_fe_step_system(p, N, eps, dt, beta[0], beta[1], _p(u), _p(rowptr), _p(col),
                                   _p(val), _p(b))
+    assert rc == 0, rc
+    return rowptr, col, val, b
+
+
+def assemble_field(p, N, cm, ck, cn, bxn, byn, u=None, dirichlet=True, pat=None):
+    """val = cm*M + ck*K + cn*N(u; b_h), b_h the interpolant of nodal (bxn, byn)."""
+    rowptr, col = pat if pat is not None else pattern(p, N, dirichlet)
+    val = np.zeros(len(col))
+    uu = _f64(u) if u is not None else None
+    bx, by = _f64(bxn), _f64(byn)
+    rc = lib().orc_fe_assemble_field(p, N, cm, ck, cn, _p(bx), _p(by), _p(uu), int(dirichlet),
+                                     _p(rowptr), _p(col), _p(val))
+    assert rc == 0, rc
+    return rowptr, col, val
+
+
+def paper_velocity(p, N):
+    """Sec. 6.1's cellular field at the nodes: (bxn, byn)."""
+    n = ndofs(p, N)
+    bx, by = np.zeros(n), np.zeros(n)
+    assert lib().orc_fe_paper_velocity(p, N, _p(bx), _p(by)) == 0
+    return bx, by
+
+
+def paper_forcing(p, N, c, C_amp=0.1):
+    """Sec. 6.1's forcing with mode coefficients c (c[0] = c_1) at the nodes."""
+    c = _f64(c)
+    out = np.zeros(ndofs(p, N))
+    assert lib().orc_fe_paper_forcing(p, N, len(c), _p(c), C_amp, _p(out)) == 0
+    return out
+
+
+def step_system_field(p, N, eps, dt, bxn, byn, fn, u_prev, pat=None):
+    """(rowptr, col, val, b) of one step with a nodal velocity and nodal forcing
+    (fn None: f = 1)."""
+    rowptr, col = pat if pat is not None else pattern(p, N, True)
+    val = np.zeros(len(col))
+    b = np.zeros(ndofs(p, N))
+    bx, by, u = _f64(bxn), _f64(byn), _f64(u_prev)
+    f = _f64(fn) if fn is not None else None
+    rc = lib().orc_fe_step_system_field(p, N, eps, dt, _p(bx), _p(by), _p(f), _p(u), _p(rowptr),
+                                        _p(col), _p(val), _p(b))
     assert rc == 0, rc
     return rowptr, col, val, b
 
@@ -347,10 +400,16 @@ def recycle_from_window(X, k, select_smallest=False, rel_drop=1e-7):
 # ---------------------------------------------------------------- Algorithm 1 (sequence.c)
 def sequence(p, N, eps, dt, beta, steps, u0, mode=PLAIN, m=30, k=8, window=16, ell=1,
              rtol=1e-10, maxit=20000, select_smallest=False, rel_drop=1e-7, keep_all=False,
-             guess=0):
+             guess=0, velocity=0, forcing=None, forcing_C=0.1, proj=PROJ_OBLIQUE, precond=0):
+    """velocity 1 / forcing (steps x nmodes coefficients): Sec. 6.1's benchmark."""
     n = ndofs(p, N)
+    fc = np.ascontiguousarray(forcing, dtype=np.float64) if forcing is not None else None
+    nmodes = fc.shape[1] if fc is not None else 0
+    if fc is not None:
+        assert fc.shape[0] >= steps
     cfg = _SeqCfg(p, N, eps, dt, beta[0], beta[1], steps, mode, m, k, window, ell,
-                  int(select_smallest), rtol, maxit, rel_drop, int(guess))
+                  int(select_smallest), rtol, maxit, rel_drop, int(guess), int(velocity), nmodes,
+                  forcing_C, _p(fc), int(proj), int(precond))
     u0 = _f64(u0)
     x_all = np.zeros((n, steps), order="F") if keep_all else None
     x_final = np.zeros(n)

@@ -8,6 +8,10 @@
  * lagged at u^{n-1} (the D_u L term is dropped, Sec. 2):
  *   (1/dt)(v, u^n - u^{n-1}) + eps (grad v, grad u^n)
  *       + (v, u^{n-1} beta . grad u^n) = (v, f).
+ * The paper's own benchmark (Sec. 6.1) takes beta as the cellular field
+ * b = (-sin(pi x) cos(pi y), cos(pi x) sin(pi y)) through its nodal interpolant
+ * and a forcing f of 16 random Laplace modes through its nodal interpolant
+ * (orc_fe_paper_velocity / orc_fe_paper_forcing / orc_fe_step_system_field).
  * Q_p Lagrange elements on a uniform N x N grid of [0,1]^2 with Gauss-Lobatto
  * nodes in each cell, lexicographic dof numbering (x fastest) on the
  * (pN+1)^2 node lattice, (p+1)^2 Gauss points per cell.  Homogeneous
@@ -202,9 +206,12 @@ static void make_tab(int p, tab1d *t)
     for (int g = 0; g < t->q; ++g) orc_lagrange(p, xi, t->gx[g], t->phi[g], t->dphi[g]);
 }
 
-int orc_fe_assemble(int p, int N, double cm, double ck, double cn, double bx, double by,
-                    const double *u, int dirichlet, const int64_t *rowptr,
-                    const int32_t *col, double *val)
+/* Shared by the constant-velocity and the nodal-velocity assembly: with
+ * bxn/byn set, the velocity at a quadrature point is its nodal interpolant
+ * sum_l b_l phi_l; otherwise (bx, by). */
+static int assemble_impl(int p, int N, double cm, double ck, double cn, double bx, double by,
+                         const double *bxn, const double *byn, const double *u, int dirichlet,
+                         const int64_t *rowptr, const int32_t *col, double *val)
 {
     if (p < 1 || p > 8 || N < 1) return ORC_E_ARG;
     tab1d t;
@@ -226,13 +233,22 @@ int orc_fe_assemble(int p, int N, double cm, double ck, double cn, double bx, do
             for (int gy = 0; gy < q; ++gy)
                 for (int gx = 0; gx < q; ++gx) {
                     double W = t.gw[gx] * t.gw[gy] * h * h;
-                    /* u at this quadrature point */
-                    double uq = 0.0;
+                    /* u (and a nodal velocity) at this quadrature point */
+                    double uq = 0.0, bxq = bx, byq = by;
                     if (u && cn != 0.0)
                         for (int l = 0; l < nl; ++l) {
                             int la = l % (p + 1), lb = l / (p + 1);
                             uq += u[gdof[l]] * t.phi[gx][la] * t.phi[gy][lb];
                         }
+                    if (bxn && cn != 0.0) {
+                        bxq = 0.0;
+                        byq = 0.0;
+                        for (int l = 0; l < nl; ++l) {
+                            int la = l % (p + 1), lb = l / (p + 1);
+                            bxq += bxn[gdof[l]] * t.phi[gx][la] * t.phi[gy][lb];
+                            byq += byn[gdof[l]] * t.phi[gx][la] * t.phi[gy][lb];
+                        }
+                    }
                     for (int i = 0; i < nl; ++i) {
                         int ia = i % (p + 1), ib = i / (p + 1);
                         double phii = t.phi[gx][ia] * t.phi[gy][ib];
@@ -244,7 +260,7 @@ int orc_fe_assemble(int p, int N, double cm, double ck, double cn, double bx, do
                             double dxj = t.dphi[gx][ja] * t.phi[gy][jb] / h;
                             double dyj = t.phi[gx][ja] * t.dphi[gy][jb] / h;
                             double v = cm * phii * phij + ck * (dxi * dxj + dyi * dyj)
-                                     + cn * phii * uq * (bx * dxj + by * dyj);
+                                     + cn * phii * uq * (bxq * dxj + byq * dyj);
                             Ae[i * nl + j] += W * v;       /* row i (test), column j (trial) */
                         }
                     }
@@ -273,6 +289,21 @@ int orc_fe_assemble(int p, int N, double cm, double ck, double cn, double bx, do
     return rc;
 }
 
+int orc_fe_assemble(int p, int N, double cm, double ck, double cn, double bx, double by,
+                    const double *u, int dirichlet, const int64_t *rowptr,
+                    const int32_t *col, double *val)
+{
+    return assemble_impl(p, N, cm, ck, cn, bx, by, NULL, NULL, u, dirichlet, rowptr, col, val);
+}
+
+int orc_fe_assemble_field(int p, int N, double cm, double ck, double cn, const double *bxn,
+                          const double *byn, const double *u, int dirichlet,
+                          const int64_t *rowptr, const int32_t *col, double *val)
+{
+    if (!bxn || !byn) return ORC_E_ARG;
+    return assemble_impl(p, N, cm, ck, cn, 0.0, 0.0, bxn, byn, u, dirichlet, rowptr, col, val);
+}
+
 int orc_fe_load(int p, int N, orc_scalar_fn f, void *ctx, double *F)
 {
     if (p < 1 || p > 8 || N < 1) return ORC_E_ARG;
@@ -297,31 +328,87 @@ int orc_fe_load(int p, int N, orc_scalar_fn f, void *ctx, double *F)
     return ORC_OK;
 }
 
-int orc_fe_step_system(int p, int N, double eps, double dt, double bx, double by,
-                       const double *u_prev, const int64_t *rowptr, const int32_t *col,
-                       double *val, double *b)
+/* b = M u_prev / dt + (v, f) with the full (not Dirichlet-reduced) mass
+ * matrix; (v, f) = F(f = 1) by quadrature when fn is NULL, else M fn (the
+ * load of the nodal interpolant); b_i = 0 on Dirichlet rows. */
+static int step_rhs(int p, int N, double dt, const double *u_prev, const double *fn, double *b)
 {
     const int64_t n = orc_fe_ndofs(p, N);
-    int rc = orc_fe_assemble(p, N, 1.0 / dt, eps, 1.0, bx, by, u_prev, 1, rowptr, col, val);
-    if (rc) return rc;
-    /* b = M u_prev / dt + F with the full (not Dirichlet-reduced) mass matrix */
     int64_t nnzf = orc_fe_pattern(p, N, 0, NULL, NULL);
     int64_t *rp = malloc(sizeof(int64_t) * (n + 1));
     int32_t *cl = malloc(sizeof(int32_t) * nnzf);
     double *mv = malloc(sizeof(double) * nnzf);
     if (!rp || !cl || !mv) { free(rp); free(cl); free(mv); return ORC_E_NOMEM; }
     orc_fe_pattern(p, N, 0, rp, cl);
-    rc = orc_fe_assemble(p, N, 1.0, 0.0, 0.0, 0.0, 0.0, NULL, 0, rp, cl, mv);
+    int rc = orc_fe_assemble(p, N, 1.0, 0.0, 0.0, 0.0, 0.0, NULL, 0, rp, cl, mv);
     if (rc == ORC_OK) {
-        orc_fe_load(p, N, NULL, NULL, b);
+        if (!fn) orc_fe_load(p, N, NULL, NULL, b);
         for (int64_t r = 0; r < n; ++r) {
             double s = 0.0;
             for (int64_t k = rp[r]; k < rp[r + 1]; ++k) s += mv[k] * u_prev[cl[k]];
-            b[r] += s / dt;
+            if (fn) {
+                double sf = 0.0;
+                for (int64_t k = rp[r]; k < rp[r + 1]; ++k) sf += mv[k] * fn[cl[k]];
+                b[r] = s / dt + sf;
+            } else {
+                b[r] += s / dt;
+            }
             if (on_boundary(p, N, r)) b[r] = 0.0;
         }
     }
     free(rp); free(cl); free(mv);
+    return rc;
+}
+
+int orc_fe_step_system(int p, int N, double eps, double dt, double bx, double by,
+                       const double *u_prev, const int64_t *rowptr, const int32_t *col,
+                       double *val, double *b)
+{
+    int rc = orc_fe_assemble(p, N, 1.0 / dt, eps, 1.0, bx, by, u_prev, 1, rowptr, col, val);
+    if (rc) return rc;
+    return step_rhs(p, N, dt, u_prev, NULL, b);
+}
+
+int orc_fe_step_system_field(int p, int N, double eps, double dt, const double *bxn,
+                             const double *byn, const double *fn, const double *u_prev,
+                             const int64_t *rowptr, const int32_t *col, double *val, double *b)
+{
+    int rc = orc_fe_assemble_field(p, N, 1.0 / dt, eps, 1.0, bxn, byn, u_prev, 1, rowptr, col, val);
+    if (rc) return rc;
+    return step_rhs(p, N, dt, u_prev, fn, b);
+}
+
+int orc_fe_paper_velocity(int p, int N, double *bxn, double *byn)
+{
+    const int64_t n = orc_fe_ndofs(p, N);
+    double *x = malloc(sizeof(double) * n), *y = malloc(sizeof(double) * n);
+    if (!x || !y) { free(x); free(y); return ORC_E_NOMEM; }
+    int rc = orc_fe_node_coords(p, N, x, y);
+    if (rc == ORC_OK)
+        for (int64_t i = 0; i < n; ++i) {
+            bxn[i] = -sin(M_PI * x[i]) * cos(M_PI * y[i]);
+            byn[i] = cos(M_PI * x[i]) * sin(M_PI * y[i]);
+        }
+    free(x); free(y);
+    return rc;
+}
+
+int orc_fe_paper_forcing(int p, int N, int nmodes, const double *c, double C, double *fn)
+{
+    if (nmodes < 0 || (nmodes > 0 && !c)) return ORC_E_ARG;
+    const int64_t n = orc_fe_ndofs(p, N);
+    double *x = malloc(sizeof(double) * n), *y = malloc(sizeof(double) * n);
+    if (!x || !y) { free(x); free(y); return ORC_E_NOMEM; }
+    int rc = orc_fe_node_coords(p, N, x, y);
+    if (rc == ORC_OK)
+        for (int64_t i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int j = 1; j <= nmodes; ++j)
+                s += c[j - 1] * exp(-(double)(j * j) / 20.0) * sin(2.0 * j * M_PI * x[i])
+                     * sin(2.0 * j * M_PI * y[i]);
+            fn[i] = 0.5 * C * s;
+        }
+    free(x); free(y);
     return rc;
 }
 

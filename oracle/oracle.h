@@ -66,6 +66,22 @@ int orc_fe_load(int p, int N, orc_scalar_fn f, void *ctx, double *F);
 int orc_fe_step_system(int p, int N, double eps, double dt, double bx, double by,
                        const double *u_prev, const int64_t *rowptr, const int32_t *col,
                        double *val, double *b);
+/* As orc_fe_assemble with the velocity given by nodal values (bxn, byn; n
+ * each), interpolated at the quadrature points by the element basis. */
+int orc_fe_assemble_field(int p, int N, double cm, double ck, double cn, const double *bxn,
+                          const double *byn, const double *u, int dirichlet,
+                          const int64_t *rowptr, const int32_t *col, double *val);
+/* Sec. 6.1's benchmark step: A = M/dt + eps K + N(u_prev; b_h) with the nodal
+ * velocity (bxn, byn), b = M u_prev / dt + M fn (fn: nodal forcing; NULL
+ * means (v, 1) as in orc_fe_step_system), Dirichlet rows as there. */
+int orc_fe_step_system_field(int p, int N, double eps, double dt, const double *bxn,
+                             const double *byn, const double *fn, const double *u_prev,
+                             const int64_t *rowptr, const int32_t *col, double *val, double *b);
+/* Sec. 6.1: b = (-sin(pi x) cos(pi y), cos(pi x) sin(pi y)) at the nodes. */
+int orc_fe_paper_velocity(int p, int N, double *bxn, double *byn);
+/* Sec. 6.1: f = (C/2) sum_{j=1..nmodes} c_j exp(-j^2/20) sin(2 j pi x) sin(2 j pi y)
+ * at the nodes (the paper: C = 0.1, 16 modes, c_1 = 1, c_j ~ U[-1,1] per step). */
+int orc_fe_paper_forcing(int p, int N, int nmodes, const double *c, double C, double *fn);
 /* Nodal interpolant of u0 = sum_{j=1..8} a_j sin(j pi x) sin(j pi y), zero on the boundary. */
 int orc_fe_u0(int p, int N, const double *a8, double *u0);
 
@@ -167,6 +183,12 @@ typedef struct {
     int guess;         /* 0: previous solution (plain) / zero (recycled) as x_in;
                           g = 1..3: extrapolation of order g from the g+1 most recent
                           solutions (Eq. ext2-ext4) once that many are stored    */
+    int velocity;      /* 0: constant (bx, by); 1: Sec. 6.1's cellular field    */
+    int nmodes;        /* forcing modes per step (0: f = 1)                      */
+    double fC;         /* forcing amplitude C                                    */
+    const double *forcing;  /* steps x nmodes coefficients c_j, step-major     */
+    int proj;          /* ORC_PROJ_* of the solves                                */
+    int precond;       /* ORC_PRECOND_* of the solves                             */
 } orc_seq_cfg;
 /* u0: initial nodal field.  x_all (optional): n x steps solutions.
  * iters/k_used/status (length steps) and relres (length steps) are per step. */

@@ -14,6 +14,8 @@
  * the paper's x0 = U E^{-1} U^T b), without one from the previous solution.
  * With cfg->guess = g > 0, x_in is instead the extrapolation of order g
  * (Sec. 4.1) once g+1 solutions are stored (the window must hold them).
+ * cfg->velocity / nmodes select Sec. 6.1's own benchmark (cellular velocity,
+ * random forcing with the coefficients of step i at forcing[(i-1) nmodes]).
  */
 #include "oracle.h"
 #include <stdlib.h>
@@ -37,7 +39,9 @@ int orc_sequence_timed(const orc_seq_cfg *cfg, const double *u0, double *x_all, 
                        int *iters, int *k_used, double *relres, int *status,
                        double *step_seconds)
 {
-    if (!cfg || !u0 || cfg->steps < 1 || cfg->window < 1) return ORC_E_ARG;
+    if (!cfg || !u0 || cfg->steps < 1 || cfg->window < 1 || cfg->nmodes < 0 ||
+        (cfg->nmodes > 0 && !cfg->forcing))
+        return ORC_E_ARG;
     const int p = cfg->p, N = cfg->N;
     const int64_t n = orc_fe_ndofs(p, N);
     const int64_t nnz = orc_fe_pattern(p, N, 1, NULL, NULL);
@@ -47,9 +51,16 @@ int orc_sequence_timed(const orc_seq_cfg *cfg, const double *u0, double *x_all, 
     double *u = malloc(sizeof(double) * n), *x = malloc(sizeof(double) * n);
     double *X = malloc(sizeof(double) * n * cfg->window);
     double *U = malloc(sizeof(double) * n * (cfg->k > 0 ? cfg->k : 1));
-    if (!rowptr || !col || !val || !b || !u || !x || !X || !U) {
-        free(rowptr); free(col); free(val); free(b); free(u); free(x); free(X); free(U);
+    double *vf = malloc(sizeof(double) * 3 * n);     /* nodal bx | by | f */
+    if (!rowptr || !col || !val || !b || !u || !x || !X || !U || !vf) {
+        free(rowptr); free(col); free(val); free(b); free(u); free(x); free(X); free(U); free(vf);
         return ORC_E_NOMEM;
+    }
+    double *bxn = vf, *byn = vf + n, *fn = vf + 2 * n;
+    if (cfg->velocity == 1) {
+        orc_fe_paper_velocity(p, N, bxn, byn);
+    } else {
+        for (int64_t r = 0; r < n; ++r) { bxn[r] = cfg->bx; byn[r] = cfg->by; }
     }
     orc_fe_pattern(p, N, 1, rowptr, col);
     orc_csr A = {n, rowptr, col, val};
@@ -57,7 +68,15 @@ int orc_sequence_timed(const orc_seq_cfg *cfg, const double *u0, double *x_all, 
     int count = 0, k_eff = 0, rc = ORC_OK;
     for (int i = 1; i <= cfg->steps; ++i) {
         double t0 = now_s();
-        rc = orc_fe_step_system(p, N, cfg->eps, cfg->dt, cfg->bx, cfg->by, u, rowptr, col, val, b);
+        if (cfg->velocity == 0 && cfg->nmodes == 0) {
+            rc = orc_fe_step_system(p, N, cfg->eps, cfg->dt, cfg->bx, cfg->by, u, rowptr, col, val, b);
+        } else {
+            if (cfg->nmodes > 0)
+                orc_fe_paper_forcing(p, N, cfg->nmodes, cfg->forcing + (int64_t)(i - 1) * cfg->nmodes,
+                                     cfg->fC, fn);
+            rc = orc_fe_step_system_field(p, N, cfg->eps, cfg->dt, bxn, byn,
+                                          cfg->nmodes > 0 ? fn : NULL, u, rowptr, col, val, b);
+        }
         if (rc) break;
         int use_u = (cfg->mode != ORC_PLAIN && k_eff > 0);
         if (use_u) memset(x, 0, sizeof(double) * n);
@@ -71,7 +90,7 @@ int orc_sequence_timed(const orc_seq_cfg *cfg, const double *u0, double *x_all, 
             orc_extrapolate(n, cfg->guess + 1, P, n, x);
             free(P);
         }
-        orc_opts o = {cfg->mode, cfg->m, cfg->rtol, cfg->maxit, 0, 0, 0};
+        orc_opts o = {cfg->mode, cfg->m, cfg->rtol, cfg->maxit, 0, cfg->proj, cfg->precond};
         orc_stats st;
         int s = orc_gmres(&A, b, x, use_u ? U : NULL, use_u ? k_eff : 0, &o, &st, NULL, 0);
         if (s < 0) { rc = s; break; }
@@ -96,7 +115,7 @@ int orc_sequence_timed(const orc_seq_cfg *cfg, const double *u0, double *x_all, 
         if (step_seconds) step_seconds[i - 1] = now_s() - t0;
     }
     if (x_final && rc == ORC_OK) memcpy(x_final, u, sizeof(double) * n);
-    free(rowptr); free(col); free(val); free(b); free(u); free(x); free(X); free(U);
+    free(rowptr); free(col); free(val); free(b); free(u); free(x); free(X); free(U); free(vf);
     return rc;
 }
 

@@ -305,6 +305,22 @@ class FE:
                                       C.c_void_p(b.ctypes.data), 0), "rgm_fe_assemble")
         return val, b
 
+    VELOCITIES = {"constant": 0, "cellular": 1}
+
+    def set_velocity(self, kind="cellular"):
+        """'constant' (beta of the constructor) or 'cellular' (Sec. 6.1's field)."""
+        k = self.VELOCITIES[kind] if isinstance(kind, str) else int(kind)
+        check(self._L.rgm_fe_set_velocity(self._h, k), "rgm_fe_set_velocity")
+
+    def set_forcing(self, c=None, C_amp=0.1):
+        """Sec. 6.1's forcing with mode coefficients c (c[0] = c_1); None: f = 1."""
+        if c is None:
+            check(self._L.rgm_fe_set_forcing(self._h, 0, None, 0.0, 0), "rgm_fe_set_forcing")
+            return
+        a = np.ascontiguousarray(c, dtype=np.float64)
+        check(self._L.rgm_fe_set_forcing(self._h, len(a), C.c_void_p(a.ctypes.data), float(C_amp), 0),
+              "rgm_fe_set_forcing")
+
     def initial_field(self, a8):
         a = np.ascontiguousarray(a8, dtype=np.float64)
         u0 = np.zeros(self.n)

@@ -90,6 +90,8 @@ _SIGS = {
     "rgm_fe_pattern": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "rgm_fe_assemble": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "rgm_fe_initial_field": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "rgm_fe_set_velocity": (C.c_int, [C.c_void_p, C.c_int]),
+    "rgm_fe_set_forcing": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_double, C.c_int]),
     "rgm_fe_time_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(RgmStats)]),
 }
 

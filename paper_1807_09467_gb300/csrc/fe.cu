@@ -10,6 +10,14 @@
 // so that N_ij = h sum_l u_l T[i][j][l] on each cell.  Assembly gathers row by
 // row (one warp per row, one lane per stored entry, cells visited in a fixed
 // order), so it is deterministic and needs no atomics.
+//
+// Sec. 6.1's own benchmark replaces beta by the cellular field
+// b = (-sin(pi x) cos(pi y), cos(pi x) sin(pi y)) through its nodal interpolant
+// and the load (v, 1) by (v, f_h), f_h the interpolant of 16 random Laplace
+// modes: then a first kernel forms, per cell and Gauss point q,
+//   C_x = w_q h u(q) b_x(q),  C_y = w_q h u(q) b_y(q)
+// (u, b interpolated), and N_ij sums phi_i (C_x d_x phi_j + C_y d_y phi_j) over
+// the shared cells' Gauss points; the load is M f_h.
 #include "../../include/rgmres.h"
 #include <cuda_runtime.h>
 
@@ -45,6 +53,11 @@ struct rgm_fe_s {
     double *val = nullptr;    // assembly target when not writing into a solver
     double *b = nullptr;
     double *x = nullptr;      // solve scratch for rgm_fe_time_step
+    // Sec. 6.1 benchmark fields (null: constant beta, f = 1)
+    double *bxn = nullptr, *byn = nullptr;   // nodal velocity
+    double *coef = nullptr;                  // C_x, C_y per cell and Gauss point
+    double *fn = nullptr;                    // nodal forcing
+    double *cmodes = nullptr;                // forcing coefficients (RGM_FE_MAX_MODES)
 };
 
 namespace {
@@ -117,11 +130,69 @@ struct FeDev {
     int64_t L, n;
     double h, inv_dt, eps;
     const double *M1, *K1, *F1, *T;
+    const double *PH, *DPH, *GW;   // phi_a, phi_a' at Gauss point g ([g][a]), Gauss weights
 };
+
+// Coordinate of lattice node I along one axis (GLL nodes inside each cell).
+__device__ __forceinline__ double node_coord(int64_t I, int p, int N, const double *xi)
+{
+    const int64_t cell = I / p;
+    return cell == N ? 1.0 : ((double)cell + xi[I % p]) / (double)N;
+}
+
+// Sec. 6.1's cellular velocity at the nodes.
+__global__ void fe_velocity_kernel(int p, int N, int64_t L, double x0, double x1, double x2,
+                                   double x3, double x4, double *bxn, double *byn, int64_t n)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double xi[5] = {x0, x1, x2, x3, x4};
+    const double x = node_coord(i % L, p, N, xi), y = node_coord(i / L, p, N, xi);
+    bxn[i] = -sin(M_PI * x) * cos(M_PI * y);
+    byn[i] = cos(M_PI * x) * sin(M_PI * y);
+}
+
+// Sec. 6.1's forcing at the nodes: (C/2) sum_j c_j exp(-j^2/20) sin(2 j pi x) sin(2 j pi y).
+__global__ void fe_forcing_kernel(int p, int N, int64_t L, double x0, double x1, double x2,
+                                  double x3, double x4, int nmodes, const double *c, double C,
+                                  double *fn, int64_t n)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double xi[5] = {x0, x1, x2, x3, x4};
+    const double x = node_coord(i % L, p, N, xi), y = node_coord(i / L, p, N, xi);
+    double s = 0.0;
+    for (int j = 1; j <= nmodes; ++j)
+        s += c[j - 1] * exp(-(double)(j * j) / 20.0) * sin(2.0 * j * M_PI * x) * sin(2.0 * j * M_PI * y);
+    fn[i] = 0.5 * C * s;
+}
+
+// C_x, C_y per (cell, Gauss point): one thread each.
+__global__ void fe_conv_coef_kernel(FeDev f, const double *u, const double *bxn, const double *byn,
+                                    double *coef)
+{
+    const int q1 = f.p + 1, nq = q1 * q1;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)f.N * f.N * nq) return;
+    const int g = (int)(t % nq), gx = g % q1, gy = g / q1;
+    const int64_t cell = t / nq, cx = cell % f.N, cy = cell / f.N;
+    double uq = 0.0, bx = 0.0, by = 0.0;
+    for (int lb = 0; lb <= f.p; ++lb)
+        for (int la = 0; la <= f.p; ++la) {
+            const double ph = f.PH[gx * q1 + la] * f.PH[gy * q1 + lb];
+            const int64_t d = (cy * f.p + lb) * f.L + cx * f.p + la;
+            uq += u[d] * ph;
+            bx += bxn[d] * ph;
+            by += byn[d] * ph;
+        }
+    const double w = f.GW[gx] * f.GW[gy] * f.h;
+    coef[2 * t] = w * uq * bx;
+    coef[2 * t + 1] = w * uq * by;
+}
 
 // One warp per row: values of A on the Dirichlet pattern.
 __global__ void fe_assemble_kernel(FeDev f, const int64_t *rowptr, const int32_t *col,
-                                   const double *u, double *val)
+                                   const double *u, const double *coef, double *val)
 {
     const int lane = threadIdx.x & 31;
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -150,6 +221,18 @@ __global__ void fe_assemble_kernel(FeDev f, const int64_t *rowptr, const int32_t
                 const double mx = f.M1[ia * q1 + ja], my = f.M1[ib * q1 + jb];
                 const double kx = f.K1[ia * q1 + ja], ky = f.K1[ib * q1 + jb];
                 double conv = 0.0;
+                if (coef) {     // nodal velocity: quadrature with the per-point coefficients
+                    const double *cc = coef + 2 * (((int64_t)cy * f.N + cx) * f.nl);
+                    for (int gy = 0; gy <= p; ++gy)
+                        for (int gx = 0; gx <= p; ++gx) {
+                            const double pi = f.PH[gx * q1 + ia] * f.PH[gy * q1 + ib];
+                            const int g = gy * q1 + gx;
+                            conv += pi * (cc[2 * g] * f.DPH[gx * q1 + ja] * f.PH[gy * q1 + jb] +
+                                          cc[2 * g + 1] * f.PH[gx * q1 + ja] * f.DPH[gy * q1 + jb]);
+                        }
+                    v += f.h * f.h * mx * my * f.inv_dt + f.eps * (kx * my + mx * ky) + conv;
+                    continue;
+                }
                 const int il = ib * q1 + ia, jl = jb * q1 + ja;
                 const double *Tij = f.T + ((int64_t)il * f.nl + jl) * f.nl;
                 for (int lb = 0; lb <= p; ++lb) {
@@ -163,8 +246,9 @@ __global__ void fe_assemble_kernel(FeDev f, const int64_t *rowptr, const int32_t
 }
 
 // b = M u / dt + F over the full neighbourhood (boundary columns included),
-// then b_i = 0 on Dirichlet rows.  One thread per row.
-__global__ void fe_rhs_kernel(FeDev f, const double *u, double *b)
+// then b_i = 0 on Dirichlet rows; with a nodal forcing fn, F = M fn.  One
+// thread per row.
+__global__ void fe_rhs_kernel(FeDev f, const double *u, const double *fn, double *b)
 {
     const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (row >= f.n) return;
@@ -178,11 +262,13 @@ __global__ void fe_rhs_kernel(FeDev f, const double *u, double *b)
     for (int cy = ay0; cy <= ay1; ++cy)
         for (int cx = ax0; cx <= ax1; ++cx) {
             const int ia = (int)(Ix - (int64_t)cx * p), ib = (int)(Iy - (int64_t)cy * p);
-            F += f.h * f.h * f.F1[ia] * f.F1[ib];
+            if (!fn) F += f.h * f.h * f.F1[ia] * f.F1[ib];
             for (int jb = 0; jb <= p; ++jb)
                 for (int ja = 0; ja <= p; ++ja) {
                     const int64_t cj = ((int64_t)cy * p + jb) * f.L + (int64_t)cx * p + ja;
-                    mu += f.h * f.h * f.M1[ia * q1 + ja] * f.M1[ib * q1 + jb] * u[cj];
+                    const double mij = f.h * f.h * f.M1[ia * q1 + ja] * f.M1[ib * q1 + jb];
+                    mu += mij * u[cj];
+                    if (fn) F += mij * fn[cj];
                 }
         }
     b[row] = mu * f.inv_dt + F;
@@ -216,6 +302,7 @@ FeDev dev_view(const rgm_fe_s *fe)
     f.p = fe->p; f.N = fe->N; f.nl = q1 * q1; f.L = fe->L; f.n = fe->n; f.h = fe->h;
     f.inv_dt = 1.0 / fe->dt; f.eps = fe->eps;
     f.M1 = fe->tabs; f.K1 = f.M1 + q1 * q1; f.F1 = f.K1 + q1 * q1; f.T = f.F1 + q1;
+    f.PH = f.T + (int64_t)f.nl * f.nl * f.nl; f.DPH = f.PH + q1 * q1; f.GW = f.DPH + q1 * q1;
     return f;
 }
 
@@ -263,8 +350,13 @@ int rgm_fe_create(rgm_fe *out, int p, int N, double eps, double dt, double beta_
     gll_closed(p, xi);
     gauss_closed(q1, gx, gw);
     for (int g = 0; g < q1; ++g) basis(p, xi, gx[g], ph[g], dph[g]);
-    std::vector<double> tab(2 * q1 * q1 + q1 + (size_t)nl * nl * nl, 0.0);
+    std::vector<double> tab(2 * q1 * q1 + q1 + (size_t)nl * nl * nl + 2 * q1 * q1 + q1, 0.0);
     double *M1 = tab.data(), *K1 = M1 + q1 * q1, *F1 = K1 + q1 * q1, *T = F1 + q1;
+    double *PH = T + (size_t)nl * nl * nl, *DPH = PH + q1 * q1, *GW = DPH + q1 * q1;
+    for (int g = 0; g < q1; ++g) {
+        GW[g] = gw[g];
+        for (int a = 0; a <= p; ++a) { PH[g * q1 + a] = ph[g][a]; DPH[g * q1 + a] = dph[g][a]; }
+    }
     for (int a = 0; a <= p; ++a) {
         for (int c = 0; c <= p; ++c)
             for (int g = 0; g < q1; ++g) {
@@ -308,7 +400,8 @@ int rgm_fe_create(rgm_fe *out, int p, int N, double eps, double dt, double beta_
 int rgm_fe_destroy(rgm_fe fe)
 {
     if (!fe) return RGM_E_ARG;
-    void *p[] = {fe->rowptr, fe->col, fe->tabs, fe->val, fe->b, fe->x};
+    void *p[] = {fe->rowptr, fe->col, fe->tabs, fe->val, fe->b, fe->x, fe->bxn, fe->byn, fe->coef,
+                 fe->fn, fe->cmodes};
     for (void *q : p)
         if (q) cudaFree(q);
     delete fe;
@@ -337,8 +430,13 @@ static int fe_assemble_dev(rgm_fe fe, const double *u_dev, double *val_dev, doub
     FeDev f = dev_view(fe);
     const int64_t warps = fe->n;
     const int tpb = 256;
-    fe_assemble_kernel<<<(unsigned)((warps * 32 + tpb - 1) / tpb), tpb, 0, fe->st>>>(f, fe->rowptr, fe->col, u_dev, val_dev);
-    fe_rhs_kernel<<<(unsigned)((fe->n + tpb - 1) / tpb), tpb, 0, fe->st>>>(f, u_dev, b_dev);
+    if (fe->bxn) {
+        const int64_t nt = (int64_t)fe->N * fe->N * f.nl;
+        fe_conv_coef_kernel<<<(unsigned)((nt + tpb - 1) / tpb), tpb, 0, fe->st>>>(f, u_dev, fe->bxn, fe->byn, fe->coef);
+    }
+    fe_assemble_kernel<<<(unsigned)((warps * 32 + tpb - 1) / tpb), tpb, 0, fe->st>>>(
+        f, fe->rowptr, fe->col, u_dev, fe->bxn ? fe->coef : nullptr, val_dev);
+    fe_rhs_kernel<<<(unsigned)((fe->n + tpb - 1) / tpb), tpb, 0, fe->st>>>(f, u_dev, fe->fn, b_dev);
     CKF(cudaGetLastError());
     return RGM_OK;
 }
@@ -358,6 +456,56 @@ int rgm_fe_assemble(rgm_fe fe, const double *u_prev, double *val, double *b, int
     CKF(cudaMemcpyAsync(val, fe->val, sizeof(double) * fe->nnz, cudaMemcpyDeviceToHost, fe->st));
     CKF(cudaMemcpyAsync(b, fe->b, sizeof(double) * fe->n, cudaMemcpyDeviceToHost, fe->st));
     CKF(cudaStreamSynchronize(fe->st));
+    return RGM_OK;
+}
+
+int rgm_fe_set_velocity(rgm_fe fe, int kind)
+{
+    if (!fe || kind < RGM_FE_VELOCITY_CONSTANT || kind > RGM_FE_VELOCITY_CELLULAR) return RGM_E_ARG;
+    if (kind == RGM_FE_VELOCITY_CONSTANT) {
+        CKF(cudaStreamSynchronize(fe->st));
+        void *p[] = {fe->bxn, fe->byn, fe->coef};
+        for (void *q : p)
+            if (q) cudaFree(q);
+        fe->bxn = fe->byn = fe->coef = nullptr;
+        return RGM_OK;
+    }
+    if (!fe->bxn) {
+        const int64_t ncoef = 2 * (int64_t)fe->N * fe->N * (fe->p + 1) * (fe->p + 1);
+        CKF(cudaMalloc((void **)&fe->bxn, sizeof(double) * fe->n));
+        CKF(cudaMalloc((void **)&fe->byn, sizeof(double) * fe->n));
+        CKF(cudaMalloc((void **)&fe->coef, sizeof(double) * ncoef));
+    }
+    double xi[5] = {0, 0, 0, 0, 0};
+    gll_closed(fe->p, xi);
+    fe_velocity_kernel<<<(unsigned)((fe->n + 255) / 256), 256, 0, fe->st>>>(
+        fe->p, fe->N, fe->L, xi[0], xi[1], xi[2], xi[3], xi[4], fe->bxn, fe->byn, fe->n);
+    CKF(cudaGetLastError());
+    CKF(cudaStreamSynchronize(fe->st));
+    return RGM_OK;
+}
+
+int rgm_fe_set_forcing(rgm_fe fe, int nmodes, const double *c, double C, int flags)
+{
+    if (!fe || nmodes < 0 || nmodes > RGM_FE_MAX_MODES || (nmodes > 0 && !c)) return RGM_E_ARG;
+    if (nmodes == 0) {
+        CKF(cudaStreamSynchronize(fe->st));
+        if (fe->fn) cudaFree(fe->fn);
+        fe->fn = nullptr;
+        return RGM_OK;
+    }
+    if (!fe->fn) {
+        CKF(cudaMalloc((void **)&fe->fn, sizeof(double) * fe->n));
+        CKF(cudaMalloc((void **)&fe->cmodes, sizeof(double) * RGM_FE_MAX_MODES));
+    }
+    CKF(cudaMemcpyAsync(fe->cmodes, c, sizeof(double) * nmodes,
+                        (flags & RGM_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, fe->st));
+    double xi[5] = {0, 0, 0, 0, 0};
+    gll_closed(fe->p, xi);
+    fe_forcing_kernel<<<(unsigned)((fe->n + 255) / 256), 256, 0, fe->st>>>(
+        fe->p, fe->N, fe->L, xi[0], xi[1], xi[2], xi[3], xi[4], nmodes, fe->cmodes, C, fe->fn, fe->n);
+    CKF(cudaGetLastError());
+    if (!(flags & RGM_DEVICE_PTRS)) CKF(cudaStreamSynchronize(fe->st));
     return RGM_OK;
 }
 

@@ -9,6 +9,8 @@ Workloads (the paper's benchmark of Sec. 6.1 re-parameterised; see the tables
 below): the 2D problem -div(eps grad u) + u beta.grad u = f on the unit square,
 f = 1, u = 0 on the boundary, u0 = sum_{j=1..8} a_j sin(j pi x) sin(j pi y) with
 a_j ~ U(-0.5, 0.5), implicit Euler with the convection coefficient lagged one step.
+PAPER_Q1_64 is the paper's own configuration (cellular velocity, random forcing,
+zero initial value).
 """
 from __future__ import annotations
 
@@ -57,6 +59,10 @@ class Workload:
     fixed_beta: tuple | None = None   # None: (cos t, sin t) with t ~ U(0, 2 pi)
     ell: int = 1        # SVD interval
     modes: tuple = field(default=("plain", "deflated", "augmented"))
+    velocity: str = "constant"   # or "cellular": Sec. 6.1's b = (-sin pi x cos pi y, cos pi x sin pi y)
+    forcing_modes: int = 0       # > 0: Sec. 6.1's random forcing with this many modes (else f = 1)
+    forcing_C: float = 0.1
+    u0: str = "sines"            # or "zero"
 
     @property
     def n(self) -> int:
@@ -74,7 +80,16 @@ Q2_128 = Workload("q2_128x128_eps0.01_dt0.005", 2, 128, 0.01, 0.005, 40, 30, 8, 
 Q4_256 = Workload("q4_256x256_eps0.002_dt0.002", 4, 256, 0.002, 0.002, 50, 40, 12, 24, 1e-8,
                   modes=("plain", "deflated", "augmented", "ir"))
 
-WORKLOADS = {w.name: w for w in (Q1_32, Q2_128, Q4_256)}
+# Sec. 6.1's own benchmark: Q1 64^2 (4225 dofs), the cellular velocity, forcing of
+# 16 Laplace modes with C = 0.1, c_1 = 1 and c_2..c_16 ~ U[-1, 1] drawn at every step,
+# zero initial value, dt 0.5, 1000 steps, true residual 1e-8, nu in {1e-1, 1e-2,
+# 1e-3}.  The paper sweeps the restart and the window; GMRES(30), k 8 of 16 here.
+PAPER_Q1_64 = {nu: Workload(f"paper_q1_64x64_nu{nu:g}", 1, 64, nu, 0.5, 1000, 30, 8, 16, 1e-8,
+                            fixed_beta=(0.0, 0.0), velocity="cellular", forcing_modes=16,
+                            u0="zero")
+               for nu in (1e-1, 1e-2, 1e-3)}
+
+WORKLOADS = {w.name: w for w in (Q1_32, Q2_128, Q4_256, *PAPER_Q1_64.values())}
 
 
 def sequence_draws(w: Workload, seq_index: int = 0):
@@ -84,6 +99,17 @@ def sequence_draws(w: Workload, seq_index: int = 0):
     theta = g.uniform(0.0, 2.0 * math.pi)
     beta = w.fixed_beta if w.fixed_beta is not None else (math.cos(theta), math.sin(theta))
     return a8, beta
+
+
+def forcing_draws(w: Workload, steps: int, seq_index: int = 0) -> np.ndarray:
+    """(steps, forcing_modes) coefficients of Sec. 6.1's forcing, one row per time
+    step: c_1 = 1, c_2..c_m ~ U(-1, 1) in order."""
+    g = SplitMix64(BASE_SEED + 0x6000 + seq_index)
+    out = np.ones((steps, w.forcing_modes))
+    for i in range(steps):
+        for j in range(1, w.forcing_modes):
+            out[i, j] = g.uniform(-1.0, 1.0)
+    return out
 
 
 def batch_sequences(count: int = 64, steps: int = 20, seed_index: int = 0, n_lo: int = 32,
