@@ -44,6 +44,11 @@ def parse():
                     help="a single-sequence workload, batch64 (64 uneven sequences solved together) "
                          "or serve (a Poisson stream of sequences, continuous batching)")
     ap.add_argument("--mode", default="deflated", choices=["plain", "deflated", "augmented"])
+    ap.add_argument("--k", type=int, default=None, help="override the workload's recycle dimension")
+    ap.add_argument("--window", type=int, default=None, help="override the workload's snapshot window")
+    ap.add_argument("--svd-interval", type=int, default=None, help="override the workload's SVD interval")
+    ap.add_argument("--precond", default=None, choices=["none", "jacobi"],
+                    help="override the workload's preconditioner")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_ir"])
     ap.add_argument("--cpu-steps", type=int, default=0, help="oracle steps for cpu_baseline (0: auto)")
     ap.add_argument("--quick", action="store_true", help="skip e2e, cpu baseline and side modes")
@@ -177,6 +182,22 @@ def workload_u0(np, fe, w, a8):
     return np.zeros(fe.n) if w.u0 == "zero" else fe.initial_field(a8)
 
 
+def workload_of(synth, args):
+    """The named workload with the command line's overrides applied."""
+    import dataclasses
+    w = synth.WORKLOADS[args.workload]
+    over = {}
+    if args.k is not None:
+        over["k"] = args.k
+    if args.window is not None:
+        over["window"] = args.window
+    if args.svd_interval is not None:
+        over["ell"] = args.svd_interval
+    if args.precond is not None:
+        over["precond"] = args.precond
+    return dataclasses.replace(w, **over) if over else w
+
+
 def workload_seq(synth, w, index, steps):
     """(a8, beta, forcing rows or None) of one sequence."""
     a8, beta = synth.sequence_draws(w, index)
@@ -195,7 +216,8 @@ def run_sequence(rg, torch, w, seq, mode, precision, warmup, steps, profile=Fals
     rp, col = fe.pattern()
     rtol = w.rtol if precision == "fp64" else 1e-8
     solver = rg.Solver(fe.n, m=w.m, k=w.k, window=w.window, svd_interval=w.ell, mode=mode,
-                       precision=precision, rtol=rtol, stream=stream, launch_policy=LAUNCH_POLICY[0])
+                       precision=precision, rtol=rtol, stream=stream, launch_policy=LAUNCH_POLICY[0],
+                       precond=w.precond)
     u0 = workload_u0(np, fe, w, a8)
     u = torch.tensor(u0, dtype=torch.float64, device=dev)
     solver.set_operator_csr(rp, col, torch.zeros(len(col), dtype=torch.float64).numpy())
@@ -255,7 +277,7 @@ def run_e2e(rg, np, w, seq, mode, precision, warmup, steps, inputs, torch):
     rtol = w.rtol if precision == "fp64" else 1e-8
     s = rg.Solver(n, m=w.m, k=w.k, window=w.window, svd_interval=w.ell, mode=mode,
                   launch_policy=LAUNCH_POLICY[0],
-                  precision=precision, rtol=rtol)
+                  precision=precision, rtol=rtol, precond=w.precond)
     s.set_operator_csr(rp, col, np.zeros(len(col)))
     pin_val = torch.empty(len(col), dtype=torch.float64).pin_memory()
     pin_b = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -303,7 +325,7 @@ def ours(args):
         dist.barrier()
     else:
         g.build()
-    w = synth.WORKLOADS[args.workload]
+    w = workload_of(synth, args)
     seq = workload_seq(synth, w, replica_sequence(rank), max(w.steps, args.warmup + args.steps))
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB
 
@@ -375,6 +397,7 @@ def ours(args):
         "config": {"workload": w.name, "n": n, "nnz": nnz, "p": w.p, "N": w.N, "m": w.m, "k": w.k,
                    "window": w.window, "svd_interval": w.ell, "mode": args.mode,
                    "velocity": w.velocity, "forcing_modes": w.forcing_modes, "u0": w.u0,
+                   "precond": w.precond,
                    "precision": args.precision, "launch_policy": args.launch_policy,
                    "rtol": w.rtol if args.precision == "fp64" else 1e-8,
                    "l2": "flushed (256 MiB write) before every timed step",
@@ -549,14 +572,15 @@ def cpu_baseline(args, w, seq, main, np):
     import oracle as orc
     orc.build()
     a8, beta, forcing = seq
-    S = args.cpu_steps or min(w.steps, 30 if w.n < 200000 else 3)
+    # about 10-30 s of oracle work: high-order assembly costs (p+1)^6 per cell
+    S = args.cpu_steps or min(w.steps, 2 if w.p > 4 else 30 if w.n < 200000 else 3)
     u0 = np.zeros(w.n) if w.u0 == "zero" else orc.u0_field(w.p, w.N, a8)
     mode = {"plain": 0, "deflated": 1, "augmented": 2}[args.mode]
     rtol = w.rtol if args.precision == "fp64" else 1e-8
     r = orc.sequence(w.p, w.N, w.eps, w.dt, beta, S, u0, mode=mode, m=w.m, k=w.k,
                      window=w.window, ell=w.ell, rtol=rtol, keep_all=False,
                      velocity=int(w.velocity == "cellular"), forcing=forcing,
-                     forcing_C=w.forcing_C)
+                     forcing_C=w.forcing_C, precond=int(w.precond == "jacobi"))
     secs = r["step_seconds"]
     cb = {"value": round(S / float(secs.sum()), 4), "unit": "solves/s", "cores": 1, "kind": "oracle",
           "sample": f"first {S} time steps of the same sequence ({w.name}, {args.mode}), "
@@ -579,12 +603,12 @@ def reference(args):
     import oracle as orc
     import synth
     orc.build()
-    w = synth.WORKLOADS[args.workload]
+    w = workload_of(synth, args)
     a8, beta, forcing = workload_seq(synth, w, 0, max(w.steps, args.warmup + args.steps))
     # each bench step is one time step; the oracle is slow, so a step is a
     # bounded sample (the first warmup+steps steps of the sequence, capped)
     W, K = args.warmup, args.steps
-    cap = 40 if w.n < 200000 else 4
+    cap = 3 if w.p > 4 else 40 if w.n < 200000 else 4
     tot = min(W + K, cap)
     Wc = min(W, max(tot - 1, 0))
     Kc = tot - Wc
@@ -594,7 +618,7 @@ def reference(args):
     r = orc.sequence(w.p, w.N, w.eps, w.dt, beta, tot, u0, mode=mode, m=w.m, k=w.k,
                      window=w.window, ell=w.ell, rtol=rtol,
                      velocity=int(w.velocity == "cellular"), forcing=forcing,
-                     forcing_C=w.forcing_C)
+                     forcing_C=w.forcing_C, precond=int(w.precond == "jacobi"))
     secs = r["step_seconds"][Wc:]
     value = Kc / float(secs.sum())
     sample = (f"time steps {Wc + 1}..{tot} of the {w.name} sequence ({args.mode}), FP64 oracle, "

@@ -306,7 +306,9 @@ int rgm_residual_noalloc(int64_t n, const int64_t *rowptr, const int32_t *col, c
 
 /* ------------------------------------------------------------ FE workload
  * The time-step systems of Sec. 6.1 built on the device: Q_p Lagrange elements
- * (p = 1..4, Gauss-Lobatto nodes) on a uniform N x N grid of the unit square,
+ * (p = 1..RGM_FE_MAX_P, Gauss-Lobatto nodes; high p on a coarse grid is the
+ * spectral-element discretisation of the paper's Table 4, order 23 on 2 x 2
+ * elements) on a uniform N x N grid of the unit square,
  * (p+1)^2 Gauss points per cell, implicit Euler with the convection coefficient
  * lagged one step,
  *   A = M/dt + eps K + N(u_prev; beta),  b = M u_prev / dt + F(f = 1),
@@ -317,6 +319,7 @@ int rgm_residual_noalloc(int64_t n, const int64_t *rowptr, const int32_t *col, c
  * Dofs are numbered lexicographically (x fastest) on the (pN+1)^2 lattice.
  * This is the workload the solver is measured on, not part of the method.  */
 typedef struct rgm_fe_s *rgm_fe;
+#define RGM_FE_MAX_P 32
 
 int rgm_fe_create(rgm_fe *out, int p, int N, double eps, double dt, double beta_x,
                   double beta_y, void *cuda_stream);

@@ -213,7 +213,7 @@ static int assemble_impl(int p, int N, double cm, double ck, double cn, double b
                          const double *bxn, const double *byn, const double *u, int dirichlet,
                          const int64_t *rowptr, const int32_t *col, double *val)
 {
-    if (p < 1 || p > 8 || N < 1) return ORC_E_ARG;
+    if (p < 1 || p > 32 || N < 1) return ORC_E_ARG;
     tab1d t;
     make_tab(p, &t);
     const int nl = (p + 1) * (p + 1), q = t.q;
@@ -306,7 +306,7 @@ int orc_fe_assemble_field(int p, int N, double cm, double ck, double cn, const d
 
 int orc_fe_load(int p, int N, orc_scalar_fn f, void *ctx, double *F)
 {
-    if (p < 1 || p > 8 || N < 1) return ORC_E_ARG;
+    if (p < 1 || p > 32 || N < 1) return ORC_E_ARG;
     tab1d t;
     make_tab(p, &t);
     const int nl = (p + 1) * (p + 1), q = t.q;

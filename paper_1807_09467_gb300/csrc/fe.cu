@@ -3,11 +3,12 @@
 //
 // Discrete problem (Sec. 6.1, implicit Euler, convection coefficient lagged):
 //   (1/dt)(v, u^n - u^{n-1}) + eps (grad v, grad u^n) + (v, u^{n-1} beta.grad u^n) = (v, 1)
-// on Q_p elements, p = 1..4, with Gauss-Lobatto nodes and (p+1)^2 Gauss points
+// on Q_p elements, p = 1..32, with Gauss-Lobatto nodes and (p+1)^2 Gauss points
 // per cell.  Uniform grid => one set of reference tables: the 1D mass M1 and
 // stiffness K1, the load F1, and the reference convection tensor
 //   T[(i),(j),(l)] = sum_q w_q phi_i(q) phi_l(q) (beta . grad_ref phi_j)(q)
-// so that N_ij = h sum_l u_l T[i][j][l] on each cell.  Assembly gathers row by
+// so that N_ij = h sum_l u_l T[i][j][l] on each cell (p <= 4; T has (p+1)^6
+// entries, so higher orders take the quadrature path below).  Assembly gathers row by
 // row (one warp per row, one lane per stored entry, cells visited in a fixed
 // order), so it is deterministic and needs no atomics.
 //
@@ -91,6 +92,60 @@ void gauss_closed(int q, double *x, double *w)
     for (int i = 0; i < q; ++i) { x[i] = 0.5 * (t[i] + 1.0); w[i] = 0.5 * c[i]; }
 }
 
+// Legendre P_k(t) and P_k'(t), k = 0..kmax, by Bonnet's recurrence and
+// P_k' = P_{k-2}' + (2k - 1) P_{k-1}.
+void legendre_table(int kmax, double t, double *P, double *dP)
+{
+    P[0] = 1.0; dP[0] = 0.0;
+    if (kmax >= 1) { P[1] = t; dP[1] = 1.0; }
+    for (int k = 2; k <= kmax; ++k) {
+        P[k] = ((2.0 * k - 1.0) * t * P[k - 1] - (k - 1.0) * P[k - 2]) / k;
+        dP[k] = dP[k - 2] + (2.0 * k - 1.0) * P[k - 1];
+    }
+}
+
+// Gauss-Lobatto nodes on [0,1] for any p: the zeros of P_{p+1} - P_{p-1}
+// (which vanish exactly at the Lobatto points, ends included), by Newton from
+// the Chebyshev-Lobatto points.  p <= 4: closed forms.
+void gll_nodes(int p, double *xi)
+{
+    if (p <= 4) { gll_closed(p, xi); return; }
+    double P[40], dP[40];
+    xi[0] = 0.0;
+    xi[p] = 1.0;
+    for (int i = 1; i < p; ++i) {
+        double t = -std::cos(M_PI * i / p);
+        for (int it = 0; it < 60; ++it) {
+            legendre_table(p + 1, t, P, dP);
+            const double q = P[p + 1] - P[p - 1], dq = dP[p + 1] - dP[p - 1];
+            const double step = q / dq;
+            t -= step;
+            if (std::fabs(step) <= 1e-16) break;
+        }
+        xi[i] = 0.5 * (t + 1.0);
+    }
+}
+
+// Gauss-Legendre rule on [0,1] for any q: zeros of P_q by Newton, weights
+// 2 / ((1 - t^2) P_q'(t)^2) (halved for [0,1]).  q <= 5: closed forms.
+void gauss_rule(int q, double *x, double *w)
+{
+    if (q <= 5) { gauss_closed(q, x, w); return; }
+    double P[40], dP[40];
+    for (int i = 0; i < q; ++i) {
+        double t = -std::cos(M_PI * (i + 0.75) / (q + 0.5));
+        for (int it = 0; it < 60; ++it) {
+            legendre_table(q, t, P, dP);
+            const double step = P[q] / dP[q];
+            t -= step;
+            if (std::fabs(step) <= 1e-16) break;
+        }
+        legendre_table(q, t, P, dP);
+        x[i] = 0.5 * (t + 1.0);
+        w[i] = 1.0 / ((1.0 - t * t) * dP[q] * dP[q]);
+    }
+}
+
 // Lagrange basis on `nodes` and its derivative at x (product rule).
 void basis(int p, const double *nodes, double x, double *phi, double *dphi)
 {
@@ -129,38 +184,41 @@ struct FeDev {
     int p, N, nl;
     int64_t L, n;
     double h, inv_dt, eps;
-    const double *M1, *K1, *F1, *T;
+    const double *M1, *K1, *F1, *T;   // T only for p <= 4
     const double *PH, *DPH, *GW;   // phi_a, phi_a' at Gauss point g ([g][a]), Gauss weights
+    const double *XI;              // Gauss-Lobatto nodes of a cell on [0,1]
 };
 
 // Coordinate of lattice node I along one axis (GLL nodes inside each cell).
-__device__ __forceinline__ double node_coord(int64_t I, int p, int N, const double *xi)
+__device__ __forceinline__ double node_coord(const FeDev &f, int64_t I)
 {
-    const int64_t cell = I / p;
-    return cell == N ? 1.0 : ((double)cell + xi[I % p]) / (double)N;
+    const int64_t cell = I / f.p;
+    return cell == f.N ? 1.0 : ((double)cell + f.XI[I % f.p]) * f.h;
 }
 
 // Sec. 6.1's cellular velocity at the nodes.
-__global__ void fe_velocity_kernel(int p, int N, int64_t L, double x0, double x1, double x2,
-                                   double x3, double x4, double *bxn, double *byn, int64_t n)
+__global__ void fe_velocity_kernel(FeDev f, double *bxn, double *byn)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double xi[5] = {x0, x1, x2, x3, x4};
-    const double x = node_coord(i % L, p, N, xi), y = node_coord(i / L, p, N, xi);
+    if (i >= f.n) return;
+    const double x = node_coord(f, i % f.L), y = node_coord(f, i / f.L);
     bxn[i] = -sin(M_PI * x) * cos(M_PI * y);
     byn[i] = cos(M_PI * x) * sin(M_PI * y);
 }
 
-// Sec. 6.1's forcing at the nodes: (C/2) sum_j c_j exp(-j^2/20) sin(2 j pi x) sin(2 j pi y).
-__global__ void fe_forcing_kernel(int p, int N, int64_t L, double x0, double x1, double x2,
-                                  double x3, double x4, int nmodes, const double *c, double C,
-                                  double *fn, int64_t n)
+// A constant velocity as a nodal field (the quadrature path of p > 4).
+__global__ void fe_fill2_kernel(double *a, double va, double *b, double vb, int64_t n)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double xi[5] = {x0, x1, x2, x3, x4};
-    const double x = node_coord(i % L, p, N, xi), y = node_coord(i / L, p, N, xi);
+    if (i < n) { a[i] = va; b[i] = vb; }
+}
+
+// Sec. 6.1's forcing at the nodes: (C/2) sum_j c_j exp(-j^2/20) sin(2 j pi x) sin(2 j pi y).
+__global__ void fe_forcing_kernel(FeDev f, int nmodes, const double *c, double C, double *fn)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= f.n) return;
+    const double x = node_coord(f, i % f.L), y = node_coord(f, i / f.L);
     double s = 0.0;
     for (int j = 1; j <= nmodes; ++j)
         s += c[j - 1] * exp(-(double)(j * j) / 20.0) * sin(2.0 * j * M_PI * x) * sin(2.0 * j * M_PI * y);
@@ -274,16 +332,12 @@ __global__ void fe_rhs_kernel(FeDev f, const double *u, const double *fn, double
     b[row] = mu * f.inv_dt + F;
 }
 
-__global__ void fe_u0_kernel(int p, int N, int64_t L, double x0, double x1, double x2, double x3,
-                             double x4, const double *a8, double *u0, int64_t n)
+__global__ void fe_u0_kernel(FeDev f, const double *a8, double *u0)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if (on_bnd(i, L)) { u0[i] = 0.0; return; }
-    const double xi[5] = {x0, x1, x2, x3, x4};
-    const int64_t Ix = i % L, Iy = i / L;
-    const double h = 1.0 / N;
-    const double x = ((double)(Ix / p) + xi[Ix % p]) * h, y = ((double)(Iy / p) + xi[Iy % p]) * h;
+    if (i >= f.n) return;
+    if (on_bnd(i, f.L)) { u0[i] = 0.0; return; }
+    const double x = node_coord(f, i % f.L), y = node_coord(f, i / f.L);
     double s = 0.0;
     for (int j = 1; j <= 8; ++j) s += a8[j - 1] * sin(j * M_PI * x) * sin(j * M_PI * y);
     u0[i] = s;
@@ -302,7 +356,9 @@ FeDev dev_view(const rgm_fe_s *fe)
     f.p = fe->p; f.N = fe->N; f.nl = q1 * q1; f.L = fe->L; f.n = fe->n; f.h = fe->h;
     f.inv_dt = 1.0 / fe->dt; f.eps = fe->eps;
     f.M1 = fe->tabs; f.K1 = f.M1 + q1 * q1; f.F1 = f.K1 + q1 * q1; f.T = f.F1 + q1;
-    f.PH = f.T + (int64_t)f.nl * f.nl * f.nl; f.DPH = f.PH + q1 * q1; f.GW = f.DPH + q1 * q1;
+    f.PH = f.T + (fe->p <= 4 ? (int64_t)f.nl * f.nl * f.nl : 0);
+    f.DPH = f.PH + q1 * q1; f.GW = f.DPH + q1 * q1; f.XI = f.GW + q1;
+    if (fe->p > 4) f.T = nullptr;
     return f;
 }
 
@@ -313,7 +369,7 @@ extern "C" {
 int rgm_fe_create(rgm_fe *out, int p, int N, double eps, double dt, double beta_x, double beta_y,
                   void *cuda_stream)
 {
-    if (!out || p < 1 || p > 4 || N < 1 || !(dt > 0)) return RGM_E_ARG;
+    if (!out || p < 1 || p > RGM_FE_MAX_P || N < 1 || !(dt > 0)) return RGM_E_ARG;
     *out = nullptr;
     const int64_t L = (int64_t)p * N + 1;
     if (L * L > (int64_t)1 << 31) return RGM_E_ARG;
@@ -346,26 +402,32 @@ int rgm_fe_create(rgm_fe *out, int p, int N, double eps, double dt, double beta_
     fe->nnz = (int64_t)fe->h_col.size();
     // reference tables
     const int q1 = p + 1, nl = q1 * q1;
-    double xi[5], gx[5], gw[5], ph[5][5], dph[5][5];
-    gll_closed(p, xi);
-    gauss_closed(q1, gx, gw);
-    for (int g = 0; g < q1; ++g) basis(p, xi, gx[g], ph[g], dph[g]);
-    std::vector<double> tab(2 * q1 * q1 + q1 + (size_t)nl * nl * nl + 2 * q1 * q1 + q1, 0.0);
+    // p <= 4: the reference convection tensor T (nl^3); above, the quadrature path
+    const size_t nT = p <= 4 ? (size_t)nl * nl * nl : 0;
+    double xi[RGM_FE_MAX_P + 1], gx[RGM_FE_MAX_P + 1], gw[RGM_FE_MAX_P + 1];
+    std::vector<double> phv((size_t)q1 * q1), dphv((size_t)q1 * q1);
+    gll_nodes(p, xi);
+    gauss_rule(q1, gx, gw);
+    for (int g = 0; g < q1; ++g) basis(p, xi, gx[g], &phv[(size_t)g * q1], &dphv[(size_t)g * q1]);
+    auto ph = [&](int g, int a) { return phv[(size_t)g * q1 + a]; };
+    auto dph = [&](int g, int a) { return dphv[(size_t)g * q1 + a]; };
+    std::vector<double> tab(2 * q1 * q1 + q1 + nT + 2 * q1 * q1 + q1 + q1, 0.0);
     double *M1 = tab.data(), *K1 = M1 + q1 * q1, *F1 = K1 + q1 * q1, *T = F1 + q1;
-    double *PH = T + (size_t)nl * nl * nl, *DPH = PH + q1 * q1, *GW = DPH + q1 * q1;
+    double *PH = T + nT, *DPH = PH + q1 * q1, *GW = DPH + q1 * q1, *XI = GW + q1;
     for (int g = 0; g < q1; ++g) {
         GW[g] = gw[g];
-        for (int a = 0; a <= p; ++a) { PH[g * q1 + a] = ph[g][a]; DPH[g * q1 + a] = dph[g][a]; }
+        XI[g] = xi[g];
+        for (int a = 0; a <= p; ++a) { PH[g * q1 + a] = ph(g, a); DPH[g * q1 + a] = dph(g, a); }
     }
     for (int a = 0; a <= p; ++a) {
         for (int c = 0; c <= p; ++c)
             for (int g = 0; g < q1; ++g) {
-                M1[a * q1 + c] += gw[g] * ph[g][a] * ph[g][c];
-                K1[a * q1 + c] += gw[g] * dph[g][a] * dph[g][c];
+                M1[a * q1 + c] += gw[g] * ph(g, a) * ph(g, c);
+                K1[a * q1 + c] += gw[g] * dph(g, a) * dph(g, c);
             }
-        for (int g = 0; g < q1; ++g) F1[a] += gw[g] * ph[g][a];
+        for (int g = 0; g < q1; ++g) F1[a] += gw[g] * ph(g, a);
     }
-    for (int i = 0; i < nl; ++i)
+    for (int i = 0; i < nl && nT > 0; ++i)
         for (int j = 0; j < nl; ++j)
             for (int l = 0; l < nl; ++l) {
                 const int ia = i % q1, ib = i / q1, ja = j % q1, jb = j / q1, la = l % q1, lb = l / q1;
@@ -373,9 +435,9 @@ int rgm_fe_create(rgm_fe *out, int p, int N, double eps, double dt, double beta_
                 for (int gy = 0; gy < q1; ++gy)
                     for (int gxx = 0; gxx < q1; ++gxx) {
                         double w = gw[gxx] * gw[gy];
-                        double phi_i = ph[gxx][ia] * ph[gy][ib];
-                        double phi_l = ph[gxx][la] * ph[gy][lb];
-                        double bgrad = beta_x * dph[gxx][ja] * ph[gy][jb] + beta_y * ph[gxx][ja] * dph[gy][jb];
+                        double phi_i = ph(gxx, ia) * ph(gy, ib);
+                        double phi_l = ph(gxx, la) * ph(gy, lb);
+                        double bgrad = beta_x * dph(gxx, ja) * ph(gy, jb) + beta_y * ph(gxx, ja) * dph(gy, jb);
                         s += w * phi_i * phi_l * bgrad;
                     }
                 T[((int64_t)i * nl + j) * nl + l] = s;
@@ -392,6 +454,10 @@ int rgm_fe_create(rgm_fe *out, int p, int N, double eps, double dt, double beta_
     if (e != cudaSuccess) {
         rgm_fe_destroy(fe);
         return e == cudaErrorMemoryAllocation ? RGM_E_OOM : RGM_E_CUDA;
+    }
+    if (p > 4) {   // no T table: the constant velocity goes through the quadrature path
+        const int rc = rgm_fe_set_velocity(fe, RGM_FE_VELOCITY_CONSTANT);
+        if (rc) { rgm_fe_destroy(fe); return rc; }
     }
     *out = fe;
     return RGM_OK;
@@ -462,7 +528,7 @@ int rgm_fe_assemble(rgm_fe fe, const double *u_prev, double *val, double *b, int
 int rgm_fe_set_velocity(rgm_fe fe, int kind)
 {
     if (!fe || kind < RGM_FE_VELOCITY_CONSTANT || kind > RGM_FE_VELOCITY_CELLULAR) return RGM_E_ARG;
-    if (kind == RGM_FE_VELOCITY_CONSTANT) {
+    if (kind == RGM_FE_VELOCITY_CONSTANT && fe->p <= 4) {
         CKF(cudaStreamSynchronize(fe->st));
         void *p[] = {fe->bxn, fe->byn, fe->coef};
         for (void *q : p)
@@ -476,10 +542,10 @@ int rgm_fe_set_velocity(rgm_fe fe, int kind)
         CKF(cudaMalloc((void **)&fe->byn, sizeof(double) * fe->n));
         CKF(cudaMalloc((void **)&fe->coef, sizeof(double) * ncoef));
     }
-    double xi[5] = {0, 0, 0, 0, 0};
-    gll_closed(fe->p, xi);
-    fe_velocity_kernel<<<(unsigned)((fe->n + 255) / 256), 256, 0, fe->st>>>(
-        fe->p, fe->N, fe->L, xi[0], xi[1], xi[2], xi[3], xi[4], fe->bxn, fe->byn, fe->n);
+    if (kind == RGM_FE_VELOCITY_CONSTANT)
+        fe_fill2_kernel<<<(unsigned)((fe->n + 255) / 256), 256, 0, fe->st>>>(fe->bxn, fe->bx, fe->byn, fe->by, fe->n);
+    else
+        fe_velocity_kernel<<<(unsigned)((fe->n + 255) / 256), 256, 0, fe->st>>>(dev_view(fe), fe->bxn, fe->byn);
     CKF(cudaGetLastError());
     CKF(cudaStreamSynchronize(fe->st));
     return RGM_OK;
@@ -500,10 +566,8 @@ int rgm_fe_set_forcing(rgm_fe fe, int nmodes, const double *c, double C, int fla
     }
     CKF(cudaMemcpyAsync(fe->cmodes, c, sizeof(double) * nmodes,
                         (flags & RGM_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, fe->st));
-    double xi[5] = {0, 0, 0, 0, 0};
-    gll_closed(fe->p, xi);
-    fe_forcing_kernel<<<(unsigned)((fe->n + 255) / 256), 256, 0, fe->st>>>(
-        fe->p, fe->N, fe->L, xi[0], xi[1], xi[2], xi[3], xi[4], nmodes, fe->cmodes, C, fe->fn, fe->n);
+    fe_forcing_kernel<<<(unsigned)((fe->n + 255) / 256), 256, 0, fe->st>>>(dev_view(fe), nmodes, fe->cmodes,
+                                                                          C, fe->fn);
     CKF(cudaGetLastError());
     if (!(flags & RGM_DEVICE_PTRS)) CKF(cudaStreamSynchronize(fe->st));
     return RGM_OK;
@@ -512,15 +576,12 @@ int rgm_fe_set_forcing(rgm_fe fe, int nmodes, const double *c, double C, int fla
 int rgm_fe_initial_field(rgm_fe fe, const double *a8, double *u0, int flags)
 {
     if (!fe || !a8 || !u0) return RGM_E_ARG;
-    double xi[5] = {0, 0, 0, 0, 0};
-    gll_closed(fe->p, xi);
     double *a8d = nullptr;
     CKF(cudaMalloc((void **)&a8d, sizeof(double) * 8));
     cudaError_t e = cudaMemcpyAsync(a8d, a8, sizeof(double) * 8, cudaMemcpyHostToDevice, fe->st);
     double *dst = (flags & RGM_DEVICE_PTRS) ? u0 : fe->x;
     if (e == cudaSuccess) {
-        fe_u0_kernel<<<(unsigned)((fe->n + 255) / 256), 256, 0, fe->st>>>(fe->p, fe->N, fe->L, xi[0], xi[1], xi[2],
-                                                                     xi[3], xi[4], a8d, dst, fe->n);
+        fe_u0_kernel<<<(unsigned)((fe->n + 255) / 256), 256, 0, fe->st>>>(dev_view(fe), a8d, dst);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && !(flags & RGM_DEVICE_PTRS))

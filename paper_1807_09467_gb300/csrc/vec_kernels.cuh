@@ -18,7 +18,9 @@
 #include "common.cuh"
 
 #define RGM_TILE RGM_THREADS
+#ifndef RGM_RGROUP
 #define RGM_RGROUP 32            // blocks per group of the two-level dot reduction
+#endif
 
 enum Src { SRC_SPMV = 0, SRC_RES = 1, SRC_COPY = 2, SRC_AXPY = 3, SRC_NONE = 4 };
 enum Gate {
@@ -718,7 +720,10 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op)
 #pragma unroll
     for (int q = 0; q < QMAX; ++q) {
         const int c = warp + q * NW;
-        acc[q] = (c < nd && lane < gn) ? __ldcg(op.partials + (int64_t)c * op.nblocks + gb0 + lane) : 0.0;
+        double v = 0.0;
+        if (c < nd)
+            for (int b = lane; b < gn; b += 32) v += __ldcg(op.partials + (int64_t)c * op.nblocks + gb0 + b);
+        acc[q] = v;
     }
     if (single) {
         warp_sums_store<QMAX>(acc, nd, [&](int c, double t) { dsum[c] = t; });

@@ -63,6 +63,7 @@ class Workload:
     forcing_modes: int = 0       # > 0: Sec. 6.1's random forcing with this many modes (else f = 1)
     forcing_C: float = 0.1
     u0: str = "sines"            # or "zero"
+    precond: str = "none"        # or "jacobi" (left Jacobi in place of the paper's SSOR)
 
     @property
     def n(self) -> int:
@@ -89,7 +90,15 @@ PAPER_Q1_64 = {nu: Workload(f"paper_q1_64x64_nu{nu:g}", 1, 64, nu, 0.5, 1000, 30
                             u0="zero")
                for nu in (1e-1, 1e-2, 1e-3)}
 
-WORKLOADS = {w.name: w for w in (Q1_32, Q2_128, Q4_256, *PAPER_Q1_64.values())}
+# Table 4's spectral elements: order 23 on a 2 x 2 grid (2,209 dofs, about 1.1 M
+# nonzeros), nu = 1e-2, the same fields; the paper's runs recycle 20 modes with
+# the SVD every 20..80 steps over as many solutions, GMRES(30).  High-order
+# operators need a preconditioner: left Jacobi here (the paper: SSOR).
+PAPER_SEM23 = Workload("paper_sem23_2x2_nu0.01", 23, 2, 1e-2, 0.5, 1000, 30, 20, 20, 1e-8,
+                       fixed_beta=(0.0, 0.0), velocity="cellular", forcing_modes=16, u0="zero",
+                       ell=20, precond="jacobi")
+
+WORKLOADS = {w.name: w for w in (Q1_32, Q2_128, Q4_256, *PAPER_Q1_64.values(), PAPER_SEM23)}
 
 
 def sequence_draws(w: Workload, seq_index: int = 0):

@@ -178,3 +178,35 @@ def test_paper_sequence_first_steps_by_dense_solves(orc):
         u = np.linalg.solve(A, rhs)
         np.testing.assert_allclose(out["x_all"][:, step], u, rtol=0, atol=1e-11 * np.max(np.abs(u)))
     assert np.max(np.abs(u)) > 0
+
+
+@pytest.mark.parametrize("p", [8, 23])
+def test_high_order_rules_against_numpy(orc, p):
+    """Gauss-Lobatto nodes = 0, 1 and the zeros of P_p' (numpy's Legendre
+    series routines); the (p+1)-point Gauss rule = numpy's leggauss."""
+    leg = np.polynomial.legendre
+    roots = np.sort(leg.legroots(leg.legder([0] * p + [1])))
+    np.testing.assert_allclose(orc.gll_nodes(p), np.concatenate([[0.0], (roots + 1) / 2, [1.0]]),
+                               atol=1e-14)
+    x, w = orc.gauss_rule(p + 1)
+    xe, we = leg.leggauss(p + 1)
+    np.testing.assert_allclose(x, (xe + 1) / 2, atol=1e-14)
+    np.testing.assert_allclose(w, we / 2, atol=1e-14)
+
+
+def test_spectral_element_forms_exact_on_polynomials(orc):
+    """Order 23 on one element: the mass and stiffness integrals of
+    polynomial fields in the space come out exact."""
+    p, N = 23, 1
+    x, y = orc.node_coords(p, N)
+    pat = orc.pattern(p, N, False)
+    n = len(x)
+    M = _dense(*orc.assemble(p, N, 1, 0, 0, dirichlet=False, pat=pat), n)
+    K = _dense(*orc.assemble(p, N, 0, 1, 0, dirichlet=False, pat=pat), n)
+    one = np.ones(n)
+    assert abs(one @ M @ one - 1) < 1e-12
+    assert abs(x @ M @ y - 0.25) < 1e-12
+    assert abs((x ** p) @ M @ y - 1 / (2 * (p + 1))) < 1e-12
+    assert np.abs(K @ one).max() < 1e-9 * np.abs(K).max()
+    assert abs((x ** p) @ K @ x - 1.0) < 1e-10
+    np.testing.assert_allclose(M, M.T, atol=1e-16)
