@@ -105,6 +105,8 @@ struct FinScratch {
     double rd[RGM_KMAX];                      // reciprocals of the U pivots
     int perm[RGM_KMAX];                       // composite row permutation of the LU
     double vtw[(RGM_MMAX + 1) * RGM_KMAX];    // V^T W rows 0..nb-1 (leading dim RGM_MMAX+1)
+    double g_j, wn0, tol_in;                  // scalars of the Givens step, staged
+    int iters, maxit, m;
     int flag;
 };
 #define RGM_VTW_LD (RGM_MMAX + 1)
@@ -230,6 +232,21 @@ __device__ inline void close_column(Small *s, FinScratch &f, int col)
 // block together with the loads of the partial sums (one round trip for both).
 // Counts come from the pass itself: nb = op.ndV for the first and second CGS
 // passes (DYN_NDV_NB), op.nV for the third (DYN_NV_NB).
+// The scalars the serial part of the Givens step reads, one load per thread
+// (issued together, so the serial part does no dependent global load).
+__device__ __forceinline__ void stage_givens_scalars(const Small *s, int j, FinScratch &f)
+{
+    switch (threadIdx.x) {
+    case 0: f.g_j = s->g[j]; break;
+    case 1: f.wn0 = s->wn0; break;
+    case 2: f.tol_in = s->tol_in; break;
+    case 3: f.iters = s->iters; break;
+    case 4: f.maxit = s->maxit; break;
+    case 5: f.m = s->m; break;
+    default: break;
+    }
+}
+
 template <typename T>
 __device__ void fin_stage(const VecOp<T> &op, FinScratch &f)
 {
@@ -259,6 +276,7 @@ __device__ void fin_stage(const VecOp<T> &op, FinScratch &f)
         break;
     case FIN_ARN2H: {
         const int nb = op.ndV, k = op.ndW;
+        stage_givens_scalars(s, nb - 1, f);
         for (int i = tid; i < nb; i += blockDim.x) {
             f.sc[i] = s->colscale[i];
             f.col[i] = s->hsum[i];
@@ -272,6 +290,7 @@ __device__ void fin_stage(const VecOp<T> &op, FinScratch &f)
         break;
     }
     case FIN_ARN3:
+        stage_givens_scalars(s, op.nV - 1, f);
         for (int i = tid; i < op.nV; i += blockDim.x) {
             f.col[i] = s->hsum[i];
             f.cs[i] = s->cs[i];
@@ -402,20 +421,20 @@ __device__ void finalize_block(const VecOp<T> &op, const double *d, FinScratch &
                 f.col[j + 1] = 0.0;
                 s->cs[j] = c;
                 s->sn[j] = sn;
-                const double g0 = s->g[j], g1 = -sn * g0;
+                const double g0 = f.g_j, g1 = -sn * g0;
                 s->g[j + 1] = g1;
                 s->g[j] = c * g0;
-                const bool brk = hn <= 1e-14 * s->wn0;
+                const bool brk = hn <= 1e-14 * f.wn0;
                 const double sc = brk ? 0.0 : inv_hn;
                 sc_h = sc;
                 s->J = j + 1;
-                const int it = s->iters + 1;
+                const int it = f.iters + 1;
                 s->iters = it;
                 s->colscale[nb] = sc;          // happy breakdown: v_{j+1} := 0
                 int done = 0;
                 if (brk) { s->breakdown = 1; done = 1; }
                 s->nb = nb + 1;
-                if (fabs(g1) <= s->tol_in || it >= s->maxit || j + 1 >= s->m) done = 1;
+                if (fabs(g1) <= f.tol_in || it >= f.maxit || j + 1 >= f.m) done = 1;
                 if (done) s->done = 1;
             }
         }
@@ -447,20 +466,20 @@ __device__ void finalize_block(const VecOp<T> &op, const double *d, FinScratch &
                 f.col[j + 1] = 0.0;
                 s->cs[j] = c;
                 s->sn[j] = sn;
-                const double g0 = s->g[j], g1 = -sn * g0;
+                const double g0 = f.g_j, g1 = -sn * g0;
                 s->g[j + 1] = g1;
                 s->g[j] = c * g0;
-                const bool brk = hn <= 1e-14 * s->wn0;
+                const bool brk = hn <= 1e-14 * f.wn0;
                 const double sc = brk ? 0.0 : inv_hn;
                 sc_sh = sc;
                 s->J = j + 1;
-                const int it = s->iters + 1;
+                const int it = f.iters + 1;
                 s->iters = it;
                 s->colscale[nb] = sc;          // happy breakdown: v_{j+1} := 0
                 int done = 0;
                 if (brk) { s->breakdown = 1; done = 1; }
                 s->nb = nb + 1;
-                if (fabs(g1) <= s->tol_in || it >= s->maxit || j + 1 >= s->m) done = 1;
+                if (fabs(g1) <= f.tol_in || it >= f.maxit || j + 1 >= f.m) done = 1;
                 if (done) s->done = 1;
             }
         }
@@ -716,7 +735,12 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op)
     const int gn = min(RGM_RGROUP, op.nblocks - gb0);
     if (!last_of(op.gcount + g, (unsigned)gn)) return PASS_ARRIVED;
     const bool single = (op.ngroups == 1);
-    if (single) fin_stage(op, fin);
+    // the partials' loads go out before the staging loads (whose shared-memory
+    // stores wait for their data), so the two round trips overlap; the widest
+    // variant keeps the other order (its sums would stay live across the
+    // staging and spill)
+    constexpr bool early = QMAX <= 8;
+    if (!early && single) fin_stage(op, fin);
 #pragma unroll
     for (int q = 0; q < QMAX; ++q) {
         const int c = warp + q * NW;
@@ -725,6 +749,7 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op)
             for (int b = lane; b < gn; b += 32) v += __ldcg(op.partials + (int64_t)c * op.nblocks + gb0 + b);
         acc[q] = v;
     }
+    if (early && single) fin_stage(op, fin);
     if (single) {
         warp_sums_store<QMAX>(acc, nd, [&](int c, double t) { dsum[c] = t; });
     } else {
@@ -735,7 +760,7 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op)
     if (threadIdx.x == 0) op.gcount[g] = 0u;
     if (!single) {
         if (!last_of(op.counter, (unsigned)op.ngroups)) return PASS_ARRIVED;
-        fin_stage(op, fin);
+        if (!early) fin_stage(op, fin);
 #pragma unroll
         for (int q = 0; q < QMAX; ++q) {
             const int c = warp + q * NW;
@@ -744,6 +769,7 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op)
                 for (int gg = lane; gg < op.ngroups; gg += 32) v += __ldcg(op.gpart + (int64_t)c * op.ngroups + gg);
             acc[q] = v;
         }
+        if (early) fin_stage(op, fin);
         warp_sums_store<QMAX>(acc, nd, [&](int c, double t) { dsum[c] = t; });
     }
     __syncthreads();
