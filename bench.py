@@ -41,9 +41,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="q2_128x128_eps0.01_dt0.005",
-                    help="a single-sequence workload, batch64 (64 uneven sequences solved together) "
-                         "or serve (a Poisson stream of sequences, continuous batching)")
-    ap.add_argument("--mode", default="deflated", choices=["plain", "deflated", "augmented"])
+                    help="a single-sequence workload, batch64 (64 uneven sequences solved together), "
+                         "serve (a Poisson stream of sequences, continuous batching) or table2 "
+                         "(extrapolated vs projection initial guesses on the paper's nu = 0.1 benchmark)")
+    ap.add_argument("--mode", default="deflated", choices=["plain", "deflated", "augmented", "guess"])
     ap.add_argument("--k", type=int, default=None, help="override the workload's recycle dimension")
     ap.add_argument("--window", type=int, default=None, help="override the workload's snapshot window")
     ap.add_argument("--svd-interval", type=int, default=None, help="override the workload's SVD interval")
@@ -207,7 +208,7 @@ def workload_seq(synth, w, index, steps):
 
 # ------------------------------------------------------------------ our arm
 def run_sequence(rg, torch, w, seq, mode, precision, warmup, steps, profile=False, keep=None,
-                 flush=None, stream=None):
+                 flush=None, stream=None, guess=0):
     """Runs warmup + steps time steps on the device; returns timing and stats."""
     import numpy as np
     a8, beta, forcing = seq
@@ -217,7 +218,7 @@ def run_sequence(rg, torch, w, seq, mode, precision, warmup, steps, profile=Fals
     rtol = w.rtol if precision == "fp64" else 1e-8
     solver = rg.Solver(fe.n, m=w.m, k=w.k, window=w.window, svd_interval=w.ell, mode=mode,
                        precision=precision, rtol=rtol, stream=stream, launch_policy=LAUNCH_POLICY[0],
-                       precond=w.precond)
+                       precond=w.precond, guess=guess)
     u0 = workload_u0(np, fe, w, a8)
     u = torch.tensor(u0, dtype=torch.float64, device=dev)
     solver.set_operator_csr(rp, col, torch.zeros(len(col), dtype=torch.float64).numpy())
@@ -568,6 +569,40 @@ def run_serve(args):
     print(json.dumps(out))
 
 
+def run_table2(args):
+    """Table 2's comparison on the device (Sec. 6.1 benchmark, nu = 0.1, no
+    SSOR): for s = 2, 3, 4 the extrapolated guess from s solutions (Eq.
+    ext2-ext4, GMRES(30) on A) against the projection guess with s recycled
+    modes (Sec. 4.2, RGM_GUESS, GMRES(30) on A); iterations over the timed
+    steps, and deflation with the same s for reference."""
+    import dataclasses
+    import torch
+
+    import __graft_entry__ as g
+    import paper_1807_09467_gb300 as rg
+    import synth
+    g.build()
+    w0 = synth.PAPER_Q1_64[0.1]
+    W, K = args.warmup, args.steps
+    seq = workload_seq(synth, w0, 0, max(w0.steps, W + K))
+    rows = []
+    for s_ in (2, 3, 4):
+        row = {"s": s_}
+        for name, mode, guess, k in (("ext", "plain", s_ - 1, 0), ("proj", "guess", 0, s_),
+                                     ("def", "deflated", 0, s_)):
+            w = dataclasses.replace(w0, k=k)
+            r = run_sequence(rg, torch, w, seq, mode, "fp64", W, K, guess=guess)
+            row[name] = {"iterations": iters_stats(r["iters"][W:]),
+                         "solves_per_s": round(K / (sum(r["seg_ms"]) / 1e3), 3)}
+        rows.append(row)
+    out = {"metric": METRIC, "value": rows[-1]["proj"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+           "steps": K, "warmup": W, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"table2: {w0.name}, GMRES(30), window 16, steps {W + 1}..{W + K}"},
+           "table2": rows}
+    print(json.dumps(out))
+
+
 def cpu_baseline(args, w, seq, main, np):
     import oracle as orc
     orc.build()
@@ -585,6 +620,31 @@ def cpu_baseline(args, w, seq, main, np):
     cb = {"value": round(S / float(secs.sum()), 4), "unit": "solves/s", "cores": 1, "kind": "oracle",
           "sample": f"first {S} time steps of the same sequence ({w.name}, {args.mode}), "
                     f"FE assembly + solve + window SVD per step, single thread"}
+    # the same oracle on every host core: independent sequences (their own
+    # seeded draws), one per thread; the C oracle holds no global state and
+    # its ctypes calls release the interpreter lock
+    import os
+    import synth
+    from concurrent.futures import ThreadPoolExecutor
+    ncores = os.cpu_count() or 1
+
+    def one(idx):
+        a8_i, beta_i, forcing_i = workload_seq(synth, w, 1000 + idx, S)
+        u0_i = np.zeros(w.n) if w.u0 == "zero" else orc.u0_field(w.p, w.N, a8_i)
+        ri = orc.sequence(w.p, w.N, w.eps, w.dt, beta_i, S, u0_i, mode=mode, m=w.m, k=w.k,
+                          window=w.window, ell=w.ell, rtol=rtol, keep_all=False,
+                          velocity=int(w.velocity == "cellular"), forcing=forcing_i,
+                          forcing_C=w.forcing_C, precond=int(w.precond == "jacobi"))
+        return int(ri["iters"].sum())
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=ncores) as ex:
+        list(ex.map(one, range(ncores)))
+    wall = time.perf_counter() - t0
+    cb["all_cores"] = {"value": round(ncores * S / wall, 4), "unit": "solves/s", "cores": ncores,
+                       "kind": "oracle",
+                       "sample": f"{ncores} independent sequences of {w.name} ({args.mode}), {S} time "
+                                 f"steps each, one thread per sequence"}
     # parity of the last sampled step's iteration count against the device run
     par = {"oracle_iterations": iters_stats(r["iters"]),
            "gpu_iterations_same_steps": iters_stats(main["iters"][:S]),
@@ -645,5 +705,7 @@ if __name__ == "__main__":
         run_batch(a)
     elif a.workload == "serve":
         run_serve(a)
+    elif a.workload == "table2":
+        run_table2(a)
     else:
         ours(a)

@@ -55,7 +55,9 @@ typedef enum {
     RGM_DEFLATED = 1,    /* Table 1 "deflated oblique": operator P A, start P r,
                             P = I - A U E^{-1} U^T (Eq. left_deflation), plus the coarse
                             correction x += U E^{-1} U^T (b - A x) after each cycle          */
-    RGM_AUGMENTED = 2    /* Sec. 3.1: search space K_j(A, r) + span U, constraint space A S  */
+    RGM_AUGMENTED = 2,   /* Sec. 3.1: search space K_j(A, r) + span U, constraint space A S  */
+    RGM_GUESS = 3        /* Sec. 4.2 alone: the projection initial guess
+                            x0 = x_in + U E^{-1} U^T (b - A x_in), then GMRES(m) on A       */
 } rgm_mode;
 
 typedef enum {

@@ -21,7 +21,7 @@ _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 _lib = None
 _lock = threading.Lock()
 
-PLAIN, DEFLATED, AUGMENTED = 0, 1, 2
+PLAIN, DEFLATED, AUGMENTED, GUESS = 0, 1, 2, 3
 PROJ_OBLIQUE, PROJ_ORTHOGONAL, PROJ_LS = 0, 1, 2
 PRECOND_NONE, PRECOND_JACOBI = 0, 1
 OK, W_NOT_CONVERGED, W_SINGULAR_COARSE = 0, 1, 2

@@ -19,6 +19,8 @@
  *    S = K_j(A, r0) + span U and constraint space A S.
  *  - Left Jacobi preconditioning (not the paper's SSOR, which is sequential):
  *    GMRES on D^{-1} A x = D^{-1} b with the true-residual stopping test.
+ *  - Sec. 4.2 alone (ORC_GUESS): the projection initial guess, then GMRES(m)
+ *    on A itself (the "proj" column of Table 2).
  *  - Sec. 3.3, Table 1 (and Eq. P_A_variant): the other two projectors of the
  *    deflated family, orthogonal P = I - U (U^T U)^{-1} U^T and least squares
  *    P = I - A U (U^T A^T A U)^{-1} U^T A^T; Sec. 4.4, Eq. augmented_iterate:
@@ -463,7 +465,8 @@ static int core_solve(core_t *c, const double *b, double *x, int *iters_out, int
 int orc_gmres(const orc_csr *A, const double *b, double *x, const double *U, int k,
               const orc_opts *o, orc_stats *st, double *hist, int hist_len)
 {
-    if (!A || !b || !x || !o || o->m < 1 || k < 0) return ORC_E_ARG;
+    if (!A || !b || !x || !o || o->m < 1 || k < 0 || o->mode < ORC_PLAIN || o->mode > ORC_GUESS)
+        return ORC_E_ARG;
     const int64_t n = A->n;
     orc_stats s0 = {0, 0, 0, ORC_OK, 0.0};
     double bnorm = nrm2(n, b);
@@ -538,6 +541,7 @@ int orc_gmres_ir(const orc_csr *A, const double *b, double *x, const double *U, 
 {
     if (!A || !b || !x || !o || o->m < 1 || k < 0) return ORC_E_ARG;
     if (o->precond != ORC_PRECOND_NONE) return ORC_E_ARG;   /* Jacobi: binary64 solves only */
+    if (o->mode < ORC_PLAIN || o->mode > ORC_GUESS) return ORC_E_ARG;
     const int64_t n = A->n, nnz = A->rowptr[n];
     double bnorm = nrm2(n, b);
     if (bnorm == 0.0) {

@@ -96,6 +96,7 @@ typedef struct {
 #define ORC_PLAIN      0   /* GMRES(m)                                            */
 #define ORC_DEFLATED   1   /* deflated oblique, Table 1 row 5, + coarse correction */
 #define ORC_AUGMENTED  2   /* Sec. 3.1: S = K_m(A, r) + span U, C = A S            */
+#define ORC_GUESS      3   /* Sec. 4.2: projection initial guess, then GMRES(m)   */
 
 /* Projector of the ORC_DEFLATED family (Table 1): the Krylov operator is P A. */
 #define ORC_PROJ_OBLIQUE    0   /* P = I - W E^{-1} U^T, W = A U, E = U^T W            */
@@ -103,7 +104,7 @@ typedef struct {
 #define ORC_PROJ_LS         2   /* P = I - W (W^T W)^{-1} W^T                          */
 
 typedef struct {
-    int mode;          /* ORC_PLAIN / ORC_DEFLATED / ORC_AUGMENTED                  */
+    int mode;          /* ORC_PLAIN / ORC_DEFLATED / ORC_AUGMENTED / ORC_GUESS      */
     int m;             /* restart length                                           */
     double rtol;       /* stop when ||b - A x|| <= rtol ||b||                       */
     int maxit;         /* cap on Arnoldi steps (operator applications)             */

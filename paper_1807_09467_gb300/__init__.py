@@ -16,11 +16,11 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (AUGMENTED, DEFLATED, FP32_IR, FP64, PLAIN, RGM_DEVICE_PTRS,
+from ._lib import (AUGMENTED, DEFLATED, FP32_IR, FP64, GUESS, PLAIN, RGM_DEVICE_PTRS,
                    RGM_W_NOT_CONVERGED, RGM_W_SINGULAR_COARSE, RgmConfig, RgmError,
                    RgmStats, check)
 
-MODES = {"plain": PLAIN, "deflated": DEFLATED, "augmented": AUGMENTED}
+MODES = {"plain": PLAIN, "deflated": DEFLATED, "augmented": AUGMENTED, "guess": GUESS}
 PRECISIONS = {"fp64": FP64, "fp32_ir": FP32_IR}
 LAUNCH_POLICIES = {"auto": 0, "per_pass": 1}
 PROJECTORS = {"oblique": 0, "orthogonal": 1, "ls": 2}

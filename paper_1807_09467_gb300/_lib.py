@@ -23,7 +23,7 @@ RGM_E_TIMEOUT = -5
 RGM_DEVICE_PTRS = 1
 RGM_NOALLOC_MAX_ROWS = 4096 * 2048
 
-PLAIN, DEFLATED, AUGMENTED = 0, 1, 2
+PLAIN, DEFLATED, AUGMENTED, GUESS = 0, 1, 2, 3
 FP64, FP32_IR = 0, 1
 
 

@@ -724,7 +724,8 @@ static int solve_device(rgm_solver s, rgm_stats *out)
     } else if (k > 0 && s->hs->singular) {
         status = RGM_W_SINGULAR_COARSE; k = 0;
     }
-    const int mode = k > 0 ? c.mode : RGM_PLAIN;
+    // RGM_GUESS: the projection guess below, then plain cycles
+    const int mode = (k > 0 && c.mode != RGM_GUESS) ? c.mode : RGM_PLAIN;
     if (c.guess > 0 && s->win_count >= c.guess + 1) {
         // extrapolation from the most recent snapshots replaces the x passed in
         const int newest = (s->win_head - 1 + c.window) % c.window;
@@ -908,7 +909,7 @@ int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
     *out = nullptr;
     const rgm_config &c = *cfg;
     if (c.n < 1 || c.m < 1 || c.m > RGM_MMAX || c.k < 0 || c.k > RGM_KMAX || c.window < 1 ||
-        c.window > RGM_WMAX || c.svd_interval < 1 || c.mode < 0 || c.mode > 2 || c.precision < 0 ||
+        c.window > RGM_WMAX || c.svd_interval < 1 || c.mode < RGM_PLAIN || c.mode > RGM_GUESS || c.precision < 0 ||
         c.precision > 1 || c.maxit < 0 || !(c.rtol >= 0) || c.inner_cycles < 1 ||
         c.max_refinements < 1 || !(c.inner_rtol > 0) || !(c.rel_drop >= 0) ||
         c.launch_policy < RGM_LAUNCH_AUTO || c.launch_policy > RGM_LAUNCH_PER_PASS ||

@@ -18,9 +18,7 @@
 #include "common.cuh"
 
 #define RGM_TILE RGM_THREADS
-#ifndef RGM_RGROUP
 #define RGM_RGROUP 32            // blocks per group of the two-level dot reduction
-#endif
 
 enum Src { SRC_SPMV = 0, SRC_RES = 1, SRC_COPY = 2, SRC_AXPY = 3, SRC_NONE = 4 };
 enum Gate {
@@ -741,13 +739,13 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op)
     // staging and spill)
     constexpr bool early = QMAX <= 8;
     if (!early && single) fin_stage(op, fin);
+    // one predicated load per column (gn <= 32): all QMAX loads are in
+    // flight together (a loop per column would serialise their round trips)
+    static_assert(RGM_RGROUP <= 32, "one lane per block of a group");
 #pragma unroll
     for (int q = 0; q < QMAX; ++q) {
         const int c = warp + q * NW;
-        double v = 0.0;
-        if (c < nd)
-            for (int b = lane; b < gn; b += 32) v += __ldcg(op.partials + (int64_t)c * op.nblocks + gb0 + b);
-        acc[q] = v;
+        acc[q] = (c < nd && lane < gn) ? __ldcg(op.partials + (int64_t)c * op.nblocks + gb0 + lane) : 0.0;
     }
     if (early && single) fin_stage(op, fin);
     if (single) {
@@ -761,13 +759,20 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op)
     if (!single) {
         if (!last_of(op.counter, (unsigned)op.ngroups)) return PASS_ARRIVED;
         if (!early) fin_stage(op, fin);
+        // as above: one predicated load per column for the first 32 groups
 #pragma unroll
         for (int q = 0; q < QMAX; ++q) {
             const int c = warp + q * NW;
-            double v = 0.0;
-            if (c < nd)
-                for (int gg = lane; gg < op.ngroups; gg += 32) v += __ldcg(op.gpart + (int64_t)c * op.ngroups + gg);
-            acc[q] = v;
+            acc[q] = (c < nd && lane < op.ngroups) ? __ldcg(op.gpart + (int64_t)c * op.ngroups + lane) : 0.0;
+        }
+        if (op.ngroups > 32) {
+#pragma unroll
+            for (int q = 0; q < QMAX; ++q) {
+                const int c = warp + q * NW;
+                if (c < nd)
+                    for (int gg = lane + 32; gg < op.ngroups; gg += 32)
+                        acc[q] += __ldcg(op.gpart + (int64_t)c * op.ngroups + gg);
+            }
         }
         if (early) fin_stage(op, fin);
         warp_sums_store<QMAX>(acc, nd, [&](int c, double t) { dsum[c] = t; });

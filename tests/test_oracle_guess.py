@@ -46,3 +46,44 @@ def test_sequence_with_extrapolation(orc, guess):
     assert r["iters"][guess + 1:].sum() < base["iters"][guess + 1:].sum()
     d = np.linalg.norm(r["x_all"] - base["x_all"], axis=0) / np.linalg.norm(base["x_all"], axis=0)
     assert d.max() < 1e-8
+
+
+def test_table2_qualitative(orc):
+    """Table 2's comparison (Sec. 6.1 benchmark, nu = 0.1, without SSOR): the
+    projection initial guess (Sec. 4.2, GMRES on A afterwards) needs fewer
+    iterations than extrapolation from the same number s of solutions, and
+    extrapolation gets worse as s grows.  Means over steps 21..60."""
+    w = synth.PAPER_Q1_64[0.1]
+    steps = 60
+    forcing = synth.forcing_draws(w, steps)
+    n = orc.ndofs(w.p, w.N)
+    ext, proj = {}, {}
+    for s in (2, 3, 4):
+        kw = dict(m=30, window=16, rtol=1e-8, velocity=1, forcing=forcing)
+        e = orc.sequence(w.p, w.N, w.eps, w.dt, (0.0, 0.0), steps, np.zeros(n), mode=orc.PLAIN,
+                         k=0, guess=s - 1, **kw)
+        p = orc.sequence(w.p, w.N, w.eps, w.dt, (0.0, 0.0), steps, np.zeros(n), mode=orc.GUESS,
+                         k=s, **kw)
+        assert np.all(e["status"] == 0) and np.all(p["status"] == 0)
+        ext[s], proj[s] = e["iters"][20:].mean(), p["iters"][20:].mean()
+    assert all(proj[s] <= ext[s] for s in (2, 3, 4))
+    assert proj[3] < ext[3] and proj[4] < ext[4]
+    assert ext[2] < ext[3] < ext[4]
+    assert proj[4] - proj[2] < ext[4] - ext[2]
+
+
+def test_guess_mode_is_plain_gmres_from_the_projection_guess(orc):
+    """ORC_GUESS = ORC_PLAIN started from x0 = x_in + U E^{-1} U^T (b - A x_in)."""
+    n, k = 400, 3
+    rp, col, val = synth.random_csr(n, 8, 5, diag=6.0, min_per_row=3)
+    A = orc.Csr(rp, col, val)
+    b = synth.random_vector(n, 6)
+    U = np.linalg.qr(synth.random_matrix(n, k, 7))[0]
+    x_in = synth.random_vector(n, 8)
+    D = A.dense()
+    x0 = x_in + U @ np.linalg.solve(U.T @ D @ U, U.T @ (b - D @ x_in))
+    for maxit in (1, 4, 9):
+        xg, sg, _ = orc.gmres(A, b, x_in=x_in, U=U, mode=orc.GUESS, m=5, rtol=0.0, maxit=maxit)
+        xp, sp, _ = orc.gmres(A, b, x_in=x0, mode=orc.PLAIN, m=5, rtol=0.0, maxit=maxit)
+        assert sg["iters"] == sp["iters"] == maxit and sg["k_used"] == k
+        np.testing.assert_allclose(xg, xp, rtol=0, atol=1e-12 * np.abs(xp).max())
