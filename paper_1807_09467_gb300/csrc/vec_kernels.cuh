@@ -257,13 +257,42 @@ __device__ void fin_stage(const VecOp<T> &op, FinScratch &f)
         break;
     case FIN_ARN1:
     case FIN_AUG1: {
-        const int nb = op.ndV, k = op.ndU;
-        if (k) stage_lu(s, k, f, op.lu_sel);
-        for (int i = tid; i < nb; i += blockDim.x) f.sc[i] = s->colscale[i];
-        for (int t = tid; t < nb * k; t += blockDim.x) {
-            const int i = t % nb, l = t / nb;
-            f.vtw[i + l * RGM_VTW_LD] = s->VtW[i + l * RGM_HLD];
+        // every load in flight before the first shared-memory store (a store
+        // waits for its data, and a later load would wait behind it)
+        const int nb = op.ndV, k = op.ndU, sel = op.lu_sel;
+        const double *LU = sel ? s->LUP : s->LU, *rd = sel ? s->LUPrd : s->LUrd;
+        const int *piv = sel ? s->pivP : s->piv, *pm = sel ? s->LUPperm : s->LUperm;
+        static_assert(RGM_HLD <= RGM_THREADS, "one thread per basis column");
+        double lu[2], vt[2], rdv = 0.0, scv = 0.0;
+        int pvv = 0, pmv = 0;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int t = tid + u * RGM_THREADS;
+            lu[u] = (t < k * k) ? LU[t % k + (t / k) * RGM_KMAX] : 0.0;
         }
+        if (tid < k) { pvv = piv[tid]; rdv = rd[tid]; pmv = pm[tid]; }
+        if (tid < nb) scv = s->colscale[tid];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int t = tid + u * RGM_THREADS;
+            vt[u] = (t < nb * k) ? s->VtW[t % nb + (t / nb) * RGM_HLD] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int t = tid + u * RGM_THREADS;
+            if (t < k * k) f.LU[t % k + (t / k) * RGM_KMAX] = lu[u];
+        }
+        for (int t = tid + 2 * RGM_THREADS; t < k * k; t += RGM_THREADS)
+            f.LU[t % k + (t / k) * RGM_KMAX] = LU[t % k + (t / k) * RGM_KMAX];
+        if (tid < k) { f.piv[tid] = pvv; f.rd[tid] = rdv; f.perm[tid] = pmv; }
+        if (tid < nb) f.sc[tid] = scv;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int t = tid + u * RGM_THREADS;
+            if (t < nb * k) f.vtw[t % nb + (t / nb) * RGM_VTW_LD] = vt[u];
+        }
+        for (int t = tid + 2 * RGM_THREADS; t < nb * k; t += RGM_THREADS)
+            f.vtw[t % nb + (t / nb) * RGM_VTW_LD] = s->VtW[t % nb + (t / nb) * RGM_HLD];
         break;
     }
     case FIN_ARN2:
@@ -273,18 +302,24 @@ __device__ void fin_stage(const VecOp<T> &op, FinScratch &f)
         }
         break;
     case FIN_ARN2H: {
+        // loads first, then stores (as for FIN_ARN1); nb <= RGM_HLD < threads
         const int nb = op.ndV, k = op.ndW;
+        double scv = 0.0, hv = 0.0, csv = 0.0, snv = 0.0, vt[2];
+        if (tid < nb) { scv = s->colscale[tid]; hv = s->hsum[tid]; csv = s->cs[tid]; snv = s->sn[tid]; }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int t = tid + u * RGM_THREADS;
+            vt[u] = (t < nb * k) ? s->VtW[t % nb + (t / nb) * RGM_HLD] : 0.0;
+        }
         stage_givens_scalars(s, nb - 1, f);
-        for (int i = tid; i < nb; i += blockDim.x) {
-            f.sc[i] = s->colscale[i];
-            f.col[i] = s->hsum[i];
-            f.cs[i] = s->cs[i];
-            f.sn[i] = s->sn[i];
+        if (tid < nb) { f.sc[tid] = scv; f.col[tid] = hv; f.cs[tid] = csv; f.sn[tid] = snv; }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int t = tid + u * RGM_THREADS;
+            if (t < nb * k) f.vtw[t % nb + (t / nb) * RGM_VTW_LD] = vt[u];
         }
-        for (int t = tid; t < nb * k; t += blockDim.x) {
-            const int i = t % nb, l = t / nb;
-            f.vtw[i + l * RGM_VTW_LD] = s->VtW[i + l * RGM_HLD];
-        }
+        for (int t = tid + 2 * RGM_THREADS; t < nb * k; t += RGM_THREADS)
+            f.vtw[t % nb + (t / nb) * RGM_VTW_LD] = s->VtW[t % nb + (t / nb) * RGM_HLD];
         break;
     }
     case FIN_ARN3:
@@ -440,6 +475,8 @@ __device__ void finalize_block(const VecOp<T> &op, const double *d, FinScratch &
         double *hc = s->H + (int64_t)j * RGM_HLD;
         for (int i = tid; i <= j + 1; i += blockDim.x) hc[i] = f.col[i];
         const double sc = sc_h;
+        // one thread per column l (a chain, but the fewest binary64 operations:
+        // a warp tree would multiply the pipe's work by 32)
         for (int l = tid; l < kw; l += blockDim.x) {
             double v = dW[l];
             for (int i = 0; i < nb; ++i) v = fma(-f.h2[i], f.vtw[i + l * RGM_VTW_LD], v);
