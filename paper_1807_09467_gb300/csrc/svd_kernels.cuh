@@ -217,14 +217,20 @@ __global__ void sym_eig_select_kernel(Small *s, const double *gram, int c, int k
                 double cth = 1.0, sth = 0.0, tt = 0.0;
                 const double apq2 = apq * apq;
                 if (apq2 > floor2 && apq2 > 1e-30 * fabs(app * aqq)) {
-                    // t = sgn(tau) / (|tau| + sqrt(1 + tau^2)), tau = (aqq - app) / (2 apq),
-                    // written as 2|apq| sgn(tau) / (|d| + sqrt(d^2 + 4 apq^2)), d = aqq - app
+                    // the rotation with tan(2 theta) = 2 apq / d, d = aqq - app,
+                    // |theta| <= pi/4: cos(2 theta) = |d| / sqrt(h), sin(2 theta) =
+                    // 2 apq sgn(d) / sqrt(h), h = d^2 + 4 apq^2; then cos^2(theta) =
+                    // (1 + cos(2 theta)) / 2 and sin(theta) = sin(2 theta) / (2 cos(theta))
+                    // (half-angle identities: two reciprocal square roots, no division)
                     const double d = aqq - app;
                     const double h = fma(d, d, 4.0 * apq2);
                     const double num = (d > 0.0) ? 2.0 * apq : (d < 0.0) ? -2.0 * apq : 2.0 * fabs(apq);
-                    tt = num / (fabs(d) + h * rsqrt(h));
-                    cth = rsqrt(fma(tt, tt, 1.0));
-                    sth = tt * cth;
+                    const double rh = rsqrt(h);
+                    const double x = fma(0.5 * fabs(d), rh, 0.5);     // cos^2(theta)
+                    const double y = rsqrt(x);                         // 1 / cos(theta)
+                    cth = x * y;
+                    sth = 0.5 * num * rh * y;
+                    tt = sth * y;                                      // tan(theta)
                     rot_flag[fl] = 1;
                 }
                 rc[t] = cth; rs[t] = sth; rt[t] = tt;
@@ -360,16 +366,19 @@ __global__ void chol_inv_kernel(Small *s, const double *gram, int k, const int *
         R[i + j * RGM_KMAX] = (i <= j) ? gram[packed_index(i, j)] : 0.0;
     }
     __syncthreads();
-    // upper Cholesky G = R^T R, right-looking
+    // upper Cholesky G = R^T R, right-looking; the pivots' reciprocals are
+    // kept, so no division is on the serial path
+    __shared__ double rdiag[RGM_KMAX];
     for (int j = 0; j < k; ++j) {
-        __shared__ double d;
         if (threadIdx.x == 0) {
-            double v = R[j + j * RGM_KMAX];
-            d = v > 0.0 ? sqrt(v) : 1.0;
-            R[j + j * RGM_KMAX] = d;
+            const double v = R[j + j * RGM_KMAX];
+            const double r = v > 0.0 ? rsqrt(v) : 1.0;
+            R[j + j * RGM_KMAX] = v > 0.0 ? v * r : 1.0;
+            rdiag[j] = r;
         }
         __syncthreads();
-        for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) R[j + i * RGM_KMAX] /= d;
+        const double rd = rdiag[j];
+        for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) R[j + i * RGM_KMAX] *= rd;
         __syncthreads();
         for (int t = threadIdx.x; t < (k - j - 1) * (k - j - 1); t += blockDim.x) {
             const int a = j + 1 + t % (k - j - 1), b = j + 1 + t / (k - j - 1);
@@ -381,11 +390,11 @@ __global__ void chol_inv_kernel(Small *s, const double *gram, int k, const int *
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
         double col[RGM_KMAX];
         for (int i = 0; i < k; ++i) col[i] = 0.0;
-        col[j] = 1.0 / R[j + j * RGM_KMAX];
+        col[j] = rdiag[j];
         for (int i = j - 1; i >= 0; --i) {
             double v = 0.0;
             for (int l = i + 1; l <= j; ++l) v += R[i + l * RGM_KMAX] * col[l];
-            col[i] = -v / R[i + i * RGM_KMAX];
+            col[i] = -v * rdiag[i];
         }
         for (int i = 0; i < k; ++i) s->evec[i + j * RGM_WMAX] = col[i];
     }

@@ -1154,8 +1154,7 @@ __global__ void __launch_bounds__(RGM_THREADS) gram_kernel(GramOp<T> op)
 static __global__ void ls_solve_kernel(Small *s)
 {
     __shared__ double R[RGM_LS_MAX];     // packed upper triangle, column j at j(j+1)/2
-    __shared__ double g[RGM_HLD];
-    __shared__ double yi;
+    __shared__ double g[RGM_HLD], rdg[RGM_HLD], yv[RGM_HLD];
     const int nc = s->J + s->naug;
     for (int t = threadIdx.x; t < nc * nc; t += blockDim.x) {
         const int i = t % nc, j = t / nc;
@@ -1163,23 +1162,31 @@ static __global__ void ls_solve_kernel(Small *s)
     }
     for (int i = threadIdx.x; i < nc; i += blockDim.x) g[i] = s->g[i];
     __syncthreads();
-    for (int i = nc - 1; i >= 0; --i) {
-        if (threadIdx.x == 0) {
-            const double d = R[i * (i + 1) / 2 + i];
-            yi = (d != 0.0) ? g[i] / d : 0.0;
-            s->y[i] = yi;
-        }
-        __syncthreads();
-        const double y = yi;
-        for (int t = threadIdx.x; t < i; t += blockDim.x) g[t] -= R[i * (i + 1) / 2 + t] * y;
-        __syncthreads();
+    // the diagonal's reciprocals at once, then the back substitution in one
+    // warp (no block barrier and no division on the serial path)
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+        const double d = R[i * (i + 1) / 2 + i];
+        rdg[i] = (d != 0.0) ? 1.0 / d : 0.0;
     }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        for (int i = nc - 1; i >= 0; --i) {
+            const double y = g[i] * rdg[i];
+            __syncwarp();
+            if (lane == 0) yv[i] = y;
+            for (int t = lane; t < i; t += 32) g[t] = fma(-R[i * (i + 1) / 2 + t], y, g[t]);
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) s->y[i] = yv[i];
     for (int i = threadIdx.x; i < RGM_HLD; i += blockDim.x)
-        s->coefV[i] = (i < s->J) ? s->y[i] * s->colscale[i] : 0.0;
+        s->coefV[i] = (i < s->J) ? yv[i] * s->colscale[i] : 0.0;
     for (int i = threadIdx.x; i < RGM_KMAX; i += blockDim.x) s->coefU[i] = 0.0;
     __syncthreads();
     if (threadIdx.x == 0)
-        for (int a = 0; a < s->naug; ++a) s->coefU[s->aug_idx[a]] += s->y[s->J + a];
+        for (int a = 0; a < s->naug; ++a) s->coefU[s->aug_idx[a]] += yv[s->J + a];
 }
 
 // Reset the per-cycle Hessenberg state (before the start vector kernels).
@@ -1210,6 +1217,7 @@ static __global__ void lu_kernel(Small *s, int k, const double *in, const double
 {
     __shared__ double M[RGM_KMAX * RGM_KMAX];
     __shared__ int pivrow;
+    __shared__ double pivrcp;
     for (int i = threadIdx.x; i < k * k; i += blockDim.x) {
         const int r = i % k, c = i / k;
         double v;
@@ -1237,6 +1245,8 @@ static __global__ void lu_kernel(Small *s, int k, const double *in, const double
                 if (fabs(M[i + j * RGM_KMAX]) > fabs(M[p + j * RGM_KMAX])) p = i;
             pivrow = p;
             pvo[j] = p;
+            const double dp = M[p + j * RGM_KMAX];
+            pivrcp = (dp != 0.0) ? 1.0 / dp : 0.0;   // multipliers by one reciprocal
         }
         __syncthreads();
         const int p = pivrow;
@@ -1251,7 +1261,8 @@ static __global__ void lu_kernel(Small *s, int k, const double *in, const double
         maxp = fmax(maxp, fabs(d));
         minp = fmin(minp, fabs(d));
         if (d != 0.0) {
-            for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) M[i + j * RGM_KMAX] /= d;
+            const double rd = pivrcp;
+            for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) M[i + j * RGM_KMAX] *= rd;
             __syncthreads();
             for (int t = threadIdx.x; t < (k - j - 1) * (k - j - 1); t += blockDim.x) {
                 int i = j + 1 + t % (k - j - 1), c = j + 1 + t / (k - j - 1);
