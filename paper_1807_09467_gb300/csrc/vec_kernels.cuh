@@ -78,6 +78,8 @@ struct VecOp {
     int fin;
     int gate;
     int arg;                 // phase argument (appended column index)
+    unsigned release_gen;    // FIN_ARN2H in the cycle kernel: publish this grid-barrier
+                             // generation as soon as the next pass's inputs are written
     int lu_sel;              // small solves with E's LU (0) or the projector's (1)
     int dyn;                 // DYN_* bits: counts and output column read from Small
 };
@@ -436,7 +438,17 @@ __device__ void finalize_block(const VecOp<T> &op, const double *d, FinScratch &
             f.col[i] += h;                     // the Hessenberg column h1 + h2
             s->coefV[i] = -h * sc;
         }
+        if (tid == 0) {
+            s->J = j + 1;
+            s->nb = nb + 1;
+        }
         __syncthreads();
+        // The next pass (v_{j+1} = w1 - V h2, unnormalised) needs only the
+        // coefficients and the column count above: with op.release_gen the
+        // waiting blocks are released here, and the rest of the scalar step
+        // (rotation, scale, flags, V^T W row) overlaps their next pass; its
+        // results are published by the barrier that ends that pass.
+        if (op.release_gen && tid == 0) st_release_gpu(&s->gen, op.release_gen);
         if (tid < 32) {
             double q = 0.0;
             for (int i = tid; i < nb; i += 32) q = fma(f.h2[i], f.h2[i], q);
@@ -460,13 +472,11 @@ __device__ void finalize_block(const VecOp<T> &op, const double *d, FinScratch &
                 const bool brk = hn <= 1e-14 * f.wn0;
                 const double sc = brk ? 0.0 : inv_hn;
                 sc_h = sc;
-                s->J = j + 1;
                 const int it = f.iters + 1;
                 s->iters = it;
                 s->colscale[nb] = sc;          // happy breakdown: v_{j+1} := 0
                 int done = 0;
                 if (brk) { s->breakdown = 1; done = 1; }
-                s->nb = nb + 1;
                 if (fabs(g1) <= f.tol_in || it >= f.maxit || j + 1 >= f.m) done = 1;
                 if (done) s->done = 1;
             }
@@ -600,7 +610,7 @@ __device__ __forceinline__ const T *dot_col(const VecOp<T> &op, int c)
 
 // What one block did in a pass: left without touching the completion counter
 // (gated off, or nothing to reduce), arrived, or arrived last and finalised.
-enum PassResult { PASS_SKIPPED = 0, PASS_ARRIVED = 1, PASS_LAST = 2 };
+enum PassResult { PASS_SKIPPED = 0, PASS_ARRIVED = 1, PASS_LAST = 2, PASS_RELEASED = 3 };
 
 // One fused pass over the block's rows (body of vec_kernel and of each phase
 // of cycle_kernel).  PDL: signal programmatic dependents once the partials
@@ -817,7 +827,7 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op)
     __syncthreads();
     finalize_block(op, dsum, fin);
     if (threadIdx.x == 0 && !single) *op.counter = 0u;
-    return PASS_LAST;
+    return (op.release_gen && op.fin == FIN_ARN2H) ? PASS_RELEASED : PASS_LAST;
 }
 
 template <typename T, int QMAX>
@@ -910,7 +920,12 @@ __global__ void __launch_bounds__(RGM_THREADS, 4) cycle_kernel(CycleOp<T> c)
         op.x = op.V + (int64_t)j * op.ldv;
         op.xscale = j;
         if (!grid_barrier(vec_pass<T, QMAX, false>(op), s, ++gen)) return;
-        if (!grid_barrier(vec_pass<T, QMAX, false>(c.pass[1]), s, ++gen)) return;
+        VecOp<T> op1 = c.pass[1];
+        op1.release_gen = gen + 1;
+        const int rc1 = vec_pass<T, QMAX, false>(op1);
+        ++gen;
+        // the finalising block released the others in mid scalar step
+        if (rc1 != PASS_RELEASED && !grid_barrier(rc1, s, gen)) return;
         // plain update storing v_{j+1} (also after the last step: the augmented
         // relation orthogonalises against it)
         vec_pass<T, QMAX, false>(c.pass[2]);
