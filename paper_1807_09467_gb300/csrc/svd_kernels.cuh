@@ -283,6 +283,22 @@ __global__ void sym_eig_select_kernel(Small *s, const double *gram, int c, int k
             __syncthreads();
         }
         if (!rot_flag[fl]) break;
+        // would the next sweep rotate at all?  The same test on every pair of
+        // the current matrix (a sweep that rotates nothing leaves it as is), so
+        // the sweep that only confirms convergence is not run
+        __shared__ int more;
+        if (threadIdx.x == 0) more = 0;
+        __syncthreads();
+        for (int t = threadIdx.x; t < ce * ce; t += blockDim.x) {
+            const int p = t % ce, q = t / ce;
+            if (p < q) {
+                const double app = G[p + p * RGM_WMAX], aqq = G[q + q * RGM_WMAX], apq = G[p + q * RGM_WMAX];
+                const double apq2 = apq * apq;
+                if (apq2 > floor2 && apq2 > 1e-30 * fabs(app * aqq)) more = 1;
+            }
+        }
+        __syncthreads();
+        if (!more) break;
     }
     // eigenvalues, stable descending order by rank counting (ties by index)
     __shared__ double lam[RGM_WMAX], isg[RGM_WMAX];
