@@ -824,15 +824,16 @@ static int svd_update(rgm_solver s)
     const int kmax = std::min(c.k, cnt);
     const int *kdev = &s->sm->k_new;
     if (kmax > 0) {
-        // U = X Phi_k Sigma_k^{-1}, then two CholQR passes (k_new read on the device)
+        // U = X Phi_k Sigma_k^{-1} R1^{-1} with the first CholQR pass taken in the
+        // window's coordinates, then the second pass on the formed U (k_new read
+        // on the device)
+        { ProfScope ps_(s, RGM_PROF_SMALL); cholqr_small_kernel<<<1, 256, 0, s->st>>>(s->sm, s->gwin, cnt, kdev); }
         { ProfScope ps_(s, RGM_PROF_OTHER); combine_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U, s->X, s->sm->evec, cnt, -1, kdev, s->n, s->ld, RGM_WMAX); }
         CK(cudaGetLastError());
-        for (int pass = 0; pass < 2; ++pass) {
-            if ((rc = launch_gram<double>(s, s->U, s->ld, 0, s->U, s->ld, GRAM_PACKED, kdev, kmax, s->gram_out))) return rc;
-            { ProfScope ps_(s, RGM_PROF_SMALL); chol_inv_kernel<<<1, 64, 0, s->st>>>(s->sm, s->gram_out, -1, kdev); }
-            { ProfScope ps_(s, RGM_PROF_OTHER); combine_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U, s->U, s->sm->evec, -1, -1, kdev, s->n, s->ld, RGM_WMAX); }
-            CK(cudaGetLastError());
-        }
+        if ((rc = launch_gram<double>(s, s->U, s->ld, 0, s->U, s->ld, GRAM_PACKED, kdev, kmax, s->gram_out))) return rc;
+        { ProfScope ps_(s, RGM_PROF_SMALL); chol_inv_kernel<<<1, 64, 0, s->st>>>(s->sm, s->gram_out, -1, kdev); }
+        { ProfScope ps_(s, RGM_PROF_OTHER); combine_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U, s->U, s->sm->evec, -1, -1, kdev, s->n, s->ld, RGM_WMAX); }
+        CK(cudaGetLastError());
     }
     s->k_pending = true;
     s->coarse_stale = true;

@@ -368,6 +368,79 @@ __global__ void combine_kernel(double *out, const double *in, const double *C, i
     }
 }
 
+// First CholQR pass of the recycle space in the window's coordinates: with
+// U = X C (C = Phi_k Sigma_k^{-1}, the selected columns of Small::evec) the Gram
+// matrix of U is C^T (X^T X) C, formed from the resident window Gram matrix G
+// instead of n-length dot products; its Cholesky factor R gives C <- C R^{-1},
+// so that the one n-length combination U = X C already carries the first
+// pass.  The second pass (Gram of the formed U) then removes the rounding of
+// that combination.  One block; c <= RGM_WMAX, k <= RGM_KMAX.
+__global__ void cholqr_small_kernel(Small *s, const double *gwin, int c, const int *kdev)
+{
+    __shared__ double E[RGM_WMAX * RGM_KMAX];    // C, leading dimension RGM_WMAX
+    __shared__ double T[RGM_WMAX * RGM_KMAX];    // G C, later R^{-1}
+    __shared__ double R[RGM_KMAX * RGM_KMAX];
+    __shared__ double rdiag[RGM_KMAX];
+    const int k = *kdev;
+    if (k <= 0) return;
+    for (int t = threadIdx.x; t < c * k; t += blockDim.x) {
+        const int m = t % c, l = t / c;
+        E[m + l * RGM_WMAX] = s->evec[m + l * RGM_WMAX];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < c * k; t += blockDim.x) {
+        const int m = t % c, l = t / c;
+        double v = 0.0;
+        for (int p = 0; p < c; ++p) v = fma(gwin[m + p * RGM_WMAX], E[p + l * RGM_WMAX], v);
+        T[m + l * RGM_WMAX] = v;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+        const int i = t % k, j = t / k;
+        double v = 0.0;
+        if (i <= j)
+            for (int m = 0; m < c; ++m) v = fma(E[m + i * RGM_WMAX], T[m + j * RGM_WMAX], v);
+        R[i + j * RGM_KMAX] = v;
+    }
+    __syncthreads();
+    // upper Cholesky, right-looking, pivots by rsqrt (as chol_inv_kernel)
+    for (int j = 0; j < k; ++j) {
+        if (threadIdx.x == 0) {
+            const double v = R[j + j * RGM_KMAX];
+            const double r = v > 0.0 ? rsqrt(v) : 1.0;
+            R[j + j * RGM_KMAX] = v > 0.0 ? v * r : 1.0;
+            rdiag[j] = r;
+        }
+        __syncthreads();
+        const double rd = rdiag[j];
+        for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) R[j + i * RGM_KMAX] *= rd;
+        __syncthreads();
+        for (int t = threadIdx.x; t < (k - j - 1) * (k - j - 1); t += blockDim.x) {
+            const int a = j + 1 + t % (k - j - 1), b = j + 1 + t / (k - j - 1);
+            if (a <= b) R[a + b * RGM_KMAX] -= R[j + a * RGM_KMAX] * R[j + b * RGM_KMAX];
+        }
+        __syncthreads();
+    }
+    // R^{-1} (upper), one thread per column, into T
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        for (int i = 0; i < k; ++i) T[i + j * RGM_KMAX] = 0.0;
+        T[j + j * RGM_KMAX] = rdiag[j];
+        for (int i = j - 1; i >= 0; --i) {
+            double v = 0.0;
+            for (int l = i + 1; l <= j; ++l) v += R[i + l * RGM_KMAX] * T[l + j * RGM_KMAX];
+            T[i + j * RGM_KMAX] = -v * rdiag[i];
+        }
+    }
+    __syncthreads();
+    // C <- C R^{-1}
+    for (int t = threadIdx.x; t < c * k; t += blockDim.x) {
+        const int m = t % c, l = t / c;
+        double v = 0.0;
+        for (int i = 0; i <= l; ++i) v = fma(E[m + i * RGM_WMAX], T[i + l * RGM_KMAX], v);
+        s->evec[m + l * RGM_WMAX] = v;
+    }
+}
+
 // Cholesky factor R of the packed Gram matrix of U (k x k), and its inverse
 // into Small::evec so that U R^{-1} has orthonormal columns.  One block:
 // the factorisation row by row with the trailing updates in parallel, then one
