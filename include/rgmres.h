@@ -196,7 +196,7 @@ int rgm_solve(rgm_solver s, const double *b, double *x, int flags, rgm_stats *st
 int rgm_update_recycle_svd(rgm_solver s, const double *x, int flags, int *k_used);
 
 /* Batched solve: nsys independent systems, system i on handle handles[i], solved
- * concurrently (survey: batched / served forms; the sequences of a batch are
+ * concurrently (the batched and served forms: the sequences of a batch are
  * independent problems).  Each handle's work is queued on its own stream from a
  * pool of host threads, one launch per fused pass (the cooperative cycle
  * kernel is not used inside a batch: cooperative grids on concurrent streams

@@ -114,8 +114,8 @@ typedef struct {
     int precond;       /* ORC_PRECOND_NONE / ORC_PRECOND_JACOBI                    */
 } orc_opts;
 
-/* Left Jacobi preconditioning (survey "next": a GPU-friendly preconditioner in
- * place of the paper's SSOR): GMRES on D^{-1} A x = D^{-1} b, D = diag(A) (rows
+/* Left Jacobi preconditioning (a GPU-friendly preconditioner in place of the
+ * paper's SSOR, whose triangular sweeps are sequential): GMRES on D^{-1} A x = D^{-1} b, D = diag(A) (rows
  * without a nonzero diagonal keep weight 1).  The in-cycle exit compares the
  * Givens estimate of the preconditioned residual with rtol ||D^{-1} b||; the
  * stopping test stays on the true residual ||b - A x|| <= rtol ||b||. */
