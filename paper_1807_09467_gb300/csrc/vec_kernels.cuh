@@ -1100,31 +1100,40 @@ __global__ void __launch_bounds__(RGM_THREADS) gram_kernel(GramOp<T> op)
     const int npairs = (op.mode == GRAM_UW) ? nx * nx + 2 * nx : (op.mode == GRAM_COL) ? nx : nx * (nx + 1) / 2;
     const int64_t r0 = (int64_t)blockIdx.x * op.rpb;
     const int64_t r1 = min(op.n, r0 + op.rpb);
+    auto pair_of = [&](int p, int *a, int *b) {
+        *a = 0;
+        *b = 0;
+        if (p >= npairs) return;
+        if (op.mode == GRAM_PACKED) {
+            packed_pair(p, a, b);
+        } else if (op.mode == GRAM_COL) {
+            *a = op.col;
+            *b = p;
+        } else if (p < nx * nx) {
+            *a = p % nx;
+            *b = nx + p / nx;
+        } else if (p < nx * nx + nx) {
+            *a = *b = p - nx * nx;
+        } else {
+            *a = *b = nx + (p - nx * nx - nx);
+        }
+    };
     double acc[RGM_GRAM_PMAX];
     int pa[RGM_GRAM_PMAX], pb[RGM_GRAM_PMAX];
 #pragma unroll
     for (int i = 0; i < RGM_GRAM_PMAX; ++i) {
         acc[i] = 0.0;
-        const int p = threadIdx.x + i * RGM_THREADS;
-        int a = 0, b = 0;
-        if (p < npairs) {
-            if (op.mode == GRAM_PACKED) {
-                packed_pair(p, &a, &b);
-            } else if (op.mode == GRAM_COL) {
-                a = op.col;
-                b = p;
-            } else if (p < nx * nx) {
-                a = p % nx;
-                b = nx + p / nx;
-            } else if (p < nx * nx + nx) {
-                a = b = p - nx * nx;
-            } else {
-                a = b = nx + (p - nx * nx - nx);
-            }
-        }
-        pa[i] = a;
-        pb[i] = b;
+        pair_of(threadIdx.x + i * RGM_THREADS, &pa[i], &pb[i]);
     }
+    // few pairs (the window's new column, CholQR, E): the block's threads split
+    // each pair's rows into nsl interleaved slices instead of one thread walking
+    // all rows of a pair; the slices' sums are added once at the end
+    const bool split = npairs > 0 && 2 * npairs <= RGM_THREADS;
+    const int nsl = split ? RGM_THREADS / npairs : 1;
+    const int sp = split ? (int)threadIdx.x % npairs : 0, srs = split ? (int)threadIdx.x / npairs : 0;
+    int spa = 0, spb = 0;
+    if (split) pair_of(sp, &spa, &spb);
+    double sacc = 0.0;
     for (int64_t base = r0; base < r1; base += op.tile) {
         const int nrow = (int)min((int64_t)op.tile, r1 - base);
         for (int t = threadIdx.x; t < nrow * ncol; t += RGM_THREADS) {
@@ -1133,16 +1142,33 @@ __global__ void __launch_bounds__(RGM_THREADS) gram_kernel(GramOp<T> op)
             gsm[c * ts + r] = (double)src[base + r];
         }
         __syncthreads();
+        if (split) {
+            if (srs < nsl) {
+                const double *a = gsm + spa * ts, *b = gsm + spb * ts;
+                for (int r = srs; r < nrow; r += nsl) sacc = fma(a[r], b[r], sacc);
+            }
+        } else {
 #pragma unroll
-        for (int i = 0; i < RGM_GRAM_PMAX; ++i) {
-            if (threadIdx.x + i * RGM_THREADS < npairs) {
-                const double *a = gsm + pa[i] * ts, *b = gsm + pb[i] * ts;
-                double s = 0.0;
-                for (int r = 0; r < nrow; ++r) s += a[r] * b[r];
-                acc[i] += s;
+            for (int i = 0; i < RGM_GRAM_PMAX; ++i) {
+                if (threadIdx.x + i * RGM_THREADS < npairs) {
+                    const double *a = gsm + pa[i] * ts, *b = gsm + pb[i] * ts;
+                    double s = 0.0;
+                    for (int r = 0; r < nrow; ++r) s += a[r] * b[r];
+                    acc[i] += s;
+                }
             }
         }
         __syncthreads();
+    }
+    if (split) {
+        // the tile buffer holds at least RGM_THREADS + 1 doubles (tile 256, one column)
+        gsm[threadIdx.x] = (srs < nsl) ? sacc : 0.0;
+        __syncthreads();
+        if ((int)threadIdx.x < npairs) {
+            double v = 0.0;
+            for (int q = 0; q < nsl; ++q) v += gsm[threadIdx.x + q * npairs];
+            acc[0] = v;
+        }
     }
 #pragma unroll
     for (int i = 0; i < RGM_GRAM_PMAX; ++i) {
