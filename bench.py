@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=100.0, help="serve: mean arrivals per second")
     ap.add_argument("--launch-policy", default="auto", choices=["auto", "per_pass"],
                     help="Arnoldi steps of a cycle in one cooperative launch (auto) or one launch per pass")
+    ap.add_argument("--batch-policy", default="streams", choices=["coop", "streams"],
+                    help="batch64 / serve: all systems' cycles in batched cooperative launches (coop) "
+                         "or per-pass launches on the systems' streams")
     return ap.parse_args()
 
 
@@ -442,8 +445,10 @@ def run_batch(args):
     advanced one time step at a time; per step every sequence's operator is
     assembled (outside the timed region), then timed on the device: new
     values, one rgm_batch_solve over all 64 handles (each on its own stream),
-    and the window updates.  The same steps solved one handle after another
-    give the sequential figure."""
+    and the window updates.  Both batch policies are measured (the systems'
+    cycles in batched cooperative launches, or per-pass launches on their
+    streams); the same steps solved one handle after another give the
+    sequential figure."""
     import numpy as np
     import torch
 
@@ -468,7 +473,7 @@ def run_batch(args):
             st.append(dict(fe=fe, sol=sol, u=u, stream=stream, val=None, b=None))
         return st
 
-    def step(state, batched):
+    def step(state, batched, coop):
         for e in state:                                   # assembly: outside the timed region
             e["val"], e["b"] = e["fe"].assemble(e["u"])
             # initial guess: zero with a recycle space (x0 = U E^-1 U^T b), else x_{i-1}
@@ -482,7 +487,7 @@ def run_batch(args):
             e["sol"].set_operator_values(e["val"])
         if batched:
             stats = rg.batch_solve([e["sol"] for e in state], [e["b"] for e in state],
-                                   [e["x"] for e in state])
+                                   [e["x"] for e in state], coop=coop)
         else:
             stats = [e["sol"].solve(e["b"], e["x"])[1] for e in state]
         for e in state:
@@ -497,23 +502,25 @@ def run_batch(args):
         return t0.elapsed_time(t1), stats
 
     out = {}
-    for batched in (True, False):
+    for arm, batched, coop in (("coop", True, True), ("streams", True, False), ("sequential", False, False)):
         state = setup()
         ms, its = [], []
         for i in range(args.warmup + args.steps):
-            t, stats = step(state, batched)
+            t, stats = step(state, batched, coop)
             assert all(st["status"] == 0 and st["true_relres"] <= 1e-8 for st in stats), stats
             if i >= args.warmup:
                 ms.append(t)
                 its.extend(st["iters"] for st in stats)
-        out[batched] = (ms, its)
+        out[arm] = (ms, its)
         for e in state:
             e["sol"].close()
             e["fe"].close()
         del state
         torch.cuda.synchronize()
-    ms, its = out[True]
-    mss, _ = out[False]
+    other = "streams" if args.batch_policy == "coop" else "coop"
+    ms, its = out[args.batch_policy]
+    mso, _ = out[other]
+    mss, _ = out["sequential"]
     K = args.steps
     value = 64 * K / (sum(ms) / 1e3)
     res = {"metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": 1, "steps": K,
@@ -525,8 +532,10 @@ def run_batch(args):
                       "total_dofs": int(sum(w.n for w, _, _ in seqs)), "mode": args.mode,
                       "precision": prec, "m": 30, "k": 8, "window": 16, "rtol": 1e-8,
                       "l2": "flushed (256 MiB write) before every timed step",
-                      "parallelism": "rgm_batch_solve, one stream per sequence"},
+                      "parallelism": "rgm_batch_solve, one stream per sequence",
+                      "batch_policy": args.batch_policy},
            "iterations": iters_stats(its),
+           other: {"solves_per_s": round(64 * K / (sum(mso) / 1e3), 3), "ms_per_step": round(sum(mso) / K, 4)},
            "sequential": {"solves_per_s": round(64 * K / (sum(mss) / 1e3), 3),
                           "ms_per_step": round(sum(mss) / K, 4)},
            "speedup_vs_sequential": round(sum(mss) / sum(ms), 3)}
@@ -549,7 +558,8 @@ def run_serve(args):
     reqs = [serve.Request(**r) for r in synth.serve_stream(count=args.serve_count,
                                                             rate_per_s=args.serve_rate, n_hi=128)]
     torch.cuda.synchronize()
-    res, tot = serve.Server(max_slots=64, precision="fp32_ir", mode="deflated").run(reqs, realtime=True)
+    res, tot = serve.Server(max_slots=64, precision="fp32_ir", mode="deflated",
+                            coop=args.batch_policy == "coop").run(reqs, realtime=True)
     torch.cuda.synchronize()
     base, btot = serve.Server(max_slots=1, precision="fp64", mode="plain").run(reqs, realtime=False)
     its = [i for r in res for i in r.iters]
@@ -560,7 +570,7 @@ def run_serve(args):
            "config": {"workload": f"serve: {len(reqs)} sequences, Poisson arrivals at {args.serve_rate}/s, "
                                   "Q1-Q4 on 16^2..128^2 quads, 10-100 steps, deflated GMRES-IR to 1e-8, "
                                   "continuous batching (64 slots, 80 % of free HBM)",
-                      "requests": len(reqs), "solves": tot["solves"]},
+                      "requests": len(reqs), "solves": tot["solves"], "batch_policy": args.batch_policy},
            "latency_ms": {"p50": round(tot["p50_ms"], 3), "p99": round(tot["p99_ms"], 3)},
            "iterations": iters_stats(its), "ticks": tot["ticks"], "wall_s": round(tot["wall_s"], 3),
            "plain_fp64_one_at_a_time": {"solves_per_s": round(btot["solves_per_s"], 3),

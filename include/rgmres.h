@@ -48,6 +48,7 @@ extern "C" {
 #define RGM_E_TIMEOUT         (-5)  /* a bounded device wait gave up                       */
 
 #define RGM_DEVICE_PTRS         1   /* flag: pointers are device pointers                  */
+#define RGM_BATCH_COOP          2   /* flag of rgm_batch_solve: batched cycle launches     */
 
 /* ---------------------------------------------------------------- config */
 typedef enum {
@@ -197,14 +198,25 @@ int rgm_update_recycle_svd(rgm_solver s, const double *x, int flags, int *k_used
 
 /* Batched solve: nsys independent systems, system i on handle handles[i], solved
  * concurrently (the batched and served forms: the sequences of a batch are
- * independent problems).  Each handle's work is queued on its own stream from a
- * pool of host threads, one launch per fused pass (the cooperative cycle
- * kernel is not used inside a batch: cooperative grids on concurrent streams
- * are not guaranteed to be resident together).  Handles must be distinct and
- * should have distinct streams (solves on one stream serialise).  b[i], x[i]
- * and flags as in rgm_solve; st (optional) receives nsys entries.  Returns the
- * first error if any solve failed (rgm_last_error then describes it), else
- * the largest warning, else RGM_OK. */
+ * independent problems).  Handles must be distinct and should have distinct
+ * streams (solves on one stream serialise).  b[i], x[i] and flags as in
+ * rgm_solve; st (optional) receives nsys entries.  Returns the first error if
+ * any solve failed (rgm_last_error then describes it), else the largest
+ * warning, else RGM_OK.
+ *
+ * Without RGM_BATCH_COOP each handle's work is queued on its own stream from a
+ * pool of host threads, one launch per fused pass (no cooperative cycle kernel:
+ * cooperative grids on concurrent streams are not guaranteed to be resident
+ * together).  With RGM_BATCH_COOP (all handles in one precision, launch policy
+ * auto, a device with cooperative launch; otherwise the flag is ignored) every
+ * system runs on a host thread of its own and, at each GMRES cycle, waits until
+ * all systems still solving have reached theirs; their cycles then run as one
+ * cooperative launch of batch_cycle_kernel on a stream of the batch, each
+ * system on a block range of its own (its usual block count when all fit, else
+ * one block plus a share of the resident capacity in proportion to its work per
+ * Arnoldi step).  Results then equal the handle's own solve up to the rounding
+ * of its dot-product partition: bit for bit when the system kept its block
+ * count, within rounding otherwise; a batch repeats bit for bit. */
 int rgm_batch_solve(rgm_solver *handles, int nsys, const double *const *b, double *const *x, int flags,
                     rgm_stats *st);
 /* Singular values of the last window SVD, descending (up to `window` values);

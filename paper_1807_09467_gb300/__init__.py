@@ -16,7 +16,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (AUGMENTED, DEFLATED, FP32_IR, FP64, GUESS, PLAIN, RGM_DEVICE_PTRS,
+from ._lib import (AUGMENTED, DEFLATED, FP32_IR, FP64, GUESS, PLAIN, RGM_BATCH_COOP, RGM_DEVICE_PTRS,
                    RGM_W_NOT_CONVERGED, RGM_W_SINGULAR_COARSE, RgmConfig, RgmError,
                    RgmStats, check)
 
@@ -217,10 +217,12 @@ class Solver:
         return y
 
 
-def batch_solve(solvers, bs, xs):
+def batch_solve(solvers, bs, xs, coop=False):
     """rgm_batch_solve: solves system i on solvers[i] with right-hand side bs[i]
     and initial guess / result xs[i] (CUDA tensors, updated in place),
-    concurrently.  Returns the list of stats dicts."""
+    concurrently.  coop: the systems' GMRES cycles run together as batched
+    cooperative launches (RGM_BATCH_COOP) instead of per-pass launches on the
+    handles' streams.  Returns the list of stats dicts."""
     L = _lib.load()
     n = len(solvers)
     assert len(bs) == n and len(xs) == n
@@ -230,7 +232,8 @@ def batch_solve(solvers, bs, xs):
     B = (C.c_void_p * n)(*[b.data_ptr() for b in bs])
     X = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
     st = (RgmStats * n)()
-    check(L.rgm_batch_solve(H, n, B, X, RGM_DEVICE_PTRS, st), "rgm_batch_solve")
+    flags = RGM_DEVICE_PTRS | (RGM_BATCH_COOP if coop else 0)
+    check(L.rgm_batch_solve(H, n, B, X, flags, st), "rgm_batch_solve")
     return [_stats(st[i]) for i in range(n)]
 
 

@@ -21,6 +21,7 @@ RGM_E_CUDA = -3
 RGM_E_STATE = -4
 RGM_E_TIMEOUT = -5
 RGM_DEVICE_PTRS = 1
+RGM_BATCH_COOP = 2
 RGM_NOALLOC_MAX_ROWS = 4096 * 2048
 
 PLAIN, DEFLATED, AUGMENTED, GUESS = 0, 1, 2, 3

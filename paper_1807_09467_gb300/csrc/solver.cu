@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <condition_variable>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -130,6 +131,41 @@ struct rgm_solver_s {
     // (-1: not queried yet)
     int cycle_cap[2][RGM_MAXDOTS + 2];
     bool in_batch = false;        // solving inside rgm_batch_solve: no cooperative launch
+    // inside rgm_batch_solve with RGM_BATCH_COOP: the rendezvous this handle's
+    // cycle launches join, its index there, and the event marking its inputs ready
+    struct BatchCycles *batch = nullptr;
+    int batch_idx = 0;
+    cudaEvent_t batch_ev = nullptr;
+};
+
+// Rendezvous of the systems of one rgm_batch_solve(.., RGM_BATCH_COOP, ..): each
+// system's host thread runs its own solve and, at every GMRES cycle, hands its
+// cycle (the three fused passes of CycleOp) to this object and waits.  When
+// every system still solving has arrived, the last one to arrive launches all
+// their cycles as one batch_cycle_kernel on the batch's stream (after the
+// systems' streams, before their continuations), then wakes the others.
+// A system that finishes its solve leaves, which can complete a phase too.
+struct BatchCycles {
+    struct Req {
+        int idx;
+        rgm_solver s;
+        const void *cyc;          // CycleOp<T> on the waiting thread's stack
+        int nd;                   // dot-column bound of the cycle
+    };
+    std::mutex mu;
+    std::condition_variable cv;
+    int active = 0;               // systems still inside their solve
+    unsigned long long phase = 0; // phases launched so far
+    std::vector<Req> arrived;
+    std::vector<int> rc;          // per system: result of its last phase
+    int precision = RGM_FP64;     // the same for every system of the batch
+    cudaStream_t st = nullptr;    // the batch launches' stream
+    cudaEvent_t done = nullptr;   // end of the latest phase's launches
+    void *d_ops = nullptr;        // CycleOp<T>[nsys] of a phase
+    int *d_first = nullptr;       // per wave: first block of each system, then the total
+    std::vector<char> h_ops;
+    std::vector<int> h_first;
+    int cap[RGM_MAXDOTS + 2];     // co-resident blocks by dot-column bound (-1: not queried)
 };
 
 static size_t small_header_bytes() { return offsetof(Small, H); }
@@ -556,6 +592,119 @@ static const float *res_weights(rgm_solver, const Arnoldi<float> &) { return nul
 // One recycled GMRES solve of A x = b on the device buffers of `a`, with the
 // tolerance tol_abs already in Small.  mode: effective mode (PLAIN if no U).
 // Returns the number of cycles through *cycles.
+// Launch one phase of a batched solve (the caller holds b.mu): the arrived
+// systems' cycles in waves of at most `cap` co-resident blocks.  A system asks
+// for its own block count; when the wave's requests exceed the capacity, each
+// system keeps one block plus a share of the rest in proportion to its work per
+// Arnoldi step (nnz + n x dot columns), never more than it asked for.  The
+// shares depend only on the systems in the wave, taken in index order, so a
+// batch repeats bit for bit.
+template <typename T>
+static int batch_phase(BatchCycles &b)
+{
+    std::vector<BatchCycles::Req> &rq = b.arrived;
+    std::sort(rq.begin(), rq.end(),
+              [](const BatchCycles::Req &x, const BatchCycles::Req &y) { return x.idx < y.idx; });
+    int nd = 0;
+    for (const auto &r : rq) nd = std::max(nd, r.nd);
+    int &cap = b.cap[nd];
+    if (cap < 0) cap = batch_cycle_capacity((const CycleOp<T> *)nullptr, nd);
+    if (cap <= 0) {
+        rgm_note_cuda_error((int)cudaErrorCooperativeLaunchTooLarge, "batched cycle capacity", __LINE__);
+        return RGM_E_CUDA;
+    }
+    const int ns = (int)rq.size();
+    b.h_ops.resize(sizeof(CycleOp<T>) * ns);
+    b.h_first.clear();
+    CycleOp<T> *ops = reinterpret_cast<CycleOp<T> *>(b.h_ops.data());
+    struct Wave { int s0, s1, f0, nblocks; };
+    std::vector<Wave> waves;
+    for (int w0 = 0; w0 < ns;) {
+        const int w1 = std::min(ns, w0 + cap);
+        int64_t want = 0;
+        double wsum = 0.0;
+        for (int i = w0; i < w1; ++i) {
+            ops[i] = *static_cast<const CycleOp<T> *>(rq[i].cyc);
+            want += ops[i].pass[0].nblocks;
+            wsum += (double)rq[i].s->nnz + (double)rq[i].s->n * rq[i].nd;
+        }
+        const int spare = cap - (w1 - w0);
+        Wave wv{w0, w1, (int)b.h_first.size(), 0};
+        b.h_first.push_back(0);
+        for (int i = w0; i < w1; ++i) {
+            rgm_solver si = rq[i].s;
+            int nb = ops[i].pass[0].nblocks;
+            if (want > cap) {
+                const double share = ((double)si->nnz + (double)si->n * rq[i].nd) / wsum;
+                nb = std::min(nb, 1 + (int)std::floor(spare * share));
+            }
+            const int64_t ntile = (si->n + RGM_TILE - 1) / RGM_TILE;
+            const int64_t rpb = (ntile + nb - 1) / nb * RGM_TILE;
+            const int nblk = (int)((si->n + rpb - 1) / rpb);
+            for (VecOp<T> &op : ops[i].pass) {
+                op.rpb = (int)rpb;
+                op.nblocks = nblk;
+                op.ngroups = (nblk + RGM_RGROUP - 1) / RGM_RGROUP;
+            }
+            wv.nblocks += nblk;
+            b.h_first.push_back(wv.nblocks);
+        }
+        waves.push_back(wv);
+        w0 = w1;
+    }
+    CK(cudaMemcpyAsync(b.d_ops, ops, sizeof(CycleOp<T>) * ns, cudaMemcpyHostToDevice, b.st));
+    CK(cudaMemcpyAsync(b.d_first, b.h_first.data(), sizeof(int) * b.h_first.size(), cudaMemcpyHostToDevice,
+                       b.st));
+    for (const auto &r : rq) CK(cudaStreamWaitEvent(b.st, r.s->batch_ev, 0));
+    for (const Wave &wv : waves) {
+        nvtxRangePushA(kNvtxKind[RGM_PROF_ARNOLDI_CYCLE]);
+        const int rc = launch_batch_cycle(static_cast<const CycleOp<T> *>(b.d_ops) + wv.s0, b.d_first + wv.f0,
+                                          wv.s1 - wv.s0, wv.nblocks, nd, b.st);
+        nvtxRangePop();
+        ++rq[wv.s0].s->launches;
+        if (rc) {
+            rgm_note_cuda_error(rc, "batch_cycle_kernel launch", __LINE__);
+            return RGM_E_CUDA;
+        }
+    }
+    CK(cudaEventRecord(b.done, b.st));
+    for (const auto &r : rq) CK(cudaStreamWaitEvent(r.s->st, b.done, 0));
+    return RGM_OK;
+}
+
+// Complete a phase if every system still solving has arrived (caller holds b.mu).
+static void batch_try_launch(BatchCycles &b)
+{
+    if (b.arrived.empty() || (int)b.arrived.size() < b.active) return;
+    const int rc = (b.precision == RGM_FP64) ? batch_phase<double>(b) : batch_phase<float>(b);
+    for (const auto &r : b.arrived) b.rc[r.idx] = rc;
+    b.arrived.clear();
+    ++b.phase;
+    b.cv.notify_all();
+}
+
+// A system of a batched solve at its cycle launch: join the phase, wait for it.
+template <typename T>
+static int batch_cycle(rgm_solver s, const CycleOp<T> &c, int nd)
+{
+    BatchCycles &b = *s->batch;
+    CK(cudaEventRecord(s->batch_ev, s->st));
+    std::unique_lock<std::mutex> lk(b.mu);
+    const unsigned long long ph = b.phase;
+    b.arrived.push_back({s->batch_idx, s, &c, nd});
+    batch_try_launch(b);
+    b.cv.wait(lk, [&] { return b.phase != ph; });
+    return b.rc[s->batch_idx];
+}
+
+// A system of a batched solve is done (or failed): the others stop waiting for it.
+static void batch_leave(BatchCycles &b)
+{
+    std::lock_guard<std::mutex> lk(b.mu);
+    --b.active;
+    batch_try_launch(b);
+}
+
 template <typename T>
 static int gmres_cycles(rgm_solver s, const Arnoldi<T> &a, int mode, int k, int max_cycles,
                         int *cycles_out)
@@ -594,7 +743,9 @@ static int gmres_cycles(rgm_solver s, const Arnoldi<T> &a, int mode, int k, int 
         const int kdef = (mode == RGM_DEFLATED) ? k : 0;
         CycleOp<T> cyc;
         arnoldi_passes(s, a, kdef, cyc);
-        if (use_cycle_kernel(s, cyc, kdef + m + 1)) {
+        if (s->batch) {
+            if ((rc = batch_cycle(s, cyc, kdef + m + 1))) return rc;
+        } else if (use_cycle_kernel(s, cyc, kdef + m + 1)) {
             if ((rc = launch_cycle_prof(s, cyc, kdef + m + 1))) return rc;
         } else {
             for (int j = 0; j < m; ++j) {
@@ -902,6 +1053,7 @@ static void free_all(rgm_solver s)
     if (s->hs) cudaFreeHost(s->hs);
     for (ProfRec &r : s->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+    if (s->batch_ev) cudaEventDestroy(s->batch_ev);
 }
 
 int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
@@ -1232,31 +1384,101 @@ int rgm_batch_solve(rgm_solver *handles, int nsys, const double *const *b, doubl
     }
     int dev = 0;
     CK(cudaGetDevice(&dev));
+    // batched cycle launches: every handle in the same precision, none forced
+    // to per-pass launches, and a device that launches cooperatively
+    bool coop = (flags & RGM_BATCH_COOP) && nsys > 0;
+    for (int i = 0; coop && i < nsys; ++i)
+        coop = handles[i]->cfg.precision == handles[0]->cfg.precision &&
+               handles[i]->cfg.launch_policy == RGM_LAUNCH_AUTO;
+    if (coop) {
+        const CycleOp<double> *p64 = nullptr;
+        coop = batch_cycle_capacity(p64, 1) > 0;
+    }
+    flags &= ~RGM_BATCH_COOP;
+    BatchCycles bc;
+    if (coop) {
+        for (int &v : bc.cap) v = -1;
+        bc.active = nsys;
+        bc.rc.assign(nsys, RGM_OK);
+        bc.precision = handles[0]->cfg.precision;
+        const size_t opsz = bc.precision == RGM_FP64 ? sizeof(CycleOp<double>) : sizeof(CycleOp<float>);
+        CK(cudaStreamCreateWithFlags(&bc.st, cudaStreamNonBlocking));
+        cudaError_t e = cudaEventCreateWithFlags(&bc.done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMallocAsync(&bc.d_ops, opsz * nsys, bc.st);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&bc.d_first, sizeof(int) * (2 * nsys + 2), bc.st);
+        for (int i = 0; e == cudaSuccess && i < nsys; ++i) {
+            rgm_solver s = handles[i];
+            if (!s->batch_ev) e = cudaEventCreateWithFlags(&s->batch_ev, cudaEventDisableTiming);
+            s->batch = &bc;
+            s->batch_idx = i;
+        }
+        if (e != cudaSuccess) {
+            for (int i = 0; i < nsys; ++i) handles[i]->batch = nullptr;
+            if (bc.d_ops) cudaFreeAsync(bc.d_ops, bc.st);
+            if (bc.d_first) cudaFreeAsync(bc.d_first, bc.st);
+            if (bc.done) cudaEventDestroy(bc.done);
+            cudaStreamDestroy(bc.st);
+            rgm_note_cuda_error((int)e, "batched cycle setup", __LINE__);
+            return e == cudaErrorMemoryAllocation ? RGM_E_OOM : RGM_E_CUDA;
+        }
+    }
     std::vector<int> rc(nsys, RGM_OK);
     std::atomic<int> next(0);
     std::mutex mu;
     std::string first_error;
-    auto work = [&]() {
-        if (cudaSetDevice(dev) != cudaSuccess) return;
-        for (;;) {
-            const int i = next.fetch_add(1);
-            if (i >= nsys) break;
-            rgm_solver s = handles[i];
-            s->in_batch = true;
-            rc[i] = rgm_solve(s, b[i], x[i], flags, st ? &st[i] : nullptr);
-            s->in_batch = false;
-            if (rc[i] < 0) {
-                std::lock_guard<std::mutex> lk(mu);
-                if (first_error.empty()) first_error = g_last_error;
-            }
+    auto solve_one = [&](int i) {
+        rgm_solver s = handles[i];
+        s->in_batch = true;
+        rc[i] = rgm_solve(s, b[i], x[i], flags, st ? &st[i] : nullptr);
+        s->in_batch = false;
+        if (coop) batch_leave(bc);
+        if (rc[i] < 0) {
+            std::lock_guard<std::mutex> lk(mu);
+            if (first_error.empty()) first_error = g_last_error;
         }
     };
-    const int nthr = std::max(1, std::min<int>(nsys, (int)std::max(1u, std::thread::hardware_concurrency())));
-    std::vector<std::thread> pool;
-    for (int t = 1; t < nthr; ++t) pool.emplace_back(work);
-    work();
-    for (auto &th : pool) th.join();
-    if (next.load() < nsys) return RGM_E_CUDA;            // a worker could not select the device
+    bool dev_ok = true;
+    if (coop) {
+        // one thread per system: a system waits at the rendezvous until every
+        // other system still solving has reached its own cycle launch
+        std::atomic<int> started(0);
+        auto one = [&](int i) {
+            if (cudaSetDevice(dev) != cudaSuccess) {
+                rc[i] = RGM_E_CUDA;
+                batch_leave(bc);
+                return;
+            }
+            started.fetch_add(1);
+            solve_one(i);
+        };
+        std::vector<std::thread> pool;
+        for (int i = 1; i < nsys; ++i) pool.emplace_back(one, i);
+        one(0);
+        for (auto &th : pool) th.join();
+        dev_ok = started.load() == nsys;
+        for (int i = 0; i < nsys; ++i) handles[i]->batch = nullptr;
+        cudaFreeAsync(bc.d_ops, bc.st);
+        cudaFreeAsync(bc.d_first, bc.st);
+        cudaStreamSynchronize(bc.st);
+        cudaEventDestroy(bc.done);
+        cudaStreamDestroy(bc.st);
+    } else {
+        auto work = [&]() {
+            if (cudaSetDevice(dev) != cudaSuccess) return;
+            for (;;) {
+                const int i = next.fetch_add(1);
+                if (i >= nsys) break;
+                solve_one(i);
+            }
+        };
+        const int nthr = std::max(1, std::min<int>(nsys, (int)std::max(1u, std::thread::hardware_concurrency())));
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nthr; ++t) pool.emplace_back(work);
+        work();
+        for (auto &th : pool) th.join();
+        dev_ok = next.load() >= nsys;
+    }
+    if (!dev_ok) return RGM_E_CUDA;            // a worker could not select the device
     int worst = RGM_OK;
     for (int r : rc) {
         if (r < 0) { if (worst >= 0) worst = r; }

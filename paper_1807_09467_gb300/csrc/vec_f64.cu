@@ -16,3 +16,14 @@ int launch_cycle(const CycleOp<double> &c, int nd_max, cudaStream_t st)
 {
     return launch_cycle_impl(c, nd_max, st);
 }
+
+int batch_cycle_capacity(const CycleOp<double> *, int nd_max)
+{
+    return batch_capacity_impl<double>(nd_max);
+}
+
+int launch_batch_cycle(const CycleOp<double> *ops, const int *first, int nsys, int nblocks, int nd_max,
+                       cudaStream_t st)
+{
+    return launch_batch_impl(ops, first, nsys, nblocks, nd_max, st);
+}

@@ -612,11 +612,12 @@ __device__ __forceinline__ const T *dot_col(const VecOp<T> &op, int c)
 // (gated off, or nothing to reduce), arrived, or arrived last and finalised.
 enum PassResult { PASS_SKIPPED = 0, PASS_ARRIVED = 1, PASS_LAST = 2, PASS_RELEASED = 3 };
 
-// One fused pass over the block's rows (body of vec_kernel and of each phase
-// of cycle_kernel).  PDL: signal programmatic dependents once the partials
-// are written.
+// One fused pass over the rows of block `bid` of the pass's grid (body of
+// vec_kernel and of each phase of the cycle kernels; bid is the block's index
+// among the op.nblocks blocks that run the pass).  PDL: signal programmatic
+// dependents once the partials are written.
 template <typename T, int QMAX, bool PDL>
-__device__ __forceinline__ int vec_pass(VecOp<T> op)
+__device__ __forceinline__ int vec_pass(VecOp<T> op, const int bid)
 {
     constexpr int NW = RGM_THREADS / 32;      // QMAX * NW >= number of dot columns
     Small *s = op.sm;
@@ -646,7 +647,7 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op)
     const int nd = op.ndU + op.ndV + op.ndW + op.dnorm;
     const int ndc_ = op.dnorm ? nd - 1 : -1;          // index of the ||w||^2 column
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t r0 = (int64_t)blockIdx.x * op.rpb;
+    const int64_t r0 = (int64_t)bid * op.rpb;
     const int64_t r1 = min(op.n, r0 + op.rpb);
     double acc[QMAX];
 #pragma unroll
@@ -763,7 +764,7 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op)
     }
     // per-block partials
     {
-        double *pp = op.partials + blockIdx.x;
+        double *pp = op.partials + bid;
         const int64_t nbk = op.nblocks;
         warp_sums_store<QMAX>(acc, nd, [&](int c, double t) { pp[(int64_t)c * nbk] = t; });
     }
@@ -776,7 +777,7 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op)
     // the group sums and runs the scalar step.  No block waits for another.
     __shared__ double dsum[RGM_MAXDOTS];
     __shared__ FinScratch fin;
-    const int g = blockIdx.x / RGM_RGROUP, gb0 = g * RGM_RGROUP;
+    const int g = bid / RGM_RGROUP, gb0 = g * RGM_RGROUP;
     const int gn = min(RGM_RGROUP, op.nblocks - gb0);
     if (!last_of(op.gcount + g, (unsigned)gn)) return PASS_ARRIVED;
     const bool single = (op.ngroups == 1);
@@ -836,7 +837,7 @@ __global__ void __launch_bounds__(RGM_THREADS, 4) vec_kernel(VecOp<T> op)
     // programmatic dependent launch: blocks may be scheduled while the previous
     // pass finishes; nothing it wrote is read before this wait returns
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    vec_pass<T, QMAX, true>(op);
+    vec_pass<T, QMAX, true>(op, blockIdx.x);
 }
 
 // ---------------------------------------------------------------- persistent cycle
@@ -909,8 +910,10 @@ __device__ __forceinline__ bool grid_barrier_arrive(Small *s, unsigned *counter,
     return grid_barrier(PASS_ARRIVED, s, target);
 }
 
+// The Arnoldi steps of one cycle as run by block `bid` of the cycle's
+// c.pass[0].nblocks blocks.
 template <typename T, int QMAX>
-__global__ void __launch_bounds__(RGM_THREADS, 4) cycle_kernel(CycleOp<T> c)
+__device__ __forceinline__ void cycle_body(const CycleOp<T> &c, const int bid)
 {
     Small *s = c.pass[0].sm;
     unsigned gen = 0;
@@ -919,18 +922,45 @@ __global__ void __launch_bounds__(RGM_THREADS, 4) cycle_kernel(CycleOp<T> c)
         VecOp<T> op = c.pass[0];
         op.x = op.V + (int64_t)j * op.ldv;
         op.xscale = j;
-        if (!grid_barrier(vec_pass<T, QMAX, false>(op), s, ++gen)) return;
+        if (!grid_barrier(vec_pass<T, QMAX, false>(op, bid), s, ++gen)) return;
         VecOp<T> op1 = c.pass[1];
         op1.release_gen = gen + 1;
-        const int rc1 = vec_pass<T, QMAX, false>(op1);
+        const int rc1 = vec_pass<T, QMAX, false>(op1, bid);
         ++gen;
         // the finalising block released the others in mid scalar step
         if (rc1 != PASS_RELEASED && !grid_barrier(rc1, s, gen)) return;
         // plain update storing v_{j+1} (also after the last step: the augmented
         // relation orthogonalises against it)
-        vec_pass<T, QMAX, false>(c.pass[2]);
+        vec_pass<T, QMAX, false>(c.pass[2], bid);
         if (!grid_barrier_arrive(s, c.arrive, (unsigned)c.pass[2].nblocks, ++gen)) return;
     }
+}
+
+template <typename T, int QMAX>
+__global__ void __launch_bounds__(RGM_THREADS, 4) cycle_kernel(CycleOp<T> c)
+{
+    cycle_body<T, QMAX>(c, blockIdx.x);
+}
+
+// Batched cycles: the GMRES cycles of nsys independent systems in one
+// cooperative launch.  Blocks first[i] .. first[i+1]-1 run system i's cycle as
+// its blocks 0 .. first[i+1]-first[i]-1 (ops[i] carries that block count).  A
+// system's blocks meet only at that system's own barriers (its counters and
+// generation in its own Small), so each system ends its cycle at its own step
+// and the others carry on; co-residency of the whole grid (the cooperative
+// launch) keeps every barrier's blocks resident together.
+template <typename T, int QMAX>
+__global__ void __launch_bounds__(RGM_THREADS, 4)
+    batch_cycle_kernel(const CycleOp<T> *__restrict__ ops, const int *__restrict__ first, int nsys)
+{
+    int lo = 0, hi = nsys - 1;                  // the last i with first[i] <= blockIdx.x
+    const int b = (int)blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    cycle_body<T, QMAX>(ops[lo], b - first[lo]);
 }
 
 // Self-test of the bounded wait: no block ever finishes a pass last, so the
@@ -954,6 +984,15 @@ int cycle_capacity(const CycleOp<double> &c, int nd_max);
 int cycle_capacity(const CycleOp<float> &c, int nd_max);
 int launch_cycle(const CycleOp<double> &c, int nd_max, cudaStream_t st);
 int launch_cycle(const CycleOp<float> &c, int nd_max, cudaStream_t st);
+// batch_cycle_kernel: blocks that can be resident at once (0 if not
+// cooperatively launchable), and the launch of nblocks blocks over nsys
+// systems (ops and first in device memory, first[nsys] == nblocks).
+int batch_cycle_capacity(const CycleOp<double> *, int nd_max);
+int batch_cycle_capacity(const CycleOp<float> *, int nd_max);
+int launch_batch_cycle(const CycleOp<double> *ops, const int *first, int nsys, int nblocks, int nd_max,
+                       cudaStream_t st);
+int launch_batch_cycle(const CycleOp<float> *ops, const int *first, int nsys, int nblocks, int nd_max,
+                       cudaStream_t st);
 
 template <typename T, int Q>
 static cudaError_t launch_vec_pdl(const VecOp<T> &op, cudaStream_t st)
@@ -1023,6 +1062,62 @@ static cudaError_t launch_cycle_q(const CycleOp<T> &c, cudaStream_t st)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, cycle_kernel<T, Q>, c);
+}
+
+template <typename T, int Q>
+static int batch_capacity_q(int dev)
+{
+    int coop = 0, nsm = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_cycle_kernel<T, Q>, RGM_THREADS, 0) !=
+        cudaSuccess)
+        return 0;
+    return per_sm * nsm;
+}
+
+template <typename T>
+static int batch_capacity_impl(int nd_max)
+{
+    constexpr int NW = RGM_THREADS / 32;
+    constexpr int QBIG = (RGM_MAXDOTS + NW - 1) / NW;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    const int q = (nd_max + NW - 1) / NW;
+    if (q <= 4) return batch_capacity_q<T, 4>(dev);
+    if (q <= 8) return batch_capacity_q<T, 8>(dev);
+    return batch_capacity_q<T, QBIG>(dev);
+}
+
+template <typename T, int Q>
+static cudaError_t launch_batch_q(const CycleOp<T> *ops, const int *first, int nsys, int nblocks,
+                                  cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nblocks);
+    cfg.blockDim = dim3(RGM_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;   // all blocks resident, or the launch fails
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, batch_cycle_kernel<T, Q>, ops, first, nsys);
+}
+
+template <typename T>
+static int launch_batch_impl(const CycleOp<T> *ops, const int *first, int nsys, int nblocks, int nd_max,
+                             cudaStream_t st)
+{
+    constexpr int NW = RGM_THREADS / 32;
+    constexpr int QBIG = (RGM_MAXDOTS + NW - 1) / NW;
+    const int q = (nd_max + NW - 1) / NW;
+    cudaError_t e;
+    if (q <= 4) e = launch_batch_q<T, 4>(ops, first, nsys, nblocks, st);
+    else if (q <= 8) e = launch_batch_q<T, 8>(ops, first, nsys, nblocks, st);
+    else e = launch_batch_q<T, QBIG>(ops, first, nsys, nblocks, st);
+    return (int)e;
 }
 
 template <typename T>

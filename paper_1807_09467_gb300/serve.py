@@ -90,9 +90,10 @@ class Server:
     footprint."""
 
     def __init__(self, max_slots: int = 64, hbm_fraction: float = 0.8, precision: str = "fp32_ir",
-                 mode: str = "deflated"):
+                 mode: str = "deflated", coop: bool = False):
         import torch
         self.max_slots = max_slots
+        self.coop = coop
         free, _ = torch.cuda.mem_get_info()
         self.budget = int(hbm_fraction * free)
         self.precision = precision
@@ -136,7 +137,7 @@ class Server:
                 xs.append(x)
                 bs.append(b)
             torch.cuda.synchronize()
-            stats = batch_solve([lv.sol for lv in live], bs, xs)
+            stats = batch_solve([lv.sol for lv in live], bs, xs, coop=self.coop)
             for lv, x in zip(live, xs):
                 lv.sol.update_recycle_svd(x, want_k=False)
             torch.cuda.synchronize()

@@ -1,6 +1,8 @@
 """rgm_batch_solve: independent systems of different sizes and modes solved
 concurrently on their own streams give exactly what each gives alone (same
-code path, one launch per pass), and errors are reported per batch."""
+code path, one launch per pass), and errors are reported per batch.  With
+batched cycle launches (coop=True) each system converges as it does alone, to
+its solution up to the rounding of its dot-product partition."""
 import numpy as np
 import pytest
 
@@ -73,3 +75,96 @@ def test_batch_rejects_duplicates(rg):
     with pytest.raises(rg.RgmError):
         rg.batch_solve([s, s], [b, b], [x, x.clone()])
     assert rg.batch_solve([], [], []) == []
+
+
+# ------------------------------------------------------------ batched cycle launches
+def _make_auto(rg, sysdef, stream, precision="fp64"):
+    n, mode, k, rp, col, val, b, U = sysdef
+    s = rg.Solver(n, m=20, k=max(k, 1), mode=mode, rtol=1e-10, precision=precision,
+                  stream=stream.cuda_stream if stream is not None else None)
+    s.set_operator_csr(rp, col, val)
+    if U is not None:
+        s.set_recycle_space(U)
+    return s
+
+
+def _coop_round(rg, torch, defs, coop=True, precisions=None):
+    precisions = precisions or ["fp64"] * len(defs)
+    streams = [torch.cuda.Stream() for _ in defs]
+    solvers = [_make_auto(rg, d, st, p) for d, st, p in zip(defs, streams, precisions)]
+    bs = [torch.tensor(d[6], device="cuda") for d in defs]
+    xs = [torch.zeros(d[0], dtype=torch.float64, device="cuda") for d in defs]
+    torch.cuda.synchronize()
+    stats = rg.batch_solve(solvers, bs, xs, coop=coop)
+    torch.cuda.synchronize()
+    for s in solvers:
+        s.close()
+    return [x.cpu().numpy() for x in xs], stats
+
+
+def _alone(rg, torch, defs, precisions=None):
+    precisions = precisions or ["fp64"] * len(defs)
+    out = []
+    for d, p in zip(defs, precisions):
+        s = _make_auto(rg, d, None, p)
+        x = torch.zeros(d[0], dtype=torch.float64, device="cuda")
+        _, st = s.solve(torch.tensor(d[6], device="cuda"), x)
+        out.append((x.cpu().numpy(), st))
+        s.close()
+    return out
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_coop_batch_matches_alone(rg):
+    """Uneven systems (sizes, modes, recycle dimensions) whose cycles run as
+    batched cooperative launches: each converges as it does alone (its own
+    cycle kernel), to the same solution up to rounding, and a repeated batch
+    gives the same bits."""
+    import torch
+    defs = _systems()
+    alone = _alone(rg, torch, defs)
+    xs1, st1 = _coop_round(rg, torch, defs)
+    for (xa, sa), x, sb in zip(alone, xs1, st1):
+        assert sb["status"] == 0 and sb["true_relres"] <= 1e-10, sb
+        assert abs(sb["iters"] - sa["iters"]) <= 1, (sa, sb)
+        assert _rel(x, xa) <= 1e-12
+    xs2, st2 = _coop_round(rg, torch, defs)
+    for a, b, sa, sb in zip(xs1, xs2, st1, st2):
+        assert sa["iters"] == sb["iters"]
+        np.testing.assert_array_equal(a, b)
+
+
+def test_coop_batch_shares_the_resident_grid(rg):
+    """Four systems that each want the whole resident grid: each keeps one
+    block plus a share of the rest in proportion to its work, and still
+    converges to its own solution."""
+    import torch
+    defs = []
+    for i, (n, mode, k) in enumerate([(300001, "deflated", 8), (250000, "plain", 0),
+                                      (200003, "augmented", 4), (320000, "deflated", 6)]):
+        rp, col, val = synth.random_csr(n, 9, 700 + i, diag=6.0, min_per_row=2)
+        b = synth.random_vector(n, 710 + i)
+        U = np.linalg.qr(synth.random_matrix(n, k, 720 + i))[0] if k else None
+        defs.append((n, mode, k, rp, col, val, b, U))
+    alone = _alone(rg, torch, defs)
+    xs, st = _coop_round(rg, torch, defs)
+    for (xa, sa), x, sb in zip(alone, xs, st):
+        assert sb["status"] == 0 and sb["true_relres"] <= 1e-10, sb
+        assert abs(sb["iters"] - sa["iters"]) <= 1, (sa, sb)
+        assert _rel(x, xa) <= 1e-10
+
+
+def test_coop_flag_needs_one_precision(rg):
+    """Mixed precisions: the flag is ignored and the batch runs per pass on the
+    handles' streams, bit for bit as without it."""
+    import torch
+    defs = _systems()[:4]
+    prec = ["fp64", "fp32_ir", "fp64", "fp32_ir"]
+    xa, sa = _coop_round(rg, torch, defs, coop=False, precisions=prec)
+    xb, sb = _coop_round(rg, torch, defs, coop=True, precisions=prec)
+    for a, b, s1, s2 in zip(xa, xb, sa, sb):
+        assert s1["iters"] == s2["iters"] and s1["status"] == s2["status"]
+        np.testing.assert_array_equal(a, b)
