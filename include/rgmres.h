@@ -219,6 +219,21 @@ int rgm_update_recycle_svd(rgm_solver s, const double *x, int flags, int *k_used
  * count, within rounding otherwise; a batch repeats bit for bit. */
 int rgm_batch_solve(rgm_solver *handles, int nsys, const double *const *b, double *const *x, int flags,
                     rgm_stats *st);
+
+/* The block plan of one batched cycle launch of rgm_batch_solve(.., RGM_BATCH_COOP,
+ * ..), host only (no device work; for inspection and tests).  Inputs, one entry
+ * per system in the order of the launch: n rows, nnz stored entries, nd dot
+ * columns of an Arnoldi pass, want the blocks of the system's own partition;
+ * cap the co-resident blocks of the launch.  Systems run in waves of at most
+ * cap consecutive systems.  In a wave whose wants add up to more than cap,
+ * system i gets min(want[i], 1 + floor((cap - size) * w_i / sum w)) blocks,
+ * w = nnz + n * nd, each block a run of whole 256-row tiles.  Outputs (caller
+ * owned, nsys entries): blocks[i] the block count, rpb[i] its rows per block
+ * (0: the system keeps its own partition, blocks[i] == want[i]), wave[i] its
+ * wave.  Returns the number of waves, or RGM_E_ARG (nsys < 0, cap < 1, a
+ * missing array, n < 1, nnz < 0, nd < 0 or want < 1). */
+int rgm_batch_plan(int nsys, const int64_t *n, const int64_t *nnz, const int *nd, const int *want, int cap,
+                   int *blocks, int *rpb, int *wave);
 /* Singular values of the last window SVD, descending (up to `window` values);
  * *count receives how many are valid. */
 int rgm_get_singular_values(rgm_solver s, double *sigma, int *count);

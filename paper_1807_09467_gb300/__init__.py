@@ -237,6 +237,24 @@ def batch_solve(solvers, bs, xs, coop=False):
     return [_stats(st[i]) for i in range(n)]
 
 
+def batch_plan(n, nnz, nd, want, cap):
+    """rgm_batch_plan: the block plan of one batched cycle launch (host only).
+    Returns (blocks, rows per block (0: own partition), wave) per system and the
+    number of waves."""
+    L = _lib.load()
+    k = len(n)
+    assert len(nnz) == k and len(nd) == k and len(want) == k
+    n_ = np.ascontiguousarray(n, dtype=np.int64)
+    z_ = np.ascontiguousarray(nnz, dtype=np.int64)
+    d_ = np.ascontiguousarray(nd, dtype=np.int32)
+    w_ = np.ascontiguousarray(want, dtype=np.int32)
+    blocks, rpb, wave = (np.zeros(k, dtype=np.int32) for _ in range(3))
+    nw = L.rgm_batch_plan(k, n_.ctypes.data, z_.ctypes.data, d_.ctypes.data, w_.ctypes.data, int(cap),
+                          blocks.ctypes.data, rpb.ctypes.data, wave.ctypes.data)
+    check(min(nw, 0), "rgm_batch_plan")
+    return blocks, rpb, wave, nw
+
+
 def wait_selftest(limit_ns):
     """rgm_wait_selftest: two blocks wait at a grid barrier that is never
     released, with the given wait limit.  Returns (blocks that gave up, device

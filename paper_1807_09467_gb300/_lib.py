@@ -74,6 +74,8 @@ _SIGS = {
     "rgm_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(RgmStats)]),
     "rgm_batch_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
                                   C.c_void_p]),
+    "rgm_batch_plan": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                 C.c_void_p, C.c_void_p, C.c_void_p]),
     "rgm_update_recycle_svd": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "rgm_get_singular_values": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
     "rgm_reset_recycling": (C.c_int, [C.c_void_p]),

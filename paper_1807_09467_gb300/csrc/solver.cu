@@ -592,13 +592,47 @@ static const float *res_weights(rgm_solver, const Arnoldi<float> &) { return nul
 // One recycled GMRES solve of A x = b on the device buffers of `a`, with the
 // tolerance tol_abs already in Small.  mode: effective mode (PLAIN if no U).
 // Returns the number of cycles through *cycles.
+// Block plan of a batched cycle launch (rgm_batch_plan in include/rgmres.h):
+// waves of at most cap consecutive systems; a wave whose requests exceed cap
+// gives each system one block plus a share of the rest in proportion to its
+// work per Arnoldi step (nnz + n x dot columns), never more than it asked for,
+// its rows in whole tiles per block.  rpb[i] = 0: the system keeps its own
+// partition (blocks[i] = want[i]).  Returns the number of waves.
+static int batch_plan(int nsys, const int64_t *n, const int64_t *nnz, const int *nd, const int *want, int cap,
+                      int *blocks, int *rpb, int *wave)
+{
+    int nw = 0;
+    for (int w0 = 0; w0 < nsys; ++nw) {
+        const int w1 = std::min(nsys, w0 + cap);
+        int64_t asked = 0;
+        double wsum = 0.0;
+        for (int i = w0; i < w1; ++i) {
+            asked += want[i];
+            wsum += (double)nnz[i] + (double)n[i] * nd[i];
+        }
+        const int spare = cap - (w1 - w0);
+        for (int i = w0; i < w1; ++i) {
+            wave[i] = nw;
+            blocks[i] = want[i];
+            rpb[i] = 0;
+            if (asked <= cap) continue;
+            const double share = wsum > 0.0 ? ((double)nnz[i] + (double)n[i] * nd[i]) / wsum : 0.0;
+            const int nb = std::min(want[i], 1 + (int)std::floor(spare * share));
+            if (nb >= want[i]) continue;
+            const int64_t ntile = (n[i] + RGM_TILE - 1) / RGM_TILE;
+            const int64_t r = (ntile + nb - 1) / nb * RGM_TILE;
+            rpb[i] = (int)r;
+            blocks[i] = (int)((n[i] + r - 1) / r);
+        }
+        w0 = w1;
+    }
+    return nw;
+}
+
 // Launch one phase of a batched solve (the caller holds b.mu): the arrived
-// systems' cycles in waves of at most `cap` co-resident blocks.  A system asks
-// for its own block count; when the wave's requests exceed the capacity, each
-// system keeps one block plus a share of the rest in proportion to its work per
-// Arnoldi step (nnz + n x dot columns), never more than it asked for.  The
-// shares depend only on the systems in the wave, taken in index order, so a
-// batch repeats bit for bit.
+// systems' cycles in waves of at most `cap` co-resident blocks (batch_plan).
+// The plan depends only on the systems of the phase, taken in index order, so
+// a batch repeats bit for bit.
 template <typename T>
 static int batch_phase(BatchCycles &b)
 {
@@ -615,42 +649,35 @@ static int batch_phase(BatchCycles &b)
     }
     const int ns = (int)rq.size();
     b.h_ops.resize(sizeof(CycleOp<T>) * ns);
-    b.h_first.clear();
     CycleOp<T> *ops = reinterpret_cast<CycleOp<T> *>(b.h_ops.data());
+    std::vector<int64_t> vn(ns), vnnz(ns);
+    std::vector<int> vnd(ns), want(ns), nblk(ns), rpb(ns), wave(ns);
+    for (int i = 0; i < ns; ++i) {
+        ops[i] = *static_cast<const CycleOp<T> *>(rq[i].cyc);
+        vn[i] = rq[i].s->n;
+        vnnz[i] = rq[i].s->nnz;
+        vnd[i] = rq[i].nd;
+        want[i] = ops[i].pass[0].nblocks;
+    }
+    batch_plan(ns, vn.data(), vnnz.data(), vnd.data(), want.data(), cap, nblk.data(), rpb.data(), wave.data());
     struct Wave { int s0, s1, f0, nblocks; };
     std::vector<Wave> waves;
-    for (int w0 = 0; w0 < ns;) {
-        const int w1 = std::min(ns, w0 + cap);
-        int64_t want = 0;
-        double wsum = 0.0;
-        for (int i = w0; i < w1; ++i) {
-            ops[i] = *static_cast<const CycleOp<T> *>(rq[i].cyc);
-            want += ops[i].pass[0].nblocks;
-            wsum += (double)rq[i].s->nnz + (double)rq[i].s->n * rq[i].nd;
+    b.h_first.clear();
+    for (int i = 0; i < ns; ++i) {
+        if (i == 0 || wave[i] != wave[i - 1]) {
+            waves.push_back({i, i, (int)b.h_first.size(), 0});
+            b.h_first.push_back(0);
         }
-        const int spare = cap - (w1 - w0);
-        Wave wv{w0, w1, (int)b.h_first.size(), 0};
-        b.h_first.push_back(0);
-        for (int i = w0; i < w1; ++i) {
-            rgm_solver si = rq[i].s;
-            int nb = ops[i].pass[0].nblocks;
-            if (want > cap) {
-                const double share = ((double)si->nnz + (double)si->n * rq[i].nd) / wsum;
-                nb = std::min(nb, 1 + (int)std::floor(spare * share));
-            }
-            const int64_t ntile = (si->n + RGM_TILE - 1) / RGM_TILE;
-            const int64_t rpb = (ntile + nb - 1) / nb * RGM_TILE;
-            const int nblk = (int)((si->n + rpb - 1) / rpb);
+        if (rpb[i] > 0)
             for (VecOp<T> &op : ops[i].pass) {
-                op.rpb = (int)rpb;
-                op.nblocks = nblk;
-                op.ngroups = (nblk + RGM_RGROUP - 1) / RGM_RGROUP;
+                op.rpb = rpb[i];
+                op.nblocks = nblk[i];
+                op.ngroups = (nblk[i] + RGM_RGROUP - 1) / RGM_RGROUP;
             }
-            wv.nblocks += nblk;
-            b.h_first.push_back(wv.nblocks);
-        }
-        waves.push_back(wv);
-        w0 = w1;
+        Wave &wv = waves.back();
+        wv.s1 = i + 1;
+        wv.nblocks += nblk[i];
+        b.h_first.push_back(wv.nblocks);
     }
     CK(cudaMemcpyAsync(b.d_ops, ops, sizeof(CycleOp<T>) * ns, cudaMemcpyHostToDevice, b.st));
     CK(cudaMemcpyAsync(b.d_first, b.h_first.data(), sizeof(int) * b.h_first.size(), cudaMemcpyHostToDevice,
@@ -1370,6 +1397,16 @@ int rgm_solve(rgm_solver s, const double *b, double *x, int flags, rgm_stats *st
     CK(cudaMemcpyAsync(x, s->x, sizeof(double) * s->n, kind_out(flags), s->st));
     CK(cudaStreamSynchronize(s->st));
     return rc;
+}
+
+int rgm_batch_plan(int nsys, const int64_t *n, const int64_t *nnz, const int *nd, const int *want, int cap,
+                   int *blocks, int *rpb, int *wave)
+{
+    if (nsys < 0 || cap < 1 || (nsys > 0 && (!n || !nnz || !nd || !want || !blocks || !rpb || !wave)))
+        return RGM_E_ARG;
+    for (int i = 0; i < nsys; ++i)
+        if (n[i] < 1 || nnz[i] < 0 || nd[i] < 0 || want[i] < 1) return RGM_E_ARG;
+    return batch_plan(nsys, n, nnz, nd, want, cap, blocks, rpb, wave);
 }
 
 int rgm_batch_solve(rgm_solver *handles, int nsys, const double *const *b, double *const *x, int flags,
