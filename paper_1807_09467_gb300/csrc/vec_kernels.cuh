@@ -936,8 +936,10 @@ __device__ __forceinline__ void cycle_body(const CycleOp<T> &c, const int bid)
     }
 }
 
-template <typename T, int QMAX>
-__global__ void __launch_bounds__(RGM_THREADS, 4) cycle_kernel(CycleOp<T> c)
+// MINB: resident blocks per SM the build guarantees; grids of at most two
+// blocks per SM take the variant with twice the registers per thread.
+template <typename T, int QMAX, int MINB>
+__global__ void __launch_bounds__(RGM_THREADS, MINB) cycle_kernel(CycleOp<T> c)
 {
     cycle_body<T, QMAX>(c, blockIdx.x);
 }
@@ -1023,13 +1025,13 @@ static int launch_vec_impl(const VecOp<T> &op, int nd_max, cudaStream_t st)
     return (int)e;          // cudaSuccess == 0
 }
 
-template <typename T, int Q>
+template <typename T, int Q, int MINB>
 static int cycle_capacity_q(int dev)
 {
     int coop = 0, nsm = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cycle_kernel<T, Q>, RGM_THREADS, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cycle_kernel<T, Q, MINB>, RGM_THREADS, 0) !=
         cudaSuccess)
         return 0;
     return per_sm * nsm;
@@ -1043,14 +1045,21 @@ static int cycle_capacity_impl(int nd_max)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     const int q = (nd_max + NW - 1) / NW;
-    if (q <= 4) return cycle_capacity_q<T, 4>(dev);
-    if (q <= 8) return cycle_capacity_q<T, 8>(dev);
-    return cycle_capacity_q<T, QBIG>(dev);
+    if (q <= 4) return cycle_capacity_q<T, 4, 4>(dev);
+    if (q <= 8) return cycle_capacity_q<T, 8, 4>(dev);
+    return cycle_capacity_q<T, QBIG, 4>(dev);
 }
 
 template <typename T, int Q>
 static cudaError_t launch_cycle_q(const CycleOp<T> &c, cudaStream_t st)
 {
+    // the wider-register variant when its residency holds the whole grid
+    static int cap2 = -1;
+    if (cap2 < 0) {
+        int dev = 0;
+        cap2 = (cudaGetDevice(&dev) == cudaSuccess) ? cycle_capacity_q<T, Q, 2>(dev) : 0;
+    }
+    const bool wide = c.pass[0].nblocks <= cap2;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(c.pass[0].nblocks);
     cfg.blockDim = dim3(RGM_THREADS);
@@ -1061,7 +1070,8 @@ static cudaError_t launch_cycle_q(const CycleOp<T> &c, cudaStream_t st)
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, cycle_kernel<T, Q>, c);
+    return wide ? cudaLaunchKernelEx(&cfg, cycle_kernel<T, Q, 2>, c)
+                : cudaLaunchKernelEx(&cfg, cycle_kernel<T, Q, 4>, c);
 }
 
 template <typename T, int Q>
