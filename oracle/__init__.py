@@ -67,7 +67,8 @@ class _SeqCfg(C.Structure):
                 ("select_smallest", C.c_int), ("rtol", C.c_double), ("maxit", C.c_int),
                 ("rel_drop", C.c_double), ("guess", C.c_int), ("velocity", C.c_int),
                 ("nmodes", C.c_int), ("fC", C.c_double), ("forcing", C.c_void_p),
-                ("proj", C.c_int), ("precond", C.c_int)]
+                ("proj", C.c_int), ("precond", C.c_int), ("precision", C.c_int),
+                ("inner_rtol", C.c_double), ("inner_cycles", C.c_int), ("max_refinements", C.c_int)]
 
 
 SCALAR_FN = C.CFUNCTYPE(C.c_double, C.c_double, C.c_double, C.c_void_p)
@@ -123,7 +124,7 @@ def lib():
                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
             L.orc_sequence_timed.argtypes = [C.POINTER(_SeqCfg), C.c_void_p, C.c_void_p, C.c_void_p,
                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                             C.c_void_p]
+                                             C.c_void_p, C.c_void_p]
         return _lib
 
 
@@ -321,7 +322,7 @@ def gmres(A: Csr, b, x_in=None, U=None, mode=PLAIN, m=30, rtol=1e-10, maxit=1000
 
 
 def gmres_ir(A: Csr, b, x_in=None, U=None, mode=PLAIN, m=30, rtol=1e-8, maxit=20000,
-             inner_rtol=1e-5, inner_cycles=2, max_refinements=50, proj=PROJ_OBLIQUE):
+             inner_rtol=1e-4, inner_cycles=2, max_refinements=50, proj=PROJ_OBLIQUE):
     b = _f64(b)
     x = _f64(x_in).copy() if x_in is not None else np.zeros(A.n)
     k, Uc = 0, None
@@ -400,8 +401,10 @@ def recycle_from_window(X, k, select_smallest=False, rel_drop=1e-7):
 # ---------------------------------------------------------------- Algorithm 1 (sequence.c)
 def sequence(p, N, eps, dt, beta, steps, u0, mode=PLAIN, m=30, k=8, window=16, ell=1,
              rtol=1e-10, maxit=20000, select_smallest=False, rel_drop=1e-7, keep_all=False,
-             guess=0, velocity=0, forcing=None, forcing_C=0.1, proj=PROJ_OBLIQUE, precond=0):
-    """velocity 1 / forcing (steps x nmodes coefficients): Sec. 6.1's benchmark."""
+             guess=0, velocity=0, forcing=None, forcing_C=0.1, proj=PROJ_OBLIQUE, precond=0,
+             precision=0, inner_rtol=1e-4, inner_cycles=2, max_refinements=50):
+    """velocity 1 / forcing (steps x nmodes coefficients): Sec. 6.1's benchmark.
+    precision 1: every solve is GMRES-IR (gmres_ir) with the inner parameters given."""
     n = ndofs(p, N)
     fc = np.ascontiguousarray(forcing, dtype=np.float64) if forcing is not None else None
     nmodes = fc.shape[1] if fc is not None else 0
@@ -409,7 +412,8 @@ def sequence(p, N, eps, dt, beta, steps, u0, mode=PLAIN, m=30, k=8, window=16, e
         assert fc.shape[0] >= steps
     cfg = _SeqCfg(p, N, eps, dt, beta[0], beta[1], steps, mode, m, k, window, ell,
                   int(select_smallest), rtol, maxit, rel_drop, int(guess), int(velocity), nmodes,
-                  forcing_C, _p(fc), int(proj), int(precond))
+                  forcing_C, _p(fc), int(proj), int(precond), int(precision), inner_rtol,
+                  int(inner_cycles), int(max_refinements))
     u0 = _f64(u0)
     x_all = np.zeros((n, steps), order="F") if keep_all else None
     x_final = np.zeros(n)
@@ -418,8 +422,9 @@ def sequence(p, N, eps, dt, beta, steps, u0, mode=PLAIN, m=30, k=8, window=16, e
     relres = np.zeros(steps)
     status = np.zeros(steps, dtype=np.int32)
     secs = np.zeros(steps)
+    nref = np.zeros(steps, dtype=np.int32)
     rc = lib().orc_sequence_timed(C.byref(cfg), _p(u0), _p(x_all), _p(x_final), _p(iters),
-                                  _p(k_used), _p(relres), _p(status), _p(secs))
+                                  _p(k_used), _p(relres), _p(status), _p(secs), _p(nref))
     assert rc == 0, rc
     return dict(x_final=x_final, x_all=x_all, iters=iters, k_used=k_used, relres=relres,
-                status=status, step_seconds=secs)
+                status=status, step_seconds=secs, refinements=nref)

@@ -592,6 +592,7 @@ int orc_gmres_ir(const orc_csr *A, const double *b, double *x, const double *U, 
         rf_norm = sqrt(rf_norm);
         memset(d, 0, sizeof(double) * n);
         c.tol_abs = inner_rtol * rf_norm;
+        c.tol_in = c.tol_abs;       /* the Givens estimate ends a cycle early, as in every solve */
         c.maxit = o->maxit - iters;
         int it, cy;
         double rr;

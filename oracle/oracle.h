@@ -190,16 +190,22 @@ typedef struct {
     const double *forcing;  /* steps x nmodes coefficients c_j, step-major     */
     int proj;          /* ORC_PROJ_* of the solves                                */
     int precond;       /* ORC_PRECOND_* of the solves                             */
+    int precision;     /* 0: FP64 solves; 1: GMRES-IR (orc_gmres_ir) to rtol       */
+    double inner_rtol; /* GMRES-IR: inner tolerance relative to the outer residual */
+    int inner_cycles;  /* GMRES-IR: cycles per refinement                          */
+    int max_refinements; /* GMRES-IR: cap on refinement steps                      */
 } orc_seq_cfg;
 /* u0: initial nodal field.  x_all (optional): n x steps solutions.
  * iters/k_used/status (length steps) and relres (length steps) are per step. */
 int orc_sequence(const orc_seq_cfg *cfg, const double *u0, double *x_all, double *x_final,
                  int *iters, int *k_used, double *relres, int *status);
 /* Same, also returning the wall time of each step (assembly + solve + window
- * update, seconds, CLOCK_MONOTONIC) in step_seconds (length steps). */
+ * update, seconds, CLOCK_MONOTONIC) in step_seconds (length steps) and, for
+ * GMRES-IR sequences, the refinement steps of each solve in refinements (both
+ * optional). */
 int orc_sequence_timed(const orc_seq_cfg *cfg, const double *u0, double *x_all, double *x_final,
                        int *iters, int *k_used, double *relres, int *status,
-                       double *step_seconds);
+                       double *step_seconds, int *refinements);
 
 #ifdef __cplusplus
 }

@@ -12,6 +12,9 @@
  * singular values below rel_drop * sigma_1 are dropped; step 1 runs plain;
  * with a recycle space the solve starts from x_in = 0 (so the initial guess is
  * the paper's x0 = U E^{-1} U^T b), without one from the previous solution.
+ * With cfg->precision = 1 every solve is the mixed-precision iterative
+ * refinement of orc_gmres_ir (binary32 inner recycled GMRES, FP64 residual and
+ * update) with the same recycle space.
  * With cfg->guess = g > 0, x_in is instead the extrapolation of order g
  * (Sec. 4.1) once g+1 solutions are stored (the window must hold them).
  * cfg->velocity / nmodes select Sec. 6.1's own benchmark (cellular velocity,
@@ -32,12 +35,12 @@ static double now_s(void)
 int orc_sequence(const orc_seq_cfg *cfg, const double *u0, double *x_all, double *x_final,
                  int *iters, int *k_used, double *relres, int *status)
 {
-    return orc_sequence_timed(cfg, u0, x_all, x_final, iters, k_used, relres, status, NULL);
+    return orc_sequence_timed(cfg, u0, x_all, x_final, iters, k_used, relres, status, NULL, NULL);
 }
 
 int orc_sequence_timed(const orc_seq_cfg *cfg, const double *u0, double *x_all, double *x_final,
                        int *iters, int *k_used, double *relres, int *status,
-                       double *step_seconds)
+                       double *step_seconds, int *refinements)
 {
     if (!cfg || !u0 || cfg->steps < 1 || cfg->window < 1 || cfg->nmodes < 0 ||
         (cfg->nmodes > 0 && !cfg->forcing))
@@ -92,7 +95,13 @@ int orc_sequence_timed(const orc_seq_cfg *cfg, const double *u0, double *x_all, 
         }
         orc_opts o = {cfg->mode, cfg->m, cfg->rtol, cfg->maxit, 0, cfg->proj, cfg->precond};
         orc_stats st;
-        int s = orc_gmres(&A, b, x, use_u ? U : NULL, use_u ? k_eff : 0, &o, &st, NULL, 0);
+        int s, nref = 0;
+        if (cfg->precision == 1)
+            s = orc_gmres_ir(&A, b, x, use_u ? U : NULL, use_u ? k_eff : 0, &o, cfg->inner_rtol,
+                             cfg->inner_cycles, cfg->max_refinements, &st, &nref);
+        else
+            s = orc_gmres(&A, b, x, use_u ? U : NULL, use_u ? k_eff : 0, &o, &st, NULL, 0);
+        if (refinements) refinements[i - 1] = nref;
         if (s < 0) { rc = s; break; }
         if (iters) iters[i - 1] = st.iters;
         if (k_used) k_used[i - 1] = st.k_used;
