@@ -5,10 +5,12 @@ One bench step = one time step of Algorithm 1 on the device: new operator values
 and right-hand side (assembled on the device from the previous solution, outside
 the timed segment), then, timed with CUDA events on the solver's stream,
 rgm_set_operator_values + rgm_solve + rgm_update_recycle_svd.  L2 is flushed
-(256 MiB write) before every timed segment.  Default workload: Q2 elements on a
-128 x 128 grid (66,049 dofs), eps 0.01, dt 0.005, FP64 GMRES(30), rtol 1e-10,
-k = 8 recycle vectors from a window of 16; the headline mode is the deflated
-oblique method, with plain and augmented GMRES measured on the same sequence.
+(256 MiB write) before every timed segment.  Default workload: Q4 elements on a
+256 x 256 grid (1,050,625 dofs, 37.5 M nonzeros), eps 0.002, dt 0.002,
+GMRES(40), k = 12 recycle vectors from a window of 24, true residual 1e-8; the
+headline is deflated GMRES-IR (binary32 Arnoldi and projections inside a
+binary64 refinement loop), with plain GMRES-IR and binary64 deflated, plain and
+augmented GMRES measured on the same sequence.
 
 Multi-GPU (torchrun): independent sequences per rank (replicas, no collective
 on the data path); value = all ranks' solves / slowest rank's time.
@@ -40,7 +42,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="q2_128x128_eps0.01_dt0.005",
+    ap.add_argument("--workload", default="q4_256x256_eps0.002_dt0.002",
                     help="a single-sequence workload, batch64 (64 uneven sequences solved together), "
                          "serve (a Poisson stream of sequences, continuous batching) or table2 "
                          "(extrapolated vs projection initial guesses on the paper's nu = 0.1 benchmark)")
@@ -50,7 +52,7 @@ def parse():
     ap.add_argument("--svd-interval", type=int, default=None, help="override the workload's SVD interval")
     ap.add_argument("--precond", default=None, choices=["none", "jacobi"],
                     help="override the workload's preconditioner")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_ir"])
+    ap.add_argument("--precision", default="fp32_ir", choices=["fp64", "fp32_ir"])
     ap.add_argument("--cpu-steps", type=int, default=0, help="oracle steps for cpu_baseline (0: auto)")
     ap.add_argument("--quick", action="store_true", help="skip e2e, cpu baseline and side modes")
     ap.add_argument("--serve-count", type=int, default=128, help="serve: number of sequences")
@@ -211,8 +213,9 @@ def workload_seq(synth, w, index, steps):
 
 # ------------------------------------------------------------------ our arm
 def run_sequence(rg, torch, w, seq, mode, precision, warmup, steps, profile=False, keep=None,
-                 flush=None, stream=None, guess=0):
-    """Runs warmup + steps time steps on the device; returns timing and stats."""
+                 flush=None, stream=None, guess=0, keep_x=0):
+    """Runs warmup + steps time steps on the device; returns timing and stats
+    (and the solutions of the first keep_x steps, on the host)."""
     import numpy as np
     a8, beta, forcing = seq
     dev = torch.device("cuda")
@@ -231,7 +234,7 @@ def run_sequence(rg, torch, w, seq, mode, precision, warmup, steps, profile=Fals
           for _ in range(warmup + steps)]
     eva = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(warmup + steps)]
-    its, res, kus = [], [], []
+    its, res, kus, refs, xs = [], [], [], [], []
     prof = None
     for i in range(warmup + steps):
         if i == warmup and profile:
@@ -258,6 +261,9 @@ def run_sequence(rg, torch, w, seq, mode, precision, warmup, steps, profile=Fals
         its.append(st["iters"])
         res.append(st["true_relres"])
         kus.append(st["k_used"])
+        refs.append(st["refinements"])
+        if i < keep_x:
+            xs.append(x.cpu().numpy())
     torch.cuda.synchronize()
     if profile:
         prof = solver.profile_read()
@@ -267,7 +273,8 @@ def run_sequence(rg, torch, w, seq, mode, precision, warmup, steps, profile=Fals
     solver.close()
     fe.close()
     return dict(seg_ms=seg[warmup:], asm_ms=asm[warmup:], iters=its, relres=res, k_used=kus,
-                prof=prof, n=fe.n, nnz=len(col), u_final=u.cpu().numpy())
+                refinements=refs, x_first=xs, prof=prof, n=fe.n, nnz=len(col),
+                u_final=u.cpu().numpy())
 
 
 def run_e2e(rg, np, w, seq, mode, precision, warmup, steps, inputs, torch):
@@ -310,6 +317,54 @@ def run_e2e(rg, np, w, seq, mode, precision, warmup, steps, inputs, torch):
 LAUNCH_POLICY = ["auto"]
 
 
+def fp64_peak_tflops(torch):
+    """Measured binary64 throughput of this GPU: cuBLAS DGEMM (torch.matmul on
+    float64, 4096^3, 2 n^3 flops), best of 5 after 2 warm-ups, CUDA events."""
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    best = float("inf")
+    for i in range(7):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        if i >= 2:
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+    del a, b
+    return 2.0 * n ** 3 / best / 1e12
+
+
+def cycle_roofline(prof, w, precision, hbm_peak, fp64_peak):
+    """Roofline of the dominant kernel kind of a profiled pass.  Bytes per
+    launch are the algorithmic bytes the library books (for the cycle kernel:
+    B_j = (e + 4) nnz + e n (j + 2 k + 4) summed over the steps of the launch),
+    time the kind's CUDA-event duration on the solver's stream."""
+    kinds = {k: v for k, v in prof.items() if v["launches"] > 0}
+    dom = max(kinds, key=lambda k: kinds[k]["ms"])
+    d = kinds[dom]
+    t = d["ms"] / d["launches"] * 1e-3
+    gbs = d["bytes"] / d["launches"] / t / 1e9
+    tfl = d["flops"] / d["launches"] / t / 1e12
+    hbm = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+           "frac": round(gbs / hbm_peak, 4),
+           "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs, copy)"}
+    alu = {"bound": "alu", "achieved": round(tfl, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+           "frac": round(tfl / fp64_peak, 4),
+           "peak_source": "of measured (cuBLAS DGEMM in this run, the binary64 pipe)"}
+    head = hbm if precision == "fp32_ir" else alu
+    other = alu if precision == "fp32_ir" else hbm
+    out = dict(head)
+    out.update({"kernel": dom, "launches": d["launches"], "ms_per_launch": round(t * 1e3, 5),
+                "arnoldi_steps_per_launch": round(d["units"] / d["launches"], 3),
+                "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
+                "algorithmic_flops_per_launch": d["flops"] / d["launches"],
+                "traffic": traffic_record(w.name, precision, dom),
+                "second_bound": other})
+    return out, kinds
+
+
 def ours(args):
     LAUNCH_POLICY[0] = args.launch_policy
     import numpy as np
@@ -332,6 +387,7 @@ def ours(args):
     w = workload_of(synth, args)
     seq = workload_seq(synth, w, replica_sequence(rank), max(w.steps, args.warmup + args.steps))
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB
+    S = cpu_sample_steps(args, w)
 
     keep = [] if (rank == 0 and not args.quick) else None
     if ws > 1:
@@ -341,7 +397,7 @@ def ours(args):
     clk.start()
     t_wall0 = time.perf_counter()
     main = run_sequence(rg, torch, w, seq, args.mode, args.precision, args.warmup, args.steps,
-                        profile=False, keep=keep, flush=flush)
+                        profile=False, keep=keep, flush=flush, keep_x=0 if args.quick else S)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     clocks = clk.stop()
@@ -367,32 +423,15 @@ def ours(args):
         return
     prof, launches = profd["prof"]
     n, nnz = main["n"], main["nnz"]
-    # dominant kernel by device time
-    kinds = {k: v for k, v in prof.items() if v["launches"] > 0}
-    tot_ms = sum(v["ms"] for v in kinds.values())
-    dom = max(kinds, key=lambda k: kinds[k]["ms"])
-    d = kinds[dom]
-    per_launch_ms = d["ms"] / d["launches"]
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6690.5)
-    if args.precision == "fp64":
-        achieved = d["flops"] / d["launches"] / (per_launch_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
-                "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
-                "peak_source": "FP64 FMA pipe, 152 SMs x 2 FMA/clk x 2.07 GHz (derived)",
-                "achieved_gbs": round(d["bytes"] / d["launches"] / (per_launch_ms * 1e-3) / 1e9, 1)}
-    else:
-        achieved = d["bytes"] / d["launches"] / (per_launch_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved / hbm_peak, 4), "peak_source": "of measured (MEASURED_PEAKS hbm_gbs)"}
-    roof.update({"kernel": dom, "launches": d["launches"], "ms_per_launch": round(per_launch_ms, 5),
-                 "algorithmic_flops_per_launch": d["flops"] / d["launches"],
-                 "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
-                 "traffic": traffic_record(w.name, args.precision, dom)})
+    fp64_peak = fp64_peak_tflops(torch)
+    roof, kinds = cycle_roofline(prof, w, args.precision, hbm_peak, fp64_peak)
+    tot_ms = sum(v["ms"] for v in kinds.values())
     kernel_share = {k: {"ms": round(v["ms"], 3), "share": round(v["ms"] / tot_ms, 4),
                         "launches": v["launches"]} for k, v in kinds.items()}
     seg = main["seg_ms"]
-    all_bytes = sum(v["bytes"] for v in kinds.values())
+    rtol = w.rtol if args.precision == "fp64" else 1e-8
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": ws, "steps": K,
         "warmup": args.warmup, "ms_per_step": round(tot_sec * 1e3 / K, 4), "higher_is_better": True,
@@ -403,38 +442,46 @@ def ours(args):
                    "velocity": w.velocity, "forcing_modes": w.forcing_modes, "u0": w.u0,
                    "precond": w.precond,
                    "precision": args.precision, "launch_policy": args.launch_policy,
-                   "rtol": w.rtol if args.precision == "fp64" else 1e-8,
+                   "rtol": rtol, "true_residual": "||b - A x|| / ||b|| in binary64",
                    "l2": "flushed (256 MiB write) before every timed step",
                    "parallelism": "replicas" if ws > 1 else "single"},
-        "hbm_gbs_algorithmic": round(all_bytes / (tot_ms * 1e-3) / 1e9, 1),
         "latency_ms": {"p50": round(float(np.percentile(seg, 50)), 4),
                        "p99": round(float(np.percentile(seg, 99)), 4)},
         "iterations": iters_stats(main["iters"][args.warmup:]),
+        "refinements": iters_stats(main["refinements"][args.warmup:]),
         "max_true_relres": max(main["relres"][args.warmup:]),
         "assembly_ms_per_step": round(statistics.mean(main["asm_ms"]), 4),
         "roofline": roof, "kernels": kernel_share, "gpu_launches": int(launches),
         "profiled_pass_ms_per_step": round(statistics.mean(profd["seg_ms"]), 4),
+        "fp64_peak_tflops_measured": round(fp64_peak, 4),
         "clocks": clocks, "wall_s": round(t_wall, 3),
     }
     if not args.quick:
-        # recycled vs plain on the same sequence
+        # recycled vs plain and mixed vs binary64 on the same sequence
         side = {}
-        for md in ("plain", "augmented", "deflated"):
-            if md == args.mode:
+        for prec, md in (("fp32_ir", "deflated"), ("fp32_ir", "plain"), ("fp64", "deflated"),
+                         ("fp64", "plain"), ("fp64", "augmented")):
+            if (prec, md) == (args.precision, args.mode):
                 r = main
             else:
-                r = run_sequence(rg, torch, w, seq, md, args.precision, args.warmup, K, flush=flush)
-            side[md] = {"solves_per_s": round(K / (sum(r["seg_ms"]) / 1e3), 3),
-                        "ms_per_step": round(statistics.mean(r["seg_ms"]), 4),
-                        "iterations": iters_stats(r["iters"][args.warmup:]),
-                        "max_true_relres": max(r["relres"][args.warmup:])}
+                r = run_sequence(rg, torch, w, seq, md, prec, args.warmup, K, flush=flush)
+            side[f"{prec}/{md}"] = {"solves_per_s": round(K / (sum(r["seg_ms"]) / 1e3), 3),
+                                    "ms_per_step": round(statistics.mean(r["seg_ms"]), 4),
+                                    "iterations": iters_stats(r["iters"][args.warmup:]),
+                                    "max_true_relres": max(r["relres"][args.warmup:])}
         out["modes"] = side
+        # the binary64 deflated cycle kernel on the roofline too (binary64 pipe)
+        other_prec = "fp64" if args.precision == "fp32_ir" else "fp32_ir"
+        r64 = run_sequence(rg, torch, w, seq, args.mode, other_prec, args.warmup, min(K, 10),
+                           profile=True, flush=flush)
+        out["roofline_" + other_prec], _ = cycle_roofline(r64["prof"][0], w, other_prec, hbm_peak,
+                                                          fp64_peak)
         # end to end through the public API with host buffers
         e = run_e2e(rg, np, w, seq, args.mode, args.precision, args.warmup, K, keep, torch)
         out["e2e"] = {"value": round(K / sum(e["sec"]), 3), "unit": "solves/s",
                       "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"]}
         # CPU baseline: the oracle on a bounded sample of the same sequence
-        out["cpu_baseline"], out["parity"] = cpu_baseline(args, w, seq, main, np)
+        out["cpu_baseline"], out["parity"] = cpu_baseline(args, w, seq, main, np, S)
     print(json.dumps(out))
     if ws > 1:
         dist.destroy_process_group()
@@ -613,22 +660,33 @@ def run_table2(args):
     print(json.dumps(out))
 
 
-def cpu_baseline(args, w, seq, main, np):
+def cpu_sample_steps(args, w):
+    """Oracle time steps that make about 10-30 s of CPU work: high-order
+    assembly costs (p+1)^6 per cell, a 1 M-dof step about 20 s."""
+    return args.cpu_steps or min(w.steps, 2 if w.p > 4 else 30 if w.n < 200000 else 2)
+
+
+def oracle_sequence(orc, w, seq_i, S, mode, precision, keep_all=False):
+    a8, beta, forcing = seq_i
+    import numpy as np
+    u0 = np.zeros(w.n) if w.u0 == "zero" else orc.u0_field(w.p, w.N, a8)
+    rtol = w.rtol if precision == "fp64" else 1e-8
+    return orc.sequence(w.p, w.N, w.eps, w.dt, beta, S, u0, mode=mode, m=w.m, k=w.k,
+                        window=w.window, ell=w.ell, rtol=rtol, keep_all=keep_all,
+                        velocity=int(w.velocity == "cellular"), forcing=forcing,
+                        forcing_C=w.forcing_C, precond=int(w.precond == "jacobi"),
+                        precision=int(precision == "fp32_ir"), inner_rtol=1e-4, inner_cycles=2)
+
+
+def cpu_baseline(args, w, seq, main, np, S):
     import oracle as orc
     orc.build()
-    a8, beta, forcing = seq
-    # about 10-30 s of oracle work: high-order assembly costs (p+1)^6 per cell
-    S = args.cpu_steps or min(w.steps, 2 if w.p > 4 else 30 if w.n < 200000 else 3)
-    u0 = np.zeros(w.n) if w.u0 == "zero" else orc.u0_field(w.p, w.N, a8)
-    mode = {"plain": 0, "deflated": 1, "augmented": 2}[args.mode]
-    rtol = w.rtol if args.precision == "fp64" else 1e-8
-    r = orc.sequence(w.p, w.N, w.eps, w.dt, beta, S, u0, mode=mode, m=w.m, k=w.k,
-                     window=w.window, ell=w.ell, rtol=rtol, keep_all=False,
-                     velocity=int(w.velocity == "cellular"), forcing=forcing,
-                     forcing_C=w.forcing_C, precond=int(w.precond == "jacobi"))
+    mode = {"plain": 0, "deflated": 1, "augmented": 2, "guess": 3}[args.mode]
+    r = oracle_sequence(orc, w, seq, S, mode, args.precision, keep_all=True)
     secs = r["step_seconds"]
+    kind = "GMRES-IR (binary32 inner storage, binary64 residual)" if args.precision == "fp32_ir" else "binary64"
     cb = {"value": round(S / float(secs.sum()), 4), "unit": "solves/s", "cores": 1, "kind": "oracle",
-          "sample": f"first {S} time steps of the same sequence ({w.name}, {args.mode}), "
+          "sample": f"first {S} time steps of the same sequence ({w.name}, {args.mode}, {kind}), "
                     f"FE assembly + solve + window SVD per step, single thread"}
     # the same oracle on every host core: independent sequences (their own
     # seeded draws), one per thread; the C oracle holds no global state and
@@ -637,29 +695,37 @@ def cpu_baseline(args, w, seq, main, np):
     import synth
     from concurrent.futures import ThreadPoolExecutor
     ncores = os.cpu_count() or 1
+    S1 = 1 if w.n >= 200000 else S
 
     def one(idx):
-        a8_i, beta_i, forcing_i = workload_seq(synth, w, 1000 + idx, S)
-        u0_i = np.zeros(w.n) if w.u0 == "zero" else orc.u0_field(w.p, w.N, a8_i)
-        ri = orc.sequence(w.p, w.N, w.eps, w.dt, beta_i, S, u0_i, mode=mode, m=w.m, k=w.k,
-                          window=w.window, ell=w.ell, rtol=rtol, keep_all=False,
-                          velocity=int(w.velocity == "cellular"), forcing=forcing_i,
-                          forcing_C=w.forcing_C, precond=int(w.precond == "jacobi"))
+        ri = oracle_sequence(orc, w, workload_seq(synth, w, 1000 + idx, S1), S1, mode, args.precision)
         return int(ri["iters"].sum())
 
     t0 = time.perf_counter()
     with ThreadPoolExecutor(max_workers=ncores) as ex:
         list(ex.map(one, range(ncores)))
     wall = time.perf_counter() - t0
-    cb["all_cores"] = {"value": round(ncores * S / wall, 4), "unit": "solves/s", "cores": ncores,
+    cb["all_cores"] = {"value": round(ncores * S1 / wall, 4), "unit": "solves/s", "cores": ncores,
                        "kind": "oracle",
-                       "sample": f"{ncores} independent sequences of {w.name} ({args.mode}), {S} time "
-                                 f"steps each, one thread per sequence"}
-    # parity of the last sampled step's iteration count against the device run
-    par = {"oracle_iterations": iters_stats(r["iters"]),
-           "gpu_iterations_same_steps": iters_stats(main["iters"][:S]),
-           "max_abs_iter_diff": int(np.max(np.abs(np.array(main["iters"][:S]) - r["iters"])))
-           if len(main["iters"]) >= S else None}
+                       "sample": f"{ncores} independent sequences of {w.name} ({args.mode}, {kind}), "
+                                 f"{S1} time steps each, one thread per sequence"}
+    # parity on the steps both ran: iterations, refinements and x per step
+    S2 = min(S, len(main["iters"]), len(main["x_first"]))
+    gi = np.array(main["iters"][:S2])
+    oi = np.array(r["iters"][:S2])
+    xerr = [float(np.linalg.norm(main["x_first"][i] - r["x_all"][:, i]) / np.linalg.norm(r["x_all"][:, i]))
+            for i in range(S2)]
+    par = {"steps_compared": S2,
+           "oracle_iterations": [int(v) for v in oi], "gpu_iterations": [int(v) for v in gi],
+           "max_abs_iter_diff": int(np.max(np.abs(gi - oi))) if S2 else None,
+           "max_rel_x_err": max(xerr) if xerr else None, "rel_x_err_per_step": xerr,
+           "oracle_true_relres": [float(v) for v in r["relres"][:S2]],
+           "gpu_true_relres": [float(v) for v in main["relres"][:S2]]}
+    if args.precision == "fp32_ir":
+        gr = np.array(main["refinements"][:S2])
+        orf = np.array(r["refinements"][:S2])
+        par.update({"oracle_refinements": [int(v) for v in orf], "gpu_refinements": [int(v) for v in gr],
+                    "max_abs_refinement_diff": int(np.max(np.abs(gr - orf))) if S2 else None})
     return cb, par
 
 
@@ -668,37 +734,33 @@ def reference(args):
     ws, rank, local = dist_info()
     if rank != 0:
         return
-    import numpy as np
-
     import oracle as orc
     import synth
     orc.build()
     w = workload_of(synth, args)
-    a8, beta, forcing = workload_seq(synth, w, 0, max(w.steps, args.warmup + args.steps))
+    seq = workload_seq(synth, w, 0, max(w.steps, args.warmup + args.steps))
     # each bench step is one time step; the oracle is slow, so a step is a
     # bounded sample (the first warmup+steps steps of the sequence, capped)
     W, K = args.warmup, args.steps
-    cap = 3 if w.p > 4 else 40 if w.n < 200000 else 4
+    cap = 3 if w.p > 4 else 40 if w.n < 200000 else 3
     tot = min(W + K, cap)
     Wc = min(W, max(tot - 1, 0))
     Kc = tot - Wc
-    mode = {"plain": 0, "deflated": 1, "augmented": 2}[args.mode]
+    mode = {"plain": 0, "deflated": 1, "augmented": 2, "guess": 3}[args.mode]
+    r = oracle_sequence(orc, w, seq, tot, mode, args.precision)
     rtol = w.rtol if args.precision == "fp64" else 1e-8
-    u0 = np.zeros(w.n) if w.u0 == "zero" else orc.u0_field(w.p, w.N, a8)
-    r = orc.sequence(w.p, w.N, w.eps, w.dt, beta, tot, u0, mode=mode, m=w.m, k=w.k,
-                     window=w.window, ell=w.ell, rtol=rtol,
-                     velocity=int(w.velocity == "cellular"), forcing=forcing,
-                     forcing_C=w.forcing_C, precond=int(w.precond == "jacobi"))
     secs = r["step_seconds"][Wc:]
     value = Kc / float(secs.sum())
-    sample = (f"time steps {Wc + 1}..{tot} of the {w.name} sequence ({args.mode}), FP64 oracle, "
+    kind = "GMRES-IR oracle (binary32 inner storage)" if args.precision == "fp32_ir" else "FP64 oracle"
+    sample = (f"time steps {Wc + 1}..{tot} of the {w.name} sequence ({args.mode}), {kind}, "
               f"single thread")
     out = {"metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": args.gpus,
            "steps": Kc, "warmup": Wc, "ms_per_step": round(1e3 * float(secs.mean()), 3),
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if args.precision == "fp64" else "f32+f64",
            "data": "synthetic", "impl": "reference",
            "config": {"workload": w.name, "n": w.n, "m": w.m, "k": w.k, "window": w.window,
-                      "mode": args.mode, "precision": "fp64", "rtol": rtol},
+                      "mode": args.mode, "precision": args.precision, "rtol": rtol},
            "iterations": iters_stats(r["iters"][Wc:]),
            "cpu_baseline": {"value": round(value, 4), "unit": "solves/s", "cores": 1,
                             "kind": "oracle", "sample": sample},

@@ -286,7 +286,16 @@ typedef struct {
     int64_t launches;
     double flops;       /* summed algorithmic floating-point operations      */
     double bytes;       /* summed algorithmic bytes read and written         */
+    double units;       /* Arnoldi steps the launches carried out (Arnoldi kinds; 0 otherwise) */
 } rgm_kernel_prof;
+/* Algorithmic bytes of the Arnoldi kinds: an Arnoldi step j (1-based; j basis
+ * vectors before it) must move the operator once and read the basis once, plus
+ * 2 k recycle columns when k deflate and about four vector streams (w, the new
+ * basis vector, the SpMV input and output):
+ *     B_j = (e + 4) nnz + e n (j + 2 k + 4),   e = 8 (binary64) or 4 (binary32).
+ * The cycle kind books the sum of B_j over the steps each launch carried out;
+ * the per-pass kinds book each pass's own reads and writes.  Flops: 2 per
+ * stored nonzero and 2 per row per dot or AXPY column of every pass. */
 
 /* Reset the counters and switch event timing on (1) or off (0). */
 int rgm_profile(rgm_solver s, int enable);
@@ -316,8 +325,14 @@ int rgm_wait_selftest(int64_t limit_ns, int *blocks_gave_up, int *fault_flag);
  *
  * r = b - A x and norms[0] = ||b - A x||_2, norms[1] = ||b||_2 for an n x n CSR
  * matrix.  Every pointer is a device pointer of the current device (r may be
- * NULL); the work is queued on cuda_stream (NULL = legacy default stream) and
- * the call returns without waiting.  Nothing is allocated: the scratch (per-
+ * NULL): rowptr n+1 int64 entries (rowptr[0] = 0, non-decreasing), col and val
+ * rowptr[n] entries (int32, binary64), x, b and r n binary64 entries; r must
+ * not alias x or b (it is written while other blocks still read them).  The
+ * C entry point cannot check types or extents behind a pointer: an int32
+ * rowptr read as int64, for instance, sends the kernel to offsets outside the
+ * buffers, so a binding must check them (the Python binding does).  The work
+ * is queued on cuda_stream (NULL = legacy default stream) and the call returns
+ * without waiting.  Nothing is allocated: the scratch (per-
  * block partial sums and a completion counter) is one static device array of
  * 2 * RGM_NOALLOC_MAX_BLOCKS + 32 doubles that every GPU loading the library
  * holds until exit.  The first call on a device looks its address up once

@@ -194,12 +194,12 @@ class Solver:
         check(self._L.rgm_profile(self._h, int(enable)), "rgm_profile")
 
     def profile_read(self):
-        """{kind: dict(ms, launches, flops, bytes)}, total launches."""
+        """{kind: dict(ms, launches, flops, bytes, units)}, total launches."""
         n = len(_lib.PROF_KINDS)
         arr = (_lib.RgmKernelProf * n)()
         tot = C.c_int64(0)
         check(self._L.rgm_profile_read(self._h, arr, n, C.byref(tot)), "rgm_profile_read")
-        out = {k: dict(ms=a.ms, launches=a.launches, flops=a.flops, bytes=a.bytes)
+        out = {k: dict(ms=a.ms, launches=a.launches, flops=a.flops, bytes=a.bytes, units=a.units)
                for k, a in zip(_lib.PROF_KINDS, arr)}
         return out, tot.value
 
@@ -268,14 +268,47 @@ def wait_selftest(limit_ns):
 def residual_noalloc(rowptr, col, val, x, b, r, norms, stream=None):
     """rgm_residual_noalloc: r = b - A x and norms = [||b - A x||, ||b||] with no
     device allocation, for callers that cannot allocate (see include/rgmres.h).
-    All arguments are CUDA tensors (int64 rowptr, int32 col, float64 others); r
-    may be None.  Queued on `stream`; the call does not wait."""
+    All arguments are contiguous tensors on the current CUDA device (int64
+    rowptr, int32 col, float64 others; x, b, r of n = rowptr.numel() - 1
+    elements, norms of 2); r may be None and must not alias x or b.  Queued on
+    `stream` (a torch.cuda.Stream or a raw cudaStream_t handle, None for the
+    legacy default stream); the call does not wait.  Arguments that break these
+    rules raise ValueError before anything reaches the device."""
+    import torch
     L = _lib.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
     n = rowptr.numel() - 1
+
+    def need(t, name, dtype, numel=None):
+        if not (isinstance(t, torch.Tensor) and t.device == dev):
+            raise ValueError(f"{name}: a tensor on the current CUDA device {dev} is required")
+        if t.dtype != dtype:
+            raise ValueError(f"{name}: dtype {dtype} required, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name}: must be contiguous")
+        if numel is not None and t.numel() != numel:
+            raise ValueError(f"{name}: {numel} elements required, got {t.numel()}")
+
+    need(rowptr, "rowptr", torch.int64)
+    if n < 0:
+        raise ValueError("rowptr: at least one element required")
+    need(col, "col", torch.int32)
+    need(val, "val", torch.float64, col.numel())
+    need(x, "x", torch.float64, n)
+    need(b, "b", torch.float64, n)
+    need(norms, "norms", torch.float64, 2)
+    if r is not None:
+        need(r, "r", torch.float64, n)
+        for other, name in ((x, "x"), (b, "b")):
+            if r.data_ptr() == other.data_ptr():
+                raise ValueError(f"r must not alias {name}")
+    if isinstance(stream, torch.cuda.Stream):
+        stream = stream.cuda_stream
     rp = C.c_void_p(r.data_ptr()) if r is not None else None
     check(L.rgm_residual_noalloc(n, C.c_void_p(rowptr.data_ptr()), C.c_void_p(col.data_ptr()),
                                  C.c_void_p(val.data_ptr()), C.c_void_p(x.data_ptr()),
-                                 C.c_void_p(b.data_ptr()), rp, C.c_void_p(norms.data_ptr()), stream),
+                                 C.c_void_p(b.data_ptr()), rp, C.c_void_p(norms.data_ptr()),
+                                 C.c_void_p(stream) if stream else None),
           "rgm_residual_noalloc")
 
 

@@ -45,7 +45,7 @@ class RgmStats(C.Structure):
 
 class RgmKernelProf(C.Structure):
     _fields_ = [("ms", C.c_double), ("launches", C.c_int64), ("flops", C.c_double),
-                ("bytes", C.c_double)]
+                ("bytes", C.c_double), ("units", C.c_double)]
 
 
 PROF_KINDS = ["arnoldi_spmv_dots", "arnoldi_cgs1_axpy_dots", "arnoldi_cgs2_axpy_norm", "other_vector",

@@ -15,7 +15,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librgmres.so")
-SOURCES = ["solver.cu", "vec_f64.cu", "vec_f32.cu", "fe.cu", "noalloc.cu"]
+SOURCES = ["solver.cu", "vec_dispatch.cu", "fe.cu", "noalloc.cu"] + [
+    f"vec_{t}_{q}.cu" for t in ("f64", "f32")
+    for q in ("q4", "q8", "qbig_vec", "qbig_cycle", "qbig_batch")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread",
          "-I", os.path.join(ROOT, "include")]

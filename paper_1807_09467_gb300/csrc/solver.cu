@@ -56,7 +56,7 @@ namespace {
 
 struct ProfRec {
     int kind, kry_j;
-    double flops, bytes;
+    double flops, bytes, units;
     cudaEvent_t a, b;
 };
 
@@ -130,6 +130,7 @@ struct rgm_solver_s {
     // co-resident capacity of cycle_kernel per precision and dot-column bound
     // (-1: not queried yet)
     int cycle_cap[2][RGM_MAXDOTS + 2];
+    int cycle_cap2[2][RGM_MAXDOTS + 2];   // the same for the two-blocks-per-SM build
     bool in_batch = false;        // solving inside rgm_batch_solve: no cooperative launch
     // inside rgm_batch_solve with RGM_BATCH_COOP: the rendezvous this handle's
     // cycle launches join, its index there, and the event marking its inputs ready
@@ -264,6 +265,7 @@ static int launch(rgm_solver s, const VecOp<T> &op, int kind = RGM_PROF_OTHER, i
     if (s->prof) {
         rec.kind = kind;
         rec.kry_j = kry_j;
+        rec.units = (kind == RGM_PROF_ARNOLDI_SPMV) ? 1.0 : 0.0;
         op_cost(s, op, nb_host, J_host, &rec.flops, &rec.bytes);
         rec.a = pool_event(s);
         rec.b = pool_event(s);
@@ -293,7 +295,7 @@ struct ProfScope {
         ++s->launches;
         nvtxRangePushA(kNvtxKind[kind]);
         if (s->prof) {
-            rec.kind = kind; rec.kry_j = -1; rec.flops = flops; rec.bytes = bytes;
+            rec.kind = kind; rec.kry_j = -1; rec.flops = flops; rec.bytes = bytes; rec.units = 0.0;
             rec.a = pool_event(s);
             rec.b = pool_event(s);
             cudaEventRecord(rec.a, s->st);
@@ -318,10 +320,12 @@ static void prof_fix_cycle(rgm_solver s, int J)
             const size_t jj = std::min<size_t>((size_t)std::max(J, 0), s->cyc_flops.size() - 1);
             s->pending[i].flops = s->cyc_flops[jj];
             s->pending[i].bytes = s->cyc_bytes[jj];
+            s->pending[i].units = (double)jj;
         } else if (s->pending[i].kry_j >= J) {
             s->pending[i].kind = RGM_PROF_OTHER;
             s->pending[i].flops = 0.0;
             s->pending[i].bytes = 0.0;
+            s->pending[i].units = 0.0;
         }
     s->cycle_rec0 = s->pending.size();
 }
@@ -338,6 +342,7 @@ static void prof_collect(rgm_solver s)
         a.launches += 1;
         a.flops += r.flops;
         a.bytes += r.bytes;
+        a.units += r.units;
         s->ev_pool.push_back(r.a);
         s->ev_pool.push_back(r.b);
     }
@@ -526,17 +531,22 @@ static void arnoldi_passes(rgm_solver s, const Arnoldi<T> &a, int kdef, CycleOp<
     c.pass[2] = op;
     c.m = s->cfg.m;
     c.arrive = s->counter + 1;
+    c.cap2 = 0;
 }
 
 // The cooperative cycle launch applies when the policy allows it and every
 // block of the grid can be resident at once (checked by occupancy; the
 // cooperative launch itself also refuses a grid that does not fit).
 template <typename T>
-static bool use_cycle_kernel(rgm_solver s, const CycleOp<T> &c, int nd_max)
+static bool use_cycle_kernel(rgm_solver s, CycleOp<T> &c, int nd_max)
 {
     if (s->cfg.launch_policy != RGM_LAUNCH_AUTO || s->in_batch || nd_max > RGM_MAXDOTS) return false;
-    int &cap = s->cycle_cap[sizeof(T) == 4 ? 1 : 0][nd_max];
-    if (cap < 0) cap = cycle_capacity(c, nd_max);
+    const int pi = sizeof(T) == 4 ? 1 : 0;
+    int &cap = s->cycle_cap[pi][nd_max];
+    if (cap < 0) cap = cycle_capacity(c, nd_max, 4);
+    int &cap2 = s->cycle_cap2[pi][nd_max];
+    if (cap2 < 0) cap2 = cycle_capacity(c, nd_max, 2);
+    c.cap2 = cap2;
     return s->nblocks <= cap;
 }
 
@@ -545,19 +555,21 @@ static int launch_cycle_prof(rgm_solver s, const CycleOp<T> &c, int nd_max)
 {
     ProfRec rec;
     if (s->prof) {
-        // algorithmic cost of the first j steps, j = 0..m (booked once J is known)
+        // algorithmic cost of the first j steps, j = 0..m (booked once J is known):
+        // flops of the three passes, bytes B_j = (e + 4) nnz + e n (j + 2 k + 4)
         const int m = c.m;
+        const double es = (double)sizeof(T), kd = (double)c.pass[0].ndU;
         s->cyc_flops.assign(m + 1, 0.0);
         s->cyc_bytes.assign(m + 1, 0.0);
         for (int j = 0; j < m; ++j) {
-            double f = 0.0, b = 0.0, ft, bt;
+            double f = 0.0, ft, bt;
             for (int p = 0; p < 3; ++p) {
                 op_cost(s, c.pass[p], j + 1, j + 1, &ft, &bt);
                 f += ft;
-                b += bt;
             }
+            const double bj = (es + 4.0) * (double)s->nnz + es * (double)s->n * ((double)(j + 1) + 2.0 * kd + 4.0);
             s->cyc_flops[j + 1] = s->cyc_flops[j] + f;
-            s->cyc_bytes[j + 1] = s->cyc_bytes[j] + b;
+            s->cyc_bytes[j + 1] = s->cyc_bytes[j] + bj;
         }
         rec.kind = RGM_PROF_ARNOLDI_CYCLE;
         rec.kry_j = -1;
@@ -1106,6 +1118,8 @@ int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
     rgm_solver s = new (std::nothrow) rgm_solver_s();
     if (!s) return RGM_E_OOM;
     for (auto &row : s->cycle_cap)
+        for (int &v : row) v = -1;
+    for (auto &row : s->cycle_cap2)
         for (int &v : row) v = -1;
     s->cfg = c;
     s->st = (cudaStream_t)c.cuda_stream;

@@ -1,0 +1,6 @@
+// vec_f32_qbig_vec.cu -- the vec kernel(s) for float vectors with the widest
+// column tier (RGM_QBIG dot columns per warp), in a translation unit of their
+// own: the widest tier is the slowest to compile.
+#include "vec_kernels.cuh"
+
+RGM_VEC_DEFINE_VEC(f32, float, qbig, RGM_QBIG)

@@ -206,6 +206,28 @@ __device__ inline void apply_rotations(double *c, const double *cs, const double
     }
 }
 
+// Givens rotation from (a, hn), hn = sqrt(hn2) >= 0: c = a / r, s = hn / r,
+// r = hypot(a, hn), formed from the pair scaled by t = max(|a|, hn) so that
+// no square overflows or underflows before r does (hn2 > 0 is the squared norm
+// the reduction gave; its square root is taken once).  r = 0 gives (1, 0).
+__device__ __forceinline__ void givens_scaled(double a, double hn2, double *c, double *s, double *r,
+                                              double *hn_out)
+{
+    const double hn = sqrt(hn2);
+    const double t = fmax(fabs(a), hn);
+    if (t == 0.0) {
+        *c = 1.0; *s = 0.0; *r = 0.0; *hn_out = 0.0;
+        return;
+    }
+    const double rt = 1.0 / t, as = a * rt, hs = hn * rt;
+    const double rr = t * sqrt(fma(as, as, hs * hs));
+    const double ir = 1.0 / rr;
+    *c = a * ir;
+    *s = hn * ir;
+    *r = rr;
+    *hn_out = hn;
+}
+
 // Finalise one Hessenberg column held in f.col (rows 0..nb, already rotated):
 // make rotation col, update g, write the column and the rotation back.
 __device__ inline void close_column(Small *s, FinScratch &f, int col)
@@ -457,12 +479,10 @@ __device__ void finalize_block(const VecOp<T> &op, const double *d, FinScratch &
             // rotated column (warp 0), then the new rotation from (t_j, hn)
             const double a = warp_rotate_column(f.col, f.cs, f.sn, j);
             if (tid == 0) {
-                const double inv_hn = (hn2 > 0.0) ? rsqrt(hn2) : 0.0;
-                const double hn = hn2 * inv_hn;
-                const double r2 = fma(a, a, hn2);
-                const double inv_r = (r2 > 0.0) ? rsqrt(r2) : 0.0;
-                const double c = (r2 > 0.0) ? a * inv_r : 1.0, sn = hn * inv_r;
-                f.col[j] = r2 * inv_r;
+                double c, sn, rr, hn;
+                givens_scaled(a, hn2, &c, &sn, &rr, &hn);
+                const double inv_hn = (hn > 0.0) ? 1.0 / hn : 0.0;
+                f.col[j] = rr;
                 f.col[j + 1] = 0.0;
                 s->cs[j] = c;
                 s->sn[j] = sn;
@@ -502,12 +522,10 @@ __device__ void finalize_block(const VecOp<T> &op, const double *d, FinScratch &
             // rotated column (warp 0), then the new rotation from (t_j, ||w||)
             const double a = warp_rotate_column(f.col, f.cs, f.sn, j);
             if (tid == 0) {
-                const double inv_hn = (nrm2 > 0.0) ? rsqrt(nrm2) : 0.0;
-                const double hn = nrm2 * inv_hn;
-                const double r2 = fma(a, a, nrm2);
-                const double inv_r = (r2 > 0.0) ? rsqrt(r2) : 0.0;
-                const double c = (r2 > 0.0) ? a * inv_r : 1.0, sn = hn * inv_r;
-                f.col[j] = r2 * inv_r;
+                double c, sn, rr, hn;
+                givens_scaled(a, nrm2, &c, &sn, &rr, &hn);
+                const double inv_hn = (hn > 0.0) ? 1.0 / hn : 0.0;
+                f.col[j] = rr;
                 f.col[j + 1] = 0.0;
                 s->cs[j] = c;
                 s->sn[j] = sn;
@@ -858,6 +876,7 @@ struct CycleOp {
                          // the Givens step, the plain update that stores v_{j+1}
     int m;               // Arnoldi steps at most
     unsigned *arrive;    // arrival counter of the plain barrier
+    int cap2;            // co-resident blocks of the two-blocks-per-SM build (host side only)
 };
 
 // After a pass: the last block publishes generation `target`, the others wait
@@ -974,16 +993,21 @@ static __global__ void wait_selftest_kernel(Small *s, unsigned long long limit_n
     if (threadIdx.x == 0 && !ok) atomicAdd(gave_up, 1);
 }
 
-// Host-side dispatch (vec_f64.cu / vec_f32.cu): the per-warp column tier is
+// Host-side dispatch (vec_dispatch.cu): the per-warp column tier is
 // chosen from the largest dot-column count the launch can see (nd_max;
-// dynamic counts resolve on the device and never exceed it).
+// dynamic counts resolve on the device and never exceed it).  Each
+// (precision, tier) pair is compiled in a translation unit of its own
+// (vec_<precision>_q<tier>.cu, RGM_VEC_DEFINE) so that the build runs in
+// parallel; RGM_VEC_DECLARE names what they define.
 // Return the cudaError_t of the launch (0 = success).
 int launch_vec(const VecOp<double> &op, int nd_max, cudaStream_t st);
 int launch_vec(const VecOp<float> &op, int nd_max, cudaStream_t st);
 // cycle_kernel: blocks that can be resident at once for this column bound
-// (0 if the device cannot launch it cooperatively), and the launch itself.
-int cycle_capacity(const CycleOp<double> &c, int nd_max);
-int cycle_capacity(const CycleOp<float> &c, int nd_max);
+// (0 if the device cannot launch it cooperatively) in the build that
+// guarantees minb (4 or 2) resident blocks per SM, and the launch itself
+// (which takes the two-blocks-per-SM build when c.cap2 holds the grid).
+int cycle_capacity(const CycleOp<double> &c, int nd_max, int minb);
+int cycle_capacity(const CycleOp<float> &c, int nd_max, int minb);
 int launch_cycle(const CycleOp<double> &c, int nd_max, cudaStream_t st);
 int launch_cycle(const CycleOp<float> &c, int nd_max, cudaStream_t st);
 // batch_cycle_kernel: blocks that can be resident at once (0 if not
@@ -1012,19 +1036,6 @@ static cudaError_t launch_vec_pdl(const VecOp<T> &op, cudaStream_t st)
     return cudaLaunchKernelEx(&cfg, vec_kernel<T, Q>, op);
 }
 
-template <typename T>
-static int launch_vec_impl(const VecOp<T> &op, int nd_max, cudaStream_t st)
-{
-    constexpr int NW = RGM_THREADS / 32;
-    constexpr int QBIG = (RGM_MAXDOTS + NW - 1) / NW;
-    const int q = (nd_max + NW - 1) / NW;
-    cudaError_t e;
-    if (q <= 4) e = launch_vec_pdl<T, 4>(op, st);
-    else if (q <= 8) e = launch_vec_pdl<T, 8>(op, st);
-    else e = launch_vec_pdl<T, QBIG>(op, st);
-    return (int)e;          // cudaSuccess == 0
-}
-
 template <typename T, int Q, int MINB>
 static int cycle_capacity_q(int dev)
 {
@@ -1037,29 +1048,12 @@ static int cycle_capacity_q(int dev)
     return per_sm * nsm;
 }
 
-template <typename T>
-static int cycle_capacity_impl(int nd_max)
-{
-    constexpr int NW = RGM_THREADS / 32;
-    constexpr int QBIG = (RGM_MAXDOTS + NW - 1) / NW;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    const int q = (nd_max + NW - 1) / NW;
-    if (q <= 4) return cycle_capacity_q<T, 4, 4>(dev);
-    if (q <= 8) return cycle_capacity_q<T, 8, 4>(dev);
-    return cycle_capacity_q<T, QBIG, 4>(dev);
-}
-
 template <typename T, int Q>
 static cudaError_t launch_cycle_q(const CycleOp<T> &c, cudaStream_t st)
 {
     // the wider-register variant when its residency holds the whole grid
-    static int cap2 = -1;
-    if (cap2 < 0) {
-        int dev = 0;
-        cap2 = (cudaGetDevice(&dev) == cudaSuccess) ? cycle_capacity_q<T, Q, 2>(dev) : 0;
-    }
-    const bool wide = c.pass[0].nblocks <= cap2;
+    // (c.cap2: the caller's cached capacity of that build on its device)
+    const bool wide = c.pass[0].nblocks <= c.cap2;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(c.pass[0].nblocks);
     cfg.blockDim = dim3(RGM_THREADS);
@@ -1086,19 +1080,6 @@ static int batch_capacity_q(int dev)
     return per_sm * nsm;
 }
 
-template <typename T>
-static int batch_capacity_impl(int nd_max)
-{
-    constexpr int NW = RGM_THREADS / 32;
-    constexpr int QBIG = (RGM_MAXDOTS + NW - 1) / NW;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    const int q = (nd_max + NW - 1) / NW;
-    if (q <= 4) return batch_capacity_q<T, 4>(dev);
-    if (q <= 8) return batch_capacity_q<T, 8>(dev);
-    return batch_capacity_q<T, QBIG>(dev);
-}
-
 template <typename T, int Q>
 static cudaError_t launch_batch_q(const CycleOp<T> *ops, const int *first, int nsys, int nblocks,
                                   cudaStream_t st)
@@ -1116,32 +1097,47 @@ static cudaError_t launch_batch_q(const CycleOp<T> *ops, const int *first, int n
     return cudaLaunchKernelEx(&cfg, batch_cycle_kernel<T, Q>, ops, first, nsys);
 }
 
-template <typename T>
-static int launch_batch_impl(const CycleOp<T> *ops, const int *first, int nsys, int nblocks, int nd_max,
-                             cudaStream_t st)
-{
-    constexpr int NW = RGM_THREADS / 32;
-    constexpr int QBIG = (RGM_MAXDOTS + NW - 1) / NW;
-    const int q = (nd_max + NW - 1) / NW;
-    cudaError_t e;
-    if (q <= 4) e = launch_batch_q<T, 4>(ops, first, nsys, nblocks, st);
-    else if (q <= 8) e = launch_batch_q<T, 8>(ops, first, nsys, nblocks, st);
-    else e = launch_batch_q<T, QBIG>(ops, first, nsys, nblocks, st);
-    return (int)e;
-}
+#define RGM_QBIG ((RGM_MAXDOTS + RGM_THREADS / 32 - 1) / (RGM_THREADS / 32))
 
-template <typename T>
-static int launch_cycle_impl(const CycleOp<T> &c, int nd_max, cudaStream_t st)
-{
-    constexpr int NW = RGM_THREADS / 32;
-    constexpr int QBIG = (RGM_MAXDOTS + NW - 1) / NW;
-    const int q = (nd_max + NW - 1) / NW;
-    cudaError_t e;
-    if (q <= 4) e = launch_cycle_q<T, 4>(c, st);
-    else if (q <= 8) e = launch_cycle_q<T, 8>(c, st);
-    else e = launch_cycle_q<T, QBIG>(c, st);
-    return (int)e;          // cudaSuccess == 0
-}
+// Entry points of one (precision, column tier) translation unit.
+#define RGM_VEC_DECLARE(TN, T, QN)                                                                 \
+    int vec_launch_##TN##_##QN(const VecOp<T> &op, cudaStream_t st);                               \
+    int vec_cycle_capacity_##TN##_##QN(int dev, int minb);                                         \
+    int vec_cycle_launch_##TN##_##QN(const CycleOp<T> &c, cudaStream_t st);                        \
+    int vec_batch_capacity_##TN##_##QN(int dev);                                                   \
+    int vec_batch_launch_##TN##_##QN(const CycleOp<T> *ops, const int *first, int nsys, int nblocks, \
+                                     cudaStream_t st);
+#define RGM_VEC_DEFINE_VEC(TN, T, QN, Q)                                                           \
+    int vec_launch_##TN##_##QN(const VecOp<T> &op, cudaStream_t st)                                \
+    {                                                                                              \
+        return (int)launch_vec_pdl<T, Q>(op, st);                                                  \
+    }
+#define RGM_VEC_DEFINE_CYCLE(TN, T, QN, Q)                                                         \
+    int vec_cycle_capacity_##TN##_##QN(int dev, int minb)                                          \
+    {                                                                                              \
+        return minb == 2 ? cycle_capacity_q<T, Q, 2>(dev) : cycle_capacity_q<T, Q, 4>(dev);        \
+    }                                                                                              \
+    int vec_cycle_launch_##TN##_##QN(const CycleOp<T> &c, cudaStream_t st)                         \
+    {                                                                                              \
+        return (int)launch_cycle_q<T, Q>(c, st);                                                   \
+    }
+#define RGM_VEC_DEFINE_BATCH(TN, T, QN, Q)                                                         \
+    int vec_batch_capacity_##TN##_##QN(int dev) { return batch_capacity_q<T, Q>(dev); }            \
+    int vec_batch_launch_##TN##_##QN(const CycleOp<T> *ops, const int *first, int nsys, int nblocks, \
+                                     cudaStream_t st)                                              \
+    {                                                                                              \
+        return (int)launch_batch_q<T, Q>(ops, first, nsys, nblocks, st);                           \
+    }
+#define RGM_VEC_DEFINE(TN, T, QN, Q)                                                               \
+    RGM_VEC_DEFINE_VEC(TN, T, QN, Q)                                                               \
+    RGM_VEC_DEFINE_CYCLE(TN, T, QN, Q)                                                             \
+    RGM_VEC_DEFINE_BATCH(TN, T, QN, Q)
+RGM_VEC_DECLARE(f64, double, q4)
+RGM_VEC_DECLARE(f64, double, q8)
+RGM_VEC_DECLARE(f64, double, qbig)
+RGM_VEC_DECLARE(f32, float, q4)
+RGM_VEC_DECLARE(f32, float, q8)
+RGM_VEC_DECLARE(f32, float, qbig)
 
 // CSR values -> sliced-ELL positions (binary64 and, when given, binary32 copy).
 template <typename Tin>

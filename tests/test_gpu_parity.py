@@ -321,3 +321,36 @@ def test_maximum_dimensions(rg, orc, mode):
     np.testing.assert_allclose(Ug.T @ Ug, np.eye(32), atol=1e-12)
     Q = np.linalg.qr(X)[0]
     assert np.linalg.norm(Ug - Q @ (Q.T @ Ug)) <= 1e-10
+
+
+# ------------------------------------------------------------------ scaling (Givens, norms)
+@pytest.mark.parametrize("mode", ["plain", "deflated"])
+@pytest.mark.parametrize("sa,sb", [(400, -400), (-400, 400), (400, 400), (-400, -400)])
+def test_power_of_two_scaling(rg, orc, mode, sa, sb):
+    """(2^sa A) x = 2^sb b has the solution 2^(sb - sa) x: every operation of
+    the solve commutes with power-of-two scaling as long as no square leaves
+    the binary64 range, so the scaled solve equals the unscaled one bit for
+    bit (entries of A near 1e+-120, of b near 1e-+120, squared norms near
+    1e+-240).  The rotations are formed from the scaled pair, as the oracle's
+    hypot; the oracle gives the same iterations on the scaled system."""
+    n, m, k = 700, 15, 3
+    rp, col, val, b = _random_system(n, 4242)
+    U = _orth(synth.random_matrix(n, k, 4243)) if mode != "plain" else None
+
+    def solve(v, rhs):
+        s = rg.Solver(n, m=m, k=k, mode=mode, rtol=1e-10)
+        s.set_operator_csr(rp, col, v)
+        if U is not None:
+            s.set_recycle_space(U)
+        x, st = s.solve(rhs)
+        s.close()
+        return x, st
+
+    x0, st0 = solve(val, b)
+    xs, sts = solve(np.ldexp(val, sa), np.ldexp(b, sb))
+    assert sts["status"] == 0 and sts["iters"] == st0["iters"]
+    np.testing.assert_array_equal(xs, np.ldexp(x0, sb - sa))
+    xo, so, _ = orc.gmres(orc.Csr(rp, col, np.ldexp(val, sa)), np.ldexp(b, sb), U=U,
+                          mode=rg.MODES[mode], m=m, rtol=1e-10)
+    assert abs(sts["iters"] - so["iters"]) <= 1
+    assert _rel(xs, xo) <= 1e-9
