@@ -113,7 +113,7 @@ typedef struct {
                              (needs window >= g+1); recycling then adds its projection  */
     int precond;          /* rgm_precond (not with RGM_FP32_IR)                              */
     double rtol;          /* converged when ||b - A x||_2 <= rtol ||b||_2                   */
-    double inner_rtol;    /* FP32_IR: inner solve to inner_rtol * ||r||                     */
+    double inner_rtol;    /* FP32_IR: inner solve to max(inner_rtol ||r||, rtol ||b|| / 2)  */
     double rel_drop;      /* drop singular values below rel_drop * sigma_1                 */
     void *cuda_stream;    /* cudaStream_t to run on; NULL = the legacy default stream      */
 } rgm_config;

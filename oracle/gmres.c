@@ -591,7 +591,9 @@ int orc_gmres_ir(const orc_csr *A, const double *b, double *x, const double *U, 
         for (int64_t i = 0; i < n; ++i) { r[i] = (double)(float)r[i]; rf_norm += r[i] * r[i]; }
         rf_norm = sqrt(rf_norm);
         memset(d, 0, sizeof(double) * n);
-        c.tol_abs = inner_rtol * rf_norm;
+        /* inner_rtol of the current residual, but no further than half the
+         * outer target: the refinement loop checks the binary64 residual */
+        c.tol_abs = fmax(inner_rtol * rf_norm, 0.5 * o->rtol * bnorm);
         c.tol_in = c.tol_abs;       /* the Givens estimate ends a cycle early, as in every solve */
         c.maxit = o->maxit - iters;
         int it, cy;

@@ -146,8 +146,9 @@ int orc_gmres(const orc_csr *A, const double *b, double *x, const double *U, int
               const orc_opts *o, orc_stats *st, double *hist, int hist_len);
 /* Mixed-precision iterative refinement (GMRES-IR): outer FP64 residual, inner
  * recycled GMRES with every stored vector and A's values rounded to binary32
- * (arithmetic in FP64, rounded on store).  inner_rtol is relative to the
- * current outer residual; at most inner_cycles cycles per refinement. */
+ * (arithmetic in FP64, rounded on store).  The inner solve stops at
+ * max(inner_rtol ||r||, rtol ||b|| / 2) (r the current outer residual) or
+ * after inner_cycles cycles. */
 int orc_gmres_ir(const orc_csr *A, const double *b, double *x, const double *U, int k,
                  const orc_opts *o, double inner_rtol, int inner_cycles,
                  int max_refinements, orc_stats *st, int *refinements);

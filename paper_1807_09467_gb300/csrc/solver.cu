@@ -130,7 +130,6 @@ struct rgm_solver_s {
     // co-resident capacity of cycle_kernel per precision and dot-column bound
     // (-1: not queried yet)
     int cycle_cap[2][RGM_MAXDOTS + 2];
-    int cycle_cap2[2][RGM_MAXDOTS + 2];   // the same for the two-blocks-per-SM build
     bool in_batch = false;        // solving inside rgm_batch_solve: no cooperative launch
     // inside rgm_batch_solve with RGM_BATCH_COOP: the rendezvous this handle's
     // cycle launches join, its index there, and the event marking its inputs ready
@@ -431,12 +430,13 @@ __global__ void solve_setup_kernel(Small *s, int maxit, int m, int k)
     }
 }
 
-// tol_abs bounds the true residual; tol_in the in-cycle Givens estimate, which
-// with left Jacobi measures the residual of D^{-1} A x = D^{-1} b.
-__global__ void set_tol_kernel(Small *s, double rtol, int precond)
+// tol_abs bounds the true residual (never below floor_abs); tol_in the in-cycle
+// Givens estimate, which with left Jacobi measures the residual of
+// D^{-1} A x = D^{-1} b.
+__global__ void set_tol_kernel(Small *s, double rtol, int precond, double floor_abs)
 {
     if (threadIdx.x == 0) {
-        s->tol_abs = rtol * s->bnorm;
+        s->tol_abs = fmax(rtol * s->bnorm, floor_abs);
         s->tol_in = precond ? rtol * s->bnorm_p : s->tol_abs;
     }
 }
@@ -531,22 +531,17 @@ static void arnoldi_passes(rgm_solver s, const Arnoldi<T> &a, int kdef, CycleOp<
     c.pass[2] = op;
     c.m = s->cfg.m;
     c.arrive = s->counter + 1;
-    c.cap2 = 0;
 }
 
 // The cooperative cycle launch applies when the policy allows it and every
 // block of the grid can be resident at once (checked by occupancy; the
 // cooperative launch itself also refuses a grid that does not fit).
 template <typename T>
-static bool use_cycle_kernel(rgm_solver s, CycleOp<T> &c, int nd_max)
+static bool use_cycle_kernel(rgm_solver s, const CycleOp<T> &c, int nd_max)
 {
     if (s->cfg.launch_policy != RGM_LAUNCH_AUTO || s->in_batch || nd_max > RGM_MAXDOTS) return false;
-    const int pi = sizeof(T) == 4 ? 1 : 0;
-    int &cap = s->cycle_cap[pi][nd_max];
-    if (cap < 0) cap = cycle_capacity(c, nd_max, 4);
-    int &cap2 = s->cycle_cap2[pi][nd_max];
-    if (cap2 < 0) cap2 = cycle_capacity(c, nd_max, 2);
-    c.cap2 = cap2;
+    int &cap = s->cycle_cap[sizeof(T) == 4 ? 1 : 0][nd_max];
+    if (cap < 0) cap = cycle_capacity(c, nd_max);
     return s->nblocks <= cap;
 }
 
@@ -933,7 +928,7 @@ static int solve_device(rgm_solver s, rgm_stats *out)
         CK(cudaGetLastError());
         if ((rc = norm_of(s, a, s->b, FIN_BNORMP))) return rc;
     }
-    { ProfScope ps_(s, RGM_PROF_SMALL); set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.rtol, pre); }
+    { ProfScope ps_(s, RGM_PROF_SMALL); set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.rtol, pre, 0.0); }
     if (k > 0 && (rc = coarse_correct(s, a, k))) return rc;     // x0 = x_in + Q (b - A x_in)
     if ((rc = residual_norm(s, a))) return rc;
     if ((rc = read_header(s))) return rc;
@@ -955,7 +950,10 @@ static int solve_device(rgm_solver s, rgm_stats *out)
             CK(cudaMemsetAsync(s->x32, 0, sizeof(float) * s->n, s->st));
             { ProfScope ps_(s, RGM_PROF_SMALL); solve_setup_kernel<<<1, 32, 0, s->st>>>(s->sm, c.maxit - iters_total, c.m, k); }
             if ((rc = norm_of(s, f, s->b32, FIN_BNORM))) return rc;
-            { ProfScope ps_(s, RGM_PROF_SMALL); set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.inner_rtol, 0); }
+            // inner_rtol of the current residual, but no further than half the
+            // outer target (the binary64 residual below decides convergence)
+            { ProfScope ps_(s, RGM_PROF_SMALL);
+              set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.inner_rtol, 0, 0.5 * c.rtol * bnorm); }
             if (k > 0 && (rc = coarse_correct(s, f, k))) return rc;
             if ((rc = residual_norm(s, f))) return rc;
             int cy = 0;
@@ -966,7 +964,7 @@ static int solve_device(rgm_solver s, rgm_stats *out)
             { ProfScope ps_(s, RGM_PROF_OTHER); add_f32_kernel<<<s->nblocks, 256, 0, s->st>>>(s->x, s->x32, s->n); }
             { ProfScope ps_(s, RGM_PROF_SMALL); solve_setup_kernel<<<1, 32, 0, s->st>>>(s->sm, c.maxit, c.m, k); }
             if ((rc = norm_of(s, a, s->b, FIN_BNORM))) return rc;
-            { ProfScope ps_(s, RGM_PROF_SMALL); set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.rtol, 0); }
+            { ProfScope ps_(s, RGM_PROF_SMALL); set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.rtol, 0, 0.0); }
             if ((rc = residual_norm(s, a))) return rc;
             if ((rc = read_header(s))) return rc;
             s->hs->iters = iters_total;
@@ -1119,8 +1117,6 @@ int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
     if (!s) return RGM_E_OOM;
     for (auto &row : s->cycle_cap)
         for (int &v : row) v = -1;
-    for (auto &row : s->cycle_cap2)
-        for (int &v : row) v = -1;
     s->cfg = c;
     s->st = (cudaStream_t)c.cuda_stream;
     s->nsm = nsm;
@@ -1128,7 +1124,7 @@ int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
     s->ld = (c.n + 31) / 32 * 32;
     // blocks own whole RGM_TILE-row tiles (the sliced-ELL sorting windows)
     const int64_t ntile = (s->n + RGM_TILE - 1) / RGM_TILE;
-    const int64_t nb_want = std::max<int64_t>(1, std::min<int64_t>(ntile, 4 * (int64_t)nsm));
+    const int64_t nb_want = std::max<int64_t>(1, std::min<int64_t>(ntile, RGM_MINB * (int64_t)nsm));
     const int64_t tiles_per_block = (ntile + nb_want - 1) / nb_want;
     s->rpb = (int)(tiles_per_block * RGM_TILE);
     s->nblocks = (int)((s->n + s->rpb - 1) / s->rpb);

@@ -252,3 +252,20 @@ def test_ir_sequence_matches_step_solves(orc):
         assert st["true_relres"] <= 1e-8 and st["refinements"] >= 2
         X.append(x)
         u = x
+
+
+def test_inner_stop_capped_at_half_the_target(orc):
+    """The inner solve stops at max(inner_rtol ||r||, rtol ||b|| / 2): asked for
+    an unattainable inner_rtol of 1e-14 with rtol 1e-6, it stops where binary64
+    GMRES from the same start reaches rtol / 2 (within one step), and one
+    refinement meets the target.  Without the cap it would run all of its
+    inner cycles (2 m steps)."""
+    w = synth.Q1_32
+    a8, beta = synth.sequence_draws(w, 0)
+    rp, col, val, b = orc.step_system(1, 16, w.eps, w.dt, beta, orc.u0_field(1, 16, a8))
+    A = orc.Csr(rp, col, val)
+    m = 30
+    x, st = orc.gmres_ir(A, b, m=m, rtol=1e-6, inner_rtol=1e-14, inner_cycles=2)
+    _, s64, _ = orc.gmres(A, b, m=m, rtol=0.5e-6)
+    assert st["refinements"] == 1 and st["status"] == 0 and st["true_relres"] <= 1e-6
+    assert abs(st["iters"] - s64["iters"]) <= 1 and st["iters"] < 2 * m, (st, s64)
