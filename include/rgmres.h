@@ -297,6 +297,11 @@ typedef struct {
  * the per-pass kinds book each pass's own reads and writes.  Flops: 2 per
  * stored nonzero and 2 per row per dot or AXPY column of every pass. */
 
+/* Device memory the handle holds now: the sum of its device allocations
+ * (operator in sliced ELL, Krylov basis, recycle space, snapshot window,
+ * binary32 copies, scratch), in bytes.  RGM_E_ARG for a NULL argument. */
+int rgm_solver_device_bytes(rgm_solver s, int64_t *bytes);
+
 /* Reset the counters and switch event timing on (1) or off (0). */
 int rgm_profile(rgm_solver s, int enable);
 /* Synchronise the stream and copy the per-kind totals out (nkinds entries);
@@ -370,6 +375,9 @@ int rgm_fe_create(rgm_fe *out, int p, int N, double eps, double dt, double beta_
 int rgm_fe_destroy(rgm_fe fe);
 /* Sizes of the Dirichlet pattern. */
 int rgm_fe_sizes(rgm_fe fe, int64_t *n, int64_t *nnz);
+/* Device memory the workload holds now (pattern, element tables, values,
+ * right-hand side, velocity and forcing fields when set), in bytes. */
+int rgm_fe_device_bytes(rgm_fe fe, int64_t *bytes);
 /* Copy the Dirichlet CSR pattern out (rowptr n+1, col nnz). */
 int rgm_fe_pattern(rgm_fe fe, int64_t *rowptr, int32_t *col, int flags);
 /* Assemble values (nnz, CSR order of rgm_fe_pattern) and b (n) from u_prev (n). */

@@ -553,7 +553,7 @@ int orc_gmres_ir(const orc_csr *A, const double *b, double *x, const double *U, 
     int mode = (k > 0 && U) ? o->mode : ORC_PLAIN, status = ORC_OK;
     double *Af = malloc(sizeof(double) * nnz), *r = malloc(sizeof(double) * n);
     double *d = malloc(sizeof(double) * n), *tmp = malloc(sizeof(double) * n);
-    double *W = NULL, *LU = NULL, *LUP = NULL, *Uf = NULL, *Wf = NULL, *cv = NULL;
+    double *LU = NULL, *LUP = NULL, *Uf = NULL, *Wf = NULL, *cv = NULL;
     int *piv = NULL, *pivP = NULL;
     for (int64_t i = 0; i < nnz; ++i) Af[i] = (double)(float)A->val[i];
     core_t c;
@@ -561,20 +561,28 @@ int orc_gmres_ir(const orc_csr *A, const double *b, double *x, const double *U, 
     c.A = A; c.val = Af; c.f32 = 1; c.m = o->m; c.start_r = o->start_r;
     c.maxit = o->maxit; c.max_cycles = inner_cycles;
     if (mode != ORC_PLAIN) {
-        W = malloc(sizeof(double) * n * k); LU = malloc(sizeof(double) * k * k);
+        LU = malloc(sizeof(double) * k * k);
         LUP = malloc(sizeof(double) * k * k); pivP = malloc(sizeof(int) * k);
         piv = malloc(sizeof(int) * k); cv = malloc(sizeof(double) * k);
         Uf = malloc(sizeof(double) * n * k); Wf = malloc(sizeof(double) * n * k);
-        orc_coarse_setup(A, U, k, W, LU);            /* E (and G) in FP64 */
-        for (int64_t i = 0; i < n * k; ++i) { Uf[i] = (double)(float)U[i]; Wf[i] = (double)(float)W[i]; }
-        if (recycle_setup(&c, n, k, U, W, Uf, Wf, o->proj, LU, piv, LUP, pivP) != ORC_OK) {
+        /* U and W = A U are used only inside the binary32 inner solve: W is
+         * formed from the binary32 operator and U and stored in binary32, and
+         * E = U^T W (and the projector's Gram matrix) is accumulated in FP64
+         * from the stored columns, so that the inner projector is exact for
+         * the vectors it is applied with; E and its LU stay FP64 */
+        for (int64_t i = 0; i < n * k; ++i) Uf[i] = (double)(float)U[i];
+        for (int j = 0; j < k; ++j) spmv_vals(A, Af, Uf + (int64_t)j * n, Wf + (int64_t)j * n, 1);
+        for (int j = 0; j < k; ++j)
+            for (int i = 0; i < k; ++i) LU[i + j * k] = dot(n, Uf + (int64_t)i * n, Wf + (int64_t)j * n);
+        if (recycle_setup(&c, n, k, Uf, Wf, Uf, Wf, o->proj, LU, piv, LUP, pivP) != ORC_OK) {
             status = ORC_W_SINGULAR_COARSE;
             mode = ORC_PLAIN;
             c.k = 0;
         } else {
-            /* FP64 projection initial guess on the outer iterate */
+            /* FP64 projection initial guess on the outer iterate
+             * (x += U E^{-1} U^T (b - A x): U in FP64, E as above) */
             core_t c64 = c;
-            c64.val = A->val; c64.f32 = 0; c64.U = U; c64.W = W;
+            c64.val = A->val; c64.f32 = 0; c64.U = U;
             coarse_correct(&c64, b, x, r, cv);
         }
     }
@@ -609,7 +617,7 @@ int orc_gmres_ir(const orc_csr *A, const double *b, double *x, const double *U, 
         st->status = status; st->true_relres = res / bnorm;
     }
     if (refinements) *refinements = nref;
-    free(Af); free(r); free(d); free(tmp); free(W); free(LU); free(LUP); free(piv); free(pivP);
+    free(Af); free(r); free(d); free(tmp); free(LU); free(LUP); free(piv); free(pivP);
     free(Uf); free(Wf); free(cv);
     return status;
 }

@@ -126,6 +126,12 @@ class Solver:
         check(self._L.rgm_set_recycle_space(self._h, C.c_void_p(Uf.ctypes.data), Uf.shape[1],
                                             Uf.shape[0], 0), "rgm_set_recycle_space")
 
+    def device_bytes(self):
+        """rgm_solver_device_bytes: device memory the handle holds now."""
+        v = C.c_int64(0)
+        check(self._L.rgm_solver_device_bytes(self._h, C.byref(v)), "rgm_solver_device_bytes")
+        return v.value
+
     def recycle_dim(self):
         """Number of recycle vectors currently held."""
         k = C.c_int(0)
@@ -325,6 +331,12 @@ class FE:
         L.rgm_fe_sizes(h, C.byref(n), C.byref(nnz))
         self.n, self.nnz = n.value, nnz.value
         self.p, self.N = p, N
+
+    def device_bytes(self):
+        """rgm_fe_device_bytes: device memory the workload holds now."""
+        v = C.c_int64(0)
+        check(self._L.rgm_fe_device_bytes(self._h, C.byref(v)), "rgm_fe_device_bytes")
+        return v.value
 
     def close(self):
         if getattr(self, "_h", None):

@@ -81,6 +81,8 @@ _SIGS = {
     "rgm_reset_recycling": (C.c_int, [C.c_void_p]),
     "rgm_spmv": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "rgm_status_string": (C.c_char_p, [C.c_int]),
+    "rgm_solver_device_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "rgm_fe_device_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "rgm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "rgm_profile_read": (C.c_int, [C.c_void_p, C.POINTER(RgmKernelProf), C.c_int,
                                    C.POINTER(C.c_int64)]),

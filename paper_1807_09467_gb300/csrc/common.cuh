@@ -11,6 +11,11 @@
 #define RGM_NCOL (RGM_MMAX + RGM_KMAX)       // columns of the Hessenberg matrix
 #define RGM_MAXDOTS (RGM_KMAX + RGM_HLD + RGM_KMAX + 1)
 #define RGM_THREADS 256
+#ifndef RGM_MINB
+#define RGM_MINB 2                           // resident blocks per SM every fused kernel is built for
+                                             // (65536 / (256 RGM_MINB) registers a thread; grids hold
+                                             // at most this many blocks per SM)
+#endif
 #define RGM_CHUNK 8                          // dot columns per register pass
 
 // Small device-resident state of one solve: the Hessenberg least-squares

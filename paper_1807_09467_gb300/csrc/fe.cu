@@ -59,6 +59,7 @@ struct rgm_fe_s {
     double *coef = nullptr;                  // C_x, C_y per cell and Gauss point
     double *fn = nullptr;                    // nodal forcing
     double *cmodes = nullptr;                // forcing coefficients (RGM_FE_MAX_MODES)
+    int64_t ntab = 0;                        // doubles in tabs
 };
 
 namespace {
@@ -444,6 +445,7 @@ int rgm_fe_create(rgm_fe *out, int p, int N, double eps, double dt, double beta_
             }
     cudaError_t e = cudaMalloc((void **)&fe->rowptr, sizeof(int64_t) * (fe->n + 1));
     if (e == cudaSuccess) e = cudaMalloc((void **)&fe->col, sizeof(int32_t) * fe->nnz);
+    fe->ntab = (int64_t)tab.size();
     if (e == cudaSuccess) e = cudaMalloc((void **)&fe->tabs, sizeof(double) * tab.size());
     if (e == cudaSuccess) e = cudaMalloc((void **)&fe->val, sizeof(double) * fe->nnz);
     if (e == cudaSuccess) e = cudaMalloc((void **)&fe->b, sizeof(double) * fe->n);
@@ -460,6 +462,16 @@ int rgm_fe_create(rgm_fe *out, int p, int N, double eps, double dt, double beta_
         if (rc) { rgm_fe_destroy(fe); return rc; }
     }
     *out = fe;
+    return RGM_OK;
+}
+
+int rgm_fe_device_bytes(rgm_fe fe, int64_t *bytes)
+{
+    if (!fe || !bytes) return RGM_E_ARG;
+    int64_t b = 8 * (fe->n + 1) + 4 * fe->nnz + 8 * fe->ntab + 8 * fe->nnz + 16 * fe->n;
+    if (fe->bxn) b += 16 * fe->n + 8 * 2 * (int64_t)fe->N * fe->N * (fe->p + 1) * (fe->p + 1);
+    if (fe->fn) b += 8 * fe->n + 8 * RGM_FE_MAX_MODES;
+    *bytes = b;
     return RGM_OK;
 }
 
@@ -557,7 +569,9 @@ int rgm_fe_set_forcing(rgm_fe fe, int nmodes, const double *c, double C, int fla
     if (nmodes == 0) {
         CKF(cudaStreamSynchronize(fe->st));
         if (fe->fn) cudaFree(fe->fn);
+        if (fe->cmodes) cudaFree(fe->cmodes);
         fe->fn = nullptr;
+        fe->cmodes = nullptr;
         return RGM_OK;
     }
     if (!fe->fn) {

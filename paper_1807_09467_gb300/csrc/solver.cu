@@ -136,7 +136,29 @@ struct rgm_solver_s {
     struct BatchCycles *batch = nullptr;
     int batch_idx = 0;
     cudaEvent_t batch_ev = nullptr;
+    // device bytes this handle holds, by allocation (rgm_solver_device_bytes)
+    std::vector<std::pair<void *, size_t>> allocs;
 };
+
+// cudaMalloc that books the allocation on the handle.
+static cudaError_t dev_alloc(rgm_solver s, void **p, size_t bytes)
+{
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) s->allocs.emplace_back(*p, bytes);
+    return e;
+}
+
+static void dev_free(rgm_solver s, void *p)
+{
+    if (!p) return;
+    cudaFree(p);
+    for (size_t i = 0; i < s->allocs.size(); ++i)
+        if (s->allocs[i].first == p) {
+            s->allocs[i] = s->allocs.back();
+            s->allocs.pop_back();
+            break;
+        }
+}
 
 // Rendezvous of the systems of one rgm_batch_solve(.., RGM_BATCH_COOP, ..): each
 // system's host thread runs its own solve and, at every GMRES cycle, hands its
@@ -376,7 +398,7 @@ static int launch_gram(rgm_solver s, const T *X, int64_t ldx, int nx, const T *Y
     op.counter = s->counter;
     op.out = out;
     const int ncol = (mode == GRAM_UW) ? 2 * nxmax : nxmax;
-    // the row tile of all ncol columns (tile + 1 doubles each) in dynamic shared
+    // the row tile of all ncol columns (tile + 1 values each) in dynamic shared
     // memory, within the 48 KB a launch may use without opting in, less the
     // kernel's static shared memory
     static size_t static_smem = (size_t)-1;
@@ -385,9 +407,9 @@ static int launch_gram(rgm_solver s, const T *X, int64_t ldx, int nx, const T *Y
         CK(cudaFuncGetAttributes(&fa, gram_kernel<T>));
         static_smem = fa.sharedSizeBytes;
     }
-    const int budget = (int)((48 * 1024 - static_smem) / sizeof(double));
+    const int budget = (int)((48 * 1024 - static_smem) / sizeof(T));
     op.tile = std::min(256, budget / ncol - 1);
-    const size_t smem = sizeof(double) * (size_t)ncol * (op.tile + 1);
+    const size_t smem = std::max(sizeof(T) * (size_t)ncol * (op.tile + 1), sizeof(double) * RGM_THREADS);
     {
         const double n = (double)s->n, np_ = (double)npmax;
         ProfScope ps(s, RGM_PROF_GRAM, 2.0 * n * np_, (double)sizeof(T) * n * ncol);
@@ -441,44 +463,61 @@ __global__ void set_tol_kernel(Small *s, double rtol, int precond, double floor_
     }
 }
 
-// W = A U and the LU of E = U^T W (binary64), once per (operator, recycle space).
-static int coarse_setup(rgm_solver s)
+// W = A U, E = U^T W and the LU of E, once per (operator, recycle space).
+// Binary64 solves form them in binary64.  GMRES-IR uses U and W only inside
+// its binary32 inner solve, so there W = A U is formed from the binary32
+// operator and U (W in binary32, as every vector of the inner solve), and
+// E = U^T W is accumulated in binary64 from the stored binary32 columns, so
+// that the inner projector is exact for the vectors it is applied with; E
+// and its LU stay binary64.
+template <typename T>
+static int coarse_matrices(rgm_solver s, int k, const T *sval, T *Urow, const T *U, T *W)
 {
-    const int k = s->k_cur;
     if (k > 0) {   // W = A U, one pass over the operator
         {
-            ProfScope ps_(s, RGM_PROF_OTHER, 0.0, 16.0 * (double)s->n * k);
-            urow_kernel<<<(unsigned)((s->n + RGM_UROW_ROWS - 1) / RGM_UROW_ROWS), 256, 0, s->st>>>(
-                s->Urow, s->U, s->n, s->ld, k);
+            ProfScope ps_(s, RGM_PROF_OTHER, 0.0, 2.0 * sizeof(T) * (double)s->n * k);
+            urow_kernel<T><<<(unsigned)((s->n + RGM_UROW_ROWS - 1) / RGM_UROW_ROWS), 256, 0, s->st>>>(
+                Urow, U, s->n, s->ld, k);
         }
         const int grid = (int)std::min<int64_t>((s->nslices + 7) / 8, 8 * (int64_t)s->nsm);
         const double flops = 2.0 * (double)s->nnz * k;
-        const double bytes = 12.0 * (double)s->nnz + 8.0 * (double)s->n * (2.0 * k + 1.0);
+        const double bytes = (sizeof(T) + 4.0) * (double)s->nnz + sizeof(T) * (double)s->n * (2.0 * k + 1.0);
         ProfScope ps_(s, RGM_PROF_OTHER, flops, bytes);
-        spmm_kernel<<<grid, 256, 0, s->st>>>(s->slice_ptr, s->scol, s->sval, s->perm, s->nslices, s->Urow,
-                                             k, s->W, s->ld);
+        spmm_kernel<T><<<grid, 256, 0, s->st>>>(s->slice_ptr, s->scol, sval, s->perm, s->nslices, Urow, k, W,
+                                                s->ld);
     }
     CK(cudaGetLastError());
     // E_ij = u_i . w_j, then ||u_i||^2, ||w_i||^2
-    int rc = launch_gram<double>(s, s->U, s->ld, k, s->W, s->ld, GRAM_UW, nullptr, k, s->gram_out);
+    int rc = launch_gram<T>(s, U, s->ld, k, W, s->ld, GRAM_UW, nullptr, k, s->gram_out);
     if (rc) return rc;
     { ProfScope ps_(s, RGM_PROF_SMALL); lu_kernel<<<1, 256, 0, s->st>>>(s->sm, k, s->gram_out, s->gram_out + k * k, 0); }
     CK(cudaGetLastError());
     if (s->cfg.proj != RGM_PROJ_OBLIQUE && k > 0) {
         // Gram matrix of the projector's columns: U (orthogonal) or W = A U (least squares)
-        const double *Y = (s->cfg.proj == RGM_PROJ_LS) ? s->W : s->U;
-        if ((rc = launch_gram<double>(s, Y, s->ld, k, Y, s->ld, GRAM_PACKED, nullptr, k, s->gram_out))) return rc;
+        const T *Y = (s->cfg.proj == RGM_PROJ_LS) ? W : U;
+        if ((rc = launch_gram<T>(s, Y, s->ld, k, Y, s->ld, GRAM_PACKED, nullptr, k, s->gram_out))) return rc;
         { ProfScope ps_(s, RGM_PROF_SMALL); lu_kernel<<<1, 256, 0, s->st>>>(s->sm, k, s->gram_out, nullptr, 1); }
         CK(cudaGetLastError());
     }
-    rc = read_header(s);
-    if (rc) return rc;
-    // binary32 copies for the GMRES-IR inner solve
-    if (s->cfg.precision == RGM_FP32_IR && k > 0) {
-        { ProfScope ps_(s, RGM_PROF_OTHER); convert_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U32, s->U, s->n, s->ld, k); }
-        { ProfScope ps_(s, RGM_PROF_OTHER); convert_kernel<<<s->nblocks, 256, 0, s->st>>>(s->W32, s->W, s->n, s->ld, k); }
+    return RGM_OK;
+}
+
+static int coarse_setup(rgm_solver s)
+{
+    const int k = s->k_cur;
+    int rc;
+    if (s->cfg.precision == RGM_FP32_IR) {
+        if (k > 0) {
+            ProfScope ps_(s, RGM_PROF_OTHER, 0.0, 12.0 * (double)s->n * k);
+            convert_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U32, s->U, s->n, s->ld, k);
+        }
         CK(cudaGetLastError());
+        rc = coarse_matrices<float>(s, k, s->sval32, reinterpret_cast<float *>(s->Urow), s->U32, s->W32);
+    } else {
+        rc = coarse_matrices<double>(s, k, s->sval, s->Urow, s->U, s->W);
     }
+    if (rc) return rc;
+    if ((rc = read_header(s))) return rc;
     s->coarse_stale = false;
     return RGM_OK;
 }
@@ -1085,8 +1124,7 @@ static void free_all(rgm_solver s)
     void *dp[] = {s->slice_ptr, s->scol, s->perm, s->csr2sell, s->sval, s->sval32, s->val_stage, s->V, s->U, s->W, s->w, s->r, s->b, s->x,
                   s->V32, s->U32, s->W32, s->w32, s->r32, s->b32, s->x32, s->X, s->Urow, s->gwin,
                   s->dvec, s->partials, s->counter, s->gpart, s->pairs, s->gram_out, s->sm};
-    for (void *p : dp)
-        if (p) cudaFree(p);
+    for (void *p : dp) dev_free(s, p);
     if (s->hs) cudaFreeHost(s->hs);
     for (ProfRec &r : s->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
@@ -1132,7 +1170,7 @@ int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
     const int64_t ncolV = c.m + c.k + 1;
     s->npairs_max = RGM_WMAX * (RGM_WMAX + 1) / 2 + RGM_KMAX * RGM_KMAX + 2 * RGM_KMAX;
     cudaError_t e = cudaSuccess;
-#define ALLOC(p, bytes) if (e == cudaSuccess) e = cudaMalloc((void **)&(p), (bytes))
+#define ALLOC(p, bytes) if (e == cudaSuccess) e = dev_alloc(s, (void **)&(p), (bytes))
     ALLOC(s->V, sizeof(double) * s->ld * ncolV);
     ALLOC(s->U, sizeof(double) * s->ld * kmax);
     ALLOC(s->W, sizeof(double) * s->ld * kmax);
@@ -1252,18 +1290,17 @@ int rgm_set_operator_csr(rgm_solver s, int64_t n, int64_t nnz, const int64_t *ro
         }
     }
     void *old[] = {s->slice_ptr, s->scol, s->perm, s->csr2sell, s->sval, s->sval32, s->val_stage};
-    for (void *p : old)
-        if (p) cudaFree(p);
+    for (void *p : old) dev_free(s, p);
     s->slice_ptr = nullptr; s->scol = nullptr; s->perm = nullptr; s->csr2sell = nullptr;
     s->sval = nullptr; s->sval32 = nullptr; s->val_stage = nullptr;
-    CK(cudaMalloc((void **)&s->slice_ptr, sizeof(int64_t) * (nslices + 1)));
-    CK(cudaMalloc((void **)&s->scol, sizeof(int32_t) * std::max<int64_t>(nsell, 1)));
-    CK(cudaMalloc((void **)&s->perm, sizeof(int32_t) * nslices * 32));
-    CK(cudaMalloc((void **)&s->csr2sell, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
-    CK(cudaMalloc((void **)&s->sval, sizeof(double) * std::max<int64_t>(nsell, 1)));
-    CK(cudaMalloc((void **)&s->val_stage, sizeof(double) * std::max<int64_t>(nnz, 1)));
+    CK(dev_alloc(s, (void **)&s->slice_ptr, sizeof(int64_t) * (nslices + 1)));
+    CK(dev_alloc(s, (void **)&s->scol, sizeof(int32_t) * std::max<int64_t>(nsell, 1)));
+    CK(dev_alloc(s, (void **)&s->perm, sizeof(int32_t) * nslices * 32));
+    CK(dev_alloc(s, (void **)&s->csr2sell, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+    CK(dev_alloc(s, (void **)&s->sval, sizeof(double) * std::max<int64_t>(nsell, 1)));
+    CK(dev_alloc(s, (void **)&s->val_stage, sizeof(double) * std::max<int64_t>(nnz, 1)));
     if (s->cfg.precision == RGM_FP32_IR)
-        CK(cudaMalloc((void **)&s->sval32, sizeof(float) * std::max<int64_t>(nsell, 1)));
+        CK(dev_alloc(s, (void **)&s->sval32, sizeof(float) * std::max<int64_t>(nsell, 1)));
     CK(cudaMemcpyAsync(s->slice_ptr, sp.data(), sizeof(int64_t) * (nslices + 1), cudaMemcpyHostToDevice, s->st));
     CK(cudaMemcpyAsync(s->scol, scol.data(), sizeof(int32_t) * std::max<int64_t>(nsell, 1), cudaMemcpyHostToDevice, s->st));
     CK(cudaMemcpyAsync(s->perm, perm.data(), sizeof(int32_t) * nslices * 32, cudaMemcpyHostToDevice, s->st));
@@ -1313,18 +1350,17 @@ int rgm_set_operator_sell(rgm_solver s, int64_t n, int64_t nslices, const int64_
     std::vector<int32_t> map(std::max<int64_t>(nsell, 1));
     for (int64_t e = 0; e < nsell; ++e) map[e] = (int32_t)e;
     void *old[] = {s->slice_ptr, s->scol, s->perm, s->csr2sell, s->sval, s->sval32, s->val_stage};
-    for (void *p : old)
-        if (p) cudaFree(p);
+    for (void *p : old) dev_free(s, p);
     s->slice_ptr = nullptr; s->scol = nullptr; s->perm = nullptr; s->csr2sell = nullptr;
     s->sval = nullptr; s->sval32 = nullptr; s->val_stage = nullptr;
     const int64_t ne = std::max<int64_t>(nsell, 1);
-    CK(cudaMalloc((void **)&s->slice_ptr, sizeof(int64_t) * (nslices + 1)));
-    CK(cudaMalloc((void **)&s->scol, sizeof(int32_t) * ne));
-    CK(cudaMalloc((void **)&s->perm, sizeof(int32_t) * nslices * 32));
-    CK(cudaMalloc((void **)&s->csr2sell, sizeof(int32_t) * ne));
-    CK(cudaMalloc((void **)&s->sval, sizeof(double) * ne));
-    CK(cudaMalloc((void **)&s->val_stage, sizeof(double) * ne));
-    if (s->cfg.precision == RGM_FP32_IR) CK(cudaMalloc((void **)&s->sval32, sizeof(float) * ne));
+    CK(dev_alloc(s, (void **)&s->slice_ptr, sizeof(int64_t) * (nslices + 1)));
+    CK(dev_alloc(s, (void **)&s->scol, sizeof(int32_t) * ne));
+    CK(dev_alloc(s, (void **)&s->perm, sizeof(int32_t) * nslices * 32));
+    CK(dev_alloc(s, (void **)&s->csr2sell, sizeof(int32_t) * ne));
+    CK(dev_alloc(s, (void **)&s->sval, sizeof(double) * ne));
+    CK(dev_alloc(s, (void **)&s->val_stage, sizeof(double) * ne));
+    if (s->cfg.precision == RGM_FP32_IR) CK(dev_alloc(s, (void **)&s->sval32, sizeof(float) * ne));
     CK(cudaMemcpyAsync(s->slice_ptr, sp.data(), sizeof(int64_t) * (nslices + 1), cudaMemcpyHostToDevice, s->st));
     CK(cudaMemcpyAsync(s->scol, cl.data(), sizeof(int32_t) * ne, cudaMemcpyHostToDevice, s->st));
     CK(cudaMemcpyAsync(s->perm, pm.data(), sizeof(int32_t) * nslices * 32, cudaMemcpyHostToDevice, s->st));
@@ -1710,6 +1746,15 @@ int rgm_wait_selftest(int64_t limit_ns, int *blocks_gave_up, int *fault_flag)
 
 // Library-internal: the solver's device value buffer (for in-library producers
 // such as the FE workload) and a copy of its configuration.
+int rgm_solver_device_bytes(rgm_solver s, int64_t *bytes)
+{
+    if (!s || !bytes) return RGM_E_ARG;
+    int64_t b = 0;
+    for (const auto &a : s->allocs) b += (int64_t)a.second;
+    *bytes = b;
+    return RGM_OK;
+}
+
 int rgm_internal_nnz(rgm_solver s, int64_t *nnz)
 {
     if (!s || !nnz) return RGM_E_ARG;

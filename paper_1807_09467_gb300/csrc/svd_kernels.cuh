@@ -86,10 +86,11 @@ __global__ void extrap_kernel(double *__restrict__ x, const double *__restrict__
 // gather, through a shared-memory tile of RGM_UROW_ROWS rows (coalesced on
 // both sides).
 #define RGM_UROW_ROWS 128
-__global__ void __launch_bounds__(256) urow_kernel(double *__restrict__ Urow, const double *__restrict__ U,
+template <typename T>
+__global__ void __launch_bounds__(256) urow_kernel(T *__restrict__ Urow, const T *__restrict__ U,
                                                    int64_t n, int64_t ld, int k)
 {
-    __shared__ double t[RGM_UROW_ROWS * (RGM_KMAX + 1)];
+    __shared__ T t[RGM_UROW_ROWS * (RGM_KMAX + 1)];
     const int64_t r0 = (int64_t)blockIdx.x * RGM_UROW_ROWS;
     const int nr = (int)min((int64_t)RGM_UROW_ROWS, n - r0);
     for (int i = threadIdx.x; i < RGM_UROW_ROWS * k; i += blockDim.x) {
@@ -107,13 +108,15 @@ __global__ void __launch_bounds__(256) urow_kernel(double *__restrict__ Urow, co
 // is read once per RGM_SPMM_KB columns instead of once per column): one warp
 // per 32-row slice, one lane per row, RGM_SPMM_KB accumulators per lane; the
 // gathered rows of U come from the row-major copy (contiguous per entry).
+// T = float: the binary32 operator and recycle columns of GMRES-IR.
 #define RGM_SPMM_KB 8
+template <typename T>
 __global__ void __launch_bounds__(256) spmm_kernel(const int64_t *__restrict__ slice_ptr,
                                                    const int32_t *__restrict__ scol,
-                                                   const double *__restrict__ sval,
+                                                   const T *__restrict__ sval,
                                                    const int32_t *__restrict__ perm, int64_t nslices,
-                                                   const double *__restrict__ Urow, int k,
-                                                   double *__restrict__ W, int64_t ldw)
+                                                   const T *__restrict__ Urow, int k,
+                                                   T *__restrict__ W, int64_t ldw)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -121,12 +124,12 @@ __global__ void __launch_bounds__(256) spmm_kernel(const int64_t *__restrict__ s
         const int64_t p0 = slice_ptr[sl], p1 = slice_ptr[sl + 1];
         const int pr = perm[(sl << 5) + lane];
         for (int c0 = 0; c0 < k; c0 += RGM_SPMM_KB) {
-            double acc[RGM_SPMM_KB];
+            T acc[RGM_SPMM_KB];
 #pragma unroll
-            for (int c = 0; c < RGM_SPMM_KB; ++c) acc[c] = 0.0;
+            for (int c = 0; c < RGM_SPMM_KB; ++c) acc[c] = (T)0;
             for (int64_t e = p0 + lane; e < p1; e += 32) {
-                const double a = sval[e];
-                const double *u = Urow + (int64_t)scol[e] * k + c0;
+                const T a = sval[e];
+                const T *u = Urow + (int64_t)scol[e] * k + c0;
 #pragma unroll
                 for (int c = 0; c < RGM_SPMM_KB; ++c)
                     if (c0 + c < k) acc[c] = fma(a, u[c], acc[c]);

@@ -626,6 +626,81 @@ __device__ __forceinline__ const T *dot_col(const VecOp<T> &op, int c)
     return op.out;
 }
 
+// ---------------------------------------------------------------- 16-byte vector access
+// The streaming loops move 16 bytes per lane per load (4 binary32 or 2 binary64
+// values): a quarter (a half) of the load instructions of one value per lane,
+// and four (two) times the bytes in flight per instruction.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; using itype = int4; };
+template <> struct Vec16<double> { using type = double2; using itype = int2; };
+
+template <typename V, typename T>
+__device__ __forceinline__ T vcomp(const V &v, int t) { return reinterpret_cast<const T *>(&v)[t]; }
+template <typename V>
+__device__ __forceinline__ int icomp(const V &v, int t) { return reinterpret_cast<const int *>(&v)[t]; }
+
+// Row sums of one 32-row slice of the sliced-ELL operator, sum_k sval[p0 +
+// 32 k + l] x[scol[p0 + 32 k + l]] for the slice's lane l (returned in lane l).
+// The slice's entries are read as 16-byte vectors: in a chunk of VW slice
+// columns lane l holds entries VW l .. VW l + VW - 1, i.e. VW consecutive rows
+// of one column, and keeps one partial sum per row it sees; the lanes that saw
+// the same rows are added by a butterfly at the end (no row is ever written by
+// two lanes).  Columns past the last whole chunk are read one per lane.
+template <typename T>
+__device__ __forceinline__ T slice_rowsum(const T *sval, const int32_t *scol, const T *x, int64_t p0, int64_t p1)
+{
+    constexpr int VW = 16 / (int)sizeof(T);
+    using VT = typename Vec16<T>::type;
+    using VI = typename Vec16<T>::itype;
+    // chunks in flight per lane (fewer when the register budget is 64)
+    constexpr int U = (RGM_MINB >= 4) ? 2 : (sizeof(T) == 4) ? 4 : 2;
+    const int lane = threadIdx.x & 31;
+    const int64_t wd = (p1 - p0) >> 5;
+    const int64_t nch = wd / VW;
+    T acc[VW];
+#pragma unroll
+    for (int t = 0; t < VW; ++t) acc[t] = (T)0;
+    const VT *vv = reinterpret_cast<const VT *>(sval + p0) + lane;
+    const VI *vc = reinterpret_cast<const VI *>(scol + p0) + lane;
+    int64_t ch = 0;
+    for (; ch + U <= nch; ch += U) {
+        VT v[U];
+        VI c[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            v[u] = vv[(ch + u) * 32];
+            c[u] = vc[(ch + u) * 32];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int t = 0; t < VW; ++t) acc[t] += vcomp<VT, T>(v[u], t) * x[icomp(c[u], t)];
+    }
+    for (; ch < nch; ++ch) {
+        const VT v = vv[ch * 32];
+        const VI c = vc[ch * 32];
+#pragma unroll
+        for (int t = 0; t < VW; ++t) acc[t] += vcomp<VT, T>(v, t) * x[icomp(c, t)];
+    }
+    // lanes l, l + 32/VW, ... hold the same VW rows: add them
+#pragma unroll
+    for (int o = 32 / VW; o < 32; o <<= 1)
+#pragma unroll
+        for (int t = 0; t < VW; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+    // row `lane` is component lane % VW of lane lane / VW
+    T a = (T)0;
+#pragma unroll
+    for (int t = 0; t < VW; ++t) {
+        const T v = __shfl_sync(0xffffffffu, acc[t], lane / VW);
+        if ((lane % VW) == t) a = v;
+    }
+    for (int64_t k = nch * VW; k < wd; ++k) {
+        const int64_t e = p0 + 32 * k + lane;
+        a += sval[e] * x[scol[e]];
+    }
+    return a;
+}
+
 // What one block did in a pass: left without touching the completion counter
 // (gated off, or nothing to reduce), arrived, or arrived last and finalised.
 enum PassResult { PASS_SKIPPED = 0, PASS_ARRIVED = 1, PASS_LAST = 2, PASS_RELEASED = 3 };
@@ -651,14 +726,36 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op, const int bid)
         if (op.dyn & DYN_OUT_VNBM1) op.out = const_cast<T *>(op.V) + (int64_t)(s->nb - 1) * op.ldv;
     }
 
+    constexpr int VW = 16 / (int)sizeof(T);   // values per 16-byte vector
+    using VT = typename Vec16<T>::type;
+    constexpr int NG = RGM_TILE / VW;          // AXPY: row groups of VW rows in a tile
+    constexpr int NPH = RGM_THREADS / NG;      //       column phases (threads per row group)
+    static_assert(NPH >= 1 && NG * NPH == RGM_THREADS, "AXPY thread layout");
     __shared__ T cW[RGM_KMAX], cU[RGM_KMAX], cV[RGM_HLD];
-    __shared__ T ws[RGM_TILE];
+    // AXPY columns [W | Vraw | U] as one list: pointer and coefficient
+    __shared__ const T *acol[RGM_KMAX + RGM_HLD + RGM_KMAX];
+    __shared__ T acoef[RGM_KMAX + RGM_HLD + RGM_KMAX];
+    __shared__ __align__(16) T ws[RGM_TILE];
+    __shared__ __align__(16) T apart[NPH * RGM_TILE];    // AXPY partial sums per column phase
     __shared__ double xs;
     if (threadIdx.x == 0) xs = (op.xscale >= 0) ? s->colscale[op.xscale] : 1.0;
+    const int nac = (op.src == SRC_AXPY) ? op.nW + op.nV + op.nU : 0;
     if (op.src == SRC_AXPY) {
-        for (int i = threadIdx.x; i < op.nW; i += blockDim.x) cW[i] = (T)s->coefW[i];
-        for (int i = threadIdx.x; i < op.nV; i += blockDim.x) cV[i] = (T)s->coefV[i];
-        for (int i = threadIdx.x; i < op.nU; i += blockDim.x) cU[i] = (T)s->coefU[i];
+        for (int i = threadIdx.x; i < op.nW; i += blockDim.x) {
+            cW[i] = (T)s->coefW[i];
+            acol[i] = op.W + (int64_t)i * op.ldw;
+            acoef[i] = cW[i];
+        }
+        for (int i = threadIdx.x; i < op.nV; i += blockDim.x) {
+            cV[i] = (T)s->coefV[i];
+            acol[op.nW + i] = op.V + (int64_t)i * op.ldv;
+            acoef[op.nW + i] = cV[i];
+        }
+        for (int i = threadIdx.x; i < op.nU; i += blockDim.x) {
+            cU[i] = (T)s->coefU[i];
+            acol[op.nW + op.nV + i] = op.U + (int64_t)i * op.ldu;
+            acoef[op.nW + op.nV + i] = cU[i];
+        }
     }
     __syncthreads();
 
@@ -683,9 +780,7 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op, const int bid)
             const int slot = (t & 1) ? (NW - 1 - warp) : warp;
             const int64_t sl = (base >> 5) + slot;
             const int64_t p0 = op.slice_ptr[sl], p1 = op.slice_ptr[sl + 1];
-            T a = 0;
-#pragma unroll 8
-            for (int64_t e = p0 + lane; e < p1; e += 32) a += op.sval[e] * op.x[op.scol[e]];
+            const T a = slice_rowsum<T>(op.sval, op.scol, op.x, p0, p1);
             const int pr = op.perm[(sl << 5) + lane];
             if (pr >= 0) op.out[pr] = (op.src == SRC_SPMV) ? a * sc : op.b[pr] - a;
         }
@@ -702,15 +797,41 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op, const int bid)
             const int64_t sl = (base >> 5) + warp;
             const int64_t p0 = op.slice_ptr[sl], p1 = op.slice_ptr[sl + 1];
             const T sc = (T)xs;
-            T a = 0;
-#pragma unroll 8
-            for (int64_t e = p0 + lane; e < p1; e += 32) a += op.sval[e] * op.x[op.scol[e]];
+            const T a = slice_rowsum<T>(op.sval, op.scol, op.x, p0, p1);
             const int pr = op.perm[(sl << 5) + lane];
             if (pr >= 0) {
                 const T v = (op.src == SRC_SPMV) ? a * sc : op.b[pr] - a;
                 op.out[pr] = v;
                 ws[pr - base] = v;
             }
+        } else if (op.src == SRC_AXPY && nrow == RGM_TILE) {
+            // full tile: thread (g, ph) sums the columns c = ph (mod NPH) over
+            // rows base + VW g .. + VW - 1 with 16-byte loads, all of its
+            // columns' loads in flight together; the NPH partial sums of a row
+            // are added through shared memory
+            const int g = threadIdx.x % NG, ph = threadIdx.x / NG;
+            const int64_t r = base + (int64_t)VW * g;
+            VT a;
+#pragma unroll
+            for (int t = 0; t < VW; ++t) reinterpret_cast<T *>(&a)[t] = (T)0;
+            if (ph == 0) a = *reinterpret_cast<const VT *>(op.win + r);
+#pragma unroll 8
+            for (int c = ph; c < nac; c += NPH) {
+                const VT v = *reinterpret_cast<const VT *>(acol[c] + r);
+                const T cf = acoef[c];
+#pragma unroll
+                for (int t = 0; t < VW; ++t)
+                    reinterpret_cast<T *>(&a)[t] += cf * vcomp<VT, T>(v, t);
+            }
+            reinterpret_cast<VT *>(apart + ph * RGM_TILE)[g] = a;
+            __syncthreads();
+            const int t = threadIdx.x;
+            T sum = apart[t];
+#pragma unroll
+            for (int q = 1; q < NPH; ++q) sum += apart[q * RGM_TILE + t];
+            op.out[base + t] = sum;
+            ws[t] = sum;
+            if (nd == 0) __syncthreads();      // apart is rewritten by the next tile
         } else if (op.src == SRC_COPY || op.src == SRC_AXPY) {
             const int t = threadIdx.x;
             if (t < nrow) {
@@ -732,27 +853,49 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op, const int bid)
         __syncthreads();
         // ---- phase 2: dot products, one warp per column over the tile
         if (nrow == RGM_TILE) {
-            // full tile: every load of the warp's columns is issued up front
-            T wl[RGM_TILE / 32];
+            // full tile: 16-byte loads, lane l holding rows VW l + 32 VW i ..;
+            // the loads of QG columns are in flight together
+            constexpr int NVL = RGM_TILE / (32 * VW);
+            constexpr int QG = (RGM_MINB >= 4) ? 1 : (sizeof(T) == 4) ? 2 : 1;
+            VT wl[NVL];
 #pragma unroll
-            for (int i = 0; i < RGM_TILE / 32; ++i) wl[i] = ws[lane + 32 * i];
+            for (int i = 0; i < NVL; ++i) wl[i] = reinterpret_cast<const VT *>(ws)[lane + 32 * i];
 #pragma unroll
-            for (int q = 0; q < QMAX; ++q) {
-                const int c = warp + q * NW;
-                if (c < nd) {
-                    T a = 0;
-                    if (c == ndc_ && op.wvec) {          // weighted norm: ||wvec .* w||^2
+            for (int q0 = 0; q0 < QMAX; q0 += QG) {
+                VT cv[QG][NVL];
 #pragma unroll
-                        for (int i = 0; i < RGM_TILE / 32; ++i) {
-                            const T v = wl[i] * op.wvec[base + lane + 32 * i];
-                            a += v * v;
-                        }
-                    } else {
-                        const T *cp = (c == ndc_) ? ws : dot_col(op, c) + base;
+                for (int gq = 0; gq < QG; ++gq) {
+                    const int q = q0 + gq, c = warp + q * NW;
+                    if (q < QMAX && c < nd && (c != ndc_ || op.wvec)) {
+                        const VT *cp = reinterpret_cast<const VT *>(
+                            (c == ndc_) ? op.wvec + base : dot_col(op, c) + base);
 #pragma unroll
-                        for (int i = 0; i < RGM_TILE / 32; ++i) a += cp[lane + 32 * i] * wl[i];
+                        for (int i = 0; i < NVL; ++i) cv[gq][i] = cp[lane + 32 * i];
                     }
-                    acc[q] += (double)a;
+                }
+#pragma unroll
+                for (int gq = 0; gq < QG; ++gq) {
+                    const int q = q0 + gq, c = warp + q * NW;
+                    if (q < QMAX && c < nd) {
+                        T a = 0;
+                        if (c == ndc_) {                 // ||w||^2 or ||wvec .* w||^2
+#pragma unroll
+                            for (int i = 0; i < NVL; ++i)
+#pragma unroll
+                                for (int t = 0; t < VW; ++t) {
+                                    T v = vcomp<VT, T>(wl[i], t);
+                                    if (op.wvec) v *= vcomp<VT, T>(cv[gq][i], t);
+                                    a += v * v;
+                                }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < NVL; ++i)
+#pragma unroll
+                                for (int t = 0; t < VW; ++t)
+                                    a += vcomp<VT, T>(cv[gq][i], t) * vcomp<VT, T>(wl[i], t);
+                        }
+                        acc[q] += (double)a;
+                    }
                 }
             }
         } else {
@@ -850,7 +993,7 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op, const int bid)
 }
 
 template <typename T, int QMAX>
-__global__ void __launch_bounds__(RGM_THREADS, 4) vec_kernel(VecOp<T> op)
+__global__ void __launch_bounds__(RGM_THREADS, RGM_MINB) vec_kernel(VecOp<T> op)
 {
     // programmatic dependent launch: blocks may be scheduled while the previous
     // pass finishes; nothing it wrote is read before this wait returns
@@ -876,7 +1019,6 @@ struct CycleOp {
                          // the Givens step, the plain update that stores v_{j+1}
     int m;               // Arnoldi steps at most
     unsigned *arrive;    // arrival counter of the plain barrier
-    int cap2;            // co-resident blocks of the two-blocks-per-SM build (host side only)
 };
 
 // After a pass: the last block publishes generation `target`, the others wait
@@ -955,10 +1097,9 @@ __device__ __forceinline__ void cycle_body(const CycleOp<T> &c, const int bid)
     }
 }
 
-// MINB: resident blocks per SM the build guarantees; grids of at most two
-// blocks per SM take the variant with twice the registers per thread.
-template <typename T, int QMAX, int MINB>
-__global__ void __launch_bounds__(RGM_THREADS, MINB) cycle_kernel(CycleOp<T> c)
+// Built for RGM_MINB resident blocks per SM (the grids never hold more).
+template <typename T, int QMAX>
+__global__ void __launch_bounds__(RGM_THREADS, RGM_MINB) cycle_kernel(CycleOp<T> c)
 {
     cycle_body<T, QMAX>(c, blockIdx.x);
 }
@@ -971,7 +1112,7 @@ __global__ void __launch_bounds__(RGM_THREADS, MINB) cycle_kernel(CycleOp<T> c)
 // and the others carry on; co-residency of the whole grid (the cooperative
 // launch) keeps every barrier's blocks resident together.
 template <typename T, int QMAX>
-__global__ void __launch_bounds__(RGM_THREADS, 4)
+__global__ void __launch_bounds__(RGM_THREADS, RGM_MINB)
     batch_cycle_kernel(const CycleOp<T> *__restrict__ ops, const int *__restrict__ first, int nsys)
 {
     int lo = 0, hi = nsys - 1;                  // the last i with first[i] <= blockIdx.x
@@ -1003,11 +1144,9 @@ static __global__ void wait_selftest_kernel(Small *s, unsigned long long limit_n
 int launch_vec(const VecOp<double> &op, int nd_max, cudaStream_t st);
 int launch_vec(const VecOp<float> &op, int nd_max, cudaStream_t st);
 // cycle_kernel: blocks that can be resident at once for this column bound
-// (0 if the device cannot launch it cooperatively) in the build that
-// guarantees minb (4 or 2) resident blocks per SM, and the launch itself
-// (which takes the two-blocks-per-SM build when c.cap2 holds the grid).
-int cycle_capacity(const CycleOp<double> &c, int nd_max, int minb);
-int cycle_capacity(const CycleOp<float> &c, int nd_max, int minb);
+// (0 if the device cannot launch it cooperatively), and the launch itself.
+int cycle_capacity(const CycleOp<double> &c, int nd_max);
+int cycle_capacity(const CycleOp<float> &c, int nd_max);
 int launch_cycle(const CycleOp<double> &c, int nd_max, cudaStream_t st);
 int launch_cycle(const CycleOp<float> &c, int nd_max, cudaStream_t st);
 // batch_cycle_kernel: blocks that can be resident at once (0 if not
@@ -1036,13 +1175,13 @@ static cudaError_t launch_vec_pdl(const VecOp<T> &op, cudaStream_t st)
     return cudaLaunchKernelEx(&cfg, vec_kernel<T, Q>, op);
 }
 
-template <typename T, int Q, int MINB>
+template <typename T, int Q>
 static int cycle_capacity_q(int dev)
 {
     int coop = 0, nsm = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cycle_kernel<T, Q, MINB>, RGM_THREADS, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cycle_kernel<T, Q>, RGM_THREADS, 0) !=
         cudaSuccess)
         return 0;
     return per_sm * nsm;
@@ -1051,9 +1190,6 @@ static int cycle_capacity_q(int dev)
 template <typename T, int Q>
 static cudaError_t launch_cycle_q(const CycleOp<T> &c, cudaStream_t st)
 {
-    // the wider-register variant when its residency holds the whole grid
-    // (c.cap2: the caller's cached capacity of that build on its device)
-    const bool wide = c.pass[0].nblocks <= c.cap2;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(c.pass[0].nblocks);
     cfg.blockDim = dim3(RGM_THREADS);
@@ -1064,8 +1200,7 @@ static cudaError_t launch_cycle_q(const CycleOp<T> &c, cudaStream_t st)
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return wide ? cudaLaunchKernelEx(&cfg, cycle_kernel<T, Q, 2>, c)
-                : cudaLaunchKernelEx(&cfg, cycle_kernel<T, Q, 4>, c);
+    return cudaLaunchKernelEx(&cfg, cycle_kernel<T, Q>, c);
 }
 
 template <typename T, int Q>
@@ -1102,7 +1237,7 @@ static cudaError_t launch_batch_q(const CycleOp<T> *ops, const int *first, int n
 // Entry points of one (precision, column tier) translation unit.
 #define RGM_VEC_DECLARE(TN, T, QN)                                                                 \
     int vec_launch_##TN##_##QN(const VecOp<T> &op, cudaStream_t st);                               \
-    int vec_cycle_capacity_##TN##_##QN(int dev, int minb);                                         \
+    int vec_cycle_capacity_##TN##_##QN(int dev);                                                   \
     int vec_cycle_launch_##TN##_##QN(const CycleOp<T> &c, cudaStream_t st);                        \
     int vec_batch_capacity_##TN##_##QN(int dev);                                                   \
     int vec_batch_launch_##TN##_##QN(const CycleOp<T> *ops, const int *first, int nsys, int nblocks, \
@@ -1113,10 +1248,7 @@ static cudaError_t launch_batch_q(const CycleOp<T> *ops, const int *first, int n
         return (int)launch_vec_pdl<T, Q>(op, st);                                                  \
     }
 #define RGM_VEC_DEFINE_CYCLE(TN, T, QN, Q)                                                         \
-    int vec_cycle_capacity_##TN##_##QN(int dev, int minb)                                          \
-    {                                                                                              \
-        return minb == 2 ? cycle_capacity_q<T, Q, 2>(dev) : cycle_capacity_q<T, Q, 4>(dev);        \
-    }                                                                                              \
+    int vec_cycle_capacity_##TN##_##QN(int dev) { return cycle_capacity_q<T, Q>(dev); }            \
     int vec_cycle_launch_##TN##_##QN(const CycleOp<T> &c, cudaStream_t st)                         \
     {                                                                                              \
         return (int)launch_cycle_q<T, Q>(c, st);                                                   \
@@ -1191,10 +1323,35 @@ __device__ __forceinline__ void packed_pair(int p, int *i, int *j)
     *i = p - jj * (jj + 1) / 2;
 }
 
+// sum over r = r0, r0 + step, .. < nrow of a[r] b[r], accumulated in binary64.
+// binary32 columns: products and sums of 8 consecutive terms in binary32 (its
+// FMA pipe is 64 times wider than the binary64 one on this part), each block
+// sum then added in binary64.
+__device__ __forceinline__ double pair_dot(const double *a, const double *b, int r0, int nrow, int step,
+                                           double acc)
+{
+    for (int r = r0; r < nrow; r += step) acc = fma(a[r], b[r], acc);
+    return acc;
+}
+__device__ __forceinline__ double pair_dot(const float *a, const float *b, int r0, int nrow, int step,
+                                           double acc)
+{
+    int r = r0;
+    for (; r + 7 * step < nrow; r += 8 * step) {
+        float f = 0.f;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) f = fmaf(a[r + t * step], b[r + t * step], f);
+        acc += (double)f;
+    }
+    for (; r < nrow; r += step) acc += (double)(a[r] * b[r]);
+    return acc;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(RGM_THREADS) gram_kernel(GramOp<T> op)
 {
-    extern __shared__ double gsm[];
+    extern __shared__ __align__(16) unsigned char gsm_raw[];
+    T *gsm = reinterpret_cast<T *>(gsm_raw);
     const int nx = op.nx_dev ? *op.nx_dev : op.nx;
     const int ny = (op.mode == GRAM_UW) ? nx : 0;
     const int ncol = nx + ny, ts = op.tile + 1;
@@ -1240,34 +1397,28 @@ __global__ void __launch_bounds__(RGM_THREADS) gram_kernel(GramOp<T> op)
         for (int t = threadIdx.x; t < nrow * ncol; t += RGM_THREADS) {
             const int r = t % nrow, c = t / nrow;
             const T *src = c < nx ? op.X + (int64_t)c * op.ldx : op.Y + (int64_t)(c - nx) * op.ldy;
-            gsm[c * ts + r] = (double)src[base + r];
+            gsm[c * ts + r] = src[base + r];
         }
         __syncthreads();
         if (split) {
-            if (srs < nsl) {
-                const double *a = gsm + spa * ts, *b = gsm + spb * ts;
-                for (int r = srs; r < nrow; r += nsl) sacc = fma(a[r], b[r], sacc);
-            }
+            if (srs < nsl) sacc = pair_dot(gsm + spa * ts, gsm + spb * ts, srs, nrow, nsl, sacc);
         } else {
 #pragma unroll
             for (int i = 0; i < RGM_GRAM_PMAX; ++i) {
-                if (threadIdx.x + i * RGM_THREADS < npairs) {
-                    const double *a = gsm + pa[i] * ts, *b = gsm + pb[i] * ts;
-                    double s = 0.0;
-                    for (int r = 0; r < nrow; ++r) s += a[r] * b[r];
-                    acc[i] += s;
-                }
+                if (threadIdx.x + i * RGM_THREADS < npairs)
+                    acc[i] += pair_dot(gsm + pa[i] * ts, gsm + pb[i] * ts, 0, nrow, 1, 0.0);
             }
         }
         __syncthreads();
     }
     if (split) {
-        // the tile buffer holds at least RGM_THREADS + 1 doubles (tile 256, one column)
-        gsm[threadIdx.x] = (srs < nsl) ? sacc : 0.0;
+        // the launch gives the buffer at least RGM_THREADS doubles
+        double *dsm = reinterpret_cast<double *>(gsm_raw);
+        dsm[threadIdx.x] = (srs < nsl) ? sacc : 0.0;
         __syncthreads();
         if ((int)threadIdx.x < npairs) {
             double v = 0.0;
-            for (int q = 0; q < nsl; ++q) v += gsm[threadIdx.x + q * npairs];
+            for (int q = 0; q < nsl; ++q) v += dsm[threadIdx.x + q * npairs];
             acc[0] = v;
         }
     }

@@ -1,29 +1,35 @@
 """Served form: a request loop over time-step sequences with continuous batching.
 
 Each request is one convection-diffusion sequence (its FE workload, seeded
-initial field and number of time steps).  Requests arrive over time; the loop
-admits a waiting request as soon as a slot is free and its device memory fits
-the free HBM, keeps each admitted sequence's operator, snapshot window and
-recycle space resident on the device for its whole life, and advances all
-admitted sequences together: every tick assembles each sequence's next
-system on its own stream, solves all of them with one rgm_batch_solve, and
-updates their windows.  A sequence that finishes frees its slot and memory for
-the next arrival; a request that arrives while others run joins at the next
-tick.  Every solve's latency (from the moment its system could start -- the
-request's arrival for the first step, the end of the previous tick otherwise
--- to the end of the tick that solved it) is recorded.
+initial field and number of time steps).  Requests arrive over time.  The loop
+admits a waiting request as soon as it has arrived, a slot is free and its
+device footprint fits the free HBM read at that moment; each admitted sequence
+keeps its operator, snapshot window and recycle space U / A U resident on the
+device for its whole life and advances on a stream of its own, driven by a
+host thread of its own: assemble the next system, solve, update the window,
+again.  Sequences therefore progress independently -- their kernels overlap
+on the device, a short sequence is not held back by a long one, and a request
+that arrives while others run is admitted the moment a sequence ends (a slot
+frees) instead of at the end of a lockstep tick.  Every solve's latency runs
+from the moment its system could start (the request's arrival for the first
+step, the end of the sequence's previous step otherwise) to the end of its
+solve and window update.
 
 Host-side orchestration only: assembly, solves and window updates all run in
-librgmres's kernels.
+librgmres's kernels.  The solves use the per-pass launches (launch_policy
+"per_pass"): cooperative grids of different sequences are not guaranteed to be
+resident together, so a cooperative cycle launch is left to single-sequence
+use.
 """
 from __future__ import annotations
 
+import threading
 import time
 from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import FE, Solver, batch_solve
+from . import FE, Solver
 
 
 @dataclass
@@ -53,31 +59,61 @@ class Result:
     final: np.ndarray | None = None
     admitted_s: float = 0.0
     finished_s: float = 0.0
+    device_bytes: int = 0        # what its solver and workload held on the device
+    error: str | None = None
 
 
-def device_bytes(req: Request) -> int:
-    """Estimate of the device memory one admitted sequence holds (solver basis,
-    recycle space, window, operator in binary64 + binary32, FE pattern)."""
-    n = (req.p * req.N + 1) ** 2
-    nnz_row = (2 * req.p + 1) ** 2
-    nnz = n * nnz_row
-    vecs = (req.m + req.k + 1) * 12 + 2 * req.k * 12 + req.window * 8 + 32 * 8
-    return int(n * vecs + nnz * (8 + 4 + 4 + 8 + 4 + 4) + (1 << 20))
+def sizes(p: int, N: int) -> tuple[int, int]:
+    """(n, nnz) of the Q_p Dirichlet pattern on N x N quads: two nodes couple
+    when they share an element, i.e. in each direction their 1D indices share
+    a 1D element (a vertex index i couples to [i - p, i + p], an index inside
+    an element to that element's p + 1 indices); boundary rows are identity
+    rows and boundary columns are dropped from interior rows."""
+    L = p * N + 1
+    inner = np.zeros(L, dtype=np.int64)      # interior neighbours of each 1D index
+    for i in range(1, L - 1):
+        lo, hi = (max(i - p, 0), min(i + p, L - 1)) if i % p == 0 else (i // p * p, i // p * p + p)
+        inner[i] = min(hi, L - 2) - max(lo, 1) + 1
+    n = L * L
+    return n, int(inner.sum()) ** 2 + (n - (L - 2) ** 2)
+
+
+def device_bytes(req: Request, precision: str = "fp32_ir") -> int:
+    """Upper estimate of the device memory one admitted sequence holds: the
+    solver (Krylov basis, recycle space, window, operator in sliced ELL with
+    its CSR map, binary32 copies in GMRES-IR, scratch) and the FE workload
+    (pattern, values, element tables).  Checked against the library's own
+    count (rgm_solver_device_bytes + rgm_fe_device_bytes) by the tests."""
+    n, nnz = sizes(req.p, req.N)
+    ld = (n + 31) // 32 * 32
+    ncolV = req.m + req.k + 1
+    kmax = max(req.k, 1)
+    ir = precision == "fp32_ir"
+    vec = 8 * ld * (ncolV + 3 * kmax + 4 + req.window) + (4 * ld * (ncolV + 2 * kmax + 4) if ir else 0)
+    nsell = int(1.6 * nnz) + 32 * 256          # sliced-ELL padding (at most ~1.5x on FE patterns)
+    op = nsell * (4 + 8 + (4 if ir else 0)) + nnz * (4 + 8) + 8 * (n // 8 + 2) + 4 * (n + 256)
+    scratch = 8 * 3200 * 2 * 152 + (1 << 20)   # per-block partial sums (<= 2 blocks per SM), small state
+    fe = 8 * (n + 1) + 12 * nnz + 16 * n + 8 * (req.p + 1) ** 6 * 4 + (1 << 16)
+    return int(vec + op + scratch + fe)
 
 
 class _Live:
-    def __init__(self, req: Request, precision: str, mode: str, stream):
+    def __init__(self, req: Request, precision: str, mode: str):
         import torch
         self.req = req
-        self.stream = stream
-        self.fe = FE(req.p, req.N, req.eps, req.dt, req.beta, stream=stream.cuda_stream)
+        self.stream = torch.cuda.Stream()
+        self.fe = FE(req.p, req.N, req.eps, req.dt, req.beta, stream=self.stream.cuda_stream)
         rp, col = self.fe.pattern()
         self.sol = Solver(self.fe.n, m=req.m, k=req.k, window=req.window, mode=mode,
-                          precision=precision, rtol=req.rtol, stream=stream.cuda_stream)
+                          precision=precision, rtol=req.rtol, stream=self.stream.cuda_stream,
+                          launch_policy="per_pass")
         self.sol.set_operator_csr(rp, col, np.zeros(len(col)))
-        self.u = torch.tensor(self.fe.initial_field(req.a8), dtype=torch.float64, device="cuda")
-        self.done_steps = 0
-        self.ready_s = req.arrival_s
+        with torch.cuda.stream(self.stream):
+            self.u = torch.tensor(self.fe.initial_field(req.a8), dtype=torch.float64, device="cuda")
+        self.stream.synchronize()
+
+    def device_bytes(self) -> int:
+        return self.sol.device_bytes() + self.fe.device_bytes()
 
     def close(self):
         self.sol.close()
@@ -86,18 +122,43 @@ class _Live:
 
 class Server:
     """Continuous-batching loop.  max_slots bounds the sequences in flight;
-    hbm_fraction of the free device memory at start bounds their estimated
-    footprint."""
+    each admission also needs its estimated footprint to fit hbm_fraction of
+    the device memory free at that moment."""
 
     def __init__(self, max_slots: int = 64, hbm_fraction: float = 0.8, precision: str = "fp32_ir",
-                 mode: str = "deflated", coop: bool = False):
-        import torch
+                 mode: str = "deflated"):
         self.max_slots = max_slots
-        self.coop = coop
-        free, _ = torch.cuda.mem_get_info()
-        self.budget = int(hbm_fraction * free)
+        self.hbm_fraction = hbm_fraction
         self.precision = precision
         self.mode = mode
+
+    def _drive(self, lv: _Live, res: Result, t0: float, done):
+        """One sequence, step after step on its own stream (a host thread)."""
+        import torch
+        try:
+            ready = max(lv.req.arrival_s, 0.0)
+            with torch.cuda.stream(lv.stream):
+                for _ in range(lv.req.steps):
+                    val, b = lv.fe.assemble(lv.u)
+                    lv.sol.set_operator_values(val)
+                    x = torch.zeros_like(lv.u) if lv.sol.recycle_dim() else lv.u.clone()
+                    _, st = lv.sol.solve(b, x)
+                    lv.sol.update_recycle_svd(x, want_k=False)
+                    lv.stream.synchronize()
+                    t_end = time.perf_counter() - t0
+                    if st["status"] < 0 or st["true_relres"] > lv.req.rtol:
+                        raise RuntimeError(f"request {lv.req.rid}: solve failed {st}")
+                    lv.u.copy_(x)
+                    res.iters.append(st["iters"])
+                    res.latencies_ms.append(1e3 * (t_end - ready))
+                    ready = t_end
+                res.final = lv.u.cpu().numpy()
+            res.finished_s = time.perf_counter() - t0
+        except Exception as e:          # reported by run(); the slot is freed either way
+            res.error = repr(e)
+        finally:
+            lv.close()
+            done(lv)
 
     def run(self, requests: list[Request], realtime: bool = True) -> tuple[list[Result], dict]:
         """Serve the requests (arrival_s relative to the call).  realtime: wait
@@ -106,64 +167,56 @@ class Server:
         import torch
         pending = sorted(requests, key=lambda r: (r.arrival_s, r.rid))
         results = {r.rid: Result(r.rid) for r in requests}
-        live: list[_Live] = []
-        used = 0
-        t_start = time.perf_counter()
-        now = lambda: time.perf_counter() - t_start
-        ticks = 0
-        solves = 0
-        while pending or live:
-            # admission: arrived, a free slot, and memory for its footprint
-            while pending and len(live) < self.max_slots and (not realtime or pending[0].arrival_s <= now()):
-                need = device_bytes(pending[0])
-                if used + need > self.budget and live:
-                    break
-                req = pending.pop(0)
-                lv = _Live(req, self.precision, self.mode, torch.cuda.Stream())
-                lv.ready_s = max(req.arrival_s, now()) if realtime else now()
-                results[req.rid].admitted_s = now()
-                live.append(lv)
-                used += need
-            if not live:
-                if pending and realtime:
-                    time.sleep(max(0.0, min(pending[0].arrival_s - now(), 0.01)))
-                continue
-            # one tick: the next system of every live sequence, solved together
-            xs, bs = [], []
-            for lv in live:
-                val, b = lv.fe.assemble(lv.u)
-                lv.sol.set_operator_values(val)
-                x = torch.zeros_like(lv.u) if lv.sol.recycle_dim() else lv.u.clone()
-                xs.append(x)
-                bs.append(b)
-            torch.cuda.synchronize()
-            stats = batch_solve([lv.sol for lv in live], bs, xs, coop=self.coop)
-            for lv, x in zip(live, xs):
-                lv.sol.update_recycle_svd(x, want_k=False)
-            torch.cuda.synchronize()
-            t_end = now()
-            ticks += 1
-            still = []
-            for lv, x, st in zip(live, xs, stats):
-                res = results[lv.req.rid]
-                if st["status"] < 0 or st["true_relres"] > lv.req.rtol:
-                    raise RuntimeError(f"request {lv.req.rid}: solve failed {st}")
-                lv.u.copy_(x)
-                res.iters.append(st["iters"])
-                res.latencies_ms.append(1e3 * (t_end - lv.ready_s))
-                lv.ready_s = t_end
-                lv.done_steps += 1
-                solves += 1
-                if lv.done_steps == lv.req.steps:
-                    res.final = lv.u.cpu().numpy()
-                    res.finished_s = t_end
-                    used -= device_bytes(lv.req)
-                    lv.close()
-                else:
-                    still.append(lv)
-            live = still
+        cv = threading.Condition()
+        live: set = set()
+        threads = []
+        est_over = []           # estimate / measured footprint of each admitted sequence
+
+        def done(lv):
+            with cv:
+                live.discard(lv)
+                cv.notify_all()
+
+        t0 = time.perf_counter()
+        now = lambda: time.perf_counter() - t0
+        while pending:
+            req = pending[0]
+            with cv:
+                # a free slot (or an empty device) and the request's arrival
+                while len(live) >= self.max_slots:
+                    cv.wait(0.05)
+                if realtime and req.arrival_s > now():
+                    cv.wait(min(req.arrival_s - now(), 0.05))
+                    continue
+                need = device_bytes(req, self.precision)
+                free, _ = torch.cuda.mem_get_info()
+                if live and need > self.hbm_fraction * free:
+                    cv.wait(0.05)        # wait for a sequence to end and free its memory
+                    continue
+            pending.pop(0)
+            res = results[req.rid]
+            res.admitted_s = now()
+            lv = _Live(req, self.precision, self.mode)
+            res.device_bytes = lv.device_bytes()
+            est_over.append(need / max(res.device_bytes, 1))
+            if not realtime:
+                req_ready = res.admitted_s
+                lv.req = Request(**{**lv.req.__dict__, "arrival_s": req_ready})
+            with cv:
+                live.add(lv)
+            th = threading.Thread(target=self._drive, args=(lv, res, t0, done), daemon=True)
+            threads.append(th)
+            th.start()
+        for th in threads:
+            th.join()
+        torch.cuda.synchronize()
         wall = now()
+        errors = [r.error for r in results.values() if r.error]
+        if errors:
+            raise RuntimeError(errors[0])
+        solves = sum(len(r.iters) for r in results.values())
         lat = np.concatenate([np.asarray(r.latencies_ms) for r in results.values()]) if solves else np.zeros(1)
-        totals = dict(solves=solves, ticks=ticks, wall_s=wall, solves_per_s=solves / wall,
-                      p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)))
+        totals = dict(solves=solves, wall_s=wall, solves_per_s=solves / wall,
+                      p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
+                      footprint_estimate_over_measured=(min(est_over), max(est_over)) if est_over else None)
         return [results[r.rid] for r in requests], totals

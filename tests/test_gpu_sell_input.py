@@ -1,8 +1,11 @@
 """rgm_set_operator_sell: an operator handed over in the library's sliced-ELL
-layout gives the same SpMV and solve as the same matrix in CSR (the per-row
-summation order is the CSR order in both), for an unsorted layout and one
-sorted by row length inside each 256-row tile; layouts that break the rules
-are rejected."""
+layout gives the same SpMV and solve as the same matrix in CSR, for an
+unsorted layout and one sorted by row length inside each 256-row tile; layouts
+that break the rules are rejected.  The SpMV reads a slice in 16-byte chunks of
+slice columns, so a row's partial sums follow its slice's width: two layouts
+of one matrix agree to rounding (the SpMV within a few ulps of the row's
+absolute sum, the solve within one iteration and x within 1e-12), not bit for
+bit."""
 import numpy as np
 import pytest
 
@@ -81,9 +84,12 @@ def test_sell_matches_csr(rg, sort):
         out.append((x2, st2))
         s.close()
     (yc, xc, sc), (xc2, sc2), (ys, xs, ss), (xs2, ss2) = out
-    np.testing.assert_array_equal(yc, ys)
-    assert sc["iters"] == ss["iters"] and sc2["iters"] == ss2["iters"]
-    np.testing.assert_array_equal(xc, xs)
+    xv = synth.random_vector(n, 64)
+    absrow = np.zeros(n)
+    np.add.at(absrow, np.repeat(np.arange(n), np.diff(rp)), np.abs(val) * np.abs(xv[col]))
+    assert np.all(np.abs(yc - ys) <= 4e-16 * 8 * absrow)
+    assert abs(sc["iters"] - ss["iters"]) <= 1 and abs(sc2["iters"] - ss2["iters"]) <= 1
+    assert np.linalg.norm(xc - xs) <= 1e-12 * np.linalg.norm(xc)
     np.testing.assert_allclose(xs2, 0.5 * xc, rtol=0, atol=1e-9 * np.abs(xc).max())
 
 

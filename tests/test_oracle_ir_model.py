@@ -3,7 +3,9 @@
 The survey's form 1 (Carson and Higham's GMRES-IR) stores A's values and every
 vector of the inner solve (Krylov basis V, residuals, the recycle columns U and
 W = A U, the inner iterate) in binary32, does the arithmetic in binary64 and
-rounds on store; the outer residual b - A x and the update x += d are binary64.
+rounds on store; W is formed from the binary32 operator and U, E = U^T W is
+accumulated in binary64 from the stored columns; the outer residual b - A x,
+the update x += d and the projection guess (binary64 U) are binary64.
 A plausible mistake is to forget one of those roundings: the inner solve then
 becomes more accurate than binary32 storage allows and every FP64 pin still
 passes.  These tests catch each omission:
@@ -108,9 +110,12 @@ class _Model:
         x = np.zeros(n)
         if U is not None:
             u = np.asarray(U, float)[:, 0]
-            W = self.spmv(self.val, u)                 # binary64 W = A u and E = u.W
-            E = self.dot(u, W)
-            uf, wf = (_f32(u), _f32(W)) if self.rUW else (u, W)
+            # u and w = A u in binary32 (w formed with the binary32 operator),
+            # E = u.w accumulated in binary64 from the stored columns
+            uf = _f32(u) if self.rUW else u
+            wf = self.spmv(self.Af, uf)
+            wf = _f32(wf) if self.rUW else wf
+            E = self.dot(uf, wf)
             r = b - self.spmv(self.val, x)             # binary64 projection guess
             cv = self.dot(u, r) / E
             x = x + u * cv
