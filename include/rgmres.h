@@ -49,6 +49,8 @@ extern "C" {
 
 #define RGM_DEVICE_PTRS         1   /* flag: pointers are device pointers                  */
 #define RGM_BATCH_COOP          2   /* flag of rgm_batch_solve: batched cycle launches     */
+#define RGM_ZERO_GUESS          4   /* flag of rgm_solve / rgm_batch_solve: x_in = 0 (x is
+                                       output only; b - A x_in = b needs no SpMV)            */
 
 /* ---------------------------------------------------------------- config */
 typedef enum {
@@ -88,7 +90,8 @@ typedef enum {
 typedef enum {
     RGM_LAUNCH_AUTO = 0,     /* the Arnoldi steps of a cycle run in one cooperative launch
                                 (grid barriers between the fused passes) when the grid fits
-                                on the device at once; otherwise one launch per pass        */
+                                on the device at once and a block owns at most two 256-row
+                                tiles; otherwise one launch per pass                        */
     RGM_LAUNCH_PER_PASS = 1  /* one launch per fused pass (same arithmetic)                 */
 } rgm_launch_policy;
 
@@ -180,9 +183,11 @@ int rgm_get_recycle_space(rgm_solver s, double *U, int64_t ld, int *k, int flags
 
 /* Solve A x = b.  x: in = x_in, out = solution.  With a recycle space the solve
  * starts from x0 = x_in + U E^{-1} U^T (b - A x_in) (Sec. 4.2, Eq.
- * projection_t_s; the paper's x0 = U E^{-1} U^T b is x_in = 0).  st may be NULL.
- * Returns RGM_OK, RGM_W_NOT_CONVERGED or RGM_W_SINGULAR_COARSE (x valid in all
- * three), or an error. */
+ * projection_t_s; the paper's x0 = U E^{-1} U^T b is x_in = 0).  With
+ * RGM_ZERO_GUESS in flags x_in = 0 and x is not read (the result is the same
+ * as passing zeros; the first residual b - A x_in = b then costs no SpMV).
+ * st may be NULL.  Returns RGM_OK, RGM_W_NOT_CONVERGED or
+ * RGM_W_SINGULAR_COARSE (x valid in all three), or an error. */
 int rgm_solve(rgm_solver s, const double *b, double *x, int flags, rgm_stats *st);
 
 /* Algorithm 1 after a solve: append x (n doubles) to the snapshot window (the
@@ -279,7 +284,10 @@ const char *rgm_status_string(int code);
 #define RGM_PROF_SMALL        5   /* single-block scalar kernels                 */
 #define RGM_PROF_ARNOLDI_CYCLE 6  /* all Arnoldi steps of a cycle in one cooperative
                                      launch (RGM_LAUNCH_AUTO)                       */
-#define RGM_PROF_KINDS        7
+#define RGM_PROF_SVD          7   /* U = X C combinations of the window SVD          */
+#define RGM_PROF_COARSE       8   /* W = A U and the binary32 copy of U              */
+#define RGM_PROF_OPERATOR     9   /* new operator values into the sliced ELL         */
+#define RGM_PROF_KINDS        10
 
 typedef struct {
     double ms;          /* summed device time of the launches                */
@@ -287,15 +295,18 @@ typedef struct {
     double flops;       /* summed algorithmic floating-point operations      */
     double bytes;       /* summed algorithmic bytes read and written         */
     double units;       /* Arnoldi steps the launches carried out (Arnoldi kinds; 0 otherwise) */
+    double step_bytes;  /* algorithmic bytes of those Arnoldi steps, B_j summed (below) */
 } rgm_kernel_prof;
-/* Algorithmic bytes of the Arnoldi kinds: an Arnoldi step j (1-based; j basis
- * vectors before it) must move the operator once and read the basis once, plus
- * 2 k recycle columns when k deflate and about four vector streams (w, the new
- * basis vector, the SpMV input and output):
- *     B_j = (e + 4) nnz + e n (j + 2 k + 4),   e = 8 (binary64) or 4 (binary32).
- * The cycle kind books the sum of B_j over the steps each launch carried out;
- * the per-pass kinds book each pass's own reads and writes.  Flops: 2 per
- * stored nonzero and 2 per row per dot or AXPY column of every pass. */
+/* bytes: what each launch's passes read and write once (the vectors a pass
+ * produces and the columns it reads, the operator for a SpMV).  step_bytes:
+ * what an Arnoldi step j (1-based; j basis vectors before it) must move at
+ * least -- the operator once, the basis once, 2 k recycle columns when k
+ * deflate and about four vector streams (w, the new basis vector, the SpMV
+ * input and output):
+ *     B_j = (e + 4) nnz + e n (j + 2 k + 4),   e = 8 (binary64) or 4 (binary32),
+ * booked on the cycle kind and on the first pass of each step (the SpMV kind).
+ * Flops: 2 per stored nonzero and 2 per row per dot or AXPY column of every
+ * pass. */
 
 /* Device memory the handle holds now: the sum of its device allocations
  * (operator in sliced ELL, Krylov basis, recycle space, snapshot window,

@@ -17,7 +17,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import (AUGMENTED, DEFLATED, FP32_IR, FP64, GUESS, PLAIN, RGM_BATCH_COOP, RGM_DEVICE_PTRS,
-                   RGM_W_NOT_CONVERGED, RGM_W_SINGULAR_COARSE, RgmConfig, RgmError,
+                   RGM_ZERO_GUESS, RGM_W_NOT_CONVERGED, RGM_W_SINGULAR_COARSE, RgmConfig, RgmError,
                    RgmStats, check)
 
 MODES = {"plain": PLAIN, "deflated": DEFLATED, "augmented": AUGMENTED, "guess": GUESS}
@@ -147,18 +147,20 @@ class Solver:
                                                 C.byref(k), 0), "rgm_get_recycle_space")
         return U
 
-    def solve(self, b, x=None):
-        """Returns (x, stats).  Host arrays: a new numpy x.  Device tensors: x in place."""
+    def solve(self, b, x=None, zero_guess=False):
+        """Returns (x, stats).  Host arrays: a new numpy x.  Device tensors: x in place.
+        zero_guess: x_in = 0 whatever x holds (RGM_ZERO_GUESS; x is output only)."""
         st = RgmStats()
+        zf = RGM_ZERO_GUESS if zero_guess else 0
         if _is_dev(b):
             assert x is not None and _is_dev(x)
             rc = self._L.rgm_solve(self._h, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()),
-                                   RGM_DEVICE_PTRS, C.byref(st))
+                                   RGM_DEVICE_PTRS | zf, C.byref(st))
             check(rc, "rgm_solve")
             return x, _stats(st)
         bb = np.ascontiguousarray(b, dtype=np.float64)
         xx = np.zeros(self.n) if x is None else np.array(x, dtype=np.float64, copy=True)
-        rc = self._L.rgm_solve(self._h, C.c_void_p(bb.ctypes.data), C.c_void_p(xx.ctypes.data), 0,
+        rc = self._L.rgm_solve(self._h, C.c_void_p(bb.ctypes.data), C.c_void_p(xx.ctypes.data), zf,
                                C.byref(st))
         check(rc, "rgm_solve")
         return xx, _stats(st)
@@ -200,12 +202,13 @@ class Solver:
         check(self._L.rgm_profile(self._h, int(enable)), "rgm_profile")
 
     def profile_read(self):
-        """{kind: dict(ms, launches, flops, bytes, units)}, total launches."""
+        """{kind: dict(ms, launches, flops, bytes, units, step_bytes)}, total launches."""
         n = len(_lib.PROF_KINDS)
         arr = (_lib.RgmKernelProf * n)()
         tot = C.c_int64(0)
         check(self._L.rgm_profile_read(self._h, arr, n, C.byref(tot)), "rgm_profile_read")
-        out = {k: dict(ms=a.ms, launches=a.launches, flops=a.flops, bytes=a.bytes, units=a.units)
+        out = {k: dict(ms=a.ms, launches=a.launches, flops=a.flops, bytes=a.bytes, units=a.units,
+                       step_bytes=a.step_bytes)
                for k, a in zip(_lib.PROF_KINDS, arr)}
         return out, tot.value
 
@@ -223,7 +226,7 @@ class Solver:
         return y
 
 
-def batch_solve(solvers, bs, xs, coop=False):
+def batch_solve(solvers, bs, xs, coop=False, zero_guess=False):
     """rgm_batch_solve: solves system i on solvers[i] with right-hand side bs[i]
     and initial guess / result xs[i] (CUDA tensors, updated in place),
     concurrently.  coop: the systems' GMRES cycles run together as batched
@@ -238,7 +241,7 @@ def batch_solve(solvers, bs, xs, coop=False):
     B = (C.c_void_p * n)(*[b.data_ptr() for b in bs])
     X = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
     st = (RgmStats * n)()
-    flags = RGM_DEVICE_PTRS | (RGM_BATCH_COOP if coop else 0)
+    flags = RGM_DEVICE_PTRS | (RGM_BATCH_COOP if coop else 0) | (RGM_ZERO_GUESS if zero_guess else 0)
     check(L.rgm_batch_solve(H, n, B, X, flags, st), "rgm_batch_solve")
     return [_stats(st[i]) for i in range(n)]
 

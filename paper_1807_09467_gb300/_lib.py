@@ -22,6 +22,7 @@ RGM_E_STATE = -4
 RGM_E_TIMEOUT = -5
 RGM_DEVICE_PTRS = 1
 RGM_BATCH_COOP = 2
+RGM_ZERO_GUESS = 4
 RGM_NOALLOC_MAX_ROWS = 4096 * 2048
 
 PLAIN, DEFLATED, AUGMENTED, GUESS = 0, 1, 2, 3
@@ -45,11 +46,11 @@ class RgmStats(C.Structure):
 
 class RgmKernelProf(C.Structure):
     _fields_ = [("ms", C.c_double), ("launches", C.c_int64), ("flops", C.c_double),
-                ("bytes", C.c_double), ("units", C.c_double)]
+                ("bytes", C.c_double), ("units", C.c_double), ("step_bytes", C.c_double)]
 
 
 PROF_KINDS = ["arnoldi_spmv_dots", "arnoldi_cgs1_axpy_dots", "arnoldi_cgs2_axpy_norm", "other_vector",
-              "gram", "small", "arnoldi_cycle"]
+              "gram", "small", "arnoldi_cycle", "window_svd", "coarse_setup", "operator_values"]
 
 _lib = None
 _lock = threading.Lock()

@@ -12,11 +12,14 @@
 #define RGM_MAXDOTS (RGM_KMAX + RGM_HLD + RGM_KMAX + 1)
 #define RGM_THREADS 256
 #ifndef RGM_MINB
-#define RGM_MINB 2                           // resident blocks per SM every fused kernel is built for
+#define RGM_MINB 4                           // resident blocks per SM every fused kernel is built for
                                              // (65536 / (256 RGM_MINB) registers a thread; grids hold
                                              // at most this many blocks per SM)
 #endif
+#define RGM_COOP_MAX_TILES 2                 // RGM_LAUNCH_AUTO takes the cooperative cycle kernel when
+                                             // a block owns at most this many row tiles
 #define RGM_CHUNK 8                          // dot columns per register pass
+#define RGM_GATHER_SMEM_MAX (160 * 1024)     // shared memory of sell_gather_kernel at most
 
 // Small device-resident state of one solve: the Hessenberg least-squares
 // problem, Givens rotations, coefficient vectors handed from one fused kernel

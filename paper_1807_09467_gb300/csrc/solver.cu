@@ -56,7 +56,7 @@ namespace {
 
 struct ProfRec {
     int kind, kry_j;
-    double flops, bytes, units;
+    double flops, bytes, units, step_bytes;
     cudaEvent_t a, b;
 };
 
@@ -89,6 +89,12 @@ struct rgm_solver_s {
     int64_t nslices = 0, nsell = 0;
     int64_t *slice_ptr = nullptr;
     int32_t *scol = nullptr, *perm = nullptr, *csr2sell = nullptr;
+    // gather route of new values (sell_gather_kernel): per sliced-ELL entry its
+    // CSR offset inside its tile (-1 padding), per tile its first CSR entry, and
+    // the shared memory the largest tile needs (0: the scatter route)
+    int32_t *sell_src = nullptr;
+    int64_t *tile_csr = nullptr;
+    size_t gather_smem = 0;
     double *sval = nullptr;
     float *sval32 = nullptr;
     double *val_stage = nullptr;  // host values land here before the scatter
@@ -126,11 +132,13 @@ struct rgm_solver_s {
     size_t cycle_rec0 = 0;
     rgm_kernel_prof acc[RGM_PROF_KINDS];
     int64_t launches = 0;
-    std::vector<double> cyc_flops, cyc_bytes;   // cost of the first j steps of a cycle launch
+    std::vector<double> cyc_flops, cyc_bytes, cyc_step_bytes;   // cost of the first j steps of a cycle launch
     // co-resident capacity of cycle_kernel per precision and dot-column bound
     // (-1: not queried yet)
     int cycle_cap[2][RGM_MAXDOTS + 2];
+    int cycle_cap2[2][RGM_MAXDOTS + 2];   // the same for the two-blocks-per-SM build
     bool in_batch = false;        // solving inside rgm_batch_solve: no cooperative launch
+    bool zero_guess = false;      // this solve's x_in is zero (RGM_ZERO_GUESS)
     // inside rgm_batch_solve with RGM_BATCH_COOP: the rendezvous this handle's
     // cycle launches join, its index there, and the event marking its inputs ready
     struct BatchCycles *batch = nullptr;
@@ -269,11 +277,20 @@ static void op_cost(rgm_solver s, const VecOp<T> &op, int nb, int J, double *flo
     *bytes = b;
 }
 
+// Algorithmic bytes an Arnoldi step with j basis vectors before it must move
+// (rgm_kernel_prof::step_bytes): B_j = (e + 4) nnz + e n (j + 2 kdef + 4).
+template <typename T>
+static double step_bytes(rgm_solver s, int j, int kdef)
+{
+    const double es = (double)sizeof(T);
+    return (es + 4.0) * (double)s->nnz + es * (double)s->n * ((double)j + 2.0 * kdef + 4.0);
+}
+
 // NVTX range names, one per profiling kind (a profiler can select or rename
 // launches by them; with no tool attached a range push is a no-op call).
 static const char *const kNvtxKind[RGM_PROF_KINDS] = {
     "arnoldi_spmv_dots", "arnoldi_cgs1_axpy_dots", "arnoldi_cgs2_axpy_norm", "other_vector", "gram", "small",
-    "arnoldi_cycle"};
+    "arnoldi_cycle", "window_svd", "coarse_setup", "operator_values"};
 
 template <typename T>
 static int launch(rgm_solver s, const VecOp<T> &op, int kind = RGM_PROF_OTHER, int kry_j = -1,
@@ -287,6 +304,7 @@ static int launch(rgm_solver s, const VecOp<T> &op, int kind = RGM_PROF_OTHER, i
         rec.kind = kind;
         rec.kry_j = kry_j;
         rec.units = (kind == RGM_PROF_ARNOLDI_SPMV) ? 1.0 : 0.0;
+        rec.step_bytes = (kind == RGM_PROF_ARNOLDI_SPMV) ? step_bytes<T>(s, kry_j + 1, op.ndU) : 0.0;
         op_cost(s, op, nb_host, J_host, &rec.flops, &rec.bytes);
         rec.a = pool_event(s);
         rec.b = pool_event(s);
@@ -317,6 +335,7 @@ struct ProfScope {
         nvtxRangePushA(kNvtxKind[kind]);
         if (s->prof) {
             rec.kind = kind; rec.kry_j = -1; rec.flops = flops; rec.bytes = bytes; rec.units = 0.0;
+            rec.step_bytes = 0.0;
             rec.a = pool_event(s);
             rec.b = pool_event(s);
             cudaEventRecord(rec.a, s->st);
@@ -341,12 +360,14 @@ static void prof_fix_cycle(rgm_solver s, int J)
             const size_t jj = std::min<size_t>((size_t)std::max(J, 0), s->cyc_flops.size() - 1);
             s->pending[i].flops = s->cyc_flops[jj];
             s->pending[i].bytes = s->cyc_bytes[jj];
+            s->pending[i].step_bytes = s->cyc_step_bytes[jj];
             s->pending[i].units = (double)jj;
         } else if (s->pending[i].kry_j >= J) {
             s->pending[i].kind = RGM_PROF_OTHER;
             s->pending[i].flops = 0.0;
             s->pending[i].bytes = 0.0;
             s->pending[i].units = 0.0;
+            s->pending[i].step_bytes = 0.0;
         }
     s->cycle_rec0 = s->pending.size();
 }
@@ -364,6 +385,7 @@ static void prof_collect(rgm_solver s)
         a.flops += r.flops;
         a.bytes += r.bytes;
         a.units += r.units;
+        a.step_bytes += r.step_bytes;
         s->ev_pool.push_back(r.a);
         s->ev_pool.push_back(r.b);
     }
@@ -396,6 +418,9 @@ static int launch_gram(rgm_solver s, const T *X, int64_t ldx, int nx, const T *Y
     op.col = col;
     op.partials = s->partials;
     op.counter = s->counter;
+    op.gcount = s->counter + 4;
+    op.gpart = s->gpart;
+    op.ngroups = s->ngroups;
     op.out = out;
     const int ncol = (mode == GRAM_UW) ? 2 * nxmax : nxmax;
     // the row tile of all ncol columns (tile + 1 values each) in dynamic shared
@@ -473,18 +498,19 @@ __global__ void set_tol_kernel(Small *s, double rtol, int precond, double floor_
 template <typename T>
 static int coarse_matrices(rgm_solver s, int k, const T *sval, T *Urow, const T *U, T *W)
 {
+    const int kp = (k + (16 / (int)sizeof(T)) - 1) / (16 / (int)sizeof(T)) * (16 / (int)sizeof(T));
     if (k > 0) {   // W = A U, one pass over the operator
         {
-            ProfScope ps_(s, RGM_PROF_OTHER, 0.0, 2.0 * sizeof(T) * (double)s->n * k);
+            ProfScope ps_(s, RGM_PROF_COARSE, 0.0, 2.0 * sizeof(T) * (double)s->n * k);
             urow_kernel<T><<<(unsigned)((s->n + RGM_UROW_ROWS - 1) / RGM_UROW_ROWS), 256, 0, s->st>>>(
-                Urow, U, s->n, s->ld, k);
+                Urow, U, s->n, s->ld, k, kp);
         }
         const int grid = (int)std::min<int64_t>((s->nslices + 7) / 8, 8 * (int64_t)s->nsm);
         const double flops = 2.0 * (double)s->nnz * k;
         const double bytes = (sizeof(T) + 4.0) * (double)s->nnz + sizeof(T) * (double)s->n * (2.0 * k + 1.0);
-        ProfScope ps_(s, RGM_PROF_OTHER, flops, bytes);
-        spmm_kernel<T><<<grid, 256, 0, s->st>>>(s->slice_ptr, s->scol, sval, s->perm, s->nslices, Urow, k, W,
-                                                s->ld);
+        ProfScope ps_(s, RGM_PROF_COARSE, flops, bytes);
+        spmm_kernel<T><<<grid, 256, 0, s->st>>>(s->slice_ptr, s->scol, sval, s->perm, s->nslices, Urow, k, kp,
+                                                W, s->ld);
     }
     CK(cudaGetLastError());
     // E_ij = u_i . w_j, then ||u_i||^2, ||w_i||^2
@@ -508,7 +534,7 @@ static int coarse_setup(rgm_solver s)
     int rc;
     if (s->cfg.precision == RGM_FP32_IR) {
         if (k > 0) {
-            ProfScope ps_(s, RGM_PROF_OTHER, 0.0, 12.0 * (double)s->n * k);
+            ProfScope ps_(s, RGM_PROF_COARSE, 0.0, 12.0 * (double)s->n * k);
             convert_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U32, s->U, s->n, s->ld, k);
         }
         CK(cudaGetLastError());
@@ -570,17 +596,27 @@ static void arnoldi_passes(rgm_solver s, const Arnoldi<T> &a, int kdef, CycleOp<
     c.pass[2] = op;
     c.m = s->cfg.m;
     c.arrive = s->counter + 1;
+    c.cap2 = 0;
 }
 
 // The cooperative cycle launch applies when the policy allows it and every
 // block of the grid can be resident at once (checked by occupancy; the
 // cooperative launch itself also refuses a grid that does not fit).
 template <typename T>
-static bool use_cycle_kernel(rgm_solver s, const CycleOp<T> &c, int nd_max)
+static bool use_cycle_kernel(rgm_solver s, CycleOp<T> &c, int nd_max)
 {
     if (s->cfg.launch_policy != RGM_LAUNCH_AUTO || s->in_batch || nd_max > RGM_MAXDOTS) return false;
-    int &cap = s->cycle_cap[sizeof(T) == 4 ? 1 : 0][nd_max];
-    if (cap < 0) cap = cycle_capacity(c, nd_max);
+    // large systems: the per-pass launches (programmatic dependent launch between
+    // passes) beat the grid barriers of the cooperative kernel once a block owns
+    // several tiles (measured on GB300: Q4 256x256, 7 tiles a block, 129 against
+    // 118 solves/s in GMRES-IR, 101 against 87 in binary64)
+    if (s->rpb > RGM_COOP_MAX_TILES * RGM_TILE) return false;
+    const int pi = sizeof(T) == 4 ? 1 : 0;
+    int &cap = s->cycle_cap[pi][nd_max];
+    if (cap < 0) cap = cycle_capacity(c, nd_max, RGM_MINB);
+    int &cap2 = s->cycle_cap2[pi][nd_max];
+    if (cap2 < 0) cap2 = cycle_capacity(c, nd_max, 2);
+    c.cap2 = cap2;
     return s->nblocks <= cap;
 }
 
@@ -590,24 +626,25 @@ static int launch_cycle_prof(rgm_solver s, const CycleOp<T> &c, int nd_max)
     ProfRec rec;
     if (s->prof) {
         // algorithmic cost of the first j steps, j = 0..m (booked once J is known):
-        // flops of the three passes, bytes B_j = (e + 4) nnz + e n (j + 2 k + 4)
+        // the three passes' flops and bytes, and the steps' B_j
         const int m = c.m;
-        const double es = (double)sizeof(T), kd = (double)c.pass[0].ndU;
         s->cyc_flops.assign(m + 1, 0.0);
         s->cyc_bytes.assign(m + 1, 0.0);
+        s->cyc_step_bytes.assign(m + 1, 0.0);
         for (int j = 0; j < m; ++j) {
-            double f = 0.0, ft, bt;
+            double f = 0.0, b = 0.0, ft, bt;
             for (int p = 0; p < 3; ++p) {
                 op_cost(s, c.pass[p], j + 1, j + 1, &ft, &bt);
                 f += ft;
+                b += bt;
             }
-            const double bj = (es + 4.0) * (double)s->nnz + es * (double)s->n * ((double)(j + 1) + 2.0 * kd + 4.0);
             s->cyc_flops[j + 1] = s->cyc_flops[j] + f;
-            s->cyc_bytes[j + 1] = s->cyc_bytes[j] + bj;
+            s->cyc_bytes[j + 1] = s->cyc_bytes[j] + b;
+            s->cyc_step_bytes[j + 1] = s->cyc_step_bytes[j] + step_bytes<T>(s, j + 1, c.pass[0].ndU);
         }
         rec.kind = RGM_PROF_ARNOLDI_CYCLE;
         rec.kry_j = -1;
-        rec.flops = rec.bytes = 0.0;
+        rec.flops = rec.bytes = rec.units = rec.step_bytes = 0.0;
         rec.a = pool_event(s);
         rec.b = pool_event(s);
         cudaEventRecord(rec.a, s->st);
@@ -891,11 +928,13 @@ static int gmres_cycles(rgm_solver s, const Arnoldi<T> &a, int mode, int k, int 
 }
 
 // Projection initial guess / coarse correction on (x, b): x += U E^{-1} U^T (b - A x).
+// x_zero: x is known to be zero, so b - A x = b (a copy, no SpMV; same values).
 template <typename T>
-static int coarse_correct(rgm_solver s, const Arnoldi<T> &a, int k)
+static int coarse_correct(rgm_solver s, const Arnoldi<T> &a, int k, bool x_zero = false)
 {
     VecOp<T> op = base_op(s, a);
-    op.src = SRC_RES; op.x = a.x; op.b = a.b; op.out = a.r; op.ndU = k; op.fin = FIN_COARSE;
+    op.src = x_zero ? SRC_COPY : SRC_RES;
+    op.x = a.x; op.b = a.b; op.win = a.b; op.out = a.r; op.ndU = k; op.fin = FIN_COARSE;
     int rc = launch(s, op);
     if (rc) return rc;
     op = base_op(s, a);
@@ -968,7 +1007,7 @@ static int solve_device(rgm_solver s, rgm_stats *out)
         if ((rc = norm_of(s, a, s->b, FIN_BNORMP))) return rc;
     }
     { ProfScope ps_(s, RGM_PROF_SMALL); set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.rtol, pre, 0.0); }
-    if (k > 0 && (rc = coarse_correct(s, a, k))) return rc;     // x0 = x_in + Q (b - A x_in)
+    if (k > 0 && (rc = coarse_correct(s, a, k, s->zero_guess && c.guess == 0))) return rc;   // x0 = x_in + Q (b - A x_in)
     if ((rc = residual_norm(s, a))) return rc;
     if ((rc = read_header(s))) return rc;
     const double bnorm = s->hs->bnorm;
@@ -993,7 +1032,7 @@ static int solve_device(rgm_solver s, rgm_stats *out)
             // outer target (the binary64 residual below decides convergence)
             { ProfScope ps_(s, RGM_PROF_SMALL);
               set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.inner_rtol, 0, 0.5 * c.rtol * bnorm); }
-            if (k > 0 && (rc = coarse_correct(s, f, k))) return rc;
+            if (k > 0 && (rc = coarse_correct(s, f, k, true))) return rc;   // d = 0: residual is b32
             if ((rc = residual_norm(s, f))) return rc;
             int cy = 0;
             if ((rc = gmres_cycles(s, f, mode, k, c.inner_cycles, &cy))) return rc;
@@ -1055,11 +1094,11 @@ static int svd_update(rgm_solver s)
         // window's coordinates, then the second pass on the formed U (k_new read
         // on the device)
         { ProfScope ps_(s, RGM_PROF_SMALL); cholqr_small_kernel<<<1, 256, 0, s->st>>>(s->sm, s->gwin, cnt, kdev); }
-        { ProfScope ps_(s, RGM_PROF_OTHER); combine_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U, s->X, s->sm->evec, cnt, -1, kdev, s->n, s->ld, RGM_WMAX); }
+        { ProfScope ps_(s, RGM_PROF_SVD); combine_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U, s->X, s->sm->evec, cnt, -1, kdev, s->n, s->ld, RGM_WMAX); }
         CK(cudaGetLastError());
         if ((rc = launch_gram<double>(s, s->U, s->ld, 0, s->U, s->ld, GRAM_PACKED, kdev, kmax, s->gram_out))) return rc;
         { ProfScope ps_(s, RGM_PROF_SMALL); chol_inv_kernel<<<1, 64, 0, s->st>>>(s->sm, s->gram_out, -1, kdev); }
-        { ProfScope ps_(s, RGM_PROF_OTHER); combine_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U, s->U, s->sm->evec, -1, -1, kdev, s->n, s->ld, RGM_WMAX); }
+        { ProfScope ps_(s, RGM_PROF_SVD); combine_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U, s->U, s->sm->evec, -1, -1, kdev, s->n, s->ld, RGM_WMAX); }
         CK(cudaGetLastError());
     }
     s->k_pending = true;
@@ -1121,7 +1160,7 @@ const char *rgm_status_string(int code)
 
 static void free_all(rgm_solver s)
 {
-    void *dp[] = {s->slice_ptr, s->scol, s->perm, s->csr2sell, s->sval, s->sval32, s->val_stage, s->V, s->U, s->W, s->w, s->r, s->b, s->x,
+    void *dp[] = {s->slice_ptr, s->scol, s->perm, s->csr2sell, s->sell_src, s->tile_csr, s->sval, s->sval32, s->val_stage, s->V, s->U, s->W, s->w, s->r, s->b, s->x,
                   s->V32, s->U32, s->W32, s->w32, s->r32, s->b32, s->x32, s->X, s->Urow, s->gwin,
                   s->dvec, s->partials, s->counter, s->gpart, s->pairs, s->gram_out, s->sm};
     for (void *p : dp) dev_free(s, p);
@@ -1151,9 +1190,14 @@ int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
     if (cudaFuncSetAttribute(sym_eig_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)EIG_SMEM_BYTES) != cudaSuccess)
         return RGM_E_CUDA;
+    if (cudaFuncSetAttribute(sell_gather_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)RGM_GATHER_SMEM_MAX) != cudaSuccess)
+        return RGM_E_CUDA;
     rgm_solver s = new (std::nothrow) rgm_solver_s();
     if (!s) return RGM_E_OOM;
     for (auto &row : s->cycle_cap)
+        for (int &v : row) v = -1;
+    for (auto &row : s->cycle_cap2)
         for (int &v : row) v = -1;
     s->cfg = c;
     s->st = (cudaStream_t)c.cuda_stream;
@@ -1179,12 +1223,12 @@ int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
     ALLOC(s->b, sizeof(double) * s->ld);
     ALLOC(s->x, sizeof(double) * s->ld);
     ALLOC(s->X, sizeof(double) * s->ld * c.window);
-    ALLOC(s->Urow, sizeof(double) * s->ld * kmax);
+    ALLOC(s->Urow, sizeof(double) * s->ld * (kmax + 1));   // rows padded to whole 16-byte vectors
     ALLOC(s->gwin, sizeof(double) * RGM_WMAX * RGM_WMAX);
     ALLOC(s->partials, sizeof(double) * (size_t)std::max(RGM_MAXDOTS, s->npairs_max) * s->nblocks);
     s->ngroups = (s->nblocks + RGM_RGROUP - 1) / RGM_RGROUP;
     ALLOC(s->counter, sizeof(unsigned) * (4 + s->ngroups));
-    ALLOC(s->gpart, sizeof(double) * (size_t)RGM_MAXDOTS * s->ngroups);
+    ALLOC(s->gpart, sizeof(double) * (size_t)std::max(RGM_MAXDOTS, s->npairs_max) * s->ngroups);
     ALLOC(s->pairs, sizeof(int2) * s->npairs_max);
     ALLOC(s->gram_out, sizeof(double) * s->npairs_max);
     ALLOC(s->sm, sizeof(Small));
@@ -1273,8 +1317,14 @@ int rgm_set_operator_csr(rgm_solver s, int64_t n, int64_t nnz, const int64_t *ro
     if (nsell >= ((int64_t)1 << 31)) return RGM_E_ARG;
     std::vector<int32_t> scol(std::max<int64_t>(nsell, 1));
     std::vector<int32_t> map(std::max<int64_t>(nnz, 1));
+    std::vector<int32_t> src(std::max<int64_t>(nsell, 1));
+    std::vector<int64_t> tcsr(ntile + 1);
+    int64_t tmax = 0;
+    for (int64_t t = 0; t <= ntile; ++t) tcsr[t] = rp[std::min<int64_t>(t * RGM_TILE, n)];
+    for (int64_t t = 0; t < ntile; ++t) tmax = std::max(tmax, tcsr[t + 1] - tcsr[t]);
     for (int64_t sl = 0; sl < nslices; ++sl) {
         const int64_t width = (sp[sl + 1] - sp[sl]) / 32;
+        const int64_t c0 = tcsr[sl / (RGM_TILE / 32)];
         for (int l = 0; l < 32; ++l) {
             const int32_t r = perm[sl * 32 + l];
             const int64_t len = r >= 0 ? rp[r + 1] - rp[r] : 0;
@@ -1283,20 +1333,32 @@ int rgm_set_operator_csr(rgm_solver s, int64_t n, int64_t nnz, const int64_t *ro
                 if (k < len) {
                     scol[e] = cl[rp[r] + k];
                     map[rp[r] + k] = (int32_t)e;
+                    src[e] = (int32_t)(rp[r] + k - c0);
                 } else {
                     scol[e] = r >= 0 ? r : 0;       // padding: value 0 on a valid column
+                    src[e] = -1;
                 }
             }
         }
     }
-    void *old[] = {s->slice_ptr, s->scol, s->perm, s->csr2sell, s->sval, s->sval32, s->val_stage};
+    // the gather route when the largest tile's values fit in shared memory
+    const size_t gsmem = sizeof(double) * (size_t)std::max<int64_t>(tmax, 1);
+    const bool gather = gsmem <= RGM_GATHER_SMEM_MAX;
+    void *old[] = {s->slice_ptr, s->scol, s->perm, s->csr2sell, s->sell_src, s->tile_csr, s->sval, s->sval32,
+                   s->val_stage};
     for (void *p : old) dev_free(s, p);
     s->slice_ptr = nullptr; s->scol = nullptr; s->perm = nullptr; s->csr2sell = nullptr;
+    s->sell_src = nullptr; s->tile_csr = nullptr; s->gather_smem = 0;
     s->sval = nullptr; s->sval32 = nullptr; s->val_stage = nullptr;
     CK(dev_alloc(s, (void **)&s->slice_ptr, sizeof(int64_t) * (nslices + 1)));
     CK(dev_alloc(s, (void **)&s->scol, sizeof(int32_t) * std::max<int64_t>(nsell, 1)));
     CK(dev_alloc(s, (void **)&s->perm, sizeof(int32_t) * nslices * 32));
-    CK(dev_alloc(s, (void **)&s->csr2sell, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+    if (gather) {
+        CK(dev_alloc(s, (void **)&s->sell_src, sizeof(int32_t) * std::max<int64_t>(nsell, 1)));
+        CK(dev_alloc(s, (void **)&s->tile_csr, sizeof(int64_t) * (ntile + 1)));
+    } else {
+        CK(dev_alloc(s, (void **)&s->csr2sell, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+    }
     CK(dev_alloc(s, (void **)&s->sval, sizeof(double) * std::max<int64_t>(nsell, 1)));
     CK(dev_alloc(s, (void **)&s->val_stage, sizeof(double) * std::max<int64_t>(nnz, 1)));
     if (s->cfg.precision == RGM_FP32_IR)
@@ -1304,7 +1366,15 @@ int rgm_set_operator_csr(rgm_solver s, int64_t n, int64_t nnz, const int64_t *ro
     CK(cudaMemcpyAsync(s->slice_ptr, sp.data(), sizeof(int64_t) * (nslices + 1), cudaMemcpyHostToDevice, s->st));
     CK(cudaMemcpyAsync(s->scol, scol.data(), sizeof(int32_t) * std::max<int64_t>(nsell, 1), cudaMemcpyHostToDevice, s->st));
     CK(cudaMemcpyAsync(s->perm, perm.data(), sizeof(int32_t) * nslices * 32, cudaMemcpyHostToDevice, s->st));
-    CK(cudaMemcpyAsync(s->csr2sell, map.data(), sizeof(int32_t) * std::max<int64_t>(nnz, 1), cudaMemcpyHostToDevice, s->st));
+    if (gather) {
+        CK(cudaMemcpyAsync(s->sell_src, src.data(), sizeof(int32_t) * std::max<int64_t>(nsell, 1),
+                           cudaMemcpyHostToDevice, s->st));
+        CK(cudaMemcpyAsync(s->tile_csr, tcsr.data(), sizeof(int64_t) * (ntile + 1), cudaMemcpyHostToDevice, s->st));
+        s->gather_smem = gsmem;
+    } else {
+        CK(cudaMemcpyAsync(s->csr2sell, map.data(), sizeof(int32_t) * std::max<int64_t>(nnz, 1),
+                           cudaMemcpyHostToDevice, s->st));
+    }
     CK(cudaMemsetAsync(s->sval, 0, sizeof(double) * std::max<int64_t>(nsell, 1), s->st));
     if (s->sval32) CK(cudaMemsetAsync(s->sval32, 0, sizeof(float) * std::max<int64_t>(nsell, 1), s->st));
     CK(cudaStreamSynchronize(s->st));
@@ -1349,9 +1419,11 @@ int rgm_set_operator_sell(rgm_solver s, int64_t n, int64_t nslices, const int64_
     // values arrive in this layout: the scatter map is the identity
     std::vector<int32_t> map(std::max<int64_t>(nsell, 1));
     for (int64_t e = 0; e < nsell; ++e) map[e] = (int32_t)e;
-    void *old[] = {s->slice_ptr, s->scol, s->perm, s->csr2sell, s->sval, s->sval32, s->val_stage};
+    void *old[] = {s->slice_ptr, s->scol, s->perm, s->csr2sell, s->sell_src, s->tile_csr, s->sval, s->sval32,
+                   s->val_stage};
     for (void *p : old) dev_free(s, p);
     s->slice_ptr = nullptr; s->scol = nullptr; s->perm = nullptr; s->csr2sell = nullptr;
+    s->sell_src = nullptr; s->tile_csr = nullptr; s->gather_smem = 0;
     s->sval = nullptr; s->sval32 = nullptr; s->val_stage = nullptr;
     const int64_t ne = std::max<int64_t>(nsell, 1);
     CK(dev_alloc(s, (void **)&s->slice_ptr, sizeof(int64_t) * (nslices + 1)));
@@ -1385,16 +1457,20 @@ int rgm_set_operator_values(rgm_solver s, const double *val, int flags)
             CK(cudaMemcpyAsync(s->val_stage, val, sizeof(double) * s->nnz, cudaMemcpyHostToDevice, s->st));
             src = s->val_stage;
         }
-        const int g = (int)std::min<int64_t>((s->nnz + 255) / 256, 8 * (int64_t)s->nsm);
-        {
-            ProfScope ps_(s, RGM_PROF_OTHER);
+        if (s->gather_smem) {
+            ProfScope ps_(s, RGM_PROF_OPERATOR, 0.0, 2.0 * 8.0 * (double)s->nnz + 16.0 * (double)s->nsell);
+            sell_gather_kernel<double><<<(unsigned)((s->n + RGM_TILE - 1) / RGM_TILE), 256, s->gather_smem, s->st>>>(
+                s->sval, s->sval32, src, s->tile_csr, s->slice_ptr, s->sell_src);
+        } else {
+            const int g = (int)std::min<int64_t>((s->nnz + 255) / 256, 8 * (int64_t)s->nsm);
+            ProfScope ps_(s, RGM_PROF_OPERATOR, 0.0, 2.0 * 8.0 * (double)s->nnz + 16.0 * (double)s->nsell);
             sell_scatter_kernel<double><<<g, 256, 0, s->st>>>(s->sval, s->sval32, src, s->csr2sell, s->nnz);
         }
         CK(cudaGetLastError());
     }
     if (s->dvec) {   // left Jacobi: keep D^{-1} A, remember D
         const int g = (int)std::min<int64_t>((s->nslices + 7) / 8, 8 * (int64_t)s->nsm);
-        ProfScope ps_(s, RGM_PROF_OTHER);
+        ProfScope ps_(s, RGM_PROF_OPERATOR);
         jacobi_scale_kernel<<<std::max(g, 1), 256, 0, s->st>>>(s->sval, s->scol, s->slice_ptr, s->perm,
                                                               s->nslices, s->dvec);
         CK(cudaGetLastError());
@@ -1437,7 +1513,9 @@ int rgm_solve(rgm_solver s, const double *b, double *x, int flags, rgm_stats *st
     if (!s || !b || !x) return RGM_E_ARG;
     if (!s->have_op) return RGM_E_STATE;
     CK(cudaMemcpyAsync(s->b, b, sizeof(double) * s->n, kind_in(flags), s->st));
-    CK(cudaMemcpyAsync(s->x, x, sizeof(double) * s->n, kind_in(flags), s->st));
+    if (flags & RGM_ZERO_GUESS) CK(cudaMemsetAsync(s->x, 0, sizeof(double) * s->n, s->st));
+    else CK(cudaMemcpyAsync(s->x, x, sizeof(double) * s->n, kind_in(flags), s->st));
+    s->zero_guess = (flags & RGM_ZERO_GUESS) != 0;
     int rc = solve_device(s, st);
     if (rc < 0) return rc;
     CK(cudaMemcpyAsync(x, s->x, sizeof(double) * s->n, kind_out(flags), s->st));
@@ -1774,7 +1852,7 @@ int rgm_profile(rgm_solver s, int enable)
 {
     if (!s) return RGM_E_ARG;
     prof_collect(s);
-    for (int i = 0; i < RGM_PROF_KINDS; ++i) s->acc[i] = rgm_kernel_prof{0.0, 0, 0.0, 0.0};
+    for (int i = 0; i < RGM_PROF_KINDS; ++i) s->acc[i] = rgm_kernel_prof{0.0, 0, 0.0, 0.0, 0.0, 0.0};
     s->launches = 0;
     s->prof = enable != 0;
     return RGM_OK;

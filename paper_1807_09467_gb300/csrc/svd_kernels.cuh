@@ -88,7 +88,7 @@ __global__ void extrap_kernel(double *__restrict__ x, const double *__restrict__
 #define RGM_UROW_ROWS 128
 template <typename T>
 __global__ void __launch_bounds__(256) urow_kernel(T *__restrict__ Urow, const T *__restrict__ U,
-                                                   int64_t n, int64_t ld, int k)
+                                                   int64_t n, int64_t ld, int k, int kp)
 {
     __shared__ T t[RGM_UROW_ROWS * (RGM_KMAX + 1)];
     const int64_t r0 = (int64_t)blockIdx.x * RGM_UROW_ROWS;
@@ -98,9 +98,9 @@ __global__ void __launch_bounds__(256) urow_kernel(T *__restrict__ Urow, const T
         if (r < nr) t[r * (RGM_KMAX + 1) + c] = U[r0 + r + (int64_t)c * ld];
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nr * k; i += blockDim.x) {
-        const int r = i / k, c = i % k;
-        Urow[(r0 + r) * k + c] = t[r * (RGM_KMAX + 1) + c];
+    for (int i = threadIdx.x; i < nr * kp; i += blockDim.x) {
+        const int r = i / kp, c = i % kp;
+        Urow[(r0 + r) * kp + c] = (c < k) ? t[r * (RGM_KMAX + 1) + c] : (T)0;
     }
 }
 
@@ -108,16 +108,21 @@ __global__ void __launch_bounds__(256) urow_kernel(T *__restrict__ Urow, const T
 // is read once per RGM_SPMM_KB columns instead of once per column): one warp
 // per 32-row slice, one lane per row, RGM_SPMM_KB accumulators per lane; the
 // gathered rows of U come from the row-major copy (contiguous per entry).
-// T = float: the binary32 operator and recycle columns of GMRES-IR.
-#define RGM_SPMM_KB 8
+// T = float: the binary32 operator and recycle columns of GMRES-IR (16
+// accumulators: k <= 16 reads the operator once).
+#define RGM_SPMM_KB ((sizeof(T) == 4) ? 16 : 8)
 template <typename T>
 __global__ void __launch_bounds__(256) spmm_kernel(const int64_t *__restrict__ slice_ptr,
                                                    const int32_t *__restrict__ scol,
                                                    const T *__restrict__ sval,
                                                    const int32_t *__restrict__ perm, int64_t nslices,
-                                                   const T *__restrict__ Urow, int k,
+                                                   const T *__restrict__ Urow, int k, int kp,
                                                    T *__restrict__ W, int64_t ldw)
 {
+    // the gathered row of U is read as 16-byte vectors (row stride kp, a
+    // multiple of the vector width; columns k .. kp-1 hold zeros)
+    constexpr int VW = 16 / (int)sizeof(T);
+    using VT = typename Vec16<T>::type;
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < nslices; sl += nwarps) {
@@ -129,10 +134,15 @@ __global__ void __launch_bounds__(256) spmm_kernel(const int64_t *__restrict__ s
             for (int c = 0; c < RGM_SPMM_KB; ++c) acc[c] = (T)0;
             for (int64_t e = p0 + lane; e < p1; e += 32) {
                 const T a = sval[e];
-                const T *u = Urow + (int64_t)scol[e] * k + c0;
+                const VT *u = reinterpret_cast<const VT *>(Urow + (int64_t)scol[e] * kp + c0);
 #pragma unroll
-                for (int c = 0; c < RGM_SPMM_KB; ++c)
-                    if (c0 + c < k) acc[c] = fma(a, u[c], acc[c]);
+                for (int cv = 0; cv < RGM_SPMM_KB / VW; ++cv)
+                    if (c0 + cv * VW < k) {
+                        const VT v = u[cv];
+#pragma unroll
+                        for (int t = 0; t < VW; ++t)
+                            acc[cv * VW + t] = fma(a, vcomp<VT, T>(v, t), acc[cv * VW + t]);
+                    }
             }
             if (pr >= 0) {
 #pragma unroll

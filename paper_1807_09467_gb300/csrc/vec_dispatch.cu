@@ -17,13 +17,14 @@ inline int tier(int nd_max) { return (nd_max + kWarps - 1) / kWarps; }
         return q <= 4 ? vec_launch_##TN##_q4(op, st)                                              \
                       : q <= 8 ? vec_launch_##TN##_q8(op, st) : vec_launch_##TN##_qbig(op, st);   \
     }                                                                                             \
-    int cycle_capacity(const CycleOp<T> &, int nd_max)                                            \
+    int cycle_capacity(const CycleOp<T> &, int nd_max, int minb)                                  \
     {                                                                                             \
         int dev = 0;                                                                              \
         if (cudaGetDevice(&dev) != cudaSuccess) return 0;                                         \
         const int q = tier(nd_max);                                                               \
-        return q <= 4 ? vec_cycle_capacity_##TN##_q4(dev)                                         \
-                      : q <= 8 ? vec_cycle_capacity_##TN##_q8(dev) : vec_cycle_capacity_##TN##_qbig(dev); \
+        return q <= 4   ? vec_cycle_capacity_##TN##_q4(dev, minb)                                 \
+               : q <= 8 ? vec_cycle_capacity_##TN##_q8(dev, minb)                                 \
+                        : vec_cycle_capacity_##TN##_qbig(dev, minb);                              \
     }                                                                                             \
     int launch_cycle(const CycleOp<T> &c, int nd_max, cudaStream_t st)                            \
     {                                                                                             \

@@ -735,8 +735,9 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op, const int bid)
     // AXPY columns [W | Vraw | U] as one list: pointer and coefficient
     __shared__ const T *acol[RGM_KMAX + RGM_HLD + RGM_KMAX];
     __shared__ T acoef[RGM_KMAX + RGM_HLD + RGM_KMAX];
-    __shared__ __align__(16) T ws[RGM_TILE];
-    __shared__ __align__(16) T apart[NPH * RGM_TILE];    // AXPY partial sums per column phase
+    __shared__ __align__(16) T ws[((sizeof(T) == 4) ? 8 : 1) * RGM_TILE];   // w on a chunk (binary32) or tile
+    // AXPY partial sums per column phase (binary64 tile path only)
+    __shared__ __align__(16) T apart[(sizeof(T) == 8) ? NPH * RGM_TILE : VW];
     __shared__ double xs;
     if (threadIdx.x == 0) xs = (op.xscale >= 0) ? s->colscale[op.xscale] : 1.0;
     const int nac = (op.src == SRC_AXPY) ? op.nW + op.nV + op.nU : 0;
@@ -769,155 +770,289 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op, const int bid)
     for (int q = 0; q < QMAX; ++q) acc[q] = 0.0;
 
     const bool spmv_src = (op.src == SRC_SPMV || op.src == SRC_RES);
-    const int ntiles_blk = (int)((r1 - r0 + RGM_TILE - 1) / RGM_TILE);
-    if (spmv_src && ntiles_blk > 1) {
-        // SpMV over all of the block's slices first.  Inside a tile the slices
-        // are sorted by width (slice 0 widest), so warp w takes slice w of even
-        // tiles and slice NW-1-w of odd ones: every warp gets the same work.
-        const T sc = (T)xs;
-        for (int t = 0; t < ntiles_blk; ++t) {
-            const int64_t base = r0 + (int64_t)t * RGM_TILE;
-            const int slot = (t & 1) ? (NW - 1 - warp) : warp;
-            const int64_t sl = (base >> 5) + slot;
-            const int64_t p0 = op.slice_ptr[sl], p1 = op.slice_ptr[sl + 1];
-            const T a = slice_rowsum<T>(op.sval, op.scol, op.x, p0, p1);
-            const int pr = op.perm[(sl << 5) + lane];
-            if (pr >= 0) op.out[pr] = (op.src == SRC_SPMV) ? a * sc : op.b[pr] - a;
-        }
-        __syncthreads();      // the block's own writes are visible to it now
-    }
-    for (int64_t base = r0; base < r1; base += RGM_TILE) {
-        const int nrow = (int)min((int64_t)RGM_TILE, r1 - base);
-        // ---- phase 1: produce and store w on this tile
-        if (spmv_src && ntiles_blk > 1) {
-            if ((int)threadIdx.x < nrow) ws[threadIdx.x] = op.out[base + threadIdx.x];
-        } else if (spmv_src) {
-            // one warp per 32-row slice of the tile, one lane per row; the
-            // slice's entries are independent loads (unrolled below)
-            const int64_t sl = (base >> 5) + warp;
-            const int64_t p0 = op.slice_ptr[sl], p1 = op.slice_ptr[sl + 1];
-            const T sc = (T)xs;
-            const T a = slice_rowsum<T>(op.sval, op.scol, op.x, p0, p1);
-            const int pr = op.perm[(sl << 5) + lane];
-            if (pr >= 0) {
-                const T v = (op.src == SRC_SPMV) ? a * sc : op.b[pr] - a;
-                op.out[pr] = v;
-                ws[pr - base] = v;
-            }
-        } else if (op.src == SRC_AXPY && nrow == RGM_TILE) {
-            // full tile: thread (g, ph) sums the columns c = ph (mod NPH) over
-            // rows base + VW g .. + VW - 1 with 16-byte loads, all of its
-            // columns' loads in flight together; the NPH partial sums of a row
-            // are added through shared memory
-            const int g = threadIdx.x % NG, ph = threadIdx.x / NG;
-            const int64_t r = base + (int64_t)VW * g;
-            VT a;
-#pragma unroll
-            for (int t = 0; t < VW; ++t) reinterpret_cast<T *>(&a)[t] = (T)0;
-            if (ph == 0) a = *reinterpret_cast<const VT *>(op.win + r);
-#pragma unroll 8
-            for (int c = ph; c < nac; c += NPH) {
-                const VT v = *reinterpret_cast<const VT *>(acol[c] + r);
-                const T cf = acoef[c];
-#pragma unroll
-                for (int t = 0; t < VW; ++t)
-                    reinterpret_cast<T *>(&a)[t] += cf * vcomp<VT, T>(v, t);
-            }
-            reinterpret_cast<VT *>(apart + ph * RGM_TILE)[g] = a;
-            __syncthreads();
-            const int t = threadIdx.x;
-            T sum = apart[t];
-#pragma unroll
-            for (int q = 1; q < NPH; ++q) sum += apart[q * RGM_TILE + t];
-            op.out[base + t] = sum;
-            ws[t] = sum;
-            if (nd == 0) __syncthreads();      // apart is rewritten by the next tile
-        } else if (op.src == SRC_COPY || op.src == SRC_AXPY) {
-            const int t = threadIdx.x;
-            if (t < nrow) {
-                const int64_t r = base + t;
-                T a = op.win[r];
-                if (op.src == SRC_AXPY) {
-#pragma unroll 4
-                    for (int c = 0; c < op.nW; ++c) a += cW[c] * op.W[r + (int64_t)c * op.ldw];
-#pragma unroll 8
-                    for (int c = 0; c < op.nV; ++c) a += cV[c] * op.V[r + (int64_t)c * op.ldv];
-#pragma unroll 4
-                    for (int c = 0; c < op.nU; ++c) a += cU[c] * op.U[r + (int64_t)c * op.ldu];
-                }
-                op.out[r] = a;
-                ws[t] = a;
-            }
-        }
-        if (nd == 0) continue;
-        __syncthreads();
-        // ---- phase 2: dot products, one warp per column over the tile
-        if (nrow == RGM_TILE) {
-            // full tile: 16-byte loads, lane l holding rows VW l + 32 VW i ..;
-            // the loads of QG columns are in flight together
-            constexpr int NVL = RGM_TILE / (32 * VW);
-            constexpr int QG = (RGM_MINB >= 4) ? 1 : (sizeof(T) == 4) ? 2 : 1;
-            VT wl[NVL];
-#pragma unroll
-            for (int i = 0; i < NVL; ++i) wl[i] = reinterpret_cast<const VT *>(ws)[lane + 32 * i];
-#pragma unroll
-            for (int q0 = 0; q0 < QMAX; q0 += QG) {
-                VT cv[QG][NVL];
-#pragma unroll
-                for (int gq = 0; gq < QG; ++gq) {
-                    const int q = q0 + gq, c = warp + q * NW;
-                    if (q < QMAX && c < nd && (c != ndc_ || op.wvec)) {
-                        const VT *cp = reinterpret_cast<const VT *>(
-                            (c == ndc_) ? op.wvec + base : dot_col(op, c) + base);
-#pragma unroll
-                        for (int i = 0; i < NVL; ++i) cv[gq][i] = cp[lane + 32 * i];
+    if constexpr (sizeof(T) == 4) {
+        // Rows are taken in chunks of up to CHT tiles: phase 1 produces w on every
+        // row of the chunk (stored, and kept in shared memory), phase 2 streams each
+        // dot column over the whole chunk, one warp per column -- long runs of
+        // independent 16-byte loads instead of one short tile at a time.
+        constexpr int CHT = 8;                                  // tiles per chunk (8 KB of w)
+    #ifndef RGM_DU
+    #define RGM_DU 4
+    #endif
+        constexpr int DU = RGM_DU;                                  // vectors in flight per lane
+        for (int64_t cb = r0; cb < r1; cb += (int64_t)CHT * RGM_TILE) {
+            const int64_t ce = min(r1, cb + (int64_t)CHT * RGM_TILE);
+            const int nr = (int)(ce - cb);
+            const int ntc = (nr + RGM_TILE - 1) / RGM_TILE;
+            // ---- phase 1: produce and store w on the chunk
+            if (spmv_src) {
+                // one warp per 32-row slice, one lane per row.  Inside a tile the
+                // slices are sorted by width (slice 0 widest), so warp w takes slice
+                // w of even tiles and slice NW-1-w of odd ones: every warp gets the
+                // same work.
+                const T sc = (T)xs;
+                for (int t = 0; t < ntc; ++t) {
+                    const int64_t base = cb + (int64_t)t * RGM_TILE;
+                    const int slot = (t & 1) ? (NW - 1 - warp) : warp;
+                    const int64_t sl = (base >> 5) + slot;
+                    const int64_t p0 = op.slice_ptr[sl], p1 = op.slice_ptr[sl + 1];
+                    const T a = slice_rowsum<T>(op.sval, op.scol, op.x, p0, p1);
+                    const int pr = op.perm[(sl << 5) + lane];
+                    if (pr >= 0) {
+                        const T v = (op.src == SRC_SPMV) ? a * sc : op.b[pr] - a;
+                        op.out[pr] = v;
+                        ws[pr - cb] = v;
                     }
                 }
+            } else if (op.src == SRC_AXPY) {
+                // thread t takes the 16-byte row groups t, t + 256, .. of the
+                // chunk over all columns [W | Vraw | U]: its loads are independent
+                // (no per-tile barrier); rows past the last whole group (the end of
+                // the matrix only) one per thread
+                const int G = nr / VW;
+                for (int g = threadIdx.x; g < G; g += RGM_THREADS) {
+                    const int64_t r = cb + (int64_t)VW * g;
+                    VT a = *reinterpret_cast<const VT *>(op.win + r);
+#pragma unroll 8
+                    for (int c = 0; c < nac; ++c) {
+                        const VT v = *reinterpret_cast<const VT *>(acol[c] + r);
+                        const T cf = acoef[c];
 #pragma unroll
-                for (int gq = 0; gq < QG; ++gq) {
-                    const int q = q0 + gq, c = warp + q * NW;
-                    if (q < QMAX && c < nd) {
+                        for (int q = 0; q < VW; ++q)
+                            reinterpret_cast<T *>(&a)[q] += cf * vcomp<VT, T>(v, q);
+                    }
+                    *reinterpret_cast<VT *>(op.out + r) = a;
+                    reinterpret_cast<VT *>(ws)[g] = a;
+                }
+                for (int i = VW * G + (int)threadIdx.x; i < nr; i += RGM_THREADS) {
+                    const int64_t r = cb + i;
+                    T a = op.win[r];
+                    for (int c = 0; c < nac; ++c) a += acoef[c] * acol[c][r];
+                    op.out[r] = a;
+                    ws[i] = a;
+                }
+            } else if (op.src == SRC_COPY) {
+                for (int i = threadIdx.x; i < nr; i += RGM_THREADS) {
+                    const T a = op.win[cb + i];
+                    op.out[cb + i] = a;
+                    ws[i] = a;
+                }
+            }
+            if (nd == 0) continue;     // nothing reads ws; the next chunk's writes need no barrier
+            __syncthreads();
+            // ---- phase 2: dot products, one warp per column streaming over the
+            // chunk: lane l reads the 16-byte vectors l, l + 32, .. of its column
+            // (and of w from shared memory), DU of them in flight; binary32 products
+            // are summed 4 vectors at a time and those sums added in binary64
+            const int G = nr / VW;                               // whole vectors in the chunk
+            const VT *wv = reinterpret_cast<const VT *>(ws);
+    #pragma unroll
+            for (int q = 0; q < QMAX; ++q) {
+                const int c = warp + q * NW;
+                if (c >= nd) continue;
+                const bool norm = (c == ndc_);
+                const T *cp = norm ? op.wvec : dot_col(op, c);
+                const bool load = !norm || cp != nullptr;
+                const VT *cv = load ? reinterpret_cast<const VT *>(cp + cb) : nullptr;
+                double sacc = 0.0;
+                for (int g0 = 0; g0 < G; g0 += 32 * DU) {
+                    VT x[DU];
+    #pragma unroll
+                    for (int u = 0; u < DU; ++u) {
+                        const int gi = g0 + lane + 32 * u;
+                        if (load && gi < G) x[u] = cv[gi];
+                    }
+    #pragma unroll
+                    for (int h = 0; h < DU; h += 4) {
                         T a = 0;
-                        if (c == ndc_) {                 // ||w||^2 or ||wvec .* w||^2
-#pragma unroll
-                            for (int i = 0; i < NVL; ++i)
-#pragma unroll
+    #pragma unroll
+                        for (int u = h; u < h + 4 && u < DU; ++u) {
+                            const int gi = g0 + lane + 32 * u;
+                            if (gi < G) {
+                                const VT w = wv[gi];
+    #pragma unroll
                                 for (int t = 0; t < VW; ++t) {
-                                    T v = vcomp<VT, T>(wl[i], t);
-                                    if (op.wvec) v *= vcomp<VT, T>(cv[gq][i], t);
-                                    a += v * v;
+                                    const T wt = vcomp<VT, T>(w, t);
+                                    if (!norm) {
+                                        a += vcomp<VT, T>(x[u], t) * wt;
+                                    } else {
+                                        const T v = load ? wt * vcomp<VT, T>(x[u], t) : wt;
+                                        a += v * v;
+                                    }
                                 }
+                            }
+                        }
+                        sacc += (double)a;
+                    }
+                }
+                // rows past the last whole vector (the end of the matrix only)
+                for (int i = VW * G + lane; i < nr; i += 32) {
+                    const T wt = ws[i];
+                    if (!norm) {
+                        sacc += (double)(cp[cb + i] * wt);
+                    } else {
+                        const T v = load ? wt * cp[cb + i] : wt;
+                        sacc += (double)(v * v);
+                    }
+                }
+                acc[q] += sacc;
+            }
+            __syncthreads();           // ws is rewritten by the next chunk
+        }
+    } else {
+        // binary64: the work is bound by the binary64 pipe rather than by
+        // loads in flight, and the tile loop (w of one tile in shared memory,
+        // the dots of each tile right after it) measured faster than chunks
+        const int ntiles_blk = (int)((r1 - r0 + RGM_TILE - 1) / RGM_TILE);
+        if (spmv_src && ntiles_blk > 1) {
+            // SpMV over all of the block's slices first.  Inside a tile the slices
+            // are sorted by width (slice 0 widest), so warp w takes slice w of even
+            // tiles and slice NW-1-w of odd ones: every warp gets the same work.
+            const T sc = (T)xs;
+            for (int t = 0; t < ntiles_blk; ++t) {
+                const int64_t base = r0 + (int64_t)t * RGM_TILE;
+                const int slot = (t & 1) ? (NW - 1 - warp) : warp;
+                const int64_t sl = (base >> 5) + slot;
+                const int64_t p0 = op.slice_ptr[sl], p1 = op.slice_ptr[sl + 1];
+                const T a = slice_rowsum<T>(op.sval, op.scol, op.x, p0, p1);
+                const int pr = op.perm[(sl << 5) + lane];
+                if (pr >= 0) op.out[pr] = (op.src == SRC_SPMV) ? a * sc : op.b[pr] - a;
+            }
+            __syncthreads();      // the block's own writes are visible to it now
+        }
+        for (int64_t base = r0; base < r1; base += RGM_TILE) {
+            const int nrow = (int)min((int64_t)RGM_TILE, r1 - base);
+            // ---- phase 1: produce and store w on this tile
+            if (spmv_src && ntiles_blk > 1) {
+                if ((int)threadIdx.x < nrow) ws[threadIdx.x] = op.out[base + threadIdx.x];
+            } else if (spmv_src) {
+                // one warp per 32-row slice of the tile, one lane per row; the
+                // slice's entries are independent loads (unrolled below)
+                const int64_t sl = (base >> 5) + warp;
+                const int64_t p0 = op.slice_ptr[sl], p1 = op.slice_ptr[sl + 1];
+                const T sc = (T)xs;
+                const T a = slice_rowsum<T>(op.sval, op.scol, op.x, p0, p1);
+                const int pr = op.perm[(sl << 5) + lane];
+                if (pr >= 0) {
+                    const T v = (op.src == SRC_SPMV) ? a * sc : op.b[pr] - a;
+                    op.out[pr] = v;
+                    ws[pr - base] = v;
+                }
+            } else if (op.src == SRC_AXPY && nrow == RGM_TILE) {
+                // full tile: thread (g, ph) sums the columns c = ph (mod NPH) over
+                // rows base + VW g .. + VW - 1 with 16-byte loads, all of its
+                // columns' loads in flight together; the NPH partial sums of a row
+                // are added through shared memory
+                const int g = threadIdx.x % NG, ph = threadIdx.x / NG;
+                const int64_t r = base + (int64_t)VW * g;
+                VT a;
+    #pragma unroll
+                for (int t = 0; t < VW; ++t) reinterpret_cast<T *>(&a)[t] = (T)0;
+                if (ph == 0) a = *reinterpret_cast<const VT *>(op.win + r);
+    #pragma unroll 8
+                for (int c = ph; c < nac; c += NPH) {
+                    const VT v = *reinterpret_cast<const VT *>(acol[c] + r);
+                    const T cf = acoef[c];
+    #pragma unroll
+                    for (int t = 0; t < VW; ++t)
+                        reinterpret_cast<T *>(&a)[t] += cf * vcomp<VT, T>(v, t);
+                }
+                reinterpret_cast<VT *>(apart + ph * RGM_TILE)[g] = a;
+                __syncthreads();
+                const int t = threadIdx.x;
+                T sum = apart[t];
+    #pragma unroll
+                for (int q = 1; q < NPH; ++q) sum += apart[q * RGM_TILE + t];
+                op.out[base + t] = sum;
+                ws[t] = sum;
+                if (nd == 0) __syncthreads();      // apart is rewritten by the next tile
+            } else if (op.src == SRC_COPY || op.src == SRC_AXPY) {
+                const int t = threadIdx.x;
+                if (t < nrow) {
+                    const int64_t r = base + t;
+                    T a = op.win[r];
+                    if (op.src == SRC_AXPY) {
+    #pragma unroll 4
+                        for (int c = 0; c < op.nW; ++c) a += cW[c] * op.W[r + (int64_t)c * op.ldw];
+    #pragma unroll 8
+                        for (int c = 0; c < op.nV; ++c) a += cV[c] * op.V[r + (int64_t)c * op.ldv];
+    #pragma unroll 4
+                        for (int c = 0; c < op.nU; ++c) a += cU[c] * op.U[r + (int64_t)c * op.ldu];
+                    }
+                    op.out[r] = a;
+                    ws[t] = a;
+                }
+            }
+            if (nd == 0) continue;
+            __syncthreads();
+            // ---- phase 2: dot products, one warp per column over the tile
+            if (nrow == RGM_TILE) {
+                // full tile: 16-byte loads, lane l holding rows VW l + 32 VW i ..;
+                // the loads of QG columns are in flight together
+                constexpr int NVL = RGM_TILE / (32 * VW);
+                constexpr int QG = (RGM_MINB >= 4) ? 1 : (sizeof(T) == 4) ? 2 : 1;
+                VT wl[NVL];
+    #pragma unroll
+                for (int i = 0; i < NVL; ++i) wl[i] = reinterpret_cast<const VT *>(ws)[lane + 32 * i];
+    #pragma unroll
+                for (int q0 = 0; q0 < QMAX; q0 += QG) {
+                    VT cv[QG][NVL];
+    #pragma unroll
+                    for (int gq = 0; gq < QG; ++gq) {
+                        const int q = q0 + gq, c = warp + q * NW;
+                        if (q < QMAX && c < nd && (c != ndc_ || op.wvec)) {
+                            const VT *cp = reinterpret_cast<const VT *>(
+                                (c == ndc_) ? op.wvec + base : dot_col(op, c) + base);
+    #pragma unroll
+                            for (int i = 0; i < NVL; ++i) cv[gq][i] = cp[lane + 32 * i];
+                        }
+                    }
+    #pragma unroll
+                    for (int gq = 0; gq < QG; ++gq) {
+                        const int q = q0 + gq, c = warp + q * NW;
+                        if (q < QMAX && c < nd) {
+                            T a = 0;
+                            if (c == ndc_) {                 // ||w||^2 or ||wvec .* w||^2
+    #pragma unroll
+                                for (int i = 0; i < NVL; ++i)
+    #pragma unroll
+                                    for (int t = 0; t < VW; ++t) {
+                                        T v = vcomp<VT, T>(wl[i], t);
+                                        if (op.wvec) v *= vcomp<VT, T>(cv[gq][i], t);
+                                        a += v * v;
+                                    }
+                            } else {
+    #pragma unroll
+                                for (int i = 0; i < NVL; ++i)
+    #pragma unroll
+                                    for (int t = 0; t < VW; ++t)
+                                        a += vcomp<VT, T>(cv[gq][i], t) * vcomp<VT, T>(wl[i], t);
+                            }
+                            acc[q] += (double)a;
+                        }
+                    }
+                }
+            } else {
+    #pragma unroll
+                for (int q = 0; q < QMAX; ++q) {
+                    const int c = warp + q * NW;
+                    if (c < nd) {
+                        T a = 0;
+                        if (c == ndc_ && op.wvec) {
+                            for (int i = lane; i < nrow; i += 32) {
+                                const T v = ws[i] * op.wvec[base + i];
+                                a += v * v;
+                            }
                         } else {
-#pragma unroll
-                            for (int i = 0; i < NVL; ++i)
-#pragma unroll
-                                for (int t = 0; t < VW; ++t)
-                                    a += vcomp<VT, T>(cv[gq][i], t) * vcomp<VT, T>(wl[i], t);
+                            const T *cp = (c == ndc_) ? ws : dot_col(op, c) + base;
+                            for (int i = lane; i < nrow; i += 32) a += cp[i] * ws[i];
                         }
                         acc[q] += (double)a;
                     }
                 }
             }
-        } else {
-#pragma unroll
-            for (int q = 0; q < QMAX; ++q) {
-                const int c = warp + q * NW;
-                if (c < nd) {
-                    T a = 0;
-                    if (c == ndc_ && op.wvec) {
-                        for (int i = lane; i < nrow; i += 32) {
-                            const T v = ws[i] * op.wvec[base + i];
-                            a += v * v;
-                        }
-                    } else {
-                        const T *cp = (c == ndc_) ? ws : dot_col(op, c) + base;
-                        for (int i = lane; i < nrow; i += 32) a += cp[i] * ws[i];
-                    }
-                    acc[q] += (double)a;
-                }
-            }
+            __syncthreads();
         }
-        __syncthreads();
     }
     if (nd == 0 && op.fin == FIN_NONE) {
         if (PDL) asm volatile("griddepcontrol.launch_dependents;");
@@ -1019,6 +1154,7 @@ struct CycleOp {
                          // the Givens step, the plain update that stores v_{j+1}
     int m;               // Arnoldi steps at most
     unsigned *arrive;    // arrival counter of the plain barrier
+    int cap2;            // host side: co-resident blocks of the two-blocks-per-SM build
 };
 
 // After a pass: the last block publishes generation `target`, the others wait
@@ -1097,9 +1233,12 @@ __device__ __forceinline__ void cycle_body(const CycleOp<T> &c, const int bid)
     }
 }
 
-// Built for RGM_MINB resident blocks per SM (the grids never hold more).
-template <typename T, int QMAX>
-__global__ void __launch_bounds__(RGM_THREADS, RGM_MINB) cycle_kernel(CycleOp<T> c)
+// Built twice: for RGM_MINB resident blocks per SM (the grids never hold
+// more), and for two, with twice the registers a thread, which a grid of at
+// most two blocks per SM takes (small systems, where every pass is short and
+// latency-bound: no spills in the scalar steps).
+template <typename T, int QMAX, int MINB>
+__global__ void __launch_bounds__(RGM_THREADS, MINB) cycle_kernel(CycleOp<T> c)
 {
     cycle_body<T, QMAX>(c, blockIdx.x);
 }
@@ -1144,9 +1283,10 @@ static __global__ void wait_selftest_kernel(Small *s, unsigned long long limit_n
 int launch_vec(const VecOp<double> &op, int nd_max, cudaStream_t st);
 int launch_vec(const VecOp<float> &op, int nd_max, cudaStream_t st);
 // cycle_kernel: blocks that can be resident at once for this column bound
-// (0 if the device cannot launch it cooperatively), and the launch itself.
-int cycle_capacity(const CycleOp<double> &c, int nd_max);
-int cycle_capacity(const CycleOp<float> &c, int nd_max);
+// (0 if the device cannot launch it cooperatively) in the build for minb
+// (RGM_MINB or 2) blocks per SM, and the launch itself.
+int cycle_capacity(const CycleOp<double> &c, int nd_max, int minb);
+int cycle_capacity(const CycleOp<float> &c, int nd_max, int minb);
 int launch_cycle(const CycleOp<double> &c, int nd_max, cudaStream_t st);
 int launch_cycle(const CycleOp<float> &c, int nd_max, cudaStream_t st);
 // batch_cycle_kernel: blocks that can be resident at once (0 if not
@@ -1175,13 +1315,13 @@ static cudaError_t launch_vec_pdl(const VecOp<T> &op, cudaStream_t st)
     return cudaLaunchKernelEx(&cfg, vec_kernel<T, Q>, op);
 }
 
-template <typename T, int Q>
+template <typename T, int Q, int MINB>
 static int cycle_capacity_q(int dev)
 {
     int coop = 0, nsm = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cycle_kernel<T, Q>, RGM_THREADS, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cycle_kernel<T, Q, MINB>, RGM_THREADS, 0) !=
         cudaSuccess)
         return 0;
     return per_sm * nsm;
@@ -1200,7 +1340,10 @@ static cudaError_t launch_cycle_q(const CycleOp<T> &c, cudaStream_t st)
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, cycle_kernel<T, Q>, c);
+    // the wider-register build when its residency holds the whole grid
+    // (c.cap2: the caller's cached capacity of that build on its device)
+    return (c.pass[0].nblocks <= c.cap2) ? cudaLaunchKernelEx(&cfg, cycle_kernel<T, Q, 2>, c)
+                                         : cudaLaunchKernelEx(&cfg, cycle_kernel<T, Q, RGM_MINB>, c);
 }
 
 template <typename T, int Q>
@@ -1237,7 +1380,7 @@ static cudaError_t launch_batch_q(const CycleOp<T> *ops, const int *first, int n
 // Entry points of one (precision, column tier) translation unit.
 #define RGM_VEC_DECLARE(TN, T, QN)                                                                 \
     int vec_launch_##TN##_##QN(const VecOp<T> &op, cudaStream_t st);                               \
-    int vec_cycle_capacity_##TN##_##QN(int dev);                                                   \
+    int vec_cycle_capacity_##TN##_##QN(int dev, int minb);                                         \
     int vec_cycle_launch_##TN##_##QN(const CycleOp<T> &c, cudaStream_t st);                        \
     int vec_batch_capacity_##TN##_##QN(int dev);                                                   \
     int vec_batch_launch_##TN##_##QN(const CycleOp<T> *ops, const int *first, int nsys, int nblocks, \
@@ -1248,7 +1391,10 @@ static cudaError_t launch_batch_q(const CycleOp<T> *ops, const int *first, int n
         return (int)launch_vec_pdl<T, Q>(op, st);                                                  \
     }
 #define RGM_VEC_DEFINE_CYCLE(TN, T, QN, Q)                                                         \
-    int vec_cycle_capacity_##TN##_##QN(int dev) { return cycle_capacity_q<T, Q>(dev); }            \
+    int vec_cycle_capacity_##TN##_##QN(int dev, int minb)                                          \
+    {                                                                                              \
+        return minb == 2 ? cycle_capacity_q<T, Q, 2>(dev) : cycle_capacity_q<T, Q, RGM_MINB>(dev); \
+    }                                                                                              \
     int vec_cycle_launch_##TN##_##QN(const CycleOp<T> &c, cudaStream_t st)                         \
     {                                                                                              \
         return (int)launch_cycle_q<T, Q>(c, st);                                                   \
@@ -1285,6 +1431,34 @@ __global__ void sell_scatter_kernel(double *sval, float *sval32, const Tin *val,
     }
 }
 
+// CSR values -> sliced-ELL positions, one block per 256-row tile: the tile's
+// CSR values (contiguous, rows r0 .. r0 + 255) are read into shared memory
+// with coalesced loads, then every sliced-ELL position of the tile (contiguous
+// too) is written in order from src[e], its CSR offset inside the tile (-1:
+// padding, value 0).  Both global streams are coalesced, unlike the scatter
+// above, whose writes land 32 positions apart.  Dynamic shared memory: the
+// largest tile's CSR entries in binary64.
+template <typename Tin>
+__global__ void __launch_bounds__(256) sell_gather_kernel(double *__restrict__ sval, float *__restrict__ sval32,
+                                                          const Tin *__restrict__ val,
+                                                          const int64_t *__restrict__ tile_csr,
+                                                          const int64_t *__restrict__ slice_ptr,
+                                                          const int32_t *__restrict__ src)
+{
+    extern __shared__ double tv[];
+    const int64_t t = blockIdx.x;
+    const int64_t c0 = tile_csr[t], c1 = tile_csr[t + 1];
+    for (int64_t i = threadIdx.x; i < c1 - c0; i += blockDim.x) tv[i] = (double)val[c0 + i];
+    __syncthreads();
+    const int64_t s0 = slice_ptr[t * (RGM_TILE / 32)], s1 = slice_ptr[(t + 1) * (RGM_TILE / 32)];
+    for (int64_t e = s0 + threadIdx.x; e < s1; e += blockDim.x) {
+        const int32_t k = src[e];
+        const double v = (k >= 0) ? tv[k] : 0.0;
+        sval[e] = v;
+        if (sval32) sval32[e] = (float)v;
+    }
+}
+
 // ---------------------------------------------------------------- Gram matrices
 // Pairwise dot products of columns: out[p] = col(a_p) . col(b_p) for a list of
 // pairs over the combined column list [X | Y]; binary64 accumulation.  Each
@@ -1306,10 +1480,13 @@ struct GramOp {
     int mode;
     int nxmax;               // bound on nx (shared-memory sizing)
     int col;                 // GRAM_COL: the column dotted with all others
-    double *partials;
-    unsigned *counter;
+    double *partials;        // per-block sums, pair p at p * nblocks
+    unsigned *counter;       // completion counter of the groups
+    unsigned *gcount;        // per-group completion counters (RGM_RGROUP blocks a group)
+    double *gpart;           // per-group sums, pair p at p * ngroups
+    int ngroups;
     double *out;
-    int tile;                // rows per tile (tile+1 doubles per column in smem)
+    int tile;                // rows per tile (tile+1 values per column in smem)
 };
 
 #define RGM_GRAM_PMAX 16      // pairs per thread: npairs <= RGM_GRAM_PMAX * RGM_THREADS
@@ -1427,14 +1604,38 @@ __global__ void __launch_bounds__(RGM_THREADS) gram_kernel(GramOp<T> op)
         const int p = threadIdx.x + i * RGM_THREADS;
         if (p < npairs) op.partials[(int64_t)p * op.nblocks + blockIdx.x] = acc[i];
     }
-    if (!last_block(op.counter)) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int c = warp; c < npairs; c += nw) {
-        double v = 0.0;
-        const double *p = op.partials + (int64_t)c * op.nblocks;
-        for (int b = lane; b < op.nblocks; b += 32) v += __ldcg(p + b);
-        v = warp_sum(v);
-        if (lane == 0) op.out[c] = v;
+    // two-level reduction, deterministic (fixed order): the last block of each
+    // group of RGM_RGROUP blocks adds the group's partials of every pair (one
+    // thread per pair, the group's loads in flight together), the last group
+    // adds the group sums.  No block waits for another.
+    const int g = blockIdx.x / RGM_RGROUP, gb0 = g * RGM_RGROUP;
+    const int gn = min(RGM_RGROUP, op.nblocks - gb0);
+    if (!last_of(op.gcount + g, (unsigned)gn)) return;
+    for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+        const double *pp = op.partials + (int64_t)p * op.nblocks + gb0;
+        double v[RGM_RGROUP];
+#pragma unroll
+        for (int b = 0; b < RGM_RGROUP; ++b) v[b] = (b < gn) ? __ldcg(pp + b) : 0.0;
+        double sum = 0.0;
+#pragma unroll
+        for (int b = 0; b < RGM_RGROUP; ++b) sum += v[b];
+        op.gpart[(int64_t)p * op.ngroups + g] = sum;
+    }
+    if (threadIdx.x == 0) op.gcount[g] = 0u;
+    if (!last_of(op.counter, (unsigned)op.ngroups)) return;
+    for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+        const double *gp = op.gpart + (int64_t)p * op.ngroups;
+        double sum = 0.0;
+        int gg = 0;
+        for (; gg + 8 <= op.ngroups; gg += 8) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldcg(gp + gg + u);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) sum += v[u];
+        }
+        for (; gg < op.ngroups; ++gg) sum += __ldcg(gp + gg);
+        op.out[p] = sum;
     }
     if (threadIdx.x == 0) *op.counter = 0u;
 }

@@ -89,10 +89,11 @@ def device_bytes(req: Request, precision: str = "fp32_ir") -> int:
     ncolV = req.m + req.k + 1
     kmax = max(req.k, 1)
     ir = precision == "fp32_ir"
-    vec = 8 * ld * (ncolV + 3 * kmax + 4 + req.window) + (4 * ld * (ncolV + 2 * kmax + 4) if ir else 0)
+    vec = 8 * ld * (ncolV + 3 * kmax + 1 + 4 + req.window) + (4 * ld * (ncolV + 2 * kmax + 4) if ir else 0)
     nsell = int(1.6 * nnz) + 32 * 256          # sliced-ELL padding (at most ~1.5x on FE patterns)
     op = nsell * (4 + 8 + (4 if ir else 0)) + nnz * (4 + 8) + 8 * (n // 8 + 2) + 4 * (n + 256)
-    scratch = 8 * 3200 * 2 * 152 + (1 << 20)   # per-block partial sums (<= 2 blocks per SM), small state
+    nblocks = min((n + 255) // 256, 4 * 152)  # grid of the fused kernels (<= 4 blocks per SM)
+    scratch = 8 * 3200 * nblocks + 8 * 3200 * (nblocks // 32 + 1) + 16 * 3200 + (320 << 10)
     fe = 8 * (n + 1) + 12 * nnz + 16 * n + 8 * (req.p + 1) ** 6 * 4 + (1 << 16)
     return int(vec + op + scratch + fe)
 
@@ -141,8 +142,9 @@ class Server:
                 for _ in range(lv.req.steps):
                     val, b = lv.fe.assemble(lv.u)
                     lv.sol.set_operator_values(val)
-                    x = torch.zeros_like(lv.u) if lv.sol.recycle_dim() else lv.u.clone()
-                    _, st = lv.sol.solve(b, x)
+                    zg = lv.sol.recycle_dim() > 0 and self.mode != "plain"
+                    x = torch.empty_like(lv.u) if zg else lv.u.clone()
+                    _, st = lv.sol.solve(b, x, zero_guess=zg)
                     lv.sol.update_recycle_svd(x, want_k=False)
                     lv.stream.synchronize()
                     t_end = time.perf_counter() - t0

@@ -357,3 +357,26 @@ def test_power_of_two_scaling(rg, orc, mode, sa, sb):
                           mode=rg.MODES[mode], m=m, rtol=1e-10)
     assert abs(sts["iters"] - so["iters"]) <= 1
     assert _rel(xs, xo) <= 1e-9
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_ir"])
+@pytest.mark.parametrize("mode", ["plain", "deflated"])
+def test_zero_guess_flag_equals_zero_input(rg, orc, precision, mode):
+    """RGM_ZERO_GUESS (x_in = 0 without reading x; the first residual is b, no
+    SpMV) gives bit for bit what passing a zero x gives, whatever x held."""
+    n, m, k = 1500, 20, 4
+    rp, col, val, b = _random_system(n, 808)
+    U = _orth(synth.random_matrix(n, k, 809)) if mode != "plain" else None
+    out = []
+    for zg in (False, True):
+        s = rg.Solver(n, m=m, k=k, mode=mode, precision=precision,
+                      rtol=1e-10 if precision == "fp64" else 1e-8)
+        s.set_operator_csr(rp, col, val)
+        if U is not None:
+            s.set_recycle_space(U)
+        x0 = synth.random_vector(n, 810) if zg else np.zeros(n)      # ignored under the flag
+        out.append(s.solve(b, x0, zero_guess=zg))
+        s.close()
+    (xa, sa), (xb, sb) = out
+    np.testing.assert_array_equal(xa, xb)
+    assert sa["iters"] == sb["iters"] and sa["status"] == sb["status"] == 0

@@ -63,7 +63,7 @@ def test_footprint_estimate_bounds_the_allocation(rg, precision):
     """serve.device_bytes (the admission estimate) against the library's own
     count of one sequence's allocations (rgm_solver_device_bytes +
     rgm_fe_device_bytes), over Q1-Q4 on small and large grids: never below,
-    and within a factor of two."""
+    and within a factor of 1.5 plus 2 MB (fixed per-handle scratch)."""
     from paper_1807_09467_gb300 import serve
     for p, N in ((1, 16), (2, 64), (3, 100), (4, 128), (4, 256)):
         req = serve.Request(rid=0, arrival_s=0.0, p=p, N=N, eps=0.01, dt=0.005, steps=1,
@@ -72,4 +72,4 @@ def test_footprint_estimate_bounds_the_allocation(rg, precision):
         got = lv.device_bytes()
         lv.close()
         est = serve.device_bytes(req, precision)
-        assert got <= est <= 2 * got, (p, N, got, est)
+        assert got <= est <= 1.5 * got + (2 << 20), (p, N, got, est)

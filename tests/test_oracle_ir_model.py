@@ -1,6 +1,6 @@
 """Pins of the oracle's binary32 model in GMRES-IR (orc_gmres_ir).
 
-The survey's form 1 (Carson and Higham's GMRES-IR) stores A's values and every
+The mixed-precision form (Carson and Higham's GMRES-IR) stores A's values and every
 vector of the inner solve (Krylov basis V, residuals, the recycle columns U and
 W = A U, the inner iterate) in binary32, does the arithmetic in binary64 and
 rounds on store; W is formed from the binary32 operator and U, E = U^T W is
