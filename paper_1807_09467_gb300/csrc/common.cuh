@@ -20,6 +20,8 @@
                                              // a block owns at most this many row tiles
 #define RGM_CHUNK 8                          // dot columns per register pass
 #define RGM_GATHER_SMEM_MAX (160 * 1024)     // shared memory of sell_gather_kernel at most
+#define RGM_LOOKAHEAD 3                      // per-pass launches: Arnoldi steps the host runs ahead
+#define RGM_LOOKAHEAD_WAIT_NS 200000000ll    // and the longest it waits for the device's progress
 
 // Small device-resident state of one solve: the Hessenberg least-squares
 // problem, Givens rotations, coefficient vectors handed from one fused kernel

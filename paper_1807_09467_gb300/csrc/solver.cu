@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <condition_variable>
 #include <mutex>
 #include <string>
@@ -124,6 +125,9 @@ struct rgm_solver_s {
     double *gram_out = nullptr;
     Small *sm = nullptr;
     Small *hs = nullptr;          // pinned host mirror (header fields)
+    // host-mapped {steps done, cycle done} of the running cycle, written by the
+    // Givens step: the per-pass launches look at most RGM_LOOKAHEAD steps ahead
+    unsigned *prog_host = nullptr, *prog_dev = nullptr;
     int npairs_max = 0;
     // per-launch CUDA-event timing (rgm_profile)
     bool prof = false;
@@ -672,6 +676,24 @@ static int launch_cycle_prof(rgm_solver s, const CycleOp<T> &c, int nd_max)
 static const double *res_weights(rgm_solver s, const Arnoldi<double> &) { return s->dvec; }
 static const float *res_weights(rgm_solver, const Arnoldi<float> &) { return nullptr; }
 
+// Launch lookahead of the per-pass Arnoldi steps: wait (spinning, at most
+// RGM_LOOKAHEAD_WAIT_NS) until the device has finished `steps` steps of the
+// cycle or ended it; true when the cycle has ended (launch no more steps).  A
+// wait that runs out returns false: the launches go on and the device's own
+// done flag still gates them, so nothing depends on the mirror arriving.
+static bool progress_done(volatile unsigned *prog, int steps)
+{
+    if (prog[1]) return true;
+    if ((int)prog[0] >= steps) return false;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        if (prog[1]) return true;
+        if ((int)prog[0] >= steps) return false;
+        if (std::chrono::steady_clock::now() - t0 > std::chrono::nanoseconds(RGM_LOOKAHEAD_WAIT_NS))
+            return false;
+    }
+}
+
 // One recycled GMRES solve of A x = b on the device buffers of `a`, with the
 // tolerance tol_abs already in Small.  mode: effective mode (PLAIN if no U).
 // Returns the number of cycles through *cycles.
@@ -858,7 +880,15 @@ static int gmres_cycles(rgm_solver s, const Arnoldi<T> &a, int mode, int k, int 
         } else if (use_cycle_kernel(s, cyc, kdef + m + 1)) {
             if ((rc = launch_cycle_prof(s, cyc, kdef + m + 1))) return rc;
         } else {
+            // the device gates every pass on the cycle's done flag; the host
+            // runs at most RGM_LOOKAHEAD steps ahead of the device's progress
+            // (host-mapped, written by the Givens step), so that few passes are
+            // launched past the step that ends the cycle
+            volatile unsigned *prog = s->prog_host;
+            prog[0] = 0u;
+            prog[1] = 0u;
             for (int j = 0; j < m; ++j) {
+                if (j >= RGM_LOOKAHEAD && progress_done(prog, j - RGM_LOOKAHEAD + 1)) break;
                 VecOp<T> op = cyc.pass[0];
                 op.gate = GATE_KRYLOV;
                 op.x = a.V + (int64_t)j * s->ld;
@@ -866,6 +896,7 @@ static int gmres_cycles(rgm_solver s, const Arnoldi<T> &a, int mode, int k, int 
                 if ((rc = launch(s, op, RGM_PROF_ARNOLDI_SPMV, j, j + 1))) return rc;
                 op = cyc.pass[1];
                 op.gate = GATE_KRYLOV;
+                op.mirror = s->prog_dev;
                 if ((rc = launch(s, op, RGM_PROF_ARNOLDI_CGS1, j, j + 1))) return rc;
                 op = cyc.pass[2];
                 op.gate = GATE_STEP;        // also after the step that ended the cycle
@@ -1165,6 +1196,7 @@ static void free_all(rgm_solver s)
                   s->dvec, s->partials, s->counter, s->gpart, s->pairs, s->gram_out, s->sm};
     for (void *p : dp) dev_free(s, p);
     if (s->hs) cudaFreeHost(s->hs);
+    if (s->prog_host) cudaFreeHost(s->prog_host);
     for (ProfRec &r : s->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     if (s->batch_ev) cudaEventDestroy(s->batch_ev);
@@ -1244,6 +1276,8 @@ int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
     }
 #undef ALLOC
     if (e == cudaSuccess) e = cudaMallocHost((void **)&s->hs, sizeof(Small));
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->prog_host, 2 * sizeof(unsigned), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&s->prog_dev, s->prog_host, 0);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->counter, 0, sizeof(unsigned) * (4 + s->ngroups), s->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->sm, 0, sizeof(Small), s->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->V, 0, sizeof(double) * s->ld * ncolV, s->st);

@@ -82,6 +82,8 @@ struct VecOp {
                              // generation as soon as the next pass's inputs are written
     int lu_sel;              // small solves with E's LU (0) or the projector's (1)
     int dyn;                 // DYN_* bits: counts and output column read from Small
+    volatile unsigned *mirror;  // FIN_ARN2H: host-mapped {steps done, cycle done} of the
+                                // cycle, for the host launching the passes (may be null)
 };
 
 enum Dyn {
@@ -499,6 +501,11 @@ __device__ void finalize_block(const VecOp<T> &op, const double *d, FinScratch &
                 if (brk) { s->breakdown = 1; done = 1; }
                 if (fabs(g1) <= f.tol_in || it >= f.maxit || j + 1 >= f.m) done = 1;
                 if (done) s->done = 1;
+                if (op.mirror) {          // progress for the host's launch lookahead
+                    op.mirror[1] = (unsigned)done;
+                    op.mirror[0] = (unsigned)(j + 1);
+                    __threadfence_system();
+                }
             }
         }
         __syncthreads();
