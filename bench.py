@@ -629,13 +629,18 @@ def serve_rate(serve, reqs, hbm_gbs, load=0.8, iters=25):
 
 def run_serve(args):
     """Served form (config: 512 sequences, Q1-Q4 on 16^2..256^2 quads, eps
-    log-uniform in [1e-3, 1e-1], 10-100 steps each, seeded Poisson arrivals at
-    the rate that loads 80 % of the measured HBM bandwidth): continuous batching
-    (paper_1807_09467_gb300.serve), deflated GMRES-IR to a true residual of
-    1e-8, against plain binary64 GMRES(m) served by the same loop.  Solves/s
-    and p50/p99 per-solve latency."""
+    log-uniform in [1e-3, 1e-1], 10-100 steps each, seeded Poisson arrivals):
+    continuous batching (paper_1807_09467_gb300.serve), deflated GMRES-IR to a
+    true residual of 1e-8, against plain binary64 GMRES(m) served by the same
+    loop at the same arrivals.  The arrival rate loads the server at 80 %: the
+    closed-loop capacity of the server (sequences per second with every request
+    waiting at time 0) is measured on the first 64 requests and the Poisson rate
+    set to 0.8 of it; the rate that would load 80 % of the HBM bandwidth by the
+    bytes model (serve_rate) is reported beside it.  Solves/s and p50/p99
+    per-solve latency (first solve of a sequence: from its arrival)."""
     import dataclasses
 
+    import numpy as np
     import torch
 
     import __graft_entry__ as g
@@ -645,7 +650,12 @@ def run_serve(args):
     hbm = measured_peaks().get("hbm_gbs", 6690.5)
     base = [serve.Request(**r) for r in synth.serve_stream(count=args.serve_count, rate_per_s=1.0,
                                                             n_hi=256)]
-    rate = args.serve_rate or serve_rate(serve, base, hbm)
+    hbm_rate = serve_rate(serve, base, hbm)
+    # closed-loop capacity of the deflated GMRES-IR server on the first 64 requests
+    cal = [dataclasses.replace(r, arrival_s=0.0) for r in base[:64]]
+    _, ctot = serve.Server(max_slots=64, precision="fp32_ir", mode="deflated").run(cal, realtime=False)
+    capacity = len(cal) / ctot["wall_s"]
+    rate = args.serve_rate or 0.8 * capacity
     reqs = [dataclasses.replace(r, arrival_s=r.arrival_s / rate) for r in base]
     torch.cuda.synchronize()
     res, tot = serve.Server(max_slots=64, precision="fp32_ir", mode="deflated").run(reqs, realtime=True)
@@ -653,16 +663,23 @@ def run_serve(args):
     bres, btot = serve.Server(max_slots=64, precision="fp64", mode="plain").run(reqs, realtime=True)
     its = [i for r in res for i in r.iters]
     bits = [i for r in bres for i in r.iters]
+    first = [r.latencies_ms[0] for r in res if r.latencies_ms]
+    later = [x for r in res for x in r.latencies_ms[1:]]
+    pct = lambda v, q: round(float(np.percentile(v, q)), 3) if v else None
     out = {"metric": METRIC, "value": round(tot["solves_per_s"], 3), "unit": "solves/s", "n_gpus": 1,
            "steps": tot["solves"], "warmup": 0, "ms_per_step": round(1e3 * tot["wall_s"] / tot["solves"], 4),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
            "data": "synthetic",
            "config": {"workload": f"serve: {len(reqs)} sequences, Q1-Q4 on 16^2..256^2 quads, 10-100 steps, "
-                                  f"Poisson arrivals at {rate:.2f}/s (80 % of HBM load), deflated GMRES-IR "
-                                  "to 1e-8, continuous batching (64 slots, 80 % of free HBM)",
+                                  f"Poisson arrivals at {rate:.2f} sequences/s (80 % of the server's measured "
+                                  "capacity), deflated GMRES-IR to 1e-8, continuous batching (64 slots, 80 % of "
+                                  "free HBM)",
                       "requests": len(reqs), "solves": tot["solves"], "arrival_rate_per_s": rate,
-                      "hbm_gbs_for_rate": hbm},
-           "latency_ms": {"p50": round(tot["p50_ms"], 3), "p99": round(tot["p99_ms"], 3)},
+                      "capacity_sequences_per_s": round(capacity, 3),
+                      "hbm_rule_rate_per_s": round(hbm_rate, 3), "hbm_gbs_for_rate": hbm},
+           "latency_ms": {"p50": round(tot["p50_ms"], 3), "p99": round(tot["p99_ms"], 3),
+                          "first_solve_p50": pct(first, 50), "first_solve_p99": pct(first, 99),
+                          "later_solves_p50": pct(later, 50), "later_solves_p99": pct(later, 99)},
            "iterations": iters_stats(its), "wall_s": round(tot["wall_s"], 3),
            "footprint_estimate_over_measured": tot["footprint_estimate_over_measured"],
            "plain_fp64_same_loop": {"solves_per_s": round(btot["solves_per_s"], 3),
