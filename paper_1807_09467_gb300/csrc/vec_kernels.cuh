@@ -646,6 +646,26 @@ __device__ __forceinline__ T vcomp(const V &v, int t) { return reinterpret_cast<
 template <typename V>
 __device__ __forceinline__ int icomp(const V &v, int t) { return reinterpret_cast<const int *>(&v)[t]; }
 
+// Loads of the operator's stored values and columns.  They are read once per
+// Arnoldi step, while the Krylov basis, W, U and the vector being multiplied
+// are read again by the next passes: the operator is loaded with the streaming
+// (evict-first) hint so that it does not push those out of L2.
+#ifndef RGM_STREAM_A
+#define RGM_STREAM_A 1
+#endif
+#ifndef RGM_PF
+#define RGM_PF 0
+#endif
+template <typename V>
+__device__ __forceinline__ V ld_op(const V *p)
+{
+#if RGM_STREAM_A
+    return __ldcs(p);
+#else
+    return *p;
+#endif
+}
+
 // Row sums of one 32-row slice of the sliced-ELL operator, sum_k sval[p0 +
 // 32 k + l] x[scol[p0 + 32 k + l]] for the slice's lane l (returned in lane l).
 // The slice's entries are read as 16-byte vectors: in a chunk of VW slice
@@ -660,7 +680,11 @@ __device__ __forceinline__ T slice_rowsum(const T *sval, const int32_t *scol, co
     using VT = typename Vec16<T>::type;
     using VI = typename Vec16<T>::itype;
     // chunks in flight per lane (fewer when the register budget is 64)
+#ifdef RGM_SPMV_U
+    constexpr int U = RGM_SPMV_U;
+#else
     constexpr int U = (RGM_MINB >= 4) ? 2 : (sizeof(T) == 4) ? 4 : 2;
+#endif
     const int lane = threadIdx.x & 31;
     const int64_t wd = (p1 - p0) >> 5;
     const int64_t nch = wd / VW;
@@ -675,8 +699,8 @@ __device__ __forceinline__ T slice_rowsum(const T *sval, const int32_t *scol, co
         VI c[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            v[u] = vv[(ch + u) * 32];
-            c[u] = vc[(ch + u) * 32];
+            v[u] = ld_op(vv + (ch + u) * 32);
+            c[u] = ld_op(vc + (ch + u) * 32);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
@@ -684,8 +708,8 @@ __device__ __forceinline__ T slice_rowsum(const T *sval, const int32_t *scol, co
             for (int t = 0; t < VW; ++t) acc[t] += vcomp<VT, T>(v[u], t) * x[icomp(c[u], t)];
     }
     for (; ch < nch; ++ch) {
-        const VT v = vv[ch * 32];
-        const VI c = vc[ch * 32];
+        const VT v = ld_op(vv + ch * 32);
+        const VI c = ld_op(vc + ch * 32);
 #pragma unroll
         for (int t = 0; t < VW; ++t) acc[t] += vcomp<VT, T>(v, t) * x[icomp(c, t)];
     }
@@ -703,7 +727,7 @@ __device__ __forceinline__ T slice_rowsum(const T *sval, const int32_t *scol, co
     }
     for (int64_t k = nch * VW; k < wd; ++k) {
         const int64_t e = p0 + 32 * k + lane;
-        a += sval[e] * x[scol[e]];
+        a += ld_op(sval + e) * x[ld_op(scol + e)];
     }
     return a;
 }
@@ -782,7 +806,11 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op, const int bid)
         // row of the chunk (stored, and kept in shared memory), phase 2 streams each
         // dot column over the whole chunk, one warp per column -- long runs of
         // independent 16-byte loads instead of one short tile at a time.
-        constexpr int CHT = 8;                                  // tiles per chunk (8 KB of w)
+    #ifndef RGM_CHT
+    #define RGM_CHT 8
+    #endif
+        constexpr int CHT = RGM_CHT;                            // tiles per chunk (8: 8 KB of w)
+        static_assert(CHT >= 1 && CHT <= 8, "ws holds 8 tiles");
     #ifndef RGM_DU
     #define RGM_DU 4
     #endif
@@ -791,6 +819,22 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op, const int bid)
             const int64_t ce = min(r1, cb + (int64_t)CHT * RGM_TILE);
             const int nr = (int)(ce - cb);
             const int ntc = (nr + RGM_TILE - 1) / RGM_TILE;
+#if RGM_PF
+            // the dot columns of this chunk are read right after the SpMV below:
+            // start pulling them into L2 now (one bulk prefetch per column), so
+            // that phase 2 streams them from L2 while phase 1 streams the operator
+            if (spmv_src && nd > 0) {
+                static_assert(RGM_MAXDOTS <= RGM_THREADS, "one dot column per thread");
+                const int c = threadIdx.x;
+                if (c < nd) {
+                    const T *cp = (c == ndc_) ? op.wvec : dot_col(op, c);
+                    const uint32_t bytes = (uint32_t)(((nr + 3) & ~3) * (int)sizeof(T));
+                    if (cp != nullptr && cp != op.out && ((uintptr_t)(cp + cb) & 15) == 0)
+                        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(cp + cb), "r"(bytes)
+                                     : "memory");
+                }
+            }
+#endif
             // ---- phase 1: produce and store w on the chunk
             if (spmv_src) {
                 // one warp per 32-row slice, one lane per row.  Inside a tile the
