@@ -653,9 +653,6 @@ __device__ __forceinline__ int icomp(const V &v, int t) { return reinterpret_cas
 #ifndef RGM_STREAM_A
 #define RGM_STREAM_A 1
 #endif
-#ifndef RGM_PF
-#define RGM_PF 0
-#endif
 template <typename V>
 __device__ __forceinline__ V ld_op(const V *p)
 {
@@ -664,6 +661,34 @@ __device__ __forceinline__ V ld_op(const V *p)
 #else
     return *p;
 #endif
+}
+
+// The end of a slice's row sums: acc[t] of lane l holds the partial sum of row
+// VW (l % (32/VW)) + t over the whole chunks of the slice; lanes l, l + 32/VW,
+// .. saw the same rows and are added by a butterfly, then row `lane` takes the
+// columns k0 .. wd - 1 past the last whole chunk one entry at a time.
+template <typename T>
+__device__ __forceinline__ T slice_combine(T (&acc)[16 / sizeof(T)], const T *sval, const int32_t *scol,
+                                           const T *x, int64_t p0, int64_t k0, int64_t wd)
+{
+    constexpr int VW = 16 / (int)sizeof(T);
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 32 / VW; o < 32; o <<= 1)
+#pragma unroll
+        for (int t = 0; t < VW; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+    // row `lane` is component lane % VW of lane lane / VW
+    T a = (T)0;
+#pragma unroll
+    for (int t = 0; t < VW; ++t) {
+        const T v = __shfl_sync(0xffffffffu, acc[t], lane / VW);
+        if ((lane % VW) == t) a = v;
+    }
+    for (int64_t k = k0; k < wd; ++k) {
+        const int64_t e = p0 + 32 * k + lane;
+        a += ld_op(sval + e) * x[ld_op(scol + e)];
+    }
+    return a;
 }
 
 // Row sums of one 32-row slice of the sliced-ELL operator, sum_k sval[p0 +
@@ -680,11 +705,7 @@ __device__ __forceinline__ T slice_rowsum(const T *sval, const int32_t *scol, co
     using VT = typename Vec16<T>::type;
     using VI = typename Vec16<T>::itype;
     // chunks in flight per lane (fewer when the register budget is 64)
-#ifdef RGM_SPMV_U
-    constexpr int U = RGM_SPMV_U;
-#else
     constexpr int U = (RGM_MINB >= 4) ? 2 : (sizeof(T) == 4) ? 4 : 2;
-#endif
     const int lane = threadIdx.x & 31;
     const int64_t wd = (p1 - p0) >> 5;
     const int64_t nch = wd / VW;
@@ -713,23 +734,7 @@ __device__ __forceinline__ T slice_rowsum(const T *sval, const int32_t *scol, co
 #pragma unroll
         for (int t = 0; t < VW; ++t) acc[t] += vcomp<VT, T>(v, t) * x[icomp(c, t)];
     }
-    // lanes l, l + 32/VW, ... hold the same VW rows: add them
-#pragma unroll
-    for (int o = 32 / VW; o < 32; o <<= 1)
-#pragma unroll
-        for (int t = 0; t < VW; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
-    // row `lane` is component lane % VW of lane lane / VW
-    T a = (T)0;
-#pragma unroll
-    for (int t = 0; t < VW; ++t) {
-        const T v = __shfl_sync(0xffffffffu, acc[t], lane / VW);
-        if ((lane % VW) == t) a = v;
-    }
-    for (int64_t k = nch * VW; k < wd; ++k) {
-        const int64_t e = p0 + 32 * k + lane;
-        a += ld_op(sval + e) * x[ld_op(scol + e)];
-    }
-    return a;
+    return slice_combine<T>(acc, sval, scol, x, p0, nch * VW, wd);
 }
 
 // What one block did in a pass: left without touching the completion counter
@@ -766,9 +771,16 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op, const int bid)
     // AXPY columns [W | Vraw | U] as one list: pointer and coefficient
     __shared__ const T *acol[RGM_KMAX + RGM_HLD + RGM_KMAX];
     __shared__ T acoef[RGM_KMAX + RGM_HLD + RGM_KMAX];
-    __shared__ __align__(16) T ws[((sizeof(T) == 4) ? 8 : 1) * RGM_TILE];   // w on a chunk (binary32) or tile
-    // AXPY partial sums per column phase (binary64 tile path only)
-    __shared__ __align__(16) T apart[(sizeof(T) == 8) ? NPH * RGM_TILE : VW];
+    // One pool for the large shared arrays: w on a chunk (binary32) or a tile
+    // (binary64) and the binary64 AXPY partial sums per column phase, and -- in
+    // the block that finalises, after those are dead -- the scalar step's scratch.
+    constexpr int WS_BYTES = ((sizeof(T) == 4) ? 8 : 1) * RGM_TILE * (int)sizeof(T);
+    constexpr int AP_BYTES = ((sizeof(T) == 8) ? NPH * RGM_TILE : VW) * (int)sizeof(T);
+    constexpr int MAIN_BYTES = WS_BYTES + AP_BYTES;
+    constexpr int POOL_BYTES = MAIN_BYTES > (int)sizeof(FinScratch) ? MAIN_BYTES : (int)sizeof(FinScratch);
+    __shared__ __align__(16) unsigned char pool[POOL_BYTES];
+    T *ws = reinterpret_cast<T *>(pool);
+    T *apart = reinterpret_cast<T *>(pool + WS_BYTES);
     __shared__ double xs;
     if (threadIdx.x == 0) xs = (op.xscale >= 0) ? s->colscale[op.xscale] : 1.0;
     const int nac = (op.src == SRC_AXPY) ? op.nW + op.nV + op.nU : 0;
@@ -819,22 +831,6 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op, const int bid)
             const int64_t ce = min(r1, cb + (int64_t)CHT * RGM_TILE);
             const int nr = (int)(ce - cb);
             const int ntc = (nr + RGM_TILE - 1) / RGM_TILE;
-#if RGM_PF
-            // the dot columns of this chunk are read right after the SpMV below:
-            // start pulling them into L2 now (one bulk prefetch per column), so
-            // that phase 2 streams them from L2 while phase 1 streams the operator
-            if (spmv_src && nd > 0) {
-                static_assert(RGM_MAXDOTS <= RGM_THREADS, "one dot column per thread");
-                const int c = threadIdx.x;
-                if (c < nd) {
-                    const T *cp = (c == ndc_) ? op.wvec : dot_col(op, c);
-                    const uint32_t bytes = (uint32_t)(((nr + 3) & ~3) * (int)sizeof(T));
-                    if (cp != nullptr && cp != op.out && ((uintptr_t)(cp + cb) & 15) == 0)
-                        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(cp + cb), "r"(bytes)
-                                     : "memory");
-                }
-            }
-#endif
             // ---- phase 1: produce and store w on the chunk
             if (spmv_src) {
                 // one warp per 32-row slice, one lane per row.  Inside a tile the
@@ -1123,7 +1119,7 @@ __device__ __forceinline__ int vec_pass(VecOp<T> op, const int bid)
     // partials (one warp per column, one lane per block); the last group adds
     // the group sums and runs the scalar step.  No block waits for another.
     __shared__ double dsum[RGM_MAXDOTS];
-    __shared__ FinScratch fin;
+    FinScratch &fin = *reinterpret_cast<FinScratch *>(pool);   // the main phase's arrays are dead
     const int g = bid / RGM_RGROUP, gb0 = g * RGM_RGROUP;
     const int gn = min(RGM_RGROUP, op.nblocks - gb0);
     if (!last_of(op.gcount + g, (unsigned)gn)) return PASS_ARRIVED;
