@@ -243,13 +243,20 @@ int rgm_batch_plan(int nsys, const int64_t *n, const int64_t *nnz, const int *nd
  * *count receives how many are valid. */
 int rgm_get_singular_values(rgm_solver s, double *sigma, int *count);
 
-/* Clear the snapshot window and the recycle space. */
+/* Clear the snapshot window and the recycle space (and the eigenvectors the
+ * next window SVD would start from). */
 int rgm_reset_recycling(rgm_solver s);
 
 /* Checkpoint / resume of the recycling state that Algorithm 1 carries from
  * one system of the sequence to the next: the snapshot window (its stored
  * columns, ring position, update count and the window Gram matrix that the
- * next update extends by one column) and the recycle space U.  Not
+ * next update extends by one column), the recycle space U, and the
+ * eigenvectors of the last window Gram matrix, which the next window SVD's
+ * Jacobi rotations start from (consecutive windows differ by one column, so
+ * they nearly diagonalise the next Gram matrix; the eigenpairs are unchanged,
+ * only their rounding depends on the start, hence their place in the state).
+ * Buffers written before the eigenvectors were part of the state are still
+ * accepted (the next SVD then starts from the identity).  Not
  * described in the paper; it lets a sequence continue in a new handle or a
  * new process with results identical to the uninterrupted run.  The operator
  * is not part of the state (each step sets its own), nor are the singular

@@ -71,6 +71,10 @@ struct Small {
     double eval[RGM_WMAX];
     int ord[RGM_WMAX];
     double wn_dummy;
+    // eigenvectors of the last window Gram matrix (rows: ring slots), the
+    // starting rotation of the next eigen-decomposition; phi_c = 0: none
+    double phi[RGM_WMAX * RGM_WMAX];
+    int phi_c;
 };
 
 // Reduce NV per-lane values across a warp with a butterfly that halves the

@@ -430,19 +430,23 @@ static int launch_gram(rgm_solver s, const T *X, int64_t ldx, int nx, const T *Y
     // the row tile of all ncol columns (tile + 1 values each) in dynamic shared
     // memory, within the 48 KB a launch may use without opting in, less the
     // kernel's static shared memory
-    static size_t static_smem = (size_t)-1;
-    if (static_smem == (size_t)-1) {
+    // one pair a thread when they fit the block (the per-step Gram matrices)
+    const bool one = npmax <= RGM_THREADS;
+    static size_t static_smem[2] = {(size_t)-1, (size_t)-1};
+    if (static_smem[one] == (size_t)-1) {
         cudaFuncAttributes fa;
-        CK(cudaFuncGetAttributes(&fa, gram_kernel<T>));
-        static_smem = fa.sharedSizeBytes;
+        if (one) CK(cudaFuncGetAttributes(&fa, gram_kernel<T, 1>));
+        else CK(cudaFuncGetAttributes(&fa, gram_kernel<T, RGM_GRAM_PMAX>));
+        static_smem[one] = fa.sharedSizeBytes;
     }
-    const int budget = (int)((48 * 1024 - static_smem) / sizeof(T));
-    op.tile = std::min(256, budget / ncol - 1);
+    const int budget = (int)((48 * 1024 - static_smem[one]) / sizeof(T));
+    op.tile = std::min(RGM_THREADS, budget / ncol - 1);
     const size_t smem = std::max(sizeof(T) * (size_t)ncol * (op.tile + 1), sizeof(double) * RGM_THREADS);
     {
         const double n = (double)s->n, np_ = (double)npmax;
         ProfScope ps(s, RGM_PROF_GRAM, 2.0 * n * np_, (double)sizeof(T) * n * ncol);
-        gram_kernel<T><<<s->nblocks, RGM_THREADS, smem, s->st>>>(op);
+        if (one) gram_kernel<T, 1><<<s->nblocks, RGM_THREADS, smem, s->st>>>(op);
+        else gram_kernel<T, RGM_GRAM_PMAX><<<s->nblocks, RGM_THREADS, smem, s->st>>>(op);
     }
     CK(cudaGetLastError());
     return RGM_OK;
@@ -943,7 +947,9 @@ static int gmres_cycles(rgm_solver s, const Arnoldi<T> &a, int mode, int k, int 
             op.src = SRC_AXPY; op.win = a.x; op.out = a.x; op.nU = k;
             if ((rc = launch(s, op))) return rc;
         }
-        {
+        if (mode == RGM_DEFLATED && sizeof(T) == 4) {
+            if ((rc = residual_after_coarse(s, a, k))) return rc;
+        } else {
             VecOp<T> op = base_op(s, a);
             op.src = SRC_RES; op.x = a.x; op.b = a.b; op.out = a.r; op.dnorm = 1; op.fin = FIN_RESNORM;
             op.wvec = res_weights(s, a);
@@ -970,6 +976,20 @@ static int coarse_correct(rgm_solver s, const Arnoldi<T> &a, int k, bool x_zero 
     if (rc) return rc;
     op = base_op(s, a);
     op.src = SRC_AXPY; op.win = a.x; op.out = a.x; op.nU = k;
+    return launch(s, op);
+}
+
+// The residual of x after a coarse correction x += U c: r - W c (W = A U)
+// instead of b - A x.  Used by the binary32 inner solve of GMRES-IR, whose
+// residuals only steer the inner iteration (the refinement loop recomputes the
+// binary64 residual from A); an AXPY over k columns instead of an SpMV.
+template <typename T>
+static int residual_after_coarse(rgm_solver s, const Arnoldi<T> &a, int k)
+{
+    VecOp<T> op = base_op(s, a);
+    op.src = SRC_AXPY; op.win = a.r; op.out = a.r; op.nW = k; op.W = a.W; op.dnorm = 1;
+    op.fin = FIN_RESNORM;
+    op.wvec = res_weights(s, a);
     return launch(s, op);
 }
 
@@ -1063,8 +1083,14 @@ static int solve_device(rgm_solver s, rgm_stats *out)
             // outer target (the binary64 residual below decides convergence)
             { ProfScope ps_(s, RGM_PROF_SMALL);
               set_tol_kernel<<<1, 32, 0, s->st>>>(s->sm, c.inner_rtol, 0, 0.5 * c.rtol * bnorm); }
-            if (k > 0 && (rc = coarse_correct(s, f, k, true))) return rc;   // d = 0: residual is b32
-            if ((rc = residual_norm(s, f))) return rc;
+            if (k > 0) {     // d = U c from d = 0: residual b32 - W c
+                if ((rc = coarse_correct(s, f, k, true))) return rc;
+                if ((rc = residual_after_coarse(s, f, k))) return rc;
+            } else {         // d = 0: the residual is b32
+                VecOp<float> op = base_op(s, f);
+                op.src = SRC_COPY; op.win = f.b; op.out = f.r; op.dnorm = 1; op.fin = FIN_RESNORM;
+                if ((rc = launch(s, op))) return rc;
+            }
             int cy = 0;
             if ((rc = gmres_cycles(s, f, mode, k, c.inner_cycles, &cy))) return rc;
             cycles += cy;
@@ -1493,7 +1519,8 @@ int rgm_set_operator_values(rgm_solver s, const double *val, int flags)
         }
         if (s->gather_smem) {
             ProfScope ps_(s, RGM_PROF_OPERATOR, 0.0, 2.0 * 8.0 * (double)s->nnz + 16.0 * (double)s->nsell);
-            sell_gather_kernel<double><<<(unsigned)((s->n + RGM_TILE - 1) / RGM_TILE), 256, s->gather_smem, s->st>>>(
+            sell_gather_kernel<double><<<(unsigned)((s->n + RGM_TILE - 1) / RGM_TILE), RGM_GATHER_THREADS,
+                                         s->gather_smem, s->st>>>(
                 s->sval, s->sval32, src, s->tile_csr, s->slice_ptr, s->sell_src);
         } else {
             const int g = (int)std::min<int64_t>((s->nnz + 255) / 256, 8 * (int64_t)s->nsm);
@@ -1732,6 +1759,7 @@ int rgm_reset_recycling(rgm_solver s)
     s->updates = 0;
     s->gwin_valid = false;
     s->win_last = -1;
+    CK(cudaMemsetAsync(&s->sm->phi_c, 0, sizeof(int), s->st));
     CK(cudaStreamSynchronize(s->st));
     s->k_cur = 0;
     s->k_pending = false;
@@ -1740,15 +1768,17 @@ int rgm_reset_recycling(rgm_solver s)
 }
 
 // Checkpoint layout: StateHeader, then win_used window columns (ring slots
-// 0..win_used-1, n doubles each), k_cur columns of U, and (gram set) the
-// win_used x win_used window Gram matrix the next update builds on.
+// 0..win_used-1, n doubles each), k_cur columns of U, (gram set) the
+// win_used x win_used window Gram matrix the next update builds on, and the
+// phi_c x phi_c eigenvectors of the last window Gram matrix that the next
+// eigen-decomposition starts from (version 3; version 2 has none).
 namespace {
 struct StateHeader {
     uint32_t magic, version;
     int64_t n;
     int32_t window, k_cur, win_count, win_head;
     int64_t updates;
-    int32_t gram, reserved;
+    int32_t gram, phi_c;
 };
 const uint32_t kStateMagic = 0x314d4752u;   // bytes "RGM1" in little-endian order
 }  // namespace
@@ -1760,13 +1790,18 @@ int rgm_export_state(rgm_solver s, void *buf, size_t *bytes)
     if (rc) return rc;
     const int win_used = s->win_count;   // ring slots 0..win_count-1 hold data
     const int with_gram = s->gwin_valid ? 1 : 0;
+    int pc = 0;
+    CK(cudaStreamSynchronize(s->st));
+    CK(cudaMemcpy(&pc, &s->sm->phi_c, sizeof(int), cudaMemcpyDeviceToHost));
+    if (pc < 0 || pc > win_used) pc = 0;
     const size_t need = sizeof(StateHeader) + sizeof(double) * ((size_t)s->n * (win_used + s->k_cur) +
-                                                                (size_t)with_gram * win_used * win_used);
+                                                                (size_t)with_gram * win_used * win_used +
+                                                                (size_t)pc * pc);
     if (!buf) { *bytes = need; return RGM_OK; }
     if (*bytes < need) return RGM_E_ARG;
     StateHeader h;
     h.magic = kStateMagic;
-    h.version = 2;
+    h.version = 3;
     h.n = s->n;
     h.window = s->cfg.window;
     h.k_cur = s->k_cur;
@@ -1774,7 +1809,7 @@ int rgm_export_state(rgm_solver s, void *buf, size_t *bytes)
     h.win_head = s->win_head;
     h.updates = s->updates;
     h.gram = with_gram;
-    h.reserved = 0;
+    h.phi_c = pc;
     std::memcpy(buf, &h, sizeof h);
     double *d = reinterpret_cast<double *>(static_cast<char *>(buf) + sizeof h);
     for (int i = 0; i < win_used; ++i)
@@ -1788,6 +1823,10 @@ int rgm_export_state(rgm_solver s, void *buf, size_t *bytes)
     for (int j = 0; j < win_used && with_gram; ++j)
         CK(cudaMemcpyAsync(d + (size_t)j * win_used, s->gwin + (int64_t)j * RGM_WMAX,
                            sizeof(double) * win_used, cudaMemcpyDeviceToHost, s->st));
+    d += (size_t)with_gram * win_used * win_used;
+    for (int j = 0; j < pc; ++j)
+        CK(cudaMemcpyAsync(d + (size_t)j * pc, s->sm->phi + (int64_t)j * RGM_WMAX, sizeof(double) * pc,
+                           cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
     *bytes = need;
     return RGM_OK;
@@ -1798,12 +1837,15 @@ int rgm_import_state(rgm_solver s, const void *buf, size_t bytes)
     if (!s || !buf || bytes < sizeof(StateHeader)) return RGM_E_ARG;
     StateHeader h;
     std::memcpy(&h, buf, sizeof h);
-    if (h.magic != kStateMagic || h.version != 2 || h.n != s->n || h.window != s->cfg.window ||
-        h.k_cur < 0 || h.k_cur > s->cfg.k || h.win_count < 0 || h.win_count > h.window ||
-        h.win_head < 0 || h.win_head >= h.window || h.updates < h.win_count || h.gram < 0 || h.gram > 1)
+    if (h.version == 2) h.phi_c = 0;          // written before the warm start existed
+    if (h.magic != kStateMagic || (h.version != 2 && h.version != 3) || h.n != s->n ||
+        h.window != s->cfg.window || h.k_cur < 0 || h.k_cur > s->cfg.k || h.win_count < 0 ||
+        h.win_count > h.window || h.win_head < 0 || h.win_head >= h.window || h.updates < h.win_count ||
+        h.gram < 0 || h.gram > 1 || h.phi_c < 0 || h.phi_c > h.win_count)
         return RGM_E_ARG;
     const size_t need = sizeof(StateHeader) + sizeof(double) * ((size_t)s->n * (h.win_count + h.k_cur) +
-                                                                (size_t)h.gram * h.win_count * h.win_count);
+                                                                (size_t)h.gram * h.win_count * h.win_count +
+                                                                (size_t)h.phi_c * h.phi_c);
     if (bytes != need) return RGM_E_ARG;
     CK(cudaStreamSynchronize(s->st));
     const double *d = reinterpret_cast<const double *>(static_cast<const char *>(buf) + sizeof h);
@@ -1818,6 +1860,11 @@ int rgm_import_state(rgm_solver s, const void *buf, size_t bytes)
     for (int j = 0; j < h.win_count && h.gram; ++j)
         CK(cudaMemcpyAsync(s->gwin + (int64_t)j * RGM_WMAX, d + (size_t)j * h.win_count,
                            sizeof(double) * h.win_count, cudaMemcpyHostToDevice, s->st));
+    d += (size_t)h.gram * h.win_count * h.win_count;
+    for (int j = 0; j < h.phi_c; ++j)
+        CK(cudaMemcpyAsync(s->sm->phi + (int64_t)j * RGM_WMAX, d + (size_t)j * h.phi_c,
+                           sizeof(double) * h.phi_c, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(&s->sm->phi_c, &h.phi_c, sizeof(int), cudaMemcpyHostToDevice, s->st));
     CK(cudaStreamSynchronize(s->st));
     s->gwin_valid = h.gram != 0;
     s->win_last = -1;

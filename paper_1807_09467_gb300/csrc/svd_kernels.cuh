@@ -177,24 +177,35 @@ __global__ void gram_unpack_kernel(double *gwin, const double *packed, int c)
 __device__ inline int packed_index(int i, int j) { return j * (j + 1) / 2 + i; }
 
 // Symmetric eigen-decomposition of the c x c window Gram matrix and the choice
-// of the recycle modes.  One block; G and Phi in dynamic shared memory
-// (EIG_SMEM_BYTES, above the 48 KB static limit: needs the opt-in attribute).
-#define EIG_SMEM_BYTES (2 * RGM_WMAX * RGM_WMAX * sizeof(double))
+// of the recycle modes.  One block; G, Phi and a product buffer in dynamic
+// shared memory (EIG_SMEM_BYTES, above the 48 KB static limit: needs the
+// opt-in attribute).
+//
+// Warm start: consecutive windows share all columns but the replaced ones, so
+// the eigenvectors Phi0 of the previous window Gram matrix (Small::phi, rows
+// indexed by ring slot; slots added since get unit vectors) nearly diagonalise
+// the new one.  The rotations run on Phi0^T G Phi0 with Phi accumulated from
+// Phi0 -- a similarity transform, so the eigenpairs are those of G -- and need
+// fewer sweeps than from the identity.
+#define EIG_SMEM_BYTES (3 * RGM_WMAX * RGM_WMAX * sizeof(double))
 __global__ void sym_eig_select_kernel(Small *s, const double *gram, int c, int k,
                                       int select_smallest, double rel_drop)
 // gram: the full c x c window Gram matrix, leading dimension RGM_WMAX
 {
-    extern __shared__ double eig_smem[];       // G and Phi, RGM_WMAX x RGM_WMAX each
-    double *G = eig_smem, *P = eig_smem + RGM_WMAX * RGM_WMAX;
+    extern __shared__ double eig_smem[];       // G, Phi and T, RGM_WMAX x RGM_WMAX each
+    double *G = eig_smem, *P = eig_smem + RGM_WMAX * RGM_WMAX, *T = P + RGM_WMAX * RGM_WMAX;
     __shared__ double rc[RGM_WMAX / 2], rs[RGM_WMAX / 2];
     __shared__ int rp[RGM_WMAX / 2], rq[RGM_WMAX / 2];
     const int ce = c + (c & 1);                 // even size for the tournament
+    const int pc = s->phi_c;
+    const bool warm = pc > 0 && pc <= c;        // the previous window's slots are a prefix
     for (int t = threadIdx.x; t < ce * ce; t += blockDim.x) {
         int i = t % ce, j = t / ce;
         double v = 0.0;
         if (i < c && j < c) v = gram[i + j * RGM_WMAX];
         G[i + j * RGM_WMAX] = v;
-        P[i + j * RGM_WMAX] = (i == j) ? 1.0 : 0.0;
+        P[i + j * RGM_WMAX] = (warm && i < pc && j < pc) ? s->phi[i + j * RGM_WMAX]
+                              : (warm && (i < pc || j < pc)) ? 0.0 : (i == j) ? 1.0 : 0.0;
     }
     __syncthreads();                            // G complete before its diagonal is read
     __shared__ double gmax;
@@ -202,6 +213,25 @@ __global__ void sym_eig_select_kernel(Small *s, const double *gram, int c, int k
         double m = 0.0;
         for (int i = 0; i < c; ++i) m = fmax(m, G[i + i * RGM_WMAX]);
         gmax = m;
+    }
+    if (warm) {
+        // G <- Phi0^T (G Phi0): T = G Phi0, then the upper triangle of Phi0^T T,
+        // mirrored (the rotations below keep G exactly symmetric)
+        for (int t = threadIdx.x; t < ce * ce; t += blockDim.x) {
+            const int i = t % ce, j = t / ce;
+            double v = 0.0;
+            for (int m = 0; m < ce; ++m) v = fma(G[i + m * RGM_WMAX], P[m + j * RGM_WMAX], v);
+            T[i + j * RGM_WMAX] = v;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < ce * ce; t += blockDim.x) {
+            const int i = t % ce, j = t / ce;
+            if (i > j) continue;
+            double v = 0.0;
+            for (int m = 0; m < ce; ++m) v = fma(P[m + i * RGM_WMAX], T[m + j * RGM_WMAX], v);
+            G[i + j * RGM_WMAX] = v;
+            G[j + i * RGM_WMAX] = v;
+        }
     }
     __syncthreads();
     // Stop rotating a pair when its coupling is below 1e-15 of its own
@@ -313,6 +343,12 @@ __global__ void sym_eig_select_kernel(Small *s, const double *gram, int c, int k
         __syncthreads();
         if (!more) break;
     }
+    // the next update starts from these eigenvectors
+    for (int t = threadIdx.x; t < c * c; t += blockDim.x) {
+        const int i = t % c, j = t / c;
+        s->phi[i + j * RGM_WMAX] = P[i + j * RGM_WMAX];
+    }
+    if (threadIdx.x == 0) s->phi_c = c;
     // eigenvalues, stable descending order by rank counting (ties by index)
     __shared__ double lam[RGM_WMAX], isg[RGM_WMAX];
     __shared__ int ord[RGM_WMAX];

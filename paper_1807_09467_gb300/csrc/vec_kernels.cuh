@@ -32,7 +32,7 @@ enum Fin {
     FIN_BNORM,       // ||b||
     FIN_BNORMP,      // ||D^{-1} b|| (left Jacobi)
     FIN_RESNORM,     // beta = ||r||, converged flag
-    FIN_COARSE,      // coefU = E^{-1} (U^T r)
+    FIN_COARSE,      // coefU = E^{-1} (U^T r), coefW = -coefU
     FIN_START_PLAIN, // v_0 = r / ||r||
     FIN_START_DEF1,  // coefW = -E^{-1} U^T r  (start vector P r)
     FIN_START_DEF2,  // v_0 = P r / ||P r||, VtW row 0
@@ -391,9 +391,11 @@ __device__ void finalize_block(const VecOp<T> &op, const double *d, FinScratch &
             if (tid < k) f.dd[tid] = x;
         }
         __syncthreads();
+        // FIN_COARSE: x += U c, and r -= W c (W = A U) where the residual of
+        // the corrected x is updated instead of recomputed
         for (int i = tid; i < k; i += blockDim.x) {
             if (op.fin == FIN_COARSE) s->coefU[i] = f.dd[i];
-            else s->coefW[i] = -f.dd[i];
+            s->coefW[i] = -f.dd[i];
         }
         break;
     }
@@ -1484,9 +1486,12 @@ __global__ void sell_scatter_kernel(double *sval, float *sval32, const Tin *val,
 // too) is written in order from src[e], its CSR offset inside the tile (-1:
 // padding, value 0).  Both global streams are coalesced, unlike the scatter
 // above, whose writes land 32 positions apart.  Dynamic shared memory: the
-// largest tile's CSR entries in binary64.
+// largest tile's CSR entries in binary64 (up to RGM_GATHER_SMEM_MAX, so few
+// blocks fit an SM: each block is RGM_GATHER_THREADS wide to keep loads in
+// flight).
+#define RGM_GATHER_THREADS 1024
 template <typename Tin>
-__global__ void __launch_bounds__(256) sell_gather_kernel(double *__restrict__ sval, float *__restrict__ sval32,
+__global__ void __launch_bounds__(RGM_GATHER_THREADS) sell_gather_kernel(double *__restrict__ sval, float *__restrict__ sval32,
                                                           const Tin *__restrict__ val,
                                                           const int64_t *__restrict__ tile_csr,
                                                           const int64_t *__restrict__ slice_ptr,
@@ -1571,7 +1576,10 @@ __device__ __forceinline__ double pair_dot(const float *a, const float *b, int r
     return acc;
 }
 
-template <typename T>
+// PPT: pairs a thread owns at most (1 when npairs <= RGM_THREADS: the per-step
+// Gram matrices -- the window's new column, CholQR, E -- which then run with
+// few registers and more blocks per SM; RGM_GRAM_PMAX for a full window Gram).
+template <typename T, int PPT>
 __global__ void __launch_bounds__(RGM_THREADS) gram_kernel(GramOp<T> op)
 {
     extern __shared__ __align__(16) unsigned char gsm_raw[];
@@ -1600,10 +1608,11 @@ __global__ void __launch_bounds__(RGM_THREADS) gram_kernel(GramOp<T> op)
             *a = *b = nx + (p - nx * nx - nx);
         }
     };
-    double acc[RGM_GRAM_PMAX];
-    int pa[RGM_GRAM_PMAX], pb[RGM_GRAM_PMAX];
+    static_assert(PPT >= 1 && PPT <= RGM_GRAM_PMAX, "pairs a thread");
+    double acc[PPT];
+    int pa[PPT], pb[PPT];
 #pragma unroll
-    for (int i = 0; i < RGM_GRAM_PMAX; ++i) {
+    for (int i = 0; i < PPT; ++i) {
         acc[i] = 0.0;
         pair_of(threadIdx.x + i * RGM_THREADS, &pa[i], &pb[i]);
     }
@@ -1618,17 +1627,18 @@ __global__ void __launch_bounds__(RGM_THREADS) gram_kernel(GramOp<T> op)
     double sacc = 0.0;
     for (int64_t base = r0; base < r1; base += op.tile) {
         const int nrow = (int)min((int64_t)op.tile, r1 - base);
-        for (int t = threadIdx.x; t < nrow * ncol; t += RGM_THREADS) {
-            const int r = t % nrow, c = t / nrow;
+        // column by column, one row a thread (tile <= RGM_THREADS): ncol
+        // independent coalesced loads in flight per thread
+        for (int c = 0; c < ncol; ++c) {
             const T *src = c < nx ? op.X + (int64_t)c * op.ldx : op.Y + (int64_t)(c - nx) * op.ldy;
-            gsm[c * ts + r] = src[base + r];
+            for (int r = threadIdx.x; r < nrow; r += RGM_THREADS) gsm[c * ts + r] = src[base + r];
         }
         __syncthreads();
         if (split) {
             if (srs < nsl) sacc = pair_dot(gsm + spa * ts, gsm + spb * ts, srs, nrow, nsl, sacc);
         } else {
 #pragma unroll
-            for (int i = 0; i < RGM_GRAM_PMAX; ++i) {
+            for (int i = 0; i < PPT; ++i) {
                 if (threadIdx.x + i * RGM_THREADS < npairs)
                     acc[i] += pair_dot(gsm + pa[i] * ts, gsm + pb[i] * ts, 0, nrow, 1, 0.0);
             }
@@ -1647,7 +1657,7 @@ __global__ void __launch_bounds__(RGM_THREADS) gram_kernel(GramOp<T> op)
         }
     }
 #pragma unroll
-    for (int i = 0; i < RGM_GRAM_PMAX; ++i) {
+    for (int i = 0; i < PPT; ++i) {
         const int p = threadIdx.x + i * RGM_THREADS;
         if (p < npairs) op.partials[(int64_t)p * op.nblocks + blockIdx.x] = acc[i];
     }
@@ -1660,12 +1670,16 @@ __global__ void __launch_bounds__(RGM_THREADS) gram_kernel(GramOp<T> op)
     if (!last_of(op.gcount + g, (unsigned)gn)) return;
     for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
         const double *pp = op.partials + (int64_t)p * op.nblocks + gb0;
-        double v[RGM_RGROUP];
-#pragma unroll
-        for (int b = 0; b < RGM_RGROUP; ++b) v[b] = (b < gn) ? __ldcg(pp + b) : 0.0;
         double sum = 0.0;
+        // eight loads in flight at a time, added in block order
 #pragma unroll
-        for (int b = 0; b < RGM_RGROUP; ++b) sum += v[b];
+        for (int b0 = 0; b0 < RGM_RGROUP; b0 += 8) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = (b0 + u < gn) ? __ldcg(pp + b0 + u) : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) sum += v[u];
+        }
         op.gpart[(int64_t)p * op.ngroups + g] = sum;
     }
     if (threadIdx.x == 0) op.gcount[g] = 0u;
