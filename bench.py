@@ -98,10 +98,14 @@ def measured_peaks():
 
 
 def src_digest():
+    """Digest of the sources the Arnoldi-step kernels are built and launched
+    from (the fused passes, their dispatch and the solver's launch geometry);
+    the SVD, FE and allocation-free kernels are not part of it."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1807_09467_gb300", "csrc")
     for f in sorted(os.listdir(d)):
-        h.update(open(os.path.join(d, f), "rb").read())
+        if f.startswith(("vec_", "common", "solver")):
+            h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
