@@ -181,40 +181,103 @@ __device__ inline int packed_index(int i, int j) { return j * (j + 1) / 2 + i; }
 // shared memory (EIG_SMEM_BYTES, above the 48 KB static limit: needs the
 // opt-in attribute).
 //
-// Warm start: consecutive windows share all columns but the replaced ones, so
-// the eigenvectors Phi0 of the previous window Gram matrix (Small::phi, rows
-// indexed by ring slot; slots added since get unit vectors) nearly diagonalise
-// the new one.  The rotations run on Phi0^T G Phi0 with Phi accumulated from
-// Phi0 -- a similarity transform, so the eigenpairs are those of G -- and need
-// fewer sweeps than from the identity.
-#define EIG_SMEM_BYTES (3 * RGM_WMAX * RGM_WMAX * sizeof(double))
+// Leading modes (select_smallest == 0): the rotations run on G1 = R R^T, where
+// G = R^T R is the pivoted Cholesky factorisation of G (R: r x c, one row per
+// pivot step, columns in slot order; pivot steps stop once the largest
+// remaining diagonal entry is below 1e-17 lambda_max, so the dropped part is
+// far below any mode the selection can keep).  G1 has the eigenvalues of G
+// (one step of the Cholesky LR iteration) and is much closer to diagonal on
+// graded windows -- the snapshots of a time sequence, whose Gram eigenvalues
+// fall geometrically -- so the rotations need 4-6 sweeps instead of about 12;
+// an eigenvector q of G1 gives v = R^T q / sqrt(lambda) of G.
+//
+// Trailing modes (select_smallest): the rotations run on G itself, warm
+// started: consecutive windows share all columns but the replaced ones, so the
+// eigenvectors Phi0 of the previous window Gram matrix (Small::phi, rows indexed
+// by ring slot; slots added since get unit vectors) nearly diagonalise the new
+// one.  The rotations run on Phi0^T G Phi0 with Phi accumulated from Phi0 -- a
+// similarity transform, so the eigenpairs are those of G.
+#define EIG_SMEM_BYTES (4 * RGM_WMAX * RGM_WMAX * sizeof(double))
 __global__ void sym_eig_select_kernel(Small *s, const double *gram, int c, int k,
                                       int select_smallest, double rel_drop)
 // gram: the full c x c window Gram matrix, leading dimension RGM_WMAX
 {
-    extern __shared__ double eig_smem[];       // G, Phi and T, RGM_WMAX x RGM_WMAX each
+    extern __shared__ double eig_smem[];       // G, Phi, T and R, RGM_WMAX x RGM_WMAX each
     double *G = eig_smem, *P = eig_smem + RGM_WMAX * RGM_WMAX, *T = P + RGM_WMAX * RGM_WMAX;
+    double *R = T + RGM_WMAX * RGM_WMAX;        // R[a + m RGM_WMAX]: pivot step a, slot m
     __shared__ double rc[RGM_WMAX / 2], rs[RGM_WMAX / 2];
     __shared__ int rp[RGM_WMAX / 2], rq[RGM_WMAX / 2];
-    const int ce = c + (c & 1);                 // even size for the tournament
+    const bool lr = !select_smallest;           // rotations on R R^T
+    const int c0e = c + (c & 1);
     const int pc = s->phi_c;
-    const bool warm = pc > 0 && pc <= c;        // the previous window's slots are a prefix
-    for (int t = threadIdx.x; t < ce * ce; t += blockDim.x) {
-        int i = t % ce, j = t / ce;
+    const bool warm = !lr && pc > 0 && pc <= c; // the previous window's slots are a prefix
+    for (int t = threadIdx.x; t < c0e * c0e; t += blockDim.x) {
+        int i = t % c0e, j = t / c0e;
         double v = 0.0;
         if (i < c && j < c) v = gram[i + j * RGM_WMAX];
         G[i + j * RGM_WMAX] = v;
+        T[i + j * RGM_WMAX] = v;
         P[i + j * RGM_WMAX] = (warm && i < pc && j < pc) ? s->phi[i + j * RGM_WMAX]
                               : (warm && (i < pc || j < pc)) ? 0.0 : (i == j) ? 1.0 : 0.0;
     }
     __syncthreads();                            // G complete before its diagonal is read
     __shared__ double gmax;
+    __shared__ int rsz;                         // size of the matrix the rotations run on
     if (threadIdx.x == 0) {
         double m = 0.0;
         for (int i = 0; i < c; ++i) m = fmax(m, G[i + i * RGM_WMAX]);
         gmax = m;
+        rsz = c;
+    }
+    __syncthreads();
+    if (lr) {
+        // pivoted Cholesky G = R^T R on the working copy T (Schur complements);
+        // pivot: the largest remaining diagonal entry
+        __shared__ int piv_done[RGM_WMAX];
+        __shared__ int pj;
+        __shared__ double pd;
+        for (int i = threadIdx.x; i < c; i += blockDim.x) piv_done[i] = 0;
+        const double tau = 1e-17 * gmax;
+        int r = 0;
+        for (; r < c; ++r) {
+            __syncthreads();                    // previous update and flags done
+            if (threadIdx.x == 0) {
+                int p = -1;
+                double d = tau;
+                for (int i = 0; i < c; ++i)
+                    if (!piv_done[i] && T[i + i * RGM_WMAX] > d) { d = T[i + i * RGM_WMAX]; p = i; }
+                pj = p;
+                pd = d;
+            }
+            __syncthreads();
+            const int p = pj;
+            if (p < 0) break;                   // same value in every thread
+            const double rsd = rsqrt(pd), sd = pd * rsd;
+            for (int m = threadIdx.x; m < c; m += blockDim.x)
+                R[r + m * RGM_WMAX] = (m == p) ? sd : piv_done[m] ? 0.0 : T[p + m * RGM_WMAX] * rsd;
+            __syncthreads();
+            for (int t = threadIdx.x; t < c * c; t += blockDim.x) {
+                const int a = t % c, b = t / c;
+                if (a != p && b != p && !piv_done[a] && !piv_done[b])
+                    T[a + b * RGM_WMAX] -= R[r + a * RGM_WMAX] * R[r + b * RGM_WMAX];
+            }
+            if (threadIdx.x == 0) piv_done[p] = 1;
+        }
+        __syncthreads();
+        // G <- R R^T (r x r, zero-padded to even size); P <- identity
+        const int re = r + (r & 1);
+        for (int t = threadIdx.x; t < c0e * c0e; t += blockDim.x) {
+            const int a = t % c0e, b = t / c0e;
+            double v = 0.0;
+            if (a < r && b < r)
+                for (int m = 0; m < c; ++m) v = fma(R[a + m * RGM_WMAX], R[b + m * RGM_WMAX], v);
+            G[a + b * RGM_WMAX] = v;
+            P[a + b * RGM_WMAX] = (a == b && a < re) ? 1.0 : 0.0;
+        }
+        if (threadIdx.x == 0) rsz = r;
     }
     if (warm) {
+        const int ce = c0e;
         // G <- Phi0^T (G Phi0): T = G Phi0, then the upper triangle of Phi0^T T,
         // mirrored (the rotations below keep G exactly symmetric)
         for (int t = threadIdx.x; t < ce * ce; t += blockDim.x) {
@@ -234,6 +297,8 @@ __global__ void sym_eig_select_kernel(Small *s, const double *gram, int c, int k
         }
     }
     __syncthreads();
+    const int cs = rsz;                         // c, or the Cholesky rank r
+    const int ce = cs + (cs & 1);               // even size for the tournament
     // Stop rotating a pair when its coupling is below 1e-15 of its own
     // diagonal scale or below 2e-16 of the largest eigenvalue.  A rotation of a
     // pair that couples lambda_max with a tiny eigenvalue reintroduces couplings
@@ -343,12 +408,35 @@ __global__ void sym_eig_select_kernel(Small *s, const double *gram, int c, int k
         __syncthreads();
         if (!more) break;
     }
-    // the next update starts from these eigenvectors
-    for (int t = threadIdx.x; t < c * c; t += blockDim.x) {
-        const int i = t % c, j = t / c;
-        s->phi[i + j * RGM_WMAX] = P[i + j * RGM_WMAX];
+    if (lr) {
+        // eigenvectors of G: v_j = R^T q_j / sqrt(lambda_j) for the r eigenpairs
+        // of R R^T; the c - r dropped directions get lambda = 0 and v = 0
+        for (int t = threadIdx.x; t < c * c; t += blockDim.x) {
+            const int m = t % c, j = t / c;
+            double v = 0.0;
+            if (j < cs) {
+                const double lj = G[j + j * RGM_WMAX];
+                for (int a = 0; a < cs; ++a) v = fma(R[a + m * RGM_WMAX], P[a + j * RGM_WMAX], v);
+                v = (lj > 0.0) ? v * rsqrt(lj) : 0.0;
+            }
+            T[m + j * RGM_WMAX] = v;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < c * c; t += blockDim.x) {
+            const int m = t % c, j = t / c;
+            P[m + j * RGM_WMAX] = T[m + j * RGM_WMAX];
+            if (m == j && j >= cs) G[j + j * RGM_WMAX] = 0.0;
+        }
+        if (threadIdx.x == 0) s->phi_c = 0;     // no warm start from this path
+        __syncthreads();
+    } else {
+        // the next update starts from these eigenvectors
+        for (int t = threadIdx.x; t < c * c; t += blockDim.x) {
+            const int i = t % c, j = t / c;
+            s->phi[i + j * RGM_WMAX] = P[i + j * RGM_WMAX];
+        }
+        if (threadIdx.x == 0) s->phi_c = c;
     }
-    if (threadIdx.x == 0) s->phi_c = c;
     // eigenvalues, stable descending order by rank counting (ties by index)
     __shared__ double lam[RGM_WMAX], isg[RGM_WMAX];
     __shared__ int ord[RGM_WMAX];
