@@ -1151,11 +1151,11 @@ static int svd_update(rgm_solver s)
         // window's coordinates, then the second pass on the formed U (k_new read
         // on the device)
         { ProfScope ps_(s, RGM_PROF_SMALL); cholqr_small_kernel<<<1, 256, 0, s->st>>>(s->sm, s->gwin, cnt, kdev); }
-        { ProfScope ps_(s, RGM_PROF_SVD); combine_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U, s->X, s->sm->evec, cnt, -1, kdev, s->n, s->ld, RGM_WMAX); }
+        { ProfScope ps_(s, RGM_PROF_SVD); combine_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U, s->X, s->sm->evec, cnt, -1, kdev, s->n, s->ld, RGM_WMAX, 0); }
         CK(cudaGetLastError());
         if ((rc = launch_gram<double>(s, s->U, s->ld, 0, s->U, s->ld, GRAM_PACKED, kdev, kmax, s->gram_out))) return rc;
         { ProfScope ps_(s, RGM_PROF_SMALL); chol_inv_kernel<<<1, 64, 0, s->st>>>(s->sm, s->gram_out, -1, kdev); }
-        { ProfScope ps_(s, RGM_PROF_SVD); combine_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U, s->U, s->sm->evec, -1, -1, kdev, s->n, s->ld, RGM_WMAX); }
+        { ProfScope ps_(s, RGM_PROF_SVD); combine_kernel<<<s->nblocks, 256, 0, s->st>>>(s->U, s->U, s->sm->evec, -1, -1, kdev, s->n, s->ld, RGM_WMAX, 1); }
         CK(cudaGetLastError());
     }
     s->k_pending = true;

@@ -480,8 +480,10 @@ __global__ void sym_eig_select_kernel(Small *s, const double *gram, int c, int k
 // out[:, l] = sum_m in[:, m] C[m + l * ldc] for l < kout; in-place safe
 // (each row's inputs are read before its outputs are written).  A negative
 // cin or kout is read from *kdev (the dimension chosen on the device).
+// upper: C is upper triangular (its entries below the diagonal are zeros), so
+// the sum stops at m = l -- the same values with half the binary64 FMAs.
 __global__ void combine_kernel(double *out, const double *in, const double *C, int cin, int kout,
-                               const int *kdev, int64_t n, int64_t ld, int ldc)
+                               const int *kdev, int64_t n, int64_t ld, int ldc, int upper)
 {
     __shared__ double Cs[RGM_WMAX * RGM_KMAX];
     if (cin < 0) cin = *kdev;
@@ -499,7 +501,8 @@ __global__ void combine_kernel(double *out, const double *in, const double *C, i
         for (int m = 0; m < cin; ++m) xin[m] = in[i + m * ld];
         for (int l = 0; l < kout; ++l) {
             double acc = 0.0;
-            for (int m = 0; m < cin; ++m) acc += xin[m] * Cs[m + l * RGM_WMAX];
+            const int mend = upper ? min(cin, l + 1) : cin;
+            for (int m = 0; m < mend; ++m) acc += xin[m] * Cs[m + l * RGM_WMAX];
             out[i + l * ld] = acc;
         }
     }

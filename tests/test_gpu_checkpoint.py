@@ -74,18 +74,22 @@ def test_import_rejects_mismatch(rg):
     assert s.recycle_dim() == 0
 
 
-def test_state_without_eigenvectors_is_accepted(rg):
+@pytest.mark.parametrize("smallest", [True, False])
+def test_state_without_eigenvectors_is_accepted(rg, smallest):
     """A checkpoint written before the eigenvectors of the last window SVD were
     part of the state (version 2: no trailing eigenvector block) is accepted and
     the sequence goes on converging; a version-3 header whose eigenvector count
-    exceeds the window count is refused and leaves the handle usable."""
+    exceeds the window count is refused and leaves the handle usable.  The
+    eigenvectors are stored by the warm-started eigen-solve of the trailing
+    modes (select_smallest); the leading-mode solve stores none (count 0)."""
     import struct
     import torch
     w = synth.WORKLOADS["q1_32x32_eps0.05_dt0.01"]
     a8, beta = synth.sequence_draws(w, 0)
     fe = rg.FE(w.p, w.N, w.eps, w.dt, beta)
     rp, col = fe.pattern()
-    s = rg.Solver(fe.n, m=w.m, k=w.k, window=w.window, mode="deflated", rtol=w.rtol)
+    s = rg.Solver(fe.n, m=w.m, k=w.k, window=w.window, mode="deflated", rtol=w.rtol,
+                  select_smallest=smallest)
     s.set_operator_csr(rp, col, np.zeros(len(col)))
     u = torch.tensor(fe.initial_field(a8), dtype=torch.float64, device="cuda")
     _run(rg, w, beta, u, 6, s, fe)
@@ -93,14 +97,15 @@ def test_state_without_eigenvectors_is_accepted(rg):
     fmt = "<IIqiiiiqii"
     hdr = list(struct.unpack_from(fmt, blob))
     magic, version, n, window, k_cur, win_count, win_head, updates, gram, phi_c = hdr
-    assert version == 3 and 0 < phi_c <= win_count
+    assert version == 3 and (0 < phi_c <= win_count if smallest else phi_c == 0)
     body = blob[struct.calcsize(fmt):]
     assert len(body) == 8 * (n * (win_count + k_cur) + gram * win_count ** 2 + phi_c ** 2)
     v2 = struct.pack(fmt, magic, 2, n, window, k_cur, win_count, win_head, updates, gram, 0) + \
         body[:len(body) - 8 * phi_c ** 2]
     bad = struct.pack(fmt, magic, 3, n, window, k_cur, win_count, win_head, updates, gram, win_count + 1) + \
         body + bytes(8 * ((win_count + 1) ** 2 - phi_c ** 2))
-    s2 = rg.Solver(fe.n, m=w.m, k=w.k, window=w.window, mode="deflated", rtol=w.rtol)
+    s2 = rg.Solver(fe.n, m=w.m, k=w.k, window=w.window, mode="deflated", rtol=w.rtol,
+                   select_smallest=smallest)
     s2.set_operator_csr(rp, col, np.zeros(len(col)))
     with pytest.raises(rg.RgmError):
         s2.import_state(bad)
