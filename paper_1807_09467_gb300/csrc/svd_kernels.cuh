@@ -111,6 +111,10 @@ __global__ void __launch_bounds__(256) urow_kernel(T *__restrict__ Urow, const T
 // T = float: the binary32 operator and recycle columns of GMRES-IR (16
 // accumulators: k <= 16 reads the operator once).
 #define RGM_SPMM_KB ((sizeof(T) == 4) ? 16 : 8)
+#ifndef RGM_SPMM_UNROLL
+#define RGM_SPMM_UNROLL 2
+#endif
+constexpr int kSpmmUnroll = RGM_SPMM_UNROLL;   // entries in flight per lane
 template <typename T>
 __global__ void __launch_bounds__(256) spmm_kernel(const int64_t *__restrict__ slice_ptr,
                                                    const int32_t *__restrict__ scol,
@@ -132,6 +136,9 @@ __global__ void __launch_bounds__(256) spmm_kernel(const int64_t *__restrict__ s
             T acc[RGM_SPMM_KB];
 #pragma unroll
             for (int c = 0; c < RGM_SPMM_KB; ++c) acc[c] = (T)0;
+            // the iterations are independent but for the accumulators: unrolled,
+            // their gathers of U rows overlap
+#pragma unroll kSpmmUnroll
             for (int64_t e = p0 + lane; e < p1; e += 32) {
                 const T a = sval[e];
                 const VT *u = reinterpret_cast<const VT *>(Urow + (int64_t)scol[e] * kp + c0);
