@@ -549,18 +549,20 @@ def run_batch(args):
     import paper_1807_09467_gb300 as rg
     import synth
     g.build()
+    from paper_1807_09467_gb300 import tune
     seqs = synth.batch_sequences(64)
     prec = args.precision
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
-    def setup():
+    def setup(cap=None):
         st = []
         for w, a8, beta in seqs:
             stream = torch.cuda.Stream()
             fe = rg.FE(w.p, w.N, w.eps, w.dt, beta, stream=stream.cuda_stream)
             rp, col = fe.pattern()
             sol = rg.Solver(fe.n, m=w.m, k=w.k, window=w.window, mode=args.mode, precision=prec,
-                            rtol=w.rtol, stream=stream.cuda_stream)
+                            rtol=w.rtol, stream=stream.cuda_stream,
+                            tiles_per_block=tune.tiles_per_block(fe.n, cap))
             sol.set_operator_csr(rp, col, np.zeros(len(col)))
             u = torch.tensor(fe.initial_field(a8), dtype=torch.float64, device="cuda")
             st.append(dict(fe=fe, sol=sol, u=u, stream=stream, val=None, b=None))
@@ -594,22 +596,34 @@ def run_batch(args):
             e["u"].copy_(e["x"])
         return t0.elapsed_time(t1), stats
 
-    out = {}
-    for arm, batched, coop in (("coop", True, True), ("streams", True, False), ("sequential", False, False)):
-        state = setup()
+    def run_arm(batched, coop, cap, warmup, steps):
+        state = setup(cap)
         ms, its = [], []
-        for i in range(args.warmup + args.steps):
+        for i in range(warmup + steps):
             t, stats = step(state, batched, coop)
             assert all(st["status"] == 0 and st["true_relres"] <= 1e-8 for st in stats), stats
-            if i >= args.warmup:
+            if i >= warmup:
                 ms.append(t)
                 its.extend(st["iters"] for st in stats)
-        out[arm] = (ms, its)
         for e in state:
             e["sol"].close()
             e["fe"].close()
         del state
         torch.cuda.synchronize()
+        return ms, its
+
+    # autotuner: the cap on the blocks of any one system (more 256-row tiles a
+    # block), trial = the mean batch step of the chosen policy over steps
+    # 4..5 of the sequences; the default (no cap) is listed first
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    caps = [None, 2 * nsm, nsm, nsm // 2]
+    policy_coop = args.batch_policy == "coop"
+    best, trials = tune.tune(lambda c: statistics.mean(run_arm(True, policy_coop, c, 3, 2)[0]), caps)
+    out = {}
+    for arm, batched, coop in (("coop", True, True), ("streams", True, False), ("sequential", False, False)):
+        out[arm] = run_arm(batched, coop, best if batched and coop == policy_coop else None,
+                           args.warmup, args.steps)
+    untuned = run_arm(True, policy_coop, None, args.warmup, args.steps) if best is not None else None
     other = "streams" if args.batch_policy == "coop" else "coop"
     ms, its = out[args.batch_policy]
     mso, _ = out[other]
@@ -631,7 +645,12 @@ def run_batch(args):
            other: {"solves_per_s": round(64 * K / (sum(mso) / 1e3), 3), "ms_per_step": round(sum(mso) / K, 4)},
            "sequential": {"solves_per_s": round(64 * K / (sum(mss) / 1e3), 3),
                           "ms_per_step": round(sum(mss) / K, 4)},
-           "speedup_vs_sequential": round(sum(mss) / sum(ms), 3)}
+           "speedup_vs_sequential": round(sum(mss) / sum(ms), 3),
+           "autotune": {"knob": "cap on the blocks of one system (tiles_per_block of each handle)",
+                        "chosen_max_blocks": best,
+                        "trial_ms_per_batch_step": {str(c): round(t, 3) for c, t in trials.items()},
+                        "untuned_solves_per_s": (round(64 * K / (sum(untuned[0]) / 1e3), 3)
+                                                 if untuned else round(value, 3))}}
     print(json.dumps(res))
 
 

@@ -115,6 +115,12 @@ typedef struct {
                              g+1 most recent window snapshots once the window holds them
                              (needs window >= g+1); recycling then adds its projection  */
     int precond;          /* rgm_precond (not with RGM_FP32_IR)                              */
+    int tiles_per_block;  /* rows each block of the fused passes owns, in 256-row tiles; 0 =
+                             automatic (the fewest tiles that keep the grid within the
+                             blocks the device holds at once).  Not in the paper: a launch-
+                             shape knob for the batched form's autotuner (more tiles a block
+                             = fewer blocks a system, so more systems share the device).  A
+                             value above the tile count is clamped to it                  */
     double rtol;          /* converged when ||b - A x||_2 <= rtol ||b||_2                   */
     double inner_rtol;    /* FP32_IR: inner solve to max(inner_rtol ||r||, rtol ||b|| / 2)  */
     double rel_drop;      /* drop singular values below rel_drop * sigma_1                 */

@@ -54,7 +54,7 @@ class Solver:
     def __init__(self, n, m=30, k=8, window=16, svd_interval=1, select_smallest=False,
                  mode="deflated", precision="fp64", start_r=False, maxit=20000, inner_cycles=2,
                  max_refinements=50, rtol=1e-10, inner_rtol=1e-4, rel_drop=1e-7, stream=None,
-                 launch_policy="auto", proj="oblique", guess=0, precond="none"):
+                 launch_policy="auto", proj="oblique", guess=0, precond="none", tiles_per_block=0):
         L = _lib.load()
         cfg = RgmConfig()
         L.rgm_config_default(C.byref(cfg))
@@ -70,6 +70,7 @@ class Solver:
         cfg.proj = PROJECTORS[proj] if isinstance(proj, str) else int(proj)
         cfg.guess = int(guess)
         cfg.precond = PRECONDS[precond] if isinstance(precond, str) else int(precond)
+        cfg.tiles_per_block = int(tiles_per_block)
         cfg.cuda_stream = stream
         self.cfg = cfg
         self.n = n

@@ -34,7 +34,7 @@ class RgmConfig(C.Structure):
                 ("svd_interval", C.c_int), ("select_smallest", C.c_int), ("mode", C.c_int),
                 ("precision", C.c_int), ("start_r", C.c_int), ("maxit", C.c_int),
                 ("inner_cycles", C.c_int), ("max_refinements", C.c_int), ("launch_policy", C.c_int),
-                ("proj", C.c_int), ("guess", C.c_int), ("precond", C.c_int),
+                ("proj", C.c_int), ("guess", C.c_int), ("precond", C.c_int), ("tiles_per_block", C.c_int),
                 ("rtol", C.c_double),
                 ("inner_rtol", C.c_double), ("rel_drop", C.c_double), ("cuda_stream", C.c_void_p)]
 

@@ -1240,7 +1240,8 @@ int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
         c.launch_policy < RGM_LAUNCH_AUTO || c.launch_policy > RGM_LAUNCH_PER_PASS ||
         c.proj < RGM_PROJ_OBLIQUE || c.proj > RGM_PROJ_LS || c.guess < 0 || c.guess > 3 ||
         (c.guess > 0 && c.window < c.guess + 1) || c.precond < RGM_PRECOND_NONE ||
-        c.precond > RGM_PRECOND_JACOBI || (c.precond != RGM_PRECOND_NONE && c.precision != RGM_FP64))
+        c.precond > RGM_PRECOND_JACOBI || (c.precond != RGM_PRECOND_NONE && c.precision != RGM_FP64) ||
+        c.tiles_per_block < 0)
         return RGM_E_ARG;
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RGM_E_CUDA;
@@ -1265,7 +1266,8 @@ int rgm_solver_create(rgm_solver *out, const rgm_config *cfg)
     // blocks own whole RGM_TILE-row tiles (the sliced-ELL sorting windows)
     const int64_t ntile = (s->n + RGM_TILE - 1) / RGM_TILE;
     const int64_t nb_want = std::max<int64_t>(1, std::min<int64_t>(ntile, RGM_MINB * (int64_t)nsm));
-    const int64_t tiles_per_block = (ntile + nb_want - 1) / nb_want;
+    const int64_t tiles_per_block = (c.tiles_per_block > 0) ? std::min<int64_t>(c.tiles_per_block, ntile)
+                                                            : (ntile + nb_want - 1) / nb_want;
     s->rpb = (int)(tiles_per_block * RGM_TILE);
     s->nblocks = (int)((s->n + s->rpb - 1) / s->rpb);
     const int kmax = std::max(c.k, 1);

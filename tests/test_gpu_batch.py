@@ -168,3 +168,34 @@ def test_coop_flag_needs_one_precision(rg):
     for a, b, s1, s2 in zip(xa, xb, sa, sb):
         assert s1["iters"] == s2["iters"] and s1["status"] == s2["status"]
         np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("tpb", [1, 3, 8, 100000])
+def test_tiles_per_block_same_solution(rg, tpb):
+    """The autotuner's knob (tiles_per_block: rows a block owns) changes only the
+    launch shape: a deflated binary64 solve and a deflated GMRES-IR solve reach
+    the tolerance with iteration counts within one of the automatic shape's, and
+    x within the rounding of the dot-product partition (a count above the tile
+    count is clamped: one block)."""
+    n = 66049
+    rp, col, val = synth.random_csr(n, 9, 321, diag=6.0, min_per_row=2)
+    b = synth.random_vector(n, 322)
+    U = np.linalg.qr(synth.random_matrix(n, 6, 323))[0]
+    for prec, tol in (("fp64", 1e-10), ("fp32_ir", 1e-8)):
+        res = []
+        for t in (0, tpb):
+            s = rg.Solver(n, m=20, k=6, mode="deflated", precision=prec, rtol=tol, tiles_per_block=t)
+            s.set_operator_csr(rp, col, val)
+            s.set_recycle_space(U)
+            x, st = s.solve(b)
+            s.close()
+            assert st["status"] == 0 and st["true_relres"] <= tol, (t, st)
+            res.append((x, st))
+        (xa, sa), (xb, sb) = res
+        assert abs(sa["iters"] - sb["iters"]) <= 1, (sa, sb)
+        assert np.linalg.norm(xa - xb) <= 100 * tol * np.linalg.norm(xa)
+
+
+def test_tiles_per_block_rejects_negative(rg):
+    with pytest.raises(rg.RgmError):
+        rg.Solver(1000, tiles_per_block=-1)
