@@ -692,14 +692,26 @@ def run_serve(args):
     hbm_rate = serve_rate(serve, base, hbm)
     # closed-loop capacity of the deflated GMRES-IR server on the first 64 requests
     cal = [dataclasses.replace(r, arrival_s=0.0) for r in base[:64]]
-    _, ctot = serve.Server(max_slots=64, precision="fp32_ir", mode="deflated").run(cal, realtime=False)
-    capacity = len(cal) / ctot["wall_s"]
+    # launch-shape autotuner: the closed-loop wall time of those requests for
+    # each cap on the blocks of one sequence; the fastest cap serves both arms
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+
+    def cal_wall(cap):
+        _, t = serve.Server(max_slots=64, precision="fp32_ir", mode="deflated", max_blocks=cap).run(
+            cal, realtime=False)
+        return 1e3 * t["wall_s"]
+    from paper_1807_09467_gb300 import tune
+    cal_wall(None)                      # untimed: first-use costs out of the trials
+    cap, cal_trials = tune.tune(cal_wall, [None, 2 * nsm, nsm])
+    capacity = len(cal) / (cal_trials[cap] / 1e3)
     rate = args.serve_rate or 0.8 * capacity
     reqs = [dataclasses.replace(r, arrival_s=r.arrival_s / rate) for r in base]
     torch.cuda.synchronize()
-    res, tot = serve.Server(max_slots=64, precision="fp32_ir", mode="deflated").run(reqs, realtime=True)
+    res, tot = serve.Server(max_slots=64, precision="fp32_ir", mode="deflated", max_blocks=cap).run(
+        reqs, realtime=True)
     torch.cuda.synchronize()
-    bres, btot = serve.Server(max_slots=64, precision="fp64", mode="plain").run(reqs, realtime=True)
+    bres, btot = serve.Server(max_slots=64, precision="fp64", mode="plain", max_blocks=cap).run(
+        reqs, realtime=True)
     its = [i for r in res for i in r.iters]
     bits = [i for r in bres for i in r.iters]
     first = [r.latencies_ms[0] for r in res if r.latencies_ms]
@@ -720,6 +732,9 @@ def run_serve(args):
                           "first_solve_p50": pct(first, 50), "first_solve_p99": pct(first, 99),
                           "later_solves_p50": pct(later, 50), "later_solves_p99": pct(later, 99)},
            "iterations": iters_stats(its), "wall_s": round(tot["wall_s"], 3),
+           "autotune": {"knob": "cap on the blocks of one sequence (tiles_per_block of each handle)",
+                        "chosen_max_blocks": cap,
+                        "trial_ms_64_requests_closed_loop": {str(c): round(t, 1) for c, t in cal_trials.items()}},
            "footprint_estimate_over_measured": tot["footprint_estimate_over_measured"],
            "plain_fp64_same_loop": {"solves_per_s": round(btot["solves_per_s"], 3),
                                     "p50_ms": round(btot["p50_ms"], 3), "p99_ms": round(btot["p99_ms"], 3),

@@ -29,7 +29,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import FE, Solver
+from . import FE, Solver, tune
 
 
 @dataclass
@@ -99,7 +99,7 @@ def device_bytes(req: Request, precision: str = "fp32_ir") -> int:
 
 
 class _Live:
-    def __init__(self, req: Request, precision: str, mode: str):
+    def __init__(self, req: Request, precision: str, mode: str, max_blocks: int | None = None):
         import torch
         self.req = req
         self.stream = torch.cuda.Stream()
@@ -107,7 +107,8 @@ class _Live:
         rp, col = self.fe.pattern()
         self.sol = Solver(self.fe.n, m=req.m, k=req.k, window=req.window, mode=mode,
                           precision=precision, rtol=req.rtol, stream=self.stream.cuda_stream,
-                          launch_policy="per_pass")
+                          launch_policy="per_pass",
+                          tiles_per_block=tune.tiles_per_block(self.fe.n, max_blocks))
         self.sol.set_operator_csr(rp, col, np.zeros(len(col)))
         with torch.cuda.stream(self.stream):
             self.u = torch.tensor(self.fe.initial_field(req.a8), dtype=torch.float64, device="cuda")
@@ -124,14 +125,17 @@ class _Live:
 class Server:
     """Continuous-batching loop.  max_slots bounds the sequences in flight;
     each admission also needs its estimated footprint to fit hbm_fraction of
-    the device memory free at that moment."""
+    the device memory free at that moment.  max_blocks caps the blocks of any
+    one sequence's passes (tiles_per_block of its handle; None: the library's
+    automatic shape), the knob of the launch-shape autotuner (tune.py)."""
 
     def __init__(self, max_slots: int = 64, hbm_fraction: float = 0.8, precision: str = "fp32_ir",
-                 mode: str = "deflated"):
+                 mode: str = "deflated", max_blocks: int | None = None):
         self.max_slots = max_slots
         self.hbm_fraction = hbm_fraction
         self.precision = precision
         self.mode = mode
+        self.max_blocks = max_blocks
 
     def _drive(self, lv: _Live, res: Result, t0: float, done):
         """One sequence, step after step on its own stream (a host thread)."""
@@ -198,7 +202,7 @@ class Server:
             pending.pop(0)
             res = results[req.rid]
             res.admitted_s = now()
-            lv = _Live(req, self.precision, self.mode)
+            lv = _Live(req, self.precision, self.mode, self.max_blocks)
             res.device_bytes = lv.device_bytes()
             est_over.append(need / max(res.device_bytes, 1))
             if not realtime:
