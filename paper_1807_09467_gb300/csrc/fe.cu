@@ -7,10 +7,16 @@
 // per cell.  Uniform grid => one set of reference tables: the 1D mass M1 and
 // stiffness K1, the load F1, and the reference convection tensor
 //   T[(i),(j),(l)] = sum_q w_q phi_i(q) phi_l(q) (beta . grad_ref phi_j)(q)
-// so that N_ij = h sum_l u_l T[i][j][l] on each cell (p <= 4; T has (p+1)^6
-// entries, so higher orders take the quadrature path below).  Assembly gathers row by
-// row (one warp per row, one lane per stored entry, cells visited in a fixed
-// order), so it is deterministic and needs no atomics.
+// so that N_ij = h sum_l u_l T[i][j][l] on each cell.  With the tensor-product
+// basis and Gauss rule T factors into 1D tables,
+//   T = beta_x A1[ia][ja][la] B1[ib][jb][lb] + beta_y B1[ia][ja][la] A1[ib][jb][lb],
+//   A1[i][j][l] = sum_g w_g phi_i phi_l phi_j',  B1[i][j][l] = sum_g w_g phi_i phi_j phi_l,
+// so a first kernel forms each cell's convection matrix sum_l u_l T[i][j][l] by
+// sum factorisation (contract lb, then la: 2 (p+1)^5 FMAs a cell instead of
+// (p+1)^6) into a per-cell buffer (p <= 4; higher orders take the quadrature
+// path below).  Assembly then gathers row by row (one warp per row, one lane per
+// stored entry, cells visited in a fixed order), so it is deterministic and
+// needs no atomics.
 //
 // Sec. 6.1's own benchmark replaces beta by the cellular field
 // b = (-sin(pi x) cos(pi y), cos(pi x) sin(pi y)) through its nodal interpolant
@@ -59,6 +65,7 @@ struct rgm_fe_s {
     double *coef = nullptr;                  // C_x, C_y per cell and Gauss point
     double *fn = nullptr;                    // nodal forcing
     double *cmodes = nullptr;                // forcing coefficients (RGM_FE_MAX_MODES)
+    double *elm = nullptr;                   // per-cell convection matrices (p <= 4), N^2 nl^2
     int64_t ntab = 0;                        // doubles in tabs
 };
 
@@ -185,7 +192,9 @@ struct FeDev {
     int p, N, nl;
     int64_t L, n;
     double h, inv_dt, eps;
-    const double *M1, *K1, *F1, *T;   // T only for p <= 4
+    const double *M1, *K1, *F1;
+    const double *A1, *B1;            // 1D factors of the convection tensor (p <= 4)
+    double bx, by;                    // constant velocity
     const double *PH, *DPH, *GW;   // phi_a, phi_a' at Gauss point g ([g][a]), Gauss weights
     const double *XI;              // Gauss-Lobatto nodes of a cell on [0,1]
 };
@@ -250,8 +259,58 @@ __global__ void fe_conv_coef_kernel(FeDev f, const double *u, const double *bxn,
 }
 
 // One warp per row: values of A on the Dirichlet pattern.
+// Convection matrices of the cells (constant velocity, p <= 4), one warp per
+// cell: elm[cell][i][j] = sum_l u_l T[i][j][l], i = (ia, ib), j = (ja, jb)
+// local node indices, by sum factorisation over the two directions:
+//   Y1[la][ib][jb] = sum_lb B1[ib][jb][lb] u[la][lb],  Y2 likewise with A1,
+//   elm = beta_x sum_la A1[ia][ja][la] Y1[la][ib][jb] + beta_y sum_la B1[ia][ja][la] Y2[la][ib][jb].
+#define FE_ELM_WARPS 8
+__global__ void __launch_bounds__(32 * FE_ELM_WARPS) fe_elem_conv_kernel(FeDev f, const double *u, double *elm)
+{
+    constexpr int QM = 5;                               // p + 1 <= 5
+    __shared__ double A1[QM * QM * QM], B1[QM * QM * QM];
+    __shared__ double us[FE_ELM_WARPS][QM * QM], Y1[FE_ELM_WARPS][QM * QM * QM], Y2[FE_ELM_WARPS][QM * QM * QM];
+    const int q1 = f.p + 1, q3 = q1 * q1 * q1, nl = f.nl;
+    for (int t = threadIdx.x; t < q3; t += blockDim.x) { A1[t] = f.A1[t]; B1[t] = f.B1[t]; }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t cell = (int64_t)blockIdx.x * FE_ELM_WARPS + w;
+    if (cell >= (int64_t)f.N * f.N) return;             // warp-uniform; no block barrier follows
+    const int64_t cx = cell % f.N, cy = cell / f.N;
+    if (lane < nl) {
+        const int la = lane % q1, lb = lane / q1;
+        us[w][la * QM + lb] = u[(cy * f.p + lb) * f.L + cx * f.p + la];
+    }
+    __syncwarp();
+    for (int t = lane; t < q3; t += 32) {               // t = (la, ib, jb)
+        const int la = t / (q1 * q1), ib = (t / q1) % q1, jb = t % q1;
+        const double *ul = &us[w][la * QM];
+        double y1 = 0.0, y2 = 0.0;
+        for (int lb = 0; lb < q1; ++lb) {
+            const int k = (ib * q1 + jb) * q1 + lb;
+            y1 = fma(B1[k], ul[lb], y1);
+            y2 = fma(A1[k], ul[lb], y2);
+        }
+        Y1[w][t] = y1;
+        Y2[w][t] = y2;
+    }
+    __syncwarp();
+    double *out = elm + cell * nl * nl;
+    for (int t = lane; t < nl * nl; t += 32) {          // t = i nl + j, i = ib q1 + ia, j = jb q1 + ja
+        const int i = t / nl, j = t % nl;
+        const int ia = i % q1, ib = i / q1, ja = j % q1, jb = j / q1;
+        double sx = 0.0, sy = 0.0;
+        for (int la = 0; la < q1; ++la) {
+            const int k = (ia * q1 + ja) * q1 + la, y = (la * q1 + ib) * q1 + jb;
+            sx = fma(A1[k], Y1[w][y], sx);
+            sy = fma(B1[k], Y2[w][y], sy);
+        }
+        out[t] = f.bx * sx + f.by * sy;
+    }
+}
+
 __global__ void fe_assemble_kernel(FeDev f, const int64_t *rowptr, const int32_t *col,
-                                   const double *u, const double *coef, double *val)
+                                   const double *u, const double *coef, const double *elm, double *val)
 {
     const int lane = threadIdx.x & 31;
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -293,11 +352,7 @@ __global__ void fe_assemble_kernel(FeDev f, const int64_t *rowptr, const int32_t
                     continue;
                 }
                 const int il = ib * q1 + ia, jl = jb * q1 + ja;
-                const double *Tij = f.T + ((int64_t)il * f.nl + jl) * f.nl;
-                for (int lb = 0; lb <= p; ++lb) {
-                    const int64_t rowoff = ((int64_t)cy * p + lb) * f.L + (int64_t)cx * p;
-                    for (int la = 0; la <= p; ++la) conv += Tij[lb * q1 + la] * u[rowoff + la];
-                }
+                conv = elm[(((int64_t)cy * f.N + cx) * f.nl + il) * f.nl + jl];
                 v += f.h * f.h * mx * my * f.inv_dt + f.eps * (kx * my + mx * ky) + f.h * conv;
             }
         val[e] = v;
@@ -356,10 +411,12 @@ FeDev dev_view(const rgm_fe_s *fe)
     FeDev f;
     f.p = fe->p; f.N = fe->N; f.nl = q1 * q1; f.L = fe->L; f.n = fe->n; f.h = fe->h;
     f.inv_dt = 1.0 / fe->dt; f.eps = fe->eps;
-    f.M1 = fe->tabs; f.K1 = f.M1 + q1 * q1; f.F1 = f.K1 + q1 * q1; f.T = f.F1 + q1;
-    f.PH = f.T + (fe->p <= 4 ? (int64_t)f.nl * f.nl * f.nl : 0);
+    f.M1 = fe->tabs; f.K1 = f.M1 + q1 * q1; f.F1 = f.K1 + q1 * q1; f.A1 = f.F1 + q1;
+    f.B1 = f.A1 + q1 * q1 * q1;
+    f.PH = f.A1 + (fe->p <= 4 ? 2 * q1 * q1 * q1 : 0);
     f.DPH = f.PH + q1 * q1; f.GW = f.DPH + q1 * q1; f.XI = f.GW + q1;
-    if (fe->p > 4) f.T = nullptr;
+    f.bx = fe->bx; f.by = fe->by;
+    if (fe->p > 4) f.A1 = f.B1 = nullptr;
     return f;
 }
 
@@ -403,8 +460,9 @@ int rgm_fe_create(rgm_fe *out, int p, int N, double eps, double dt, double beta_
     fe->nnz = (int64_t)fe->h_col.size();
     // reference tables
     const int q1 = p + 1, nl = q1 * q1;
-    // p <= 4: the reference convection tensor T (nl^3); above, the quadrature path
-    const size_t nT = p <= 4 ? (size_t)nl * nl * nl : 0;
+    // p <= 4: the 1D factors A1, B1 of the reference convection tensor; above,
+    // the quadrature path
+    const size_t nT = p <= 4 ? 2 * (size_t)q1 * q1 * q1 : 0;
     double xi[RGM_FE_MAX_P + 1], gx[RGM_FE_MAX_P + 1], gw[RGM_FE_MAX_P + 1];
     std::vector<double> phv((size_t)q1 * q1), dphv((size_t)q1 * q1);
     gll_nodes(p, xi);
@@ -413,8 +471,9 @@ int rgm_fe_create(rgm_fe *out, int p, int N, double eps, double dt, double beta_
     auto ph = [&](int g, int a) { return phv[(size_t)g * q1 + a]; };
     auto dph = [&](int g, int a) { return dphv[(size_t)g * q1 + a]; };
     std::vector<double> tab(2 * q1 * q1 + q1 + nT + 2 * q1 * q1 + q1 + q1, 0.0);
-    double *M1 = tab.data(), *K1 = M1 + q1 * q1, *F1 = K1 + q1 * q1, *T = F1 + q1;
-    double *PH = T + nT, *DPH = PH + q1 * q1, *GW = DPH + q1 * q1, *XI = GW + q1;
+    double *M1 = tab.data(), *K1 = M1 + q1 * q1, *F1 = K1 + q1 * q1, *A1 = F1 + q1;
+    double *B1 = A1 + (nT ? q1 * q1 * q1 : 0);
+    double *PH = A1 + nT, *DPH = PH + q1 * q1, *GW = DPH + q1 * q1, *XI = GW + q1;
     for (int g = 0; g < q1; ++g) {
         GW[g] = gw[g];
         XI[g] = xi[g];
@@ -428,20 +487,16 @@ int rgm_fe_create(rgm_fe *out, int p, int N, double eps, double dt, double beta_
             }
         for (int g = 0; g < q1; ++g) F1[a] += gw[g] * ph(g, a);
     }
-    for (int i = 0; i < nl && nT > 0; ++i)
-        for (int j = 0; j < nl; ++j)
-            for (int l = 0; l < nl; ++l) {
-                const int ia = i % q1, ib = i / q1, ja = j % q1, jb = j / q1, la = l % q1, lb = l / q1;
-                double s = 0.0;
-                for (int gy = 0; gy < q1; ++gy)
-                    for (int gxx = 0; gxx < q1; ++gxx) {
-                        double w = gw[gxx] * gw[gy];
-                        double phi_i = ph(gxx, ia) * ph(gy, ib);
-                        double phi_l = ph(gxx, la) * ph(gy, lb);
-                        double bgrad = beta_x * dph(gxx, ja) * ph(gy, jb) + beta_y * ph(gxx, ja) * dph(gy, jb);
-                        s += w * phi_i * phi_l * bgrad;
-                    }
-                T[((int64_t)i * nl + j) * nl + l] = s;
+    for (int i = 0; i <= p && nT > 0; ++i)
+        for (int j = 0; j <= p; ++j)
+            for (int l = 0; l <= p; ++l) {
+                double a = 0.0, bb = 0.0;
+                for (int g = 0; g < q1; ++g) {
+                    a += gw[g] * ph(g, i) * ph(g, l) * dph(g, j);
+                    bb += gw[g] * ph(g, i) * ph(g, j) * ph(g, l);
+                }
+                A1[(i * q1 + j) * q1 + l] = a;
+                B1[(i * q1 + j) * q1 + l] = bb;
             }
     cudaError_t e = cudaMalloc((void **)&fe->rowptr, sizeof(int64_t) * (fe->n + 1));
     if (e == cudaSuccess) e = cudaMalloc((void **)&fe->col, sizeof(int32_t) * fe->nnz);
@@ -450,6 +505,8 @@ int rgm_fe_create(rgm_fe *out, int p, int N, double eps, double dt, double beta_
     if (e == cudaSuccess) e = cudaMalloc((void **)&fe->val, sizeof(double) * fe->nnz);
     if (e == cudaSuccess) e = cudaMalloc((void **)&fe->b, sizeof(double) * fe->n);
     if (e == cudaSuccess) e = cudaMalloc((void **)&fe->x, sizeof(double) * fe->n);
+    if (e == cudaSuccess && p <= 4)
+        e = cudaMalloc((void **)&fe->elm, sizeof(double) * (size_t)fe->N * fe->N * nl * nl);
     if (e == cudaSuccess) e = cudaMemcpy(fe->rowptr, fe->h_rowptr.data(), sizeof(int64_t) * (fe->n + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(fe->col, fe->h_col.data(), sizeof(int32_t) * fe->nnz, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(fe->tabs, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
@@ -471,6 +528,7 @@ int rgm_fe_device_bytes(rgm_fe fe, int64_t *bytes)
     int64_t b = 8 * (fe->n + 1) + 4 * fe->nnz + 8 * fe->ntab + 8 * fe->nnz + 16 * fe->n;
     if (fe->bxn) b += 16 * fe->n + 8 * 2 * (int64_t)fe->N * fe->N * (fe->p + 1) * (fe->p + 1);
     if (fe->fn) b += 8 * fe->n + 8 * RGM_FE_MAX_MODES;
+    if (fe->elm) b += 8 * (int64_t)fe->N * fe->N * (fe->p + 1) * (fe->p + 1) * (fe->p + 1) * (fe->p + 1);
     *bytes = b;
     return RGM_OK;
 }
@@ -479,7 +537,7 @@ int rgm_fe_destroy(rgm_fe fe)
 {
     if (!fe) return RGM_E_ARG;
     void *p[] = {fe->rowptr, fe->col, fe->tabs, fe->val, fe->b, fe->x, fe->bxn, fe->byn, fe->coef,
-                 fe->fn, fe->cmodes};
+                 fe->fn, fe->cmodes, fe->elm};
     for (void *q : p)
         if (q) cudaFree(q);
     delete fe;
@@ -512,8 +570,13 @@ static int fe_assemble_dev(rgm_fe fe, const double *u_dev, double *val_dev, doub
         const int64_t nt = (int64_t)fe->N * fe->N * f.nl;
         fe_conv_coef_kernel<<<(unsigned)((nt + tpb - 1) / tpb), tpb, 0, fe->st>>>(f, u_dev, fe->bxn, fe->byn, fe->coef);
     }
+    if (!fe->bxn) {
+        const int64_t cells = (int64_t)fe->N * fe->N;
+        fe_elem_conv_kernel<<<(unsigned)((cells + FE_ELM_WARPS - 1) / FE_ELM_WARPS), 32 * FE_ELM_WARPS, 0,
+                              fe->st>>>(f, u_dev, fe->elm);
+    }
     fe_assemble_kernel<<<(unsigned)((warps * 32 + tpb - 1) / tpb), tpb, 0, fe->st>>>(
-        f, fe->rowptr, fe->col, u_dev, fe->bxn ? fe->coef : nullptr, val_dev);
+        f, fe->rowptr, fe->col, u_dev, fe->bxn ? fe->coef : nullptr, fe->elm, val_dev);
     fe_rhs_kernel<<<(unsigned)((fe->n + tpb - 1) / tpb), tpb, 0, fe->st>>>(f, u_dev, fe->fn, b_dev);
     CKF(cudaGetLastError());
     return RGM_OK;
