@@ -13,10 +13,11 @@
 //   A1[i][j][l] = sum_g w_g phi_i phi_l phi_j',  B1[i][j][l] = sum_g w_g phi_i phi_j phi_l,
 // so a first kernel forms each cell's convection matrix sum_l u_l T[i][j][l] by
 // sum factorisation (contract lb, then la: 2 (p+1)^5 FMAs a cell instead of
-// (p+1)^6) into a per-cell buffer (p <= 4; higher orders take the quadrature
-// path below).  Assembly then gathers row by row (one warp per row, one lane per
-// stored entry, cells visited in a fixed order), so it is deterministic and
-// needs no atomics.
+// (p+1)^6), adds the cell's mass/dt and diffusion matrix (the same on every
+// cell) and stores the result in a per-cell buffer (p <= 4; higher orders take
+// the quadrature path below).  Assembly then gathers row by row (one warp per
+// row, one lane per stored entry, cells visited in a fixed order), so it is
+// deterministic and needs no atomics.
 //
 // Sec. 6.1's own benchmark replaces beta by the cellular field
 // b = (-sin(pi x) cos(pi y), cos(pi x) sin(pi y)) through its nodal interpolant
@@ -65,7 +66,7 @@ struct rgm_fe_s {
     double *coef = nullptr;                  // C_x, C_y per cell and Gauss point
     double *fn = nullptr;                    // nodal forcing
     double *cmodes = nullptr;                // forcing coefficients (RGM_FE_MAX_MODES)
-    double *elm = nullptr;                   // per-cell convection matrices (p <= 4), N^2 nl^2
+    double *elm = nullptr;                   // per-cell matrices (p <= 4, constant velocity), N^2 nl^2
     int64_t ntab = 0;                        // doubles in tabs
 };
 
@@ -197,6 +198,8 @@ struct FeDev {
     double bx, by;                    // constant velocity
     const double *PH, *DPH, *GW;   // phi_a, phi_a' at Gauss point g ([g][a]), Gauss weights
     const double *XI;              // Gauss-Lobatto nodes of a cell on [0,1]
+    const double *ME;              // p <= 4: the cell's mass/dt + diffusion matrix, nl x nl
+    const double *AX, *BY;         // p <= 4: h beta_x A1 and h beta_y B1
 };
 
 // Coordinate of lattice node I along one axis (GLL nodes inside each cell).
@@ -258,20 +261,24 @@ __global__ void fe_conv_coef_kernel(FeDev f, const double *u, const double *bxn,
     coef[2 * t + 1] = w * uq * by;
 }
 
-// One warp per row: values of A on the Dirichlet pattern.
-// Convection matrices of the cells (constant velocity, p <= 4), one warp per
-// cell: elm[cell][i][j] = sum_l u_l T[i][j][l], i = (ia, ib), j = (ja, jb)
-// local node indices, by sum factorisation over the two directions:
+// Matrices of the cells (constant velocity, p <= 4), one warp per cell:
+// elm[cell][i][j] = ME[i][j] + h sum_l u_l T[i][j][l], i = (ia, ib), j = (ja, jb)
+// local node indices (ME: mass/dt and diffusion, the same on every cell), the
+// convection part by sum factorisation over the two directions:
 //   Y1[la][ib][jb] = sum_lb B1[ib][jb][lb] u[la][lb],  Y2 likewise with A1,
-//   elm = beta_x sum_la A1[ia][ja][la] Y1[la][ib][jb] + beta_y sum_la B1[ia][ja][la] Y2[la][ib][jb].
+//   elm = ME + sum_la (AX[ia][ja][la] Y1[la][ib][jb] + BY[ia][ja][la] Y2[la][ib][jb])
+// with AX = h beta_x A1 and BY = h beta_y B1 scaled once on the host, so an
+// entry of the second stage costs 2 (p+1) binary64 FMAs and nothing more.
 #define FE_ELM_WARPS 8
 __global__ void __launch_bounds__(32 * FE_ELM_WARPS) fe_elem_conv_kernel(FeDev f, const double *u, double *elm)
 {
     constexpr int QM = 5;                               // p + 1 <= 5
-    __shared__ double A1[QM * QM * QM], B1[QM * QM * QM];
+    __shared__ double A1[QM * QM * QM], B1[QM * QM * QM], AX[QM * QM * QM], BY[QM * QM * QM];
     __shared__ double us[FE_ELM_WARPS][QM * QM], Y1[FE_ELM_WARPS][QM * QM * QM], Y2[FE_ELM_WARPS][QM * QM * QM];
     const int q1 = f.p + 1, q3 = q1 * q1 * q1, nl = f.nl;
-    for (int t = threadIdx.x; t < q3; t += blockDim.x) { A1[t] = f.A1[t]; B1[t] = f.B1[t]; }
+    for (int t = threadIdx.x; t < q3; t += blockDim.x) {
+        A1[t] = f.A1[t]; B1[t] = f.B1[t]; AX[t] = f.AX[t]; BY[t] = f.BY[t];
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t cell = (int64_t)blockIdx.x * FE_ELM_WARPS + w;
@@ -299,18 +306,20 @@ __global__ void __launch_bounds__(32 * FE_ELM_WARPS) fe_elem_conv_kernel(FeDev f
     for (int t = lane; t < nl * nl; t += 32) {          // t = i nl + j, i = ib q1 + ia, j = jb q1 + ja
         const int i = t / nl, j = t % nl;
         const int ia = i % q1, ib = i / q1, ja = j % q1, jb = j / q1;
-        double sx = 0.0, sy = 0.0;
+        double s = f.ME[t];
         for (int la = 0; la < q1; ++la) {
             const int k = (ia * q1 + ja) * q1 + la, y = (la * q1 + ib) * q1 + jb;
-            sx = fma(A1[k], Y1[w][y], sx);
-            sy = fma(B1[k], Y2[w][y], sy);
+            s = fma(AX[k], Y1[w][y], s);
+            s = fma(BY[k], Y2[w][y], s);
         }
-        out[t] = f.bx * sx + f.by * sy;
+        out[t] = s;
     }
 }
 
+// Quadrature path (nodal velocity, or p > 4): one warp per row, a lane per
+// stored entry, the entry's (p+1)^2 Gauss points summed for each shared cell.
 __global__ void fe_assemble_kernel(FeDev f, const int64_t *rowptr, const int32_t *col,
-                                   const double *u, const double *coef, const double *elm, double *val)
+                                   const double *coef, double *val)
 {
     const int lane = threadIdx.x & 31;
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -338,30 +347,99 @@ __global__ void fe_assemble_kernel(FeDev f, const int64_t *rowptr, const int32_t
                 const int ja = (int)(Jx - (int64_t)cx * p), jb = (int)(Jy - (int64_t)cy * p);
                 const double mx = f.M1[ia * q1 + ja], my = f.M1[ib * q1 + jb];
                 const double kx = f.K1[ia * q1 + ja], ky = f.K1[ib * q1 + jb];
+                // nodal velocity: quadrature with the per-point coefficients
+                const double *cc = coef + 2 * (((int64_t)cy * f.N + cx) * f.nl);
                 double conv = 0.0;
-                if (coef) {     // nodal velocity: quadrature with the per-point coefficients
-                    const double *cc = coef + 2 * (((int64_t)cy * f.N + cx) * f.nl);
-                    for (int gy = 0; gy <= p; ++gy)
-                        for (int gx = 0; gx <= p; ++gx) {
-                            const double pi = f.PH[gx * q1 + ia] * f.PH[gy * q1 + ib];
-                            const int g = gy * q1 + gx;
-                            conv += pi * (cc[2 * g] * f.DPH[gx * q1 + ja] * f.PH[gy * q1 + jb] +
-                                          cc[2 * g + 1] * f.PH[gx * q1 + ja] * f.DPH[gy * q1 + jb]);
-                        }
-                    v += f.h * f.h * mx * my * f.inv_dt + f.eps * (kx * my + mx * ky) + conv;
-                    continue;
-                }
-                const int il = ib * q1 + ia, jl = jb * q1 + ja;
-                conv = elm[(((int64_t)cy * f.N + cx) * f.nl + il) * f.nl + jl];
-                v += f.h * f.h * mx * my * f.inv_dt + f.eps * (kx * my + mx * ky) + f.h * conv;
+                for (int gy = 0; gy <= p; ++gy)
+                    for (int gx = 0; gx <= p; ++gx) {
+                        const double pi = f.PH[gx * q1 + ia] * f.PH[gy * q1 + ib];
+                        const int g = gy * q1 + gx;
+                        conv += pi * (cc[2 * g] * f.DPH[gx * q1 + ja] * f.PH[gy * q1 + jb] +
+                                      cc[2 * g + 1] * f.PH[gx * q1 + ja] * f.DPH[gy * q1 + jb]);
+                    }
+                v += f.h * f.h * mx * my * f.inv_dt + f.eps * (kx * my + mx * ky) + conv;
             }
         val[e] = v;
     }
 }
 
+// Per-cell matrix path (constant velocity, p <= 4): the value of entry (I, J)
+// is the sum of elm[cell][i][j] over the (at most four) cells holding both
+// nodes.  One warp per row, a lane per stored entry.  A row's columns are the
+// product of its two 1D coupling ranges with the boundary nodes left out, in
+// y-major order (the pattern rgm_fe_create builds), so a lane finds its
+// column from its offset in the row instead of reading col; with P a
+// compile-time constant and 32-bit node indices (L^2 <= 2^31) no 64-bit
+// division remains.
+template <int P>
+__global__ void fe_assemble_elm_kernel(FeDev f, const int64_t *rowptr, const double *elm, double *val)
+{
+    constexpr int Q1 = P + 1, NL = Q1 * Q1;
+    const int lane = threadIdx.x & 31;
+    const int64_t wrow = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (wrow >= f.n) return;
+    const int row = (int)wrow, L = (int)f.L, N = f.N;
+    const int64_t e0 = rowptr[row];
+    const int len = (int)(rowptr[row + 1] - e0);
+    const int Iy = row / L, Ix = row - Iy * L;
+    if (Ix == 0 || Iy == 0 || Ix == L - 1 || Iy == L - 1) {
+        for (int k = lane; k < len; k += 32) val[e0 + k] = 1.0;
+        return;
+    }
+    // 1D coupling range of a node, clipped to the interior nodes 1 .. L-2
+    auto crange = [&](int I, int *lo, int *hi) {
+        if (I % P == 0) { *lo = max(I - P, 1); *hi = min(I + P, L - 2); }
+        else { *lo = max((I / P) * P, 1); *hi = min((I / P) * P + P, L - 2); }
+    };
+    // cells holding a node along one axis
+    auto cells = [&](int I, int *c0, int *c1) {
+        const int c = I / P;
+        if (I % P == 0) { *c0 = c > 0 ? c - 1 : 0; *c1 = c < N ? c : N - 1; }
+        else { *c0 = c; *c1 = c; }
+    };
+    int xl, xh, yl, yh, ax0, ax1, ay0, ay1;
+    crange(Ix, &xl, &xh);
+    crange(Iy, &yl, &yh);
+    cells(Ix, &ax0, &ax1);
+    cells(Iy, &ay0, &ay1);
+    const int wx = xh - xl + 1;
+    // k / wx for k < 2^10 and wx <= 2P + 1 <= 9: (k + 1/2) / wx lies at least
+    // 1/(2 wx) from an integer, far above binary32's rounding of the product
+    const float rwx = 1.0f / (float)wx;
+    // at most (2P + 1)^2 entries a row: all of a lane's entries and their (at
+    // most four) cells' loads are issued before the first sum
+    constexpr int KMAX = ((2 * P + 1) * (2 * P + 1) + 31) / 32;
+#pragma unroll
+    for (int it = 0; it < KMAX; ++it) {
+        const int k = lane + 32 * it;
+        if (k >= len) break;
+        const int dy = (int)(((float)k + 0.5f) * rwx);
+        const int Jy = yl + dy, Jx = xl + (k - dy * wx);
+        int bx0, bx1, by0, by1;
+        cells(Jx, &bx0, &bx1);
+        cells(Jy, &by0, &by1);
+        const int cy0 = max(ay0, by0), cy1 = min(ay1, by1), cx0 = max(ax0, bx0), cx1 = min(ax1, bx1);
+        double t[4];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int cy = cy0 + a, cx = cx0 + c;
+                const int il = (Iy - cy * P) * Q1 + (Ix - cx * P);
+                const int jl = (Jy - cy * P) * Q1 + (Jx - cx * P);
+                t[2 * a + c] = (cy <= cy1 && cx <= cx1)
+                                   ? __ldg(&elm[((int64_t)cy * N + cx) * (NL * NL) + il * NL + jl]) : 0.0;
+            }
+        // the cells in a fixed order (absent ones add +0)
+        val[e0 + k] = ((t[0] + t[1]) + t[2]) + t[3];
+    }
+}
+
 // b = M u / dt + F over the full neighbourhood (boundary columns included),
 // then b_i = 0 on Dirichlet rows; with a nodal forcing fn, F = M fn.  One
-// thread per row.
+// thread per row.  The cell mass matrix is h^2 (M1 x M1), so a cell's
+// contribution is h^2 sum_jb M1[ib][jb] (sum_ja M1[ia][ja] u[jb][ja]): 2 (p+1)
+// products per column line instead of (p+1)^2 per cell node.
 __global__ void fe_rhs_kernel(FeDev f, const double *u, const double *fn, double *b)
 {
     const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -376,16 +454,20 @@ __global__ void fe_rhs_kernel(FeDev f, const double *u, const double *fn, double
     for (int cy = ay0; cy <= ay1; ++cy)
         for (int cx = ax0; cx <= ax1; ++cx) {
             const int ia = (int)(Ix - (int64_t)cx * p), ib = (int)(Iy - (int64_t)cy * p);
-            if (!fn) F += f.h * f.h * f.F1[ia] * f.F1[ib];
-            for (int jb = 0; jb <= p; ++jb)
+            const double *mxr = f.M1 + ia * q1, *myr = f.M1 + ib * q1;
+            if (!fn) F += f.F1[ia] * f.F1[ib];
+            for (int jb = 0; jb <= p; ++jb) {
+                const int64_t c0 = ((int64_t)cy * p + jb) * f.L + (int64_t)cx * p;
+                double su = 0.0, sf = 0.0;
                 for (int ja = 0; ja <= p; ++ja) {
-                    const int64_t cj = ((int64_t)cy * p + jb) * f.L + (int64_t)cx * p + ja;
-                    const double mij = f.h * f.h * f.M1[ia * q1 + ja] * f.M1[ib * q1 + jb];
-                    mu += mij * u[cj];
-                    if (fn) F += mij * fn[cj];
+                    su = fma(mxr[ja], u[c0 + ja], su);
+                    if (fn) sf = fma(mxr[ja], fn[c0 + ja], sf);
                 }
+                mu = fma(myr[jb], su, mu);
+                if (fn) F = fma(myr[jb], sf, F);
+            }
         }
-    b[row] = mu * f.inv_dt + F;
+    b[row] = f.h * f.h * (mu * f.inv_dt + F);
 }
 
 __global__ void fe_u0_kernel(FeDev f, const double *a8, double *u0)
@@ -416,7 +498,9 @@ FeDev dev_view(const rgm_fe_s *fe)
     f.PH = f.A1 + (fe->p <= 4 ? 2 * q1 * q1 * q1 : 0);
     f.DPH = f.PH + q1 * q1; f.GW = f.DPH + q1 * q1; f.XI = f.GW + q1;
     f.bx = fe->bx; f.by = fe->by;
-    if (fe->p > 4) f.A1 = f.B1 = nullptr;
+    f.ME = f.XI + q1;
+    f.AX = f.ME + q1 * q1 * q1 * q1; f.BY = f.AX + q1 * q1 * q1;
+    if (fe->p > 4) f.A1 = f.B1 = f.ME = f.AX = f.BY = nullptr;
     return f;
 }
 
@@ -470,10 +554,12 @@ int rgm_fe_create(rgm_fe *out, int p, int N, double eps, double dt, double beta_
     for (int g = 0; g < q1; ++g) basis(p, xi, gx[g], &phv[(size_t)g * q1], &dphv[(size_t)g * q1]);
     auto ph = [&](int g, int a) { return phv[(size_t)g * q1 + a]; };
     auto dph = [&](int g, int a) { return dphv[(size_t)g * q1 + a]; };
-    std::vector<double> tab(2 * q1 * q1 + q1 + nT + 2 * q1 * q1 + q1 + q1, 0.0);
+    const size_t nME = p <= 4 ? (size_t)nl * nl : 0;
+    std::vector<double> tab(2 * q1 * q1 + q1 + nT + 2 * q1 * q1 + q1 + q1 + nME + nT, 0.0);
     double *M1 = tab.data(), *K1 = M1 + q1 * q1, *F1 = K1 + q1 * q1, *A1 = F1 + q1;
     double *B1 = A1 + (nT ? q1 * q1 * q1 : 0);
-    double *PH = A1 + nT, *DPH = PH + q1 * q1, *GW = DPH + q1 * q1, *XI = GW + q1;
+    double *PH = A1 + nT, *DPH = PH + q1 * q1, *GW = DPH + q1 * q1, *XI = GW + q1, *ME = XI + q1;
+    double *AX = ME + nME, *BY = AX + (nT ? q1 * q1 * q1 : 0);
     for (int g = 0; g < q1; ++g) {
         GW[g] = gw[g];
         XI[g] = xi[g];
@@ -497,7 +583,17 @@ int rgm_fe_create(rgm_fe *out, int p, int N, double eps, double dt, double beta_
                 }
                 A1[(i * q1 + j) * q1 + l] = a;
                 B1[(i * q1 + j) * q1 + l] = bb;
+                AX[(i * q1 + j) * q1 + l] = fe->h * beta_x * a;
+                BY[(i * q1 + j) * q1 + l] = fe->h * beta_y * bb;
             }
+    // the same on every cell of the uniform grid: h^2 (M1 x M1) / dt + eps (K1 x M1 + M1 x K1)
+    for (int i = 0; i < nl && nME > 0; ++i)
+        for (int j = 0; j < nl; ++j) {
+            const int ia = i % q1, ib = i / q1, ja = j % q1, jb = j / q1;
+            const double mx = M1[ia * q1 + ja], my = M1[ib * q1 + jb];
+            const double kx = K1[ia * q1 + ja], ky = K1[ib * q1 + jb];
+            ME[(size_t)i * nl + j] = fe->h * fe->h * mx * my / dt + eps * (kx * my + mx * ky);
+        }
     cudaError_t e = cudaMalloc((void **)&fe->rowptr, sizeof(int64_t) * (fe->n + 1));
     if (e == cudaSuccess) e = cudaMalloc((void **)&fe->col, sizeof(int32_t) * fe->nnz);
     fe->ntab = (int64_t)tab.size();
@@ -575,8 +671,17 @@ static int fe_assemble_dev(rgm_fe fe, const double *u_dev, double *val_dev, doub
         fe_elem_conv_kernel<<<(unsigned)((cells + FE_ELM_WARPS - 1) / FE_ELM_WARPS), 32 * FE_ELM_WARPS, 0,
                               fe->st>>>(f, u_dev, fe->elm);
     }
-    fe_assemble_kernel<<<(unsigned)((warps * 32 + tpb - 1) / tpb), tpb, 0, fe->st>>>(
-        f, fe->rowptr, fe->col, u_dev, fe->bxn ? fe->coef : nullptr, fe->elm, val_dev);
+    const unsigned ablocks = (unsigned)((warps * 32 + tpb - 1) / tpb);
+    if (fe->bxn)
+        fe_assemble_kernel<<<ablocks, tpb, 0, fe->st>>>(f, fe->rowptr, fe->col, fe->coef, val_dev);
+    else if (fe->p == 1)
+        fe_assemble_elm_kernel<1><<<ablocks, tpb, 0, fe->st>>>(f, fe->rowptr, fe->elm, val_dev);
+    else if (fe->p == 2)
+        fe_assemble_elm_kernel<2><<<ablocks, tpb, 0, fe->st>>>(f, fe->rowptr, fe->elm, val_dev);
+    else if (fe->p == 3)
+        fe_assemble_elm_kernel<3><<<ablocks, tpb, 0, fe->st>>>(f, fe->rowptr, fe->elm, val_dev);
+    else
+        fe_assemble_elm_kernel<4><<<ablocks, tpb, 0, fe->st>>>(f, fe->rowptr, fe->elm, val_dev);
     fe_rhs_kernel<<<(unsigned)((fe->n + tpb - 1) / tpb), tpb, 0, fe->st>>>(f, u_dev, fe->fn, b_dev);
     CKF(cudaGetLastError());
     return RGM_OK;

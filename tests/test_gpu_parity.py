@@ -46,7 +46,7 @@ def test_spmv_random_csr(rg, orc, n, maxr, minr, seed):
 
 
 # ------------------------------------------------------------------ FE workload (a0)
-@pytest.mark.parametrize("p,N", [(1, 5), (2, 4), (3, 3), (4, 3), (1, 32)])
+@pytest.mark.parametrize("p,N", [(1, 5), (2, 4), (3, 3), (4, 3), (1, 32), (2, 11), (3, 7), (4, 9)])
 def test_fe_pattern_values_rhs(rg, orc, p, N):
     beta = (0.6, -0.8)
     eps, dt = 0.02, 0.003
