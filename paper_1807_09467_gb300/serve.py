@@ -82,7 +82,7 @@ def device_bytes(req: Request, precision: str = "fp32_ir") -> int:
     """Upper estimate of the device memory one admitted sequence holds: the
     solver (Krylov basis, recycle space, window, operator in sliced ELL with
     its CSR map, binary32 copies in GMRES-IR, scratch) and the FE workload
-    (pattern, values, element tables, per-cell convection matrices).  Checked against the library's own
+    (pattern, values, element tables, per-cell matrices).  Checked against the library's own
     count (rgm_solver_device_bytes + rgm_fe_device_bytes) by the tests."""
     n, nnz = sizes(req.p, req.N)
     ld = (n + 31) // 32 * 32
@@ -95,7 +95,7 @@ def device_bytes(req: Request, precision: str = "fp32_ir") -> int:
     nblocks = min((n + 255) // 256, 4 * 152)  # grid of the fused kernels (<= 4 blocks per SM)
     scratch = 8 * 3200 * nblocks + 8 * 3200 * (nblocks // 32 + 1) + 16 * 3200 + (320 << 10)
     fe = 8 * (n + 1) + 12 * nnz + 16 * n + 8 * (req.p + 1) ** 6 * 4 + (1 << 16)
-    if req.p <= 4:                              # per-cell convection matrices
+    if req.p <= 4:                              # per-cell matrices (constant velocity)
         fe += 8 * req.N * req.N * (req.p + 1) ** 4
     return int(vec + op + scratch + fe)
 

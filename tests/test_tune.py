@@ -31,3 +31,13 @@ def test_tune_picks_fastest_and_keeps_order_on_ties():
         tune.tune(lambda c: float("nan"), [None])
     with pytest.raises(ValueError):
         tune.tune(lambda c: 1.0, [])
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("N", [1, 2, 3, 7])
+def test_serve_pattern_sizes_match_the_oracle_pattern(orc, p, N):
+    # the admission estimate's (n, nnz) of a Q_p Dirichlet pattern, against the
+    # oracle's element-connectivity pattern (itself pinned by brute force)
+    from paper_1807_09467_gb300 import serve
+    rp, col = orc.pattern(p, N, True)
+    assert serve.sizes(p, N) == (len(rp) - 1, int(rp[-1]))
