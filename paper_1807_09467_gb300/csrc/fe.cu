@@ -470,6 +470,60 @@ __global__ void fe_rhs_kernel(FeDev f, const double *u, const double *fn, double
     b[row] = f.h * f.h * (mu * f.inv_dt + F);
 }
 
+// The same right-hand side for p <= 4 in two 1D passes.  The global mass
+// matrix of the tensor-product grid is h^2 (M_y x M_x), M_x and M_y the
+// assembled 1D mass matrices (the 2D cells are the products of the 1D cells),
+// and the load of f = 1 is h^2 F_x F_y likewise.  A first pass applies M_x
+// along every lattice row, a second M_y along the columns: (p + 1) FMAs per
+// cell of a node per pass, and lanes of a warp (consecutive nodes of one
+// lattice row) differ in their cell count only in the first pass.  With a
+// nodal forcing the first pass applies M_x to u / dt + fn.
+template <bool FN>
+__global__ void fe_rhs_x_kernel(FeDev f, const double *u, const double *fn, double *t)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= f.n) return;
+    const int p = f.p, q1 = p + 1;
+    const int64_t Iy = i / f.L, Ix = i - Iy * f.L;
+    int c0, c1;
+    cell_range(Ix, p, f.N, &c0, &c1);
+    const double *ur = u + Iy * f.L, *fr = FN ? fn + Iy * f.L : nullptr;
+    double s = 0.0;
+    for (int c = c0; c <= c1; ++c) {
+        const double *m = f.M1 + (Ix - (int64_t)c * p) * q1;
+        const int64_t j0 = (int64_t)c * p;
+        for (int a = 0; a <= p; ++a)
+            s = fma(m[a], FN ? fma(ur[j0 + a], f.inv_dt, fr[j0 + a]) : ur[j0 + a], s);
+    }
+    t[i] = s;
+}
+
+template <bool FN>
+__global__ void fe_rhs_y_kernel(FeDev f, const double *t, double *b)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= f.n) return;
+    if (on_bnd(i, f.L)) { b[i] = 0.0; return; }
+    const int p = f.p, q1 = p + 1;
+    const int64_t Iy = i / f.L, Ix = i - Iy * f.L;
+    int c0, c1;
+    cell_range(Iy, p, f.N, &c0, &c1);
+    double s = 0.0, fy = 0.0;
+    for (int c = c0; c <= c1; ++c) {
+        const int ib = (int)(Iy - (int64_t)c * p);
+        const double *m = f.M1 + ib * q1;
+        const double *tc = t + (int64_t)c * p * f.L + Ix;
+        for (int a = 0; a <= p; ++a) s = fma(m[a], tc[a * f.L], s);
+        if (!FN) fy += f.F1[ib];
+    }
+    if (FN) { b[i] = f.h * f.h * s; return; }
+    int x0, x1;
+    cell_range(Ix, p, f.N, &x0, &x1);
+    double fx = 0.0;
+    for (int c = x0; c <= x1; ++c) fx += f.F1[Ix - (int64_t)c * p];
+    b[i] = f.h * f.h * (s * f.inv_dt + fx * fy);
+}
+
 __global__ void fe_u0_kernel(FeDev f, const double *a8, double *u0)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -682,7 +736,20 @@ static int fe_assemble_dev(rgm_fe fe, const double *u_dev, double *val_dev, doub
         fe_assemble_elm_kernel<3><<<ablocks, tpb, 0, fe->st>>>(f, fe->rowptr, fe->elm, val_dev);
     else
         fe_assemble_elm_kernel<4><<<ablocks, tpb, 0, fe->st>>>(f, fe->rowptr, fe->elm, val_dev);
-    fe_rhs_kernel<<<(unsigned)((fe->n + tpb - 1) / tpb), tpb, 0, fe->st>>>(f, u_dev, fe->fn, b_dev);
+    const unsigned nblocks = (unsigned)((fe->n + tpb - 1) / tpb);
+    if (fe->elm) {
+        // p <= 4: two 1D passes through the cell-matrix buffer (n <= N^2 (p+1)^4
+        // doubles), free once the row gather before it on this stream has run
+        if (fe->fn) {
+            fe_rhs_x_kernel<true><<<nblocks, tpb, 0, fe->st>>>(f, u_dev, fe->fn, fe->elm);
+            fe_rhs_y_kernel<true><<<nblocks, tpb, 0, fe->st>>>(f, fe->elm, b_dev);
+        } else {
+            fe_rhs_x_kernel<false><<<nblocks, tpb, 0, fe->st>>>(f, u_dev, nullptr, fe->elm);
+            fe_rhs_y_kernel<false><<<nblocks, tpb, 0, fe->st>>>(f, fe->elm, b_dev);
+        }
+    } else {
+        fe_rhs_kernel<<<nblocks, tpb, 0, fe->st>>>(f, u_dev, fe->fn, b_dev);
+    }
     CKF(cudaGetLastError());
     return RGM_OK;
 }
