@@ -400,11 +400,15 @@ int rgm_fe_destroy(rgm_fe fe);
 /* Sizes of the Dirichlet pattern. */
 int rgm_fe_sizes(rgm_fe fe, int64_t *n, int64_t *nnz);
 /* Device memory the workload holds now (pattern, element tables, values,
- * right-hand side, velocity and forcing fields when set), in bytes. */
+ * right-hand side, for p <= 4 the per-cell matrices, velocity and forcing
+ * fields when set), in bytes. */
 int rgm_fe_device_bytes(rgm_fe fe, int64_t *bytes);
 /* Copy the Dirichlet CSR pattern out (rowptr n+1, col nnz). */
 int rgm_fe_pattern(rgm_fe fe, int64_t *rowptr, int32_t *col, int flags);
-/* Assemble values (nnz, CSR order of rgm_fe_pattern) and b (n) from u_prev (n). */
+/* Assemble values (nnz, CSR order of rgm_fe_pattern) and b (n) from u_prev (n).
+ * Every value is gathered row by row in a fixed order of the cells (no
+ * atomics), so repeated assemblies give the same bits.  Host pointers (flags
+ * 0) or device pointers (RGM_DEVICE_PTRS); synchronises the handle's stream. */
 int rgm_fe_assemble(rgm_fe fe, const double *u_prev, double *val, double *b, int flags);
 /* Velocity of the convection term (Sec. 6.1).  RGM_FE_VELOCITY_CONSTANT: the
  * (beta_x, beta_y) given at creation.  RGM_FE_VELOCITY_CELLULAR: the paper's
